@@ -1,0 +1,253 @@
+/*
+ * rsr_oracle.c -- plain, slow, obviously correct CPU oracle for the RSR hot path
+ * (Reference-state System Reliability, arXiv 2604.17066).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may load, call or link
+ * this file: only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py use it.  It shares no code, header, table or
+ * constant generator with the CUDA library in paper_2604_17066_gb300/csrc.
+ *
+ * Every loop follows the definition it cites, one sample and one reference at a
+ * time, with no blocking, encoding or reordering.  Floating point is IEEE fp64.
+ *
+ * Definitions followed (paper section / equation):
+ *   - problem setting, componentwise order, coherence: Sec. 2.1-2.2, Eq. (1)
+ *   - lower / upper reference sets L(m'), U(m'): Sec. 2.2, Eqs. (2)-(3)
+ *   - classification into I^L, I^U, I^u, lower taking precedence: Sec. 3.3,
+ *     the p^L / p^U / p^u definitions and Algorithm 1
+ *   - count estimators p_hat = |I|/H and c.o.v. sqrt((1-p)/(H p)): Sec. 3.3
+ *   - Stage 2 estimate of P(S <= m') after resolving I^u with Phi: Sec. 3.5
+ * Not in the paper (defined by this build, see the function comments):
+ *   - the sampler (Philox4x32-10 counter layout and integer inverse-CDF
+ *     thresholds); the paper only states that P(X) is available (Sec. 3.1)
+ *   - the score-function gradient of P(S <= m') with respect to the
+ *     component-state probabilities q_{i,k}
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11).  Ten rounds; each round multiplies counter      */
+/* words 0 and 2 by the two Philox-4x32 multipliers, takes the 64-bit        */
+/* products apart into high and low halves, xors the high halves with the    */
+/* other two counter words and the round key, and permutes the words.  The   */
+/* key is bumped by the two Weyl constants between rounds.                   */
+/* ------------------------------------------------------------------------ */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += ORC_PHILOX_W0;
+            k1 += ORC_PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampler thresholds (not in the paper; Sec. 3.1 only assumes P(X) can be    */
+/* sampled).  For component i with pmf q_{i,0..K-1}:                         */
+/*   c_{i,k} = q_{i,0} + ... + q_{i,k-1}   (fp64, summed left to right)       */
+/*   T_{i,k} = min(2^32, floor(2^32 * c_{i,k}))     for k = 1..K-1            */
+/* stored row-major as T[i*(K-1) + (k-1)].                                    */
+/* ------------------------------------------------------------------------ */
+void orc_thresholds(int32_t n, int32_t K, const double *pmf, uint64_t *T)
+{
+    for (int32_t i = 0; i < n; ++i) {
+        double c = 0.0;
+        for (int32_t k = 1; k < K; ++k) {
+            c = c + pmf[(size_t)i * K + (k - 1)];
+            double scaled = floor(ldexp(c, 32));
+            uint64_t t;
+            if (scaled <= 0.0)
+                t = 0;
+            else if (scaled >= 4294967296.0)
+                t = 4294967296ull;
+            else
+                t = (uint64_t)scaled;
+            T[(size_t)i * (K - 1) + (k - 1)] = t;
+        }
+    }
+}
+
+/* State of one component from one uniform 32-bit word u:                     */
+/*   x = #{ k in 1..K-1 : u >= T_{i,k} }                                      */
+int32_t orc_state_from_uniform(uint32_t u, int32_t K, const uint64_t *T_row)
+{
+    int32_t x = 0;
+    for (int32_t k = 1; k < K; ++k)
+        if ((uint64_t)u >= T_row[k - 1])
+            x = x + 1;
+    return x;
+}
+
+/* Sample h (global index = offset + local index), component i:               */
+/*   u_{h,i} = word (i mod 4) of Philox4x32-10(                                */
+/*               key = (seed mod 2^32, seed div 2^32),                         */
+/*               ctr = (h mod 2^32, h div 2^32, floor(i/4), 0))                */
+/* X is N x n row-major uint8.                                                 */
+void orc_sample(int32_t n, int32_t K, const uint64_t *T, uint64_t seed, uint64_t offset,
+                int64_t N, uint8_t *X)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int64_t s = 0; s < N; ++s) {
+        uint64_t h = offset + (uint64_t)s;
+        for (int32_t i = 0; i < n; ++i) {
+            uint32_t ctr[4] = {(uint32_t)(h & 0xffffffffu), (uint32_t)(h >> 32),
+                               (uint32_t)(i / 4), 0u};
+            uint32_t words[4];
+            orc_philox4x32_10(ctr, key, words);
+            uint32_t u = words[i % 4];
+            X[(size_t)s * n + i] = (uint8_t)orc_state_from_uniform(u, K, T + (size_t)i * (K - 1));
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Componentwise order (Eq. (1)): x <= r  iff  x_i <= r_i for every i.        */
+/* ------------------------------------------------------------------------ */
+static int orc_leq(int32_t n, const uint8_t *x, const uint8_t *r)
+{
+    for (int32_t i = 0; i < n; ++i)
+        if (x[i] > r[i])
+            return 0;
+    return 1;
+}
+
+/* Classification (Sec. 3.3, Algorithm 1).  Sample h is in I^L if some lower  */
+/* reference r satisfies x_h <= r; otherwise in I^U if some upper reference r  */
+/* satisfies r <= x_h; otherwise in I^u.  Lower takes precedence.              */
+/* labels: 0 = I^L (S <= m'), 1 = I^U (S >= m'+1), 2 = I^u (unclassified).     */
+/* counts3 receives |I^L|, |I^U|, |I^u|.                                       */
+void orc_classify(int32_t n, int64_t N, const uint8_t *X,
+                  int64_t R_L, const uint8_t *ref_L,
+                  int64_t R_U, const uint8_t *ref_U,
+                  uint8_t *labels, int64_t *counts3)
+{
+    counts3[0] = 0; counts3[1] = 0; counts3[2] = 0;
+    for (int64_t h = 0; h < N; ++h) {
+        const uint8_t *x = X + (size_t)h * n;
+        int label = 2;
+        for (int64_t r = 0; r < R_L && label == 2; ++r)
+            if (orc_leq(n, x, ref_L + (size_t)r * n))
+                label = 0;
+        for (int64_t r = 0; r < R_U && label == 2; ++r)
+            if (orc_leq(n, ref_U + (size_t)r * n, x))
+                label = 1;
+        labels[h] = (uint8_t)label;
+        counts3[label] += 1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Estimates (Sec. 3.3 count estimators and c.o.v.; Sec. 3.5 Stage 2).        */
+/*   p_hat^L = c_L/H, p_hat^U = c_U/H, p_hat^u = c_u/H                         */
+/*   P_hat(S <= m') = (c_L + n_u_lower)/H, where n_u_lower is the number of    */
+/*   unclassified samples that Phi resolved to S <= m' (0 before Stage 2)      */
+/*   P_hat(S >= m'+1) = (c_U + (c_u - n_u_lower))/H                            */
+/*   delta_hat(p) = sqrt((1 - p)/(H p)); +inf at p = 0 (IEEE division).         */
+/* out: [pL, pU, pu, P_lower, P_upper, cov_pL, cov_pU, cov_pu, cov_lower,     */
+/*       cov_upper]                                                            */
+/* ------------------------------------------------------------------------ */
+static double orc_cov(double p, double H)
+{
+    return sqrt((1.0 - p) / (H * p));
+}
+
+void orc_estimate(const int64_t counts3[3], int64_t N, int64_t n_u_lower, double *out)
+{
+    double H = (double)N;
+    double pL = (double)counts3[0] / H;
+    double pU = (double)counts3[1] / H;
+    double pu = (double)counts3[2] / H;
+    double P_lower = (double)(counts3[0] + n_u_lower) / H;
+    double P_upper = (double)(counts3[1] + (counts3[2] - n_u_lower)) / H;
+    out[0] = pL;
+    out[1] = pU;
+    out[2] = pu;
+    out[3] = P_lower;
+    out[4] = P_upper;
+    out[5] = orc_cov(pL, H);
+    out[6] = orc_cov(pU, H);
+    out[7] = orc_cov(pu, H);
+    out[8] = orc_cov(P_lower, H);
+    out[9] = orc_cov(P_upper, H);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Score-function gradient (not in the paper).  With independent components,  */
+/*   P(F) = sum_x 1_F(x) prod_j q_{j,x_j}                                      */
+/* is multilinear in the q's, and its unconstrained partial derivative is      */
+/*   dP(F)/dq_{i,k} = E[ 1_F(X) 1{X_i = k} ] / q_{i,k} = P(F | X_i = k).        */
+/* F is the event S <= m' (samples labelled I^L plus the unclassified samples  */
+/* that Phi resolved to S <= m').                                              */
+/*                                                                             */
+/* orc_grad_counts: C[i*K + k] = #{ h in F : x_{h,i} = k }, F given by labels  */
+/* (label 0) plus the listed unclassified indices.                             */
+/* ------------------------------------------------------------------------ */
+void orc_grad_counts(int32_t n, int32_t K, int64_t N, const uint8_t *X, const uint8_t *labels,
+                     const int64_t *u_lower_idx, int64_t n_u_lower, int64_t *C)
+{
+    for (int64_t j = 0; j < (int64_t)n * K; ++j)
+        C[j] = 0;
+    for (int64_t h = 0; h < N; ++h) {
+        if (labels[h] != 0)
+            continue;
+        for (int32_t i = 0; i < n; ++i)
+            C[(size_t)i * K + X[(size_t)h * n + i]] += 1;
+    }
+    for (int64_t j = 0; j < n_u_lower; ++j) {
+        int64_t h = u_lower_idx[j];
+        for (int32_t i = 0; i < n; ++i)
+            C[(size_t)i * K + X[(size_t)h * n + i]] += 1;
+    }
+}
+
+/* Estimator g_hat_{i,k} = (C_{i,k}/H) / q_{i,k}.  Each sample contributes     */
+/* Y = 1_F 1{x_i = k} / q_{i,k}, a Bernoulli(p) variable scaled by 1/q with     */
+/* p = C/H, so its standard error is sqrt(p (1 - p) / H) / q.  q = 0 gives      */
+/* IEEE results (0/0 = NaN).                                                   */
+void orc_grad(int32_t n, int32_t K, int64_t N, const int64_t *C, const double *pmf,
+              double *g, double *se)
+{
+    double H = (double)N;
+    for (int64_t j = 0; j < (int64_t)n * K; ++j) {
+        double p = (double)C[j] / H;
+        double q = pmf[j];
+        g[j] = p / q;
+        se[j] = sqrt(p * (1.0 - p) / H) / q;
+    }
+}
+
+/* Consistency of a reference pair (Sec. 3.3, note on precedence): the label   */
+/* sets can overlap only if some upper reference r^U lies below some lower     */
+/* reference r^L (r^U <= r^L); a sample between them satisfies both.  Returns  */
+/* the number of such (r^L, r^U) pairs.                                        */
+int64_t orc_count_overlaps(int32_t n, int64_t R_L, const uint8_t *ref_L,
+                           int64_t R_U, const uint8_t *ref_U)
+{
+    int64_t c = 0;
+    for (int64_t a = 0; a < R_L; ++a)
+        for (int64_t b = 0; b < R_U; ++b)
+            if (orc_leq(n, ref_U + (size_t)b * n, ref_L + (size_t)a * n))
+                c += 1;
+    return c;
+}
