@@ -1,0 +1,192 @@
+/*
+ * rsr.h -- C ABI of the GB300 (sm_103a) RSR hot-path library, librsr.so.
+ *
+ * Reference-state System Reliability (arXiv 2604.17066): N Monte Carlo samples
+ * of n components with K states each are classified against lower (failure,
+ * S <= m') and upper (survival, S >= m'+1) reference states; probabilities,
+ * coefficients of variation and score-function gradients follow from integer
+ * counts.
+ *
+ * Conventions (all functions):
+ *   - Return RSR_OK (0) or a negative rsr_status; no exception crosses the ABI.
+ *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller owns every buffer;
+ *     the library allocates no device memory (the caller passes a workspace of
+ *     rsr_workspace_size() bytes, 256-byte aligned).
+ *   - Calls that take a stream are asynchronous on it unless stated otherwise.
+ *     Stream 0 is the legacy default stream.
+ *   - Component states are uint8 in [0, K).  Reference and sample matrices are
+ *     row-major, one row of n states per reference / sample.
+ *   - Labels: 0 = I^L (sample lies below a lower reference: S <= m'),
+ *             1 = I^U (sample lies above an upper reference: S >= m'+1),
+ *             2 = I^u (unclassified).
+ *   - Sampler (not specified by the paper, Sec. 3.1 assumes P(X) can be
+ *     sampled): thresholds T_{i,k} = min(2^32, floor(2^32 * sum_{j<k} q_{i,j}))
+ *     with the fp64 sum taken left to right; component i of sample h
+ *     (h = offset + local index) uses u = word (i mod 4) of
+ *     Philox4x32-10(key = (seed lo32, seed hi32), ctr = (h lo32, h hi32, i/4, 0))
+ *     and takes state x = #{k in 1..K-1 : u >= T_{i,k}}.
+ *   - Limits: 1 <= n, 2 <= K <= 16, n*(K-1) <= 1024, R_L + R_U >= 1,
+ *     R_L, R_U < 2^31.
+ */
+#ifndef RSR_H
+#define RSR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RSR_API __attribute__((visibility("default")))
+#else
+#define RSR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *rsr_stream_t;
+
+typedef enum rsr_status {
+    RSR_OK = 0,
+    RSR_ERR_INVALID_ARG = -1,    /* NULL pointer, size out of range, pmf row not summing to 1 */
+    RSR_ERR_CUDA = -2,           /* a CUDA runtime call failed (rsr_last_cuda_error() has it) */
+    RSR_ERR_WORKSPACE = -3,      /* workspace too small or not 256-byte aligned */
+    RSR_ERR_TIMEOUT = -4,        /* a bounded device wait gave up (the context stays usable) */
+    RSR_ERR_UNSUPPORTED = -5,    /* sizes beyond the limits above, or no sm_100-family GPU */
+    RSR_ERR_NOT_PREPARED = -6    /* workspace not prepared for this problem / pmf */
+} rsr_status;
+
+/* Classifier implementation. */
+typedef enum rsr_path {
+    RSR_PATH_AUTO = 0,  /* tuned choice (see rsr_autotune) */
+    RSR_PATH_POPC = 1,  /* bit-packed AND / OR-reduce on the CUDA cores */
+    RSR_PATH_TC = 2     /* tcgen05 FP8 violation contraction on the tensor cores */
+} rsr_path;
+
+/* rsr_problem.flags */
+#define RSR_FLAG_DENSE 1u  /* test every sample against every reference (no early exit) */
+
+/*
+ * One classification problem for a threshold m' (Sec. 3.2-3.3).
+ *   n, K     : components and states per component (paper: N and M).
+ *   pmf      : host, n*K fp64, row i = P(X_i = 0..K-1); each row sums to 1 within 1e-9.
+ *   R_L, R_U : numbers of lower / upper reference states (paper: R^L, R^U).
+ *   ref_L    : device, R_L*n uint8, lower references x^L_r (Eq. (2)); may be NULL if R_L = 0.
+ *   ref_U    : device, R_U*n uint8, upper references x^U_r (Eq. (3)); may be NULL if R_U = 0.
+ *   path     : rsr_path.
+ *   flags    : RSR_FLAG_* bits.
+ * The library reads ref_L / ref_U only inside rsr_prepare (it keeps its own
+ * encoded copies in the workspace).
+ */
+typedef struct rsr_problem {
+    int32_t n;
+    int32_t K;
+    const double *pmf;
+    int64_t R_L;
+    int64_t R_U;
+    const uint8_t *ref_L;
+    const uint8_t *ref_U;
+    int32_t path;
+    uint32_t flags;
+} rsr_problem;
+
+/* Estimates from integer counts (Sec. 3.3 estimators and c.o.v.; Sec. 3.5). */
+typedef struct rsr_estimate_out {
+    double pL, pU, pu;   /* |I^L|/H, |I^U|/H, |I^u|/H */
+    double P_lower;      /* (|I^L| + n_u_lower)/H : P(S <= m') once I^u is resolved */
+    double P_upper;      /* (|I^U| + |I^u| - n_u_lower)/H : P(S >= m'+1) */
+    double cov_pL, cov_pU, cov_pu, cov_lower, cov_upper;  /* sqrt((1-p)/(H p)); +inf at p = 0 */
+} rsr_estimate_out;
+
+/*
+ * Workspace bytes needed to classify up to N samples of `problem` (N only
+ * bounds nothing today; it is reserved).  0 on invalid input.
+ */
+RSR_API size_t rsr_workspace_size(const rsr_problem *problem, int64_t N);
+
+/*
+ * Prepare `ws` for `problem` (Sec. 3.2 encoding, plus the sampler thresholds):
+ * computes the thresholds on the host, encodes both reference sets for the
+ * chosen path (bit-packed thermometer words; FP8 0/1 tiles in the tensor-core
+ * shared-memory layout) and runs the precedence pre-check (does any upper
+ * reference lie below a lower reference?  Algorithm 1 lets lower win; if no
+ * pair overlaps, the kernels may stop at the first match in either set).
+ * Asynchronous on `stream` except for a host->device copy of the thresholds
+ * from pageable memory.  `ref_L` / `ref_U` must stay valid until the stream
+ * reaches this point.  Not capturable in a CUDA graph.
+ */
+RSR_API int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream);
+
+/*
+ * Recompute only the sampler thresholds after `problem->pmf` changed (the
+ * references stay valid when component probabilities change, Sec. 5).  `ws`
+ * must have been prepared for the same references.
+ */
+RSR_API int rsr_update_pmf(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream);
+
+/*
+ * Classify N samples (Sec. 3.3, Algorithm 1; lower takes precedence).
+ *   seed, offset     : sampler key and index of the first sample.
+ *   samples_or_null  : device N*n uint8 states to classify instead of sampling; NULL = sample.
+ *   labels_or_null   : device N uint8 labels (0/1/2); NULL = do not write labels.
+ *   counts3          : device int64[3], |I^L|, |I^U|, |I^u| are ADDED (the caller zeroes it).
+ *   grad_counts_or_null : device int64[n*K]; C[i*K+k] += #{h in I^L : x_{h,i} = k}.
+ *   exec_tests_or_null  : device int64[1]; += reference tests actually executed
+ *                         (tiles issued x tile size on the tensor path).
+ * `ws` must be prepared for this problem and pmf (else RSR_ERR_NOT_PREPARED).
+ * Capturable in a CUDA graph.
+ */
+RSR_API int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N,
+                 const uint8_t *samples_or_null, uint8_t *labels_or_null, int64_t *counts3,
+                 int64_t *grad_counts_or_null, int64_t *exec_tests_or_null,
+                 void *ws, size_t ws_bytes, rsr_stream_t stream);
+
+/*
+ * Estimates on the host from counts3 (host int64[3]) and H = N (Sec. 3.3):
+ * p_hat = count/H and delta_hat = sqrt((1 - p)/(H p)); n_u_lower = number of
+ * unclassified samples that Phi resolved to S <= m' (Sec. 3.5 Stage 2; pass 0
+ * before Stage 2).  Synchronous, no CUDA.
+ */
+RSR_API int rsr_estimate(const int64_t counts3[3], int64_t N, int64_t n_u_lower, rsr_estimate_out *out);
+
+/*
+ * Score-function gradient of P(S <= m') with respect to every q_{i,k} (not in
+ * the paper).  dP/dq_{i,k} = E[1_F 1{X_i = k}]/q_{i,k} = P(F | X_i = k), F = S <= m'.
+ *   grad_counts : device int64[n*K] from rsr_classify over samples offset..offset+N-1;
+ *                 the states of the listed unclassified samples are ADDED to it in place.
+ *   u_lower_idx : device int64[n_u_lower], local indices (0..N-1) of unclassified samples
+ *                 that Phi resolved to S <= m'; may be NULL if n_u_lower = 0.
+ *   grad_out, se_out : host fp64[n*K]: g = (C/H)/q, se = sqrt(p(1-p)/H)/q with p = C/H.
+ * Synchronises `stream` (reads the counts back).  Uses the thresholds in `ws`.
+ */
+RSR_API int rsr_grad(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N,
+             int64_t *grad_counts, const int64_t *u_lower_idx, int64_t n_u_lower,
+             double *grad_out, double *se_out, void *ws, size_t ws_bytes, rsr_stream_t stream);
+
+/*
+ * Materialise samples offset..offset+N-1 as device N*n uint8 states (the same
+ * states rsr_classify draws).  `ws` must hold this problem's thresholds.
+ */
+RSR_API int rsr_sample(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N,
+               uint8_t *states, void *ws, size_t ws_bytes, rsr_stream_t stream);
+
+/*
+ * Device-side results of the precedence pre-check and error flag, copied to
+ * host int32[2] = {overlapping pairs > 0, device error code}.  Synchronises
+ * `stream`.
+ */
+RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t stream);
+
+/* Message for a status code (static storage). */
+RSR_API const char *rsr_status_string(int status);
+
+/* Text of the last CUDA error seen by this thread inside the library. */
+RSR_API const char *rsr_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSR_H */

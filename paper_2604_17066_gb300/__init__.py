@@ -1,0 +1,23 @@
+"""GB300-native (sm_103a) hot path of Reference-state System Reliability
+(arXiv 2604.17066): Monte Carlo samples classified against lower / upper
+reference states, estimates and score-function gradients, behind the C ABI of
+librsr.so (include/rsr.h).
+
+The CUDA library is loaded lazily on first use; importing the package needs no
+GPU.  There is no CPU fallback: the entry points raise if librsr.so is missing.
+"""
+from __future__ import annotations
+
+__all__ = [
+    "Problem", "Session", "RSRProb", "RSRError", "alloc_workspace",
+    "rsr_workspace_size", "rsr_prepare", "rsr_update_pmf", "rsr_classify", "rsr_estimate",
+    "rsr_grad", "rsr_sample", "rsr_workspace_status",
+    "RSR_PATH_AUTO", "RSR_PATH_POPC", "RSR_PATH_TC", "RSR_FLAG_DENSE",
+]
+
+
+def __getattr__(name):
+    if name in __all__:
+        from . import api
+        return getattr(api, name)
+    raise AttributeError(name)

@@ -1,0 +1,209 @@
+"""Python binding of librsr: the C entry points under the same names, taking
+torch tensors for device buffers (argument marshalling only), plus a small
+session object and a torch.autograd.Function for the score-function gradient.
+
+Every step of the hot path runs in librsr's CUDA kernels; nothing here computes
+on the host beyond building argument structs.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (RSR_FLAG_DENSE, RSR_PATH_AUTO, RSR_PATH_POPC, RSR_PATH_TC,  # noqa: F401
+                   RSRError, check, rsr_estimate_out, rsr_problem)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Problem:
+    """pmf (host, n x K fp64) and reference states (device uint8) of one
+    threshold m'.  Keeps the buffers alive for as long as the C struct points
+    at them."""
+
+    def __init__(self, pmf, ref_L, ref_U, path: int = RSR_PATH_AUTO, dense: bool = False,
+                 device: Optional[torch.device] = None):
+        self.pmf = np.ascontiguousarray(pmf, dtype=np.float64)
+        if self.pmf.ndim != 2:
+            raise ValueError("pmf must be n x K")
+        n = self.pmf.shape[0]
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.ref_L = torch.as_tensor(np.asarray(ref_L, dtype=np.uint8).reshape(-1, n)).to(dev).contiguous()
+        self.ref_U = torch.as_tensor(np.asarray(ref_U, dtype=np.uint8).reshape(-1, n)).to(dev).contiguous()
+        self.path = int(path)
+        self.dense = bool(dense)
+
+    @property
+    def n(self) -> int:
+        return int(self.pmf.shape[0])
+
+    @property
+    def K(self) -> int:
+        return int(self.pmf.shape[1])
+
+    @property
+    def R_L(self) -> int:
+        return int(self.ref_L.shape[0])
+
+    @property
+    def R_U(self) -> int:
+        return int(self.ref_U.shape[0])
+
+    def struct(self) -> rsr_problem:
+        s = rsr_problem()
+        s.n, s.K = self.n, self.K
+        s.pmf = self.pmf.ctypes.data
+        s.R_L, s.R_U = self.R_L, self.R_U
+        s.ref_L = self.ref_L.data_ptr() if self.R_L else None
+        s.ref_U = self.ref_U.data_ptr() if self.R_U else None
+        s.path = self.path
+        s.flags = RSR_FLAG_DENSE if self.dense else 0
+        return s
+
+
+# ---------------------------------------------------------------------------
+# the C entry points, same names
+# ---------------------------------------------------------------------------
+def rsr_workspace_size(problem: Problem, N: int = 0) -> int:
+    s = problem.struct()
+    size = _lib.load().rsr_workspace_size(ctypes.byref(s), int(N))
+    if size == 0:
+        raise RSRError(_lib.RSR_ERR_INVALID_ARG, "rsr_workspace_size")
+    return int(size)
+
+
+def alloc_workspace(problem: Problem, N: int = 0) -> torch.Tensor:
+    ws = torch.empty(rsr_workspace_size(problem, N) + 256, dtype=torch.uint8, device="cuda")
+    off = (-ws.data_ptr()) % 256
+    return ws[off:off + rsr_workspace_size(problem, N)]
+
+
+def rsr_prepare(problem: Problem, ws: torch.Tensor, stream=None) -> None:
+    s = problem.struct()
+    check(_lib.load().rsr_prepare(ctypes.byref(s), _ptr(ws), ws.numel(), _stream(stream)), "rsr_prepare")
+
+
+def rsr_update_pmf(problem: Problem, ws: torch.Tensor, stream=None) -> None:
+    s = problem.struct()
+    check(_lib.load().rsr_update_pmf(ctypes.byref(s), _ptr(ws), ws.numel(), _stream(stream)), "rsr_update_pmf")
+
+
+def rsr_classify(problem: Problem, seed: int, offset: int, N: int, ws: torch.Tensor,
+                 counts3: torch.Tensor, samples: Optional[torch.Tensor] = None,
+                 labels: Optional[torch.Tensor] = None, grad_counts: Optional[torch.Tensor] = None,
+                 exec_tests: Optional[torch.Tensor] = None, stream=None) -> None:
+    s = problem.struct()
+    check(_lib.load().rsr_classify(ctypes.byref(s), int(seed), int(offset), int(N), _ptr(samples), _ptr(labels),
+                                   _ptr(counts3), _ptr(grad_counts), _ptr(exec_tests), _ptr(ws), ws.numel(),
+                                   _stream(stream)), "rsr_classify")
+
+
+def rsr_estimate(counts3, N: int, n_u_lower: int = 0) -> dict:
+    c = np.ascontiguousarray(np.asarray(counts3, dtype=np.int64).reshape(3))
+    out = rsr_estimate_out()
+    check(_lib.load().rsr_estimate(c.ctypes.data, int(N), int(n_u_lower), ctypes.byref(out)), "rsr_estimate")
+    return {name: getattr(out, name) for name, _ in rsr_estimate_out._fields_}
+
+
+def rsr_grad(problem: Problem, seed: int, offset: int, N: int, grad_counts: torch.Tensor, ws: torch.Tensor,
+             u_lower_idx: Optional[torch.Tensor] = None, stream=None):
+    s = problem.struct()
+    g = np.zeros((problem.n, problem.K), dtype=np.float64)
+    se = np.zeros_like(g)
+    m = 0 if u_lower_idx is None else int(u_lower_idx.numel())
+    check(_lib.load().rsr_grad(ctypes.byref(s), int(seed), int(offset), int(N), _ptr(grad_counts),
+                               _ptr(u_lower_idx) if m else None, m, g.ctypes.data, se.ctypes.data, _ptr(ws),
+                               ws.numel(), _stream(stream)), "rsr_grad")
+    return g, se
+
+
+def rsr_sample(problem: Problem, seed: int, offset: int, N: int, ws: torch.Tensor,
+               states: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    if states is None:
+        states = torch.empty((N, problem.n), dtype=torch.uint8, device="cuda")
+    s = problem.struct()
+    check(_lib.load().rsr_sample(ctypes.byref(s), int(seed), int(offset), int(N), _ptr(states), _ptr(ws),
+                                 ws.numel(), _stream(stream)), "rsr_sample")
+    return states
+
+
+def rsr_workspace_status(ws: torch.Tensor, stream=None):
+    out = np.zeros(2, dtype=np.int32)
+    check(_lib.load().rsr_workspace_status(_ptr(ws), out.ctypes.data, _stream(stream)), "rsr_workspace_status")
+    return int(out[0]), int(out[1])
+
+
+# ---------------------------------------------------------------------------
+# convenience layer
+# ---------------------------------------------------------------------------
+class Session:
+    """A prepared workspace for one Problem: classify batches of samples,
+    estimate, and differentiate, reusing the encoded references (the references
+    stay valid when the pmf changes, Sec. 5)."""
+
+    def __init__(self, problem: Problem, stream=None):
+        self.problem = problem
+        self.stream = stream
+        self.ws = alloc_workspace(problem)
+        rsr_prepare(problem, self.ws, stream)
+
+    def set_pmf(self, pmf) -> None:
+        self.problem.pmf = np.ascontiguousarray(pmf, dtype=np.float64)
+        rsr_update_pmf(self.problem, self.ws, self.stream)
+
+    def classify(self, seed: int, offset: int, N: int, samples: Optional[torch.Tensor] = None,
+                 labels: bool = True, grad: bool = False, count_tests: bool = False) -> dict:
+        dev = self.ws.device
+        out = {"counts3": torch.zeros(3, dtype=torch.int64, device=dev)}
+        out["labels"] = torch.empty(N, dtype=torch.uint8, device=dev) if labels else None
+        out["grad_counts"] = (torch.zeros(self.problem.n * self.problem.K, dtype=torch.int64, device=dev)
+                              if grad else None)
+        out["exec_tests"] = torch.zeros(1, dtype=torch.int64, device=dev) if count_tests else None
+        rsr_classify(self.problem, seed, offset, N, self.ws, out["counts3"], samples, out["labels"],
+                     out["grad_counts"], out["exec_tests"], self.stream)
+        return out
+
+    def overlap(self) -> bool:
+        return rsr_workspace_status(self.ws, self.stream)[0] != 0
+
+
+class RSRProb(torch.autograd.Function):
+    """P_hat(S <= m') from N samples as a differentiable function of the pmf.
+
+    forward(pmf, session, seed, offset, N) -> 0-d fp64 tensor; backward gives
+    grad_output * dP/dq_{i,k} from the same samples (score function, computed
+    by rsr_grad from the per-state counts of I^L samples)."""
+
+    @staticmethod
+    def forward(ctx, pmf: torch.Tensor, session: Session, seed: int, offset: int, N: int):
+        session.set_pmf(pmf.detach().cpu().numpy())
+        out = session.classify(seed, offset, N, labels=False, grad=True)
+        counts = out["counts3"].cpu().numpy()
+        est = rsr_estimate(counts, N)
+        ctx.session, ctx.seed, ctx.offset, ctx.N = session, seed, offset, N
+        ctx.grad_counts = out["grad_counts"]
+        return torch.tensor(est["P_lower"], dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, grad_output):
+        g, _ = rsr_grad(ctx.session.problem, ctx.seed, ctx.offset, ctx.N, ctx.grad_counts, ctx.session.ws,
+                        stream=ctx.session.stream)
+        return grad_output * torch.from_numpy(g), None, None, None, None

@@ -1,0 +1,286 @@
+// classify_popc.cu -- bit-packed reference-state classifier on the CUDA cores.
+//
+// What it computes (Sec. 3.3, Algorithm 1): sample h is in I^L if x_h <= r for
+// some lower reference r, else in I^U if x_h >= r for some upper reference r,
+// else unclassified; lower takes precedence.
+//
+// How: every state is re-encoded as its thermometer bits t_{i,k} = [x_i >= k],
+// k = 1..K-1, packed into 32-bit words (equivalent to the paper's one-hot /
+// cumulative encoding of Sec. 3.2: x_i <= r_i iff t(x_i) is a bitwise subset of
+// t(r_i)).  Then
+//     x <= r^L  iff  OR_w ( t_w(x)  AND NOT t_w(r^L) ) == 0
+//     x >= r^U  iff  OR_w ( t_w(r^U) AND NOT t_w(x)  ) == 0
+// one LOP3 per word and reference.  The complement of each lower reference is
+// stored, so both tests are a single and-or-accumulate.  No violation matrix is
+// ever written; each thread keeps its sample's words in registers and streams
+// the references through shared memory (broadcast reads).
+//
+// Fused in the same pass: Philox sampling (or a read of given states), the
+// label write, the three counts, and the per-bit counts of I^L samples that the
+// score-function gradient needs.  A persistent grid walks 256-sample tiles.
+#include <cuda_runtime.h>
+
+#include "rsr_internal.cuh"
+#include "rsr_launch.h"
+
+namespace rsr {
+
+namespace {
+
+constexpr int kThreads = 256;   // one sample per thread
+constexpr int kChunk = 256;     // references per shared-memory chunk
+
+struct WordWriter {
+    // Appends per-component thermometer runs to a column of 32-bit words in
+    // shared memory (word w of thread t at col[w * kThreads]).
+    uint32_t *col;
+    int w, pos;
+    uint32_t cur;
+    int km1;
+    __device__ __forceinline__ void put(uint32_t x) {
+        const uint32_t bits = (1u << x) - 1u;  // x ones, x <= K-1 <= 15
+        cur |= bits << pos;
+        const int np = pos + km1;
+        if (np >= 32) {
+            col[w * kThreads] = cur;
+            ++w;
+            cur = (np > 32) ? (bits >> (32 - pos)) : 0u;
+            pos = np - 32;
+        } else {
+            pos = np;
+        }
+    }
+    __device__ __forceinline__ void flush(int words_b) {
+        if (pos > 0) {
+            col[w * kThreads] = cur;
+            ++w;
+        }
+        for (; w < words_b; ++w) col[w * kThreads] = 0u;
+    }
+};
+
+template <int WB>
+__global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const ClassifyParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int nthr = p.n * p.km1;
+    unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);
+    uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + ((size_t)nthr * 8 + 15) / 16 * 16);
+    uint32_t *s_ref = s_tw + WB * kThreads;
+    uint32_t *s_cum = s_ref + kChunk * WB;  // per thermometer bit: # I^L samples with the bit set
+    __shared__ unsigned long long s_cnt[3];
+    __shared__ unsigned long long s_exec;
+
+    for (int i = tid; i < nthr; i += kThreads) s_thr[i] = p.thr[i];
+    if (p.grad_counts)
+        for (int j = tid; j < WB * 32; j += kThreads) s_cum[j] = 0u;
+    if (tid < 3) s_cnt[tid] = 0ull;
+    if (tid == 0) s_exec = 0ull;
+    __syncthreads();
+
+    // Without overlapping reference pairs a sample matches at most one set, so
+    // the likelier set (upper) goes first and any match is final.  With
+    // overlaps, every lower reference is tried first (Algorithm 1 precedence).
+    const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    unsigned long long my_cnt0 = 0, my_cnt1 = 0, my_cnt2 = 0, my_exec = 0;
+
+    const int64_t ntiles = (p.N + kThreads - 1) / kThreads;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t hl = tile * kThreads + tid;
+        const bool valid = hl < p.N;
+
+        // ---- sample (or read) and encode this thread's state ----------------
+        WordWriter ww{s_tw + tid, 0, 0, 0u, p.km1};
+        if (valid) {
+            if (p.samples) {
+                const uint8_t *row = p.samples + hl * (int64_t)p.n;
+                for (int i = 0; i < p.n; ++i) ww.put(row[i]);
+            } else {
+                const uint64_t h = p.offset + (uint64_t)hl;
+                const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
+                for (int q = 0; 4 * q < p.n; ++q) {
+                    const U32x4 r = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
+                    const int i0 = 4 * q;
+                    ww.put(state_from_uniform(r.x, s_thr + (size_t)i0 * p.km1, p.km1));
+                    if (i0 + 1 < p.n) ww.put(state_from_uniform(r.y, s_thr + (size_t)(i0 + 1) * p.km1, p.km1));
+                    if (i0 + 2 < p.n) ww.put(state_from_uniform(r.z, s_thr + (size_t)(i0 + 2) * p.km1, p.km1));
+                    if (i0 + 3 < p.n) ww.put(state_from_uniform(r.w, s_thr + (size_t)(i0 + 3) * p.km1, p.km1));
+                }
+            }
+        }
+        ww.flush(WB);
+        uint32_t t[WB];
+#pragma unroll
+        for (int w = 0; w < WB; ++w) t[w] = s_tw[w * kThreads + tid];
+
+        // ---- classify ---------------------------------------------------------
+        bool mL = false, mU = false;
+        bool done = !valid;
+        for (int phase = 0; phase < 2; ++phase) {
+            const bool upper = (phase == 0) != overlap;
+            const uint32_t *refs = upper ? p.popc_U : p.popc_L;
+            const int64_t R = upper ? p.R_U : p.R_L;
+            for (int64_t base = 0; base < R; base += kChunk) {
+                const bool all_done = __syncthreads_and(done);  // also: previous chunk consumed
+                if (all_done && !p.dense) break;
+                const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
+                const uint4 *src = reinterpret_cast<const uint4 *>(refs + base * WB);
+                uint4 *dst = reinterpret_cast<uint4 *>(s_ref);
+                if ((WB & 3) == 0) {
+                    for (int idx = tid; idx < cnt * WB / 4; idx += kThreads) dst[idx] = src[idx];
+                } else {
+                    for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+                }
+                __syncthreads();
+                if (p.dense) {
+                    bool m = false;
+                    if (valid) {
+                        if (upper) {
+                            for (int r = 0; r < cnt; ++r) {
+                                uint32_t acc = 0;
+#pragma unroll
+                                for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
+                                m |= (acc == 0u);
+                            }
+                        } else {
+                            for (int r = 0; r < cnt; ++r) {
+                                uint32_t acc = 0;
+#pragma unroll
+                                for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
+                                m |= (acc == 0u);
+                            }
+                        }
+                        my_exec += (unsigned long long)cnt;
+                    }
+                    if (upper) mU |= m; else mL |= m;
+                } else if (!done) {
+                    int r = 0;
+                    bool m = false;
+                    if (upper) {
+                        for (; r < cnt; ++r) {
+                            uint32_t acc = 0;
+#pragma unroll
+                            for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
+                            if (acc == 0u) { m = true; ++r; break; }
+                        }
+                    } else {
+                        for (; r < cnt; ++r) {
+                            uint32_t acc = 0;
+#pragma unroll
+                            for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
+                            if (acc == 0u) { m = true; ++r; break; }
+                        }
+                    }
+                    my_exec += (unsigned long long)r;
+                    if (m) {
+                        if (upper) mU = true; else mL = true;
+                        done = true;
+                    }
+                }
+            }
+        }
+        const int label = mL ? 0 : (mU ? 1 : 2);
+        if (valid) {
+            if (p.labels) p.labels[hl] = (uint8_t)label;
+            my_cnt0 += label == 0;
+            my_cnt1 += label == 1;
+            my_cnt2 += label == 2;
+        }
+
+        // ---- per-bit counts of I^L samples (gradient) ------------------------
+        if (p.grad_counts) {
+            const bool isL = valid && label == 0;
+            if (__ballot_sync(0xffffffffu, isL)) {
+#pragma unroll
+                for (int w = 0; w < WB; ++w) {
+                    uint32_t mine = 0;
+                    const uint32_t tw = isL ? t[w] : 0u;
+#pragma unroll 4
+                    for (int b = 0; b < 32; ++b) {
+                        const uint32_t m = __ballot_sync(0xffffffffu, (tw >> b) & 1u);
+                        if (lane == b) mine = __popc(m);
+                    }
+                    if (mine) atomicAdd(&s_cum[w * 32 + lane], mine);
+                }
+            }
+        }
+    }
+
+    // ---- block totals -> global -------------------------------------------
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_cnt0 += __shfl_xor_sync(0xffffffffu, my_cnt0, o);
+        my_cnt1 += __shfl_xor_sync(0xffffffffu, my_cnt1, o);
+        my_cnt2 += __shfl_xor_sync(0xffffffffu, my_cnt2, o);
+        my_exec += __shfl_xor_sync(0xffffffffu, my_exec, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&s_cnt[0], my_cnt0);
+        atomicAdd(&s_cnt[1], my_cnt1);
+        atomicAdd(&s_cnt[2], my_cnt2);
+        atomicAdd(&s_exec, my_exec);
+    }
+    __syncthreads();
+    if (tid < 3 && s_cnt[tid]) atomicAdd(&p.counts3[tid], s_cnt[tid]);
+    if (tid == 0 && p.exec_tests && s_exec) atomicAdd(p.exec_tests, s_exec);
+    if (p.grad_counts && s_cnt[0]) {
+        // C[i,0] += F - cum_1 ; C[i,k] += cum_k - cum_{k+1} (cum_K = 0)
+        for (int i = tid; i < p.n; i += kThreads) {
+            long long prev = (long long)s_cnt[0];
+            for (int k = 1; k <= p.km1; ++k) {
+                const long long cum = (long long)s_cum[i * p.km1 + (k - 1)];
+                const long long d = prev - cum;
+                if (d) atomicAdd(&p.grad_counts[(size_t)i * p.K + (k - 1)], (unsigned long long)d);
+                prev = cum;
+            }
+            if (prev) atomicAdd(&p.grad_counts[(size_t)i * p.K + p.km1], (unsigned long long)prev);
+        }
+    }
+}
+
+template <int WB>
+cudaError_t launch_wb(const ClassifyParams &p, cudaStream_t s) {
+    const size_t smem = ((size_t)p.n * p.km1 * 8 + 15) / 16 * 16 +
+                        sizeof(uint32_t) * ((size_t)WB * kThreads + (size_t)kChunk * WB + (size_t)WB * 32);
+    cudaError_t e = cudaFuncSetAttribute(classify_popc_kernel<WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_popc_kernel<WB>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int64_t ntiles = (p.N + kThreads - 1) / kThreads;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)device_sm_count() * occ);
+    if (grid <= 0) return cudaSuccess;
+    classify_popc_kernel<WB><<<(unsigned)grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int popc_word_bucket(int words) {
+    static const int buckets[] = {1, 2, 4, 6, 8, 10, 12, 16, 24, 32};
+    for (int b : buckets)
+        if (words <= b) return b;
+    return -1;
+}
+
+cudaError_t launch_classify_popc(const ClassifyParams &p, cudaStream_t s) {
+    switch (p.words) {
+        case 1: return launch_wb<1>(p, s);
+        case 2: return launch_wb<2>(p, s);
+        case 4: return launch_wb<4>(p, s);
+        case 6: return launch_wb<6>(p, s);
+        case 8: return launch_wb<8>(p, s);
+        case 10: return launch_wb<10>(p, s);
+        case 12: return launch_wb<12>(p, s);
+        case 16: return launch_wb<16>(p, s);
+        case 24: return launch_wb<24>(p, s);
+        case 32: return launch_wb<32>(p, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rsr

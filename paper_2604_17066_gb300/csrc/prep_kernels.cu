@@ -1,0 +1,161 @@
+// prep_kernels.cu -- reference encoding, the precedence pre-check, sample
+// materialisation and the gradient correction pass.
+#include <algorithm>
+
+#include <cuda_runtime.h>
+
+#include "rsr_internal.cuh"
+#include "rsr_launch.h"
+
+namespace rsr {
+
+namespace {
+
+// Thermometer word w of reference r: bit j = i*(K-1) + (k-1) is [r_i >= k];
+// lower references are stored complemented (within the n*(K-1) valid bits) so
+// that the classifier's failure test is t(x) AND stored == 0 (Sec. 3.3: the
+// subset test H . Rbar = 0).
+__global__ void encode_popc_kernel(const uint8_t *__restrict__ refs, int64_t R, int n, int km1, int words_b,
+                                   int complement, uint32_t *__restrict__ out) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= R * words_b) return;
+    const int64_t r = gid / words_b;
+    const int w = (int)(gid % words_b);
+    const int kenc = n * km1;
+    uint32_t word = 0;
+    for (int b = 0; b < 32; ++b) {
+        const int j = w * 32 + b;
+        if (j >= kenc) break;
+        const int i = j / km1;
+        const int k = j % km1 + 1;
+        const uint32_t a = refs[r * n + i] >= k ? 1u : 0u;
+        word |= (complement ? (a ^ 1u) : a) << b;
+    }
+    out[gid] = word;
+}
+
+// Overlap pre-check: some upper reference r^U <= some lower reference r^L iff
+// OR_w (t_w(r^U) AND NOT t_w(r^L)) == 0 for that pair.  One upper reference
+// per thread against lower references streamed through shared memory.
+template <int WB>
+__global__ void __launch_bounds__(256) overlap_kernel(const uint32_t *__restrict__ popc_L, int64_t R_L,
+                                                      const uint32_t *__restrict__ popc_U, int64_t R_U,
+                                                      WsHeader *hdr) {
+    __shared__ __align__(16) uint32_t s_ref[256 * WB];
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t a[WB];
+#pragma unroll
+    for (int w = 0; w < WB; ++w) a[w] = (u < R_U) ? popc_U[u * WB + w] : 0xffffffffu;
+    bool found = false;
+    for (int64_t base = 0; base < R_L; base += 256) {
+        const int cnt = (int)((R_L - base) < 256 ? (R_L - base) : 256);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < cnt * WB; idx += blockDim.x) s_ref[idx] = popc_L[base * WB + idx];
+        __syncthreads();
+        if (u < R_U && !found) {
+            for (int r = 0; r < cnt; ++r) {
+                uint32_t acc = 0;
+#pragma unroll
+                for (int w = 0; w < WB; ++w) acc |= a[w] & s_ref[r * WB + w];
+                if (acc == 0u) {
+                    found = true;
+                    break;
+                }
+            }
+        }
+        if (__syncthreads_or(found)) break;
+    }
+    if (found && u < R_U) atomicOr(&hdr->overlap, 1);
+}
+
+template <int WB>
+cudaError_t launch_overlap_wb(const uint32_t *popc_L, int64_t R_L, const uint32_t *popc_U, int64_t R_U,
+                              WsHeader *hdr, cudaStream_t s) {
+    const int64_t grid = (R_U + 255) / 256;
+    overlap_kernel<WB><<<(unsigned)grid, 256, 0, s>>>(popc_L, R_L, popc_U, R_U, hdr);
+    return cudaGetLastError();
+}
+
+// Materialised samples: thread per sample, same Philox layout and thresholds
+// as the classifiers.
+__global__ void sample_kernel(const ClassifyParams p, uint8_t *__restrict__ states) {
+    const int64_t hl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (hl >= p.N) return;
+    const uint64_t h = p.offset + (uint64_t)hl;
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    uint8_t *row = states + hl * (int64_t)p.n;
+    for (int q = 0; 4 * q < p.n; ++q) {
+        const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+        const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+        for (int c = 0; c < 4 && 4 * q + c < p.n; ++c) {
+            const int i = 4 * q + c;
+            row[i] = (uint8_t)state_from_uniform(us[c], p.thr + (size_t)i * p.km1, p.km1);
+        }
+    }
+}
+
+// Gradient correction: unclassified samples that Phi resolved to S <= m' join
+// the failure set; their states are regenerated from Philox and counted.
+__global__ void grad_correction_kernel(const ClassifyParams p, const int64_t *__restrict__ idx, int64_t m) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int64_t hl = idx[j];
+    if (hl < 0 || hl >= p.N) {
+        atomicMax(&p.hdr->error, 1);  // index out of range: recorded, not counted
+        return;
+    }
+    const uint64_t h = p.offset + (uint64_t)hl;
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    for (int q = 0; 4 * q < p.n; ++q) {
+        const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+        const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+        for (int c = 0; c < 4 && 4 * q + c < p.n; ++c) {
+            const int i = 4 * q + c;
+            const uint32_t x = state_from_uniform(us[c], p.thr + (size_t)i * p.km1, p.km1);
+            atomicAdd(&p.grad_counts[(size_t)i * p.K + x], 1ull);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_encode_popc(const uint8_t *refs, int64_t R, int n, int km1, int words_b, bool complement,
+                               uint32_t *out, cudaStream_t s) {
+    const int64_t total = R * words_b;
+    if (total <= 0) return cudaSuccess;
+    encode_popc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(refs, R, n, km1, words_b,
+                                                                        complement ? 1 : 0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_overlap(const uint32_t *popc_L, int64_t R_L, const uint32_t *popc_U, int64_t R_U, int words_b,
+                           WsHeader *hdr, cudaStream_t s) {
+    if (R_L <= 0 || R_U <= 0) return cudaSuccess;
+    switch (words_b) {
+        case 1: return launch_overlap_wb<1>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 2: return launch_overlap_wb<2>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 4: return launch_overlap_wb<4>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 6: return launch_overlap_wb<6>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 8: return launch_overlap_wb<8>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 10: return launch_overlap_wb<10>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 12: return launch_overlap_wb<12>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 16: return launch_overlap_wb<16>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 24: return launch_overlap_wb<24>(popc_L, R_L, popc_U, R_U, hdr, s);
+        case 32: return launch_overlap_wb<32>(popc_L, R_L, popc_U, R_U, hdr, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sample(const ClassifyParams &p, uint8_t *states, cudaStream_t s) {
+    if (p.N <= 0) return cudaSuccess;
+    sample_kernel<<<(unsigned)((p.N + 255) / 256), 256, 0, s>>>(p, states);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_correction(const ClassifyParams &p, const int64_t *idx, int64_t m, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    grad_correction_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(p, idx, m);
+    return cudaGetLastError();
+}
+
+}  // namespace rsr

@@ -1,0 +1,135 @@
+// rsr_internal.cuh -- device helpers and workspace layout shared by the
+// kernels of librsr (RSR hot path, arXiv 2604.17066, on sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsr.h"
+
+namespace rsr {
+
+// ---------------------------------------------------------------------------
+// Limits (documented in rsr.h).
+// ---------------------------------------------------------------------------
+constexpr int kMaxK = 16;
+constexpr int kMaxKenc = 1024;                 // n*(K-1) thermometer bits
+constexpr int kMaxWords = kMaxKenc / 32;       // 32-bit words per encoded state
+constexpr int kTcKPad = 32;                    // FP8 MMA K step (bytes)
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// on counter words 0 and 2, xor of the high halves into words 1 / 3 and the
+// round key, word permutation, and a Weyl bump of the key between rounds.
+// ---------------------------------------------------------------------------
+struct U32x4 {
+    uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0;
+        const uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U32x4{c0, c1, c2, c3};
+}
+
+// Component state from one uniform word: x = #{k in 1..K-1 : u >= T_{i,k}}.
+// Thresholds are 33-bit values (T <= 2^32) held in uint64.
+__device__ __forceinline__ uint32_t state_from_uniform(uint32_t u, const unsigned long long *thr_row,
+                                                       int km1) {
+    uint32_t x = 0;
+    for (int k = 0; k < km1; ++k) x += ((unsigned long long)u >= thr_row[k]) ? 1u : 0u;
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout.  The caller passes one 256-byte aligned buffer; offsets
+// below are derived from the problem sizes only (rsr_workspace_size()).
+// ---------------------------------------------------------------------------
+struct WsHeader {
+    int32_t overlap;   // 1 if some upper reference lies below some lower reference
+    int32_t error;     // device error code (0 = none)
+    uint32_t reserved[62];
+};
+static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
+
+struct WsLayout {
+    int32_t n = 0, K = 0, kenc = 0, words = 0;
+    int64_t R_L = 0, R_U = 0;
+    int32_t tc_kpad = 0;        // FP8 row length in bytes (multiple of 32, with slack for the bias)
+    int64_t tc_rows_L = 0;      // references padded to the tensor-core tile
+    int64_t tc_rows_U = 0;
+    size_t off_thr = 0;         // uint64 [n*(K-1)]
+    size_t off_popc_L = 0;      // uint32 [R_L][words]  (complement of the reference thermometer)
+    size_t off_popc_U = 0;      // uint32 [R_U][words]  (reference thermometer)
+    size_t off_tc_L = 0;        // FP8 tiles of the lower references
+    size_t off_tc_U = 0;        // FP8 tiles of the upper references
+    size_t total = 0;
+};
+
+constexpr int kTcRefTile = 128;  // references per tensor-core B tile (N of the MMA)
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline WsLayout make_layout(int32_t n, int32_t K, int64_t R_L, int64_t R_U, int32_t words_b) {
+    WsLayout L;
+    L.n = n;
+    L.K = K;
+    L.kenc = n * (K - 1);
+    L.words = words_b;  // 32-bit words per encoded state, rounded up to a kernel bucket
+    L.R_L = R_L;
+    L.R_U = R_U;
+    // FP8 row: kenc 0/1 bytes, then a constant-one column block that carries the
+    // survival bias (see classify_tc.cu); rounded up to the 32-byte MMA K step.
+    const int bias_cols = (L.kenc + 15) / 16;
+    L.tc_kpad = ((L.kenc + bias_cols + kTcKPad - 1) / kTcKPad) * kTcKPad;
+    L.tc_rows_L = ((R_L + kTcRefTile - 1) / kTcRefTile) * kTcRefTile;
+    L.tc_rows_U = ((R_U + kTcRefTile - 1) / kTcRefTile) * kTcRefTile;
+    size_t off = align256(sizeof(WsHeader));
+    L.off_thr = off;
+    off = align256(off + sizeof(unsigned long long) * (size_t)n * (K - 1));
+    L.off_popc_L = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)R_L * L.words);
+    L.off_popc_U = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)R_U * L.words);
+    L.off_tc_L = off;
+    off = align256(off + (size_t)L.tc_rows_L * L.tc_kpad);
+    L.off_tc_U = off;
+    off = align256(off + (size_t)L.tc_rows_U * L.tc_kpad);
+    L.total = off;
+    return L;
+}
+
+// Parameters of one classification launch (both paths).
+struct ClassifyParams {
+    int32_t n, K, km1, kenc, words;
+    int64_t N;
+    uint64_t seed, offset;
+    const uint8_t *samples;            // NULL = Philox
+    const unsigned long long *thr;     // [n*(K-1)]
+    const uint32_t *popc_L, *popc_U;   // bit-packed references
+    const uint8_t *tc_L, *tc_U;        // FP8 reference tiles
+    int64_t R_L, R_U;
+    int32_t tc_kpad;
+    uint8_t *labels;
+    unsigned long long *counts3;
+    unsigned long long *grad_counts;   // [n*K] or NULL
+    unsigned long long *exec_tests;    // [1] or NULL
+    WsHeader *hdr;
+    int32_t dense;
+};
+
+}  // namespace rsr

@@ -1,0 +1,32 @@
+// rsr_launch.h -- host-side launchers of librsr's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsr_internal.cuh"
+
+namespace rsr {
+
+// Word bucket used by the bit-packed kernels for `words` 32-bit words.
+int popc_word_bucket(int words);
+
+// Preparation (prep_kernels.cu).
+cudaError_t launch_encode_popc(const uint8_t *refs, int64_t R, int n, int km1, int words_b,
+                               bool complement, uint32_t *out, cudaStream_t s);
+cudaError_t launch_overlap(const uint32_t *popc_L, int64_t R_L, const uint32_t *popc_U, int64_t R_U,
+                           int words_b, WsHeader *hdr, cudaStream_t s);
+cudaError_t launch_sample(const ClassifyParams &p, uint8_t *states, cudaStream_t s);
+cudaError_t launch_grad_correction(const ClassifyParams &p, const int64_t *idx, int64_t m,
+                                   cudaStream_t s);
+
+// Classification (classify_popc.cu, classify_tc.cu).
+cudaError_t launch_classify_popc(const ClassifyParams &p, cudaStream_t s);
+cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded, int n, int km1,
+                             int kpad, bool upper, uint8_t *out, cudaStream_t s);
+cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s);
+bool tc_supported();
+
+int device_sm_count();
+
+}  // namespace rsr

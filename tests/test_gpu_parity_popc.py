@@ -1,0 +1,184 @@
+"""GPU parity of the bit-packed (CUDA-core) path against the oracle.
+
+Labels, counts and gradient counts must be bit-exact on the same seeded
+samples; estimates and gradients identical in fp64 (they are computed from
+identical integers with the same formulas).  Sizes: small enough for the
+oracle, large enough to span several 256-sample tiles, several 256-reference
+chunks and a ragged tail.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+POPC = 1
+
+
+def make_session(rsr, prob, path=POPC, dense=False):
+    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=dense)
+    return rsr.Session(P)
+
+
+def random_refs_problem(n, K, R_L, R_U, seed, p_top=0.9):
+    """Partial, random (not boundary) references with a mix of outcomes: lower
+    references sit near the top state with a few low entries, upper references
+    near state 0 with a few high entries."""
+    rng = np.random.default_rng(seed)
+    pmf = rng.dirichlet(np.ones(K) * 0.5, size=n)
+    pmf[:, -1] += 2.0
+    pmf /= pmf.sum(1, keepdims=True)
+    ref_L = np.full((R_L, n), K - 1, dtype=np.uint8)
+    for r in range(R_L):
+        idx = rng.choice(n, size=min(n, int(rng.integers(1, 4))), replace=False)
+        ref_L[r, idx] = rng.integers(0, K - 1, size=idx.size)
+    ref_U = np.zeros((R_U, n), dtype=np.uint8)
+    for r in range(R_U):
+        idx = rng.choice(n, size=min(n, int(rng.integers(3, 12))), replace=False)
+        ref_U[r, idx] = rng.integers(1, K, size=idx.size)
+    return W.Problem("random_refs", pmf, ref_L, ref_U)
+
+
+def run(sess, seed, offset, N, samples=None, grad=True):
+    out = sess.classify(seed, offset, N, samples=samples, labels=True, grad=grad, count_tests=True)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("n,K,N,offset", [(17, 2, 777, 0), (100, 4, 1025, 1 << 40), (68, 16, 300, 5),
+                                          (295, 2, 513, 123456789)])
+def test_sampler_bit_exact(rsr, n, K, N, offset):
+    rng = np.random.default_rng(n)
+    pmf = rng.dirichlet(np.ones(K), size=n)
+    pmf[0] = [0.0] * (K - 1) + [1.0]       # degenerate component: always the top state
+    prob = W.Problem("s", pmf, np.zeros((1, n), np.uint8), np.zeros((0, n), np.uint8))
+    sess = make_session(rsr, prob)
+    got = rsr.rsr_sample(sess.problem, 0xABCDEF0123, offset, N, sess.ws).cpu().numpy()
+    want = O.sample(pmf, 0xABCDEF0123, offset, N)
+    assert np.array_equal(got, want)
+
+
+def test_grid_exhaustive_given_states(rsr):
+    p = W.c1_grid()
+    X = O.all_states(p.n, 2)
+    sess = make_session(rsr, p)
+    got = run(sess, 0, 0, X.shape[0], samples=torch.from_numpy(X).cuda(), grad=False)
+    lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+    assert np.array_equal(got["labels"], lab)
+    assert np.array_equal(got["counts3"], cnt)
+    assert cnt[2] == 0 and np.array_equal(lab, np.where(p.meta["phi_all"] == 0, 0, 1))
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_grid_philox_parity(rsr, dense):
+    p = W.c1_grid()
+    N = 100000
+    sess = make_session(rsr, p, dense=dense)
+    got = run(sess, 1, 0, N)
+    X = O.sample(p.pmf, 1, 0, N)
+    lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+    assert np.array_equal(got["labels"], lab)
+    assert np.array_equal(got["counts3"], cnt)
+    C = O.grad_counts(X, lab, p.K)
+    assert np.array_equal(got["grad_counts"].reshape(p.n, p.K), C)
+    assert rsr.rsr_estimate(got["counts3"], N) == O.estimate(cnt, N)
+    g, se = rsr.rsr_grad(sess.problem, 1, 0, N, torch.from_numpy(got["grad_counts"]).cuda(), sess.ws)
+    g_o, se_o = O.grad(C, N, p.pmf)
+    np.testing.assert_allclose(g, g_o, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(se, se_o, rtol=1e-12, atol=0)
+    if dense:
+        assert got["exec_tests"][0] == N * (p.R_L + p.R_U)
+    else:
+        assert got["exec_tests"][0] < N * (p.R_L + p.R_U)
+
+
+@pytest.mark.parametrize("n,K,R_L,R_U,N", [(295, 2, 300, 700, 5000), (100, 4, 600, 300, 3001),
+                                           (40, 5, 1, 513, 2049), (300, 2, 0, 257, 1000),
+                                           (300, 2, 300, 0, 1000), (3, 3, 2, 2, 1)])
+@pytest.mark.parametrize("dense", [False, True])
+def test_random_refs_parity(rsr, n, K, R_L, R_U, N, dense):
+    prob = random_refs_problem(n, K, R_L, R_U, seed=n * 7 + K)
+    sess = make_session(rsr, prob, dense=dense)
+    got = run(sess, 77, 1000, N)
+    X = O.sample(prob.pmf, 77, 1000, N)
+    lab, cnt = O.classify(X, prob.ref_L, prob.ref_U)
+    assert np.array_equal(got["labels"], lab)
+    assert np.array_equal(got["counts3"], cnt)
+    assert np.array_equal(got["grad_counts"].reshape(n, K), O.grad_counts(X, lab, K))
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_multistate_complete_and_inconsistent_refs(rsr, seed):
+    prob = W.random_small_system(n=6, K=4, M_S=3, seed=seed)
+    # add an upper reference that lies below a lower reference: precedence decides
+    extra_U = prob.ref_L[:1].copy()
+    extra_U[0, 0] = 0
+    prob_bad = W.Problem("bad", prob.pmf, prob.ref_L, np.concatenate([prob.ref_U, extra_U]))
+    assert O.count_overlaps(prob_bad.ref_L, prob_bad.ref_U) > 0
+    for pr, overlapping in ((prob, False), (prob_bad, True)):
+        sess = make_session(rsr, pr)
+        assert sess.overlap() == overlapping
+        got = run(sess, seed, 3, 4099)
+        X = O.sample(pr.pmf, seed, 3, 4099)
+        lab, cnt = O.classify(X, pr.ref_L, pr.ref_U)
+        assert np.array_equal(got["labels"], lab)
+        assert np.array_equal(got["counts3"], cnt)
+
+
+def test_grad_correction_with_resolved_unclassified(rsr):
+    prob = random_refs_problem(60, 3, 40, 40, seed=5)
+    N = 3000
+    sess = make_session(rsr, prob)
+    got = run(sess, 9, 0, N)
+    X = O.sample(prob.pmf, 9, 0, N)
+    lab, cnt = O.classify(X, prob.ref_L, prob.ref_U)
+    unl = np.nonzero(lab == 2)[0]
+    assert unl.size > 10
+    resolved = unl[::3].astype(np.int64)     # pretend Phi put every third one at S <= m'
+    gc = torch.from_numpy(got["grad_counts"]).cuda()
+    g, se = rsr.rsr_grad(sess.problem, 9, 0, N, gc, sess.ws, u_lower_idx=torch.from_numpy(resolved).cuda())
+    C = O.grad_counts(X, lab, prob.K, u_lower_idx=resolved)
+    assert np.array_equal(gc.cpu().numpy().reshape(prob.n, prob.K), C)
+    g_o, se_o = O.grad(C, N, prob.pmf)
+    np.testing.assert_allclose(g, g_o, rtol=1e-12, atol=0)
+    est = rsr.rsr_estimate(got["counts3"], N, resolved.size)
+    assert est == O.estimate(cnt, N, resolved.size)
+
+
+def test_pmf_change_requires_update_and_reuses_refs(rsr):
+    p = W.c1_grid()
+    sess = make_session(rsr, p)
+    new_pmf = p.pmf.copy()
+    new_pmf[3] = [0.3, 0.7]
+    sess.problem.pmf = new_pmf
+    with pytest.raises(rsr.RSRError):
+        sess.classify(1, 0, 10)
+    sess.set_pmf(new_pmf)
+    got = run(sess, 1, 0, 20000)
+    X = O.sample(new_pmf, 1, 0, 20000)
+    lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+    assert np.array_equal(got["labels"], lab)
+
+
+def test_zero_samples_is_a_no_op(rsr):
+    p = W.c1_grid()
+    sess = make_session(rsr, p)
+    got = run(sess, 1, 0, 0)
+    assert got["counts3"].tolist() == [0, 0, 0]
+
+
+def test_autograd_function_matches_oracle(rsr):
+    p = W.c1_grid()
+    N = 50000
+    sess = make_session(rsr, p)
+    q = torch.tensor(p.pmf, dtype=torch.float64, requires_grad=True)
+    P = rsr.RSRProb.apply(q, sess, 4, 0, N)
+    P.backward()
+    X = O.sample(p.pmf, 4, 0, N)
+    lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+    assert P.item() == O.estimate(cnt, N)["P_lower"]
+    g_o, _ = O.grad(O.grad_counts(X, lab, p.K), N, p.pmf)
+    np.testing.assert_allclose(q.grad.numpy(), g_o, rtol=1e-12, atol=0)
