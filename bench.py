@@ -1,0 +1,357 @@
+"""Benchmark of the RSR hot path on GB300 (one JSON line on rank 0).
+
+Default workload: the 200k-reference classifier (n = 300 binary components,
+R_U = 2e5 DNF terms, R_L = 5e4 greedy cuts, N = 4e6 Philox samples per GPU,
+p_up = 0.9), classified in dense mode (every sample against every reference,
+the paper's O(H N M R) product, Sec. 3.3 complexity) on the tensor-core path,
+with the fused gradient counts and the fp64 estimates and gradient (one step =
+every hot-path step: thresholds, sampling, encoding, classification,
+estimates, gradient).  Extra keys report the same workload with early exit,
+forward-only vs forward+gradient, and the 119-node / 295-edge graph workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "samples classified/s and dominance tests/s vs roofline; fwd vs fwd+grad"
+UNIT = "samples/s"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _workload(name):
+    import workloads.large as L
+    if name == "c3":
+        p = L.c3_dnf()
+        return p, 4_000_000, "c3_dnf300_refs200000U+50000L_N4e6_p0.9"
+    if name == "c2":
+        p = L.c2_rgg()
+        return p, 1_000_000, "c2_rgg119n295e_N1e6"
+    raise ValueError(name)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        self.uuid = uuid
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd[1:1] = ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(prob, seed, n_sample, offset=0):
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    X = O.sample(prob.pmf, seed, offset, n_sample)
+    lab, cnt = O.classify(X, prob.ref_L, prob.ref_U)
+    C = O.grad_counts(X, lab, prob.K)
+    O.grad(C, n_sample, prob.pmf)
+    O.estimate(cnt, n_sample)
+    dt = time.perf_counter() - t0
+    return n_sample / dt, dt
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob, N, wname = _workload(args.workload)
+    n_sample = args.ref_samples
+    for _ in range(args.warmup):
+        cpu_baseline(prob, 1, min(n_sample, 2000))
+    times = []
+    for k in range(args.steps):
+        _, dt = cpu_baseline(prob, 1, n_sample, offset=k * n_sample)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = n_sample / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": wname, "sample_per_step": n_sample, "mode": "oracle (first-match loops)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d samples per step of %s" % (n_sample, wname)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2"])
+    ap.add_argument("--ref-samples", type=int, default=8000)
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2604_17066_gb300 import api as rsr
+    from paper_2604_17066_gb300 import build as rsr_build
+    from paper_2604_17066_gb300.shard import shard_range
+    rsr_build.build()
+
+    prob, N, wname = _workload(args.workload)
+    path = rsr.RSR_PATH_TC if args.workload == "c3" else rsr.RSR_PATH_POPC
+    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=(args.workload == "c3"))
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    sess = rsr.Session(P)
+    torch.cuda.synchronize()
+    prep_ms = 1000 * (time.perf_counter() - t0)
+    overlap = sess.overlap()
+    offset, n_rank = shard_range(N, rank, world)
+    dev = torch.device("cuda", local)
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    gcounts = torch.zeros(P.n * P.K, dtype=torch.int64, device=dev)
+    labels = torch.empty(n_rank, dtype=torch.uint8, device=dev)
+    exec_t = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step(k, grad=True, ev=None):
+        counts.zero_()
+        gcounts.zero_()
+        if ev is not None:
+            ev[0].record(stream)
+        rsr.rsr_classify(P, 1, offset + k * N * world, n_rank, sess.ws, counts, None, labels,
+                         gcounts if grad else None, exec_t, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        if grad:
+            rsr.rsr_grad(P, 1, offset + k * N * world, n_rank, gcounts, sess.ws, stream=stream)
+        est = rsr.rsr_estimate(counts.cpu().numpy(), n_rank)
+        return est
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    launches = 0
+    kern_ms = []
+    step_ms = []
+    exec_t.zero_()
+    with Clocks(uuid) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)                      # L2 flush between timed steps (not timed)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[2].record(stream)
+            est = step(args.warmup + k, grad=True, ev=ev)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            launches += 1
+            kern_ms.append(ev[0].elapsed_time(ev[1]))
+            step_ms.append(ev[2].elapsed_time(ev[3]))
+    torch.cuda.synchronize()
+    exec_tests = int(exec_t.item())
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_step = total_ms / args.steps
+    value = world * n_rank / (ms_step / 1000.0)
+
+    # roofline of the classifier kernel: algorithmic flops (tensor path) or tests
+    peaks, peak_src = _peaks()
+    R = P.R_L + P.R_U
+    kenc = P.n * (P.K - 1)
+    kern_avg = sum(kern_ms) / len(kern_ms)
+    tests_per_launch = n_rank * R
+    if path == rsr.RSR_PATH_TC:
+        flops = 2.0 * kenc * tests_per_launch
+        achieved = flops / (kern_avg / 1000.0) / 1e12
+        peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "note": "FP8 dense peak = 2 x bf16 sustained (%s); algorithmic flops = 2*n(K-1)*N*(R_L+R_U)"
+                        % peak_src}
+    else:
+        roof = {"bound": "alu", "achieved": tests_per_launch / (kern_avg / 1000.0) / 1e12, "peak": None,
+                "unit": "Ttests/s", "frac": None, "traffic": None}
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        # forward only (no gradient counts)
+        fw = []
+        for k in range(3):
+            flush.fill_(k)
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record(stream)
+            step(100 + k, grad=False)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            fw.append(e[0].elapsed_time(e[1]))
+        extras["fwd_ms"] = sum(fw) / len(fw)
+        extras["fwd_grad_ms"] = ms_step
+        extras["fwd_grad_over_fwd"] = ms_step / extras["fwd_ms"]
+        # early exit (production mode) on the same references
+        if args.workload == "c3":
+            P2 = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=rsr.RSR_PATH_TC, dense=False)
+            s2 = rsr.Session(P2)
+            ee = []
+            for k in range(4):
+                flush.fill_(k)
+                counts.zero_()
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                e[0].record(stream)
+                rsr.rsr_classify(P2, 1, 7 * N + k * N, N, s2.ws, counts, None, labels, gcounts, None, stream)
+                e[1].record(stream)
+                torch.cuda.synchronize()
+                ee.append(e[0].elapsed_time(e[1]))
+            ee_ms = statistics.median(ee[1:])
+            extras["early_exit"] = {"ms": ee_ms, "samples_per_s": N / (ee_ms / 1000.0),
+                                    "nominal_tests_per_s": N * R / (ee_ms / 1000.0)}
+            del s2
+        extras["prepare_ms"] = prep_ms
+        extras["overlap_pairs"] = bool(overlap)
+
+    # end to end through the public API: pmf -> thresholds (H2D), classify, results (D2H)
+    e2e = None
+    if rank == 0:
+        lab_host = torch.empty(n_rank, dtype=torch.uint8, pin_memory=True)
+        cnt_host = torch.empty(3, dtype=torch.int64, pin_memory=True)
+        times = []
+        for k in range(3):
+            flush.fill_(k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sess.set_pmf(prob.pmf)                     # host thresholds -> device
+            counts.zero_()
+            gcounts.zero_()
+            rsr.rsr_classify(P, 1, 11 * N + k * N, n_rank, sess.ws, counts, None, labels, gcounts, None, stream)
+            lab_host.copy_(labels, non_blocking=True)
+            cnt_host.copy_(counts, non_blocking=True)
+            g, se = rsr.rsr_grad(P, 1, 11 * N + k * N, n_rank, gcounts, sess.ws, stream=stream)   # syncs
+            rsr.rsr_estimate(cnt_host.numpy(), n_rank)
+            times.append(time.perf_counter() - t0)
+        e2e_s = statistics.median(times)
+        e2e = {"value": n_rank / e2e_s, "unit": UNIT, "h2d_bytes_per_step": P.n * (P.K - 1) * 8,
+               "d2h_bytes_per_step": n_rank + 3 * 8 + P.n * P.K * 8}
+
+    cpu = None
+    if rank == 0:
+        n_s = 20000 if args.workload == "c3" else 100000
+        v, dt = cpu_baseline(prob, 1, n_s, offset=5 * N)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d samples of %s (oracle first-match loops, %.1f s)" % (n_s, wname, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp8-e4m3 0/1 operands, fp32 accumulate (exact integers)"
+            if path == rsr.RSR_PATH_TC else "u32 bit-packed", "data": "synthetic",
+            "config": {"workload": wname, "n": P.n, "K": P.K, "R_L": P.R_L, "R_U": P.R_U, "N_per_gpu": n_rank,
+                       "mode": "dense" if P.dense else "early-exit",
+                       "path": "tcgen05" if path == rsr.RSR_PATH_TC else "popc",
+                       "l2": "flushed between timed steps (256 MB write)", "parallelism": "samples%d" % world},
+            "dominance_tests_per_s": world * n_rank * R / (ms_step / 1000.0),
+            "executed_tests": exec_tests,
+            "kernel_ms": kern_avg,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "estimate": est,
+        }
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,9 +1,673 @@
-// classify_tc.cu -- placeholder until the tcgen05 path lands.
+// classify_tc.cu -- reference-state classification as a tensor-core
+// contraction on sm_103a (tcgen05 + TMEM + bulk async copies).
+//
+// What it computes (Sec. 3.3, Eq. for the violation matrix, Algorithm 1):
+//     V_{h,r} = sum_j A_{h,j} B_{r,j},  sample h classified by r iff V_{h,r} = 0,
+// and, exactly as the paper's two products, a sample is in I^L if some lower
+// reference gives 0, else in I^U if some upper reference gives 0.  V is never
+// written: each 128 x 128 accumulator tile is reduced to "any zero per row" in
+// the epilogue straight out of tensor memory.
+//
+// Encoding (an equivalent re-encoding of Sec. 3.2, thermometer instead of
+// one-hot for the sample): j < n(K-1) indexes (component i, level k = 1..K-1).
+//   sample row:       A_{h,j} = [x_{h,i} >= k], then `bias` columns equal to 1
+//   lower reference:  B_{r,j} = [r_i < k]   (complement), bias columns 0
+//                     -> V = #{(i,k): x_i >= k > r_i} >= 0, zero iff x <= r
+//   upper reference:  B_{r,j} = [r_i >= k], bias columns sum to -sum_i r_i
+//                     -> V = -#{(i,k): r_i >= k > x_i} <= 0, zero iff x >= r
+// All values are integers of magnitude <= 16 in FP8 e4m3 and every partial sum
+// is an integer far below 2^24, so FP32 accumulation is exact.  Padding
+// references carry a +1 in the first bias column and never give 0.
+//
+// Kernel structure (one CTA per SM, persistent over 256-sample blocks):
+//   all 8 warps : Philox-sample the block's 256 states into two FP8 A tiles
+//   warp 0      : producer, one cp.async.bulk per 128-reference tile into a
+//                 ring of shared-memory stages (references are pre-encoded in
+//                 global memory in the MMA's shared-memory layout)
+//   warp 1      : TMEM owner and MMA issuer (2 A tiles x KP/32 MMAs per stage)
+//   warps 4-7   : epilogue, each thread owns one TMEM lane = two sample rows
+// Early exit: the epilogue raises a flag once every row of the block is
+// resolved; the producer stops issuing and closes the block with an in-band
+// sentinel that walks through the same rings, so every barrier phase stays
+// consistent.  Every wait is bounded; on timeout the kernel records
+// RSR_ERR_TIMEOUT in the workspace header, frees its TMEM and returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rsr_internal.cuh"
 #include "rsr_launch.h"
+
 namespace rsr {
-bool tc_supported() { return false; }
-cudaError_t launch_encode_tc(const uint8_t *, int64_t, int64_t, int, int, int, bool, uint8_t *, cudaStream_t) {
-    return cudaErrorNotSupported;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRows = 256;           // samples per block (two 128-row A tiles)
+constexpr int kRefTile = kTcRefTile; // references per B tile (MMA N)
+constexpr int kMaxStages = 4;
+constexpr int kSmemLimit = 232448;   // 227 KB opt-in per CTA
+constexpr uint32_t kTmemCols = 512;  // 2 buffers x (2 A tiles x 128 columns)
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at the base clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-cudaError_t launch_classify_tc(const ClassifyParams &, cudaStream_t) { return cudaErrorNotSupported; }
+
+// ---- mbarrier --------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar, uint32_t count = 1) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false on timeout or when another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int32_t *err) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    uint32_t it = 0;
+    while (true) {
+        if (mbar_test(bar, parity)) return true;
+        if ((++it & 255u) == 0u) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kWaitCycles) {
+                *abort_flag = 1;
+                atomicExch(err, RSR_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// ---- bulk copy (TMA engine, no tensor map) -----------------------------------
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---- tcgen05 -----------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns; thread i receives lane (base+i).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle, K-major: core matrices of
+// 8 rows x 16 bytes stored as 128 contiguous bytes; LBO = distance between the
+// two core matrices along K, SBO = distance between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    return d;                // base offset 0, swizzle none
+}
+
+// Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major,
+// N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kRefTile >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+// Byte offset of (row, 16-byte chunk c) inside a tile of KP-byte rows.
+__device__ __forceinline__ uint32_t tile_off(int row, int c, int kp) {
+    return (uint32_t)(((row >> 3) * (kp >> 4) + c) * 128 + (row & 7) * 16);
+}
+
+// 4 bits -> 4 bytes of e4m3 {0, 1.0 = 0x38}.
+__device__ __forceinline__ uint32_t nibble_to_fp8(uint32_t x) {
+    return ((x * 0x00204081u) & 0x01010101u) * 0x38u;
+}
+
+struct Bits {
+    // appends runs of bits to a word column in shared memory
+    uint32_t *col;
+    int w, pos;
+    uint32_t cur;
+    __device__ __forceinline__ void put(uint32_t bits, int len) {  // len <= 16
+        cur |= bits << pos;
+        const int np = pos + len;
+        if (np >= 32) {
+            col[w * kThreads] = cur;
+            ++w;
+            cur = (np > 32) ? (bits >> (32 - pos)) : 0u;
+            pos = np - 32;
+        } else {
+            pos = np;
+        }
+    }
+    __device__ __forceinline__ void finish(int words) {
+        if (pos > 0) {
+            col[w * kThreads] = cur;
+            ++w;
+        }
+        for (; w < words; ++w) col[w * kThreads] = 0u;
+    }
+};
+
+struct TcSmem {
+    // offsets (bytes) from the dynamic shared memory base
+    uint32_t a, stages, tw, thr, cum, total;
+    int nstages;
+};
+
+__host__ __device__ inline TcSmem tc_smem_plan(int kp, int nthr, int stages_cap) {
+    TcSmem s{};
+    uint32_t off = 0;
+    s.a = off;
+    off += (uint32_t)kRows * kp;
+    s.tw = off;
+    off += (uint32_t)(kp / 32) * kThreads * 4;
+    s.thr = off;
+    off += (uint32_t)((nthr * 8 + 127) / 128 * 128);
+    s.cum = off;
+    off += (uint32_t)kp * 4;
+    off = (off + 1023) & ~1023u;
+    s.stages = off;
+    const uint32_t stage_bytes = (uint32_t)kRefTile * kp;
+    int ns = 0;
+    while (ns < stages_cap && off + (ns + 1) * stage_bytes + 1024 <= (uint32_t)kSmemLimit) ++ns;
+    s.nstages = ns;
+    s.total = off + ns * stage_bytes;
+    return s;
+}
+
+struct TcCtl {
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    int stage_tile[kMaxStages];
+    int acc_tile[2];
+    uint32_t tmem_base;
+    int done;
+    int nres;
+    int abort_flag;
+    unsigned long long exec;
+    unsigned long long cnt[3];
+};
+
+__global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const ClassifyParams p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ TcCtl ctl;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int kp = p.tc_kpad;
+    const int kwords = kp / 32;
+    const int nthr = p.n * p.km1;
+    const TcSmem plan = tc_smem_plan(kp, nthr, kMaxStages);
+    const int S = plan.nstages;
+    uint8_t *sA = smem + plan.a;
+    uint8_t *sStage = smem + plan.stages;
+    uint32_t *sTw = reinterpret_cast<uint32_t *>(smem + plan.tw);
+    unsigned long long *sThr = reinterpret_cast<unsigned long long *>(smem + plan.thr);
+    uint32_t *sCum = reinterpret_cast<uint32_t *>(smem + plan.cum);
+    volatile int *abort_flag = &ctl.abort_flag;
+    int32_t *err = &p.hdr->error;
+
+    for (int i = tid; i < nthr; i += kThreads) sThr[i] = p.thr[i];
+    for (int j = tid; j < kp; j += kThreads) sCum[j] = 0u;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&ctl.full[s], 1);
+            mbar_init(&ctl.empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl.tfull[b], 2);    // MMA completion + the issuer's release arrive
+            mbar_init(&ctl.tempty[b], 4);   // one arrive per epilogue warp
+        }
+        ctl.done = 0;
+        ctl.abort_flag = 0;
+        ctl.exec = 0ull;
+        ctl.cnt[0] = ctl.cnt[1] = ctl.cnt[2] = 0ull;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(&ctl.tmem_base, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl.tmem_base;
+
+    const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
+    const bool upper_first = !overlap;
+    const int64_t tiles_first = ((upper_first ? p.R_U : p.R_L) + kRefTile - 1) / kRefTile;
+    const int64_t tiles_second = ((upper_first ? p.R_L : p.R_U) + kRefTile - 1) / kRefTile;
+    const int64_t T = tiles_first + tiles_second;
+    const uint8_t *src_first = upper_first ? p.tc_U : p.tc_L;
+    const uint8_t *src_second = upper_first ? p.tc_L : p.tc_U;
+    const uint32_t tile_bytes = (uint32_t)kRefTile * kp;
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const int bias_cols = (p.kenc + 15) / 16;
+
+    // ring state (continuous across blocks)
+    int st_stage = 0;
+    uint32_t st_phase = 0;
+    int acc_buf = 0;
+    uint32_t acc_phase = 0;
+
+    // epilogue per-thread totals
+    unsigned long long c0 = 0, c1 = 0, c2 = 0;
+
+    const int64_t nblocks = (p.N + kRows - 1) / kRows;
+    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        // ---- 1. sample the block into the thermometer scratch and the A tiles --
+        {
+            const int64_t hl = blk * kRows + tid;
+            Bits bw{sTw + tid, 0, 0, 0u};
+            if (hl < p.N) {
+                if (p.samples) {
+                    const uint8_t *row = p.samples + hl * (int64_t)p.n;
+                    for (int i = 0; i < p.n; ++i) bw.put((1u << row[i]) - 1u, p.km1);
+                } else {
+                    const uint64_t h = p.offset + (uint64_t)hl;
+                    for (int q = 0; 4 * q < p.n; ++q) {
+                        const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+                        const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const int i = 4 * q + c;
+                            if (i < p.n) {
+                                const uint32_t x = state_from_uniform(us[c], sThr + (size_t)i * p.km1, p.km1);
+                                bw.put((1u << x) - 1u, p.km1);
+                            }
+                        }
+                    }
+                }
+                for (int b = bias_cols; b > 0; b -= 16) {
+                    const int len = b < 16 ? b : 16;
+                    bw.put((1u << len) - 1u, len);
+                }
+            }
+            bw.finish(kwords);
+            // expand to FP8 bytes in the MMA layout
+            const int a_tile = tid >> 7, rr = tid & 127;
+            uint8_t *tileA = sA + (size_t)a_tile * 128 * kp;
+            for (int c = 0; c < kp / 16; ++c) {
+                const uint32_t w = sTw[(c >> 1) * kThreads + tid];
+                const uint32_t b16 = (w >> ((c & 1) * 16)) & 0xFFFFu;
+                uint4 v;
+                v.x = nibble_to_fp8(b16 & 0xF);
+                v.y = nibble_to_fp8((b16 >> 4) & 0xF);
+                v.z = nibble_to_fp8((b16 >> 8) & 0xF);
+                v.w = nibble_to_fp8((b16 >> 12) & 0xF);
+                *reinterpret_cast<uint4 *>(tileA + tile_off(rr, c, kp)) = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (tid == 0) {
+            ctl.done = 0;
+            ctl.nres = 0;
+        }
+        __syncthreads();
+
+        // ---- 2. roles -----------------------------------------------------------
+        if (warp == 0) {
+            if (lane == 0) {
+                for (int64_t j = 0; j <= T; ++j) {
+                    const bool stop = (j == T) || (!p.dense && *((volatile int *)&ctl.done));
+                    if (!mbar_wait(&ctl.empty[st_stage], st_phase ^ 1u, abort_flag, err)) break;
+                    if (stop) {
+                        ctl.stage_tile[st_stage] = -1;
+                        mbar_arrive(&ctl.full[st_stage]);
+                    } else {
+                        ctl.stage_tile[st_stage] = (int)j;
+                        const uint8_t *src = (j < tiles_first) ? src_first + (size_t)j * tile_bytes
+                                                               : src_second + (size_t)(j - tiles_first) * tile_bytes;
+                        mbar_arrive_expect_tx(&ctl.full[st_stage], tile_bytes);
+                        bulk_g2s(sStage + (size_t)st_stage * tile_bytes, src, tile_bytes, &ctl.full[st_stage]);
+                    }
+                    if (++st_stage == S) {
+                        st_stage = 0;
+                        st_phase ^= 1u;
+                    }
+                    if (stop) break;
+                }
+            }
+        } else if (warp == 1) {
+            if (lane == 0) {
+                const uint32_t a_base = smem_u32(sA);
+                const uint32_t sbo = (uint32_t)kp * 8u;
+                unsigned long long issued = 0;
+                while (true) {
+                    if (!mbar_wait(&ctl.full[st_stage], st_phase, abort_flag, err)) break;
+                    const int j = ctl.stage_tile[st_stage];
+                    if (!mbar_wait(&ctl.tempty[acc_buf], acc_phase ^ 1u, abort_flag, err)) break;
+                    ctl.acc_tile[acc_buf] = j;
+                    if (j < 0) {
+                        mbar_arrive(&ctl.empty[st_stage]);
+                        mbar_arrive(&ctl.tfull[acc_buf], 2);
+                    } else {
+                        tc_fence_after();
+                        const uint32_t b_base = smem_u32(sStage + (size_t)st_stage * tile_bytes);
+#pragma unroll 1
+                        for (int a = 0; a < 2; ++a) {
+                            const uint32_t d = tmem + (uint32_t)(acc_buf * 256 + a * 128);
+                            const uint32_t at = a_base + (uint32_t)(a * 128 * kp);
+#pragma unroll 1
+                            for (int kk = 0; kk < kp / 32; ++kk) {
+                                const uint64_t ad = smem_desc(at + kk * 256, 128, sbo);
+                                const uint64_t bd = smem_desc(b_base + kk * 256, 128, sbo);
+                                mma_f8(d, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
+                            }
+                        }
+                        mma_commit(&ctl.empty[st_stage]);
+                        mma_commit(&ctl.tfull[acc_buf]);
+                        mbar_arrive(&ctl.tfull[acc_buf]);  // release of acc_tile
+                        ++issued;
+                    }
+                    if (++st_stage == S) {
+                        st_stage = 0;
+                        st_phase ^= 1u;
+                    }
+                    if (++acc_buf == 2) {
+                        acc_buf = 0;
+                        acc_phase ^= 1u;
+                    }
+                    if (j < 0) break;
+                }
+                ctl.exec += issued * (unsigned long long)(kRefTile * kRows);
+            }
+        } else if (warp >= 4) {
+            const int q = warp & 3;                   // TMEM lane quarter
+            const int row0 = q * 32 + lane;           // row in A tile 0; row0 + 128 in A tile 1
+            const int64_t h0 = blk * kRows + row0, h1 = h0 + 128;
+            const bool v0 = h0 < p.N, v1 = h1 < p.N;
+            bool mL0 = false, mU0 = false, mL1 = false, mU1 = false;
+            bool warp_resolved = false;
+            while (true) {
+                if (!mbar_wait(&ctl.tfull[acc_buf], acc_phase, abort_flag, err)) break;
+                const int j = ctl.acc_tile[acc_buf];
+                if (j >= 0) {
+                    tc_fence_after();
+                    const bool is_upper = (j < tiles_first) == upper_first;
+                    float m0 = 1.0f, m1 = 1.0f;
+                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc_buf * 256);
+#pragma unroll 1
+                    for (int c = 0; c < 4; ++c) {
+                        uint32_t va[32], vb[32];
+                        tmem_ld32(tbase + c * 32, va);
+                        tmem_ld32(tbase + 128 + c * 32, vb);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) {
+                            m0 = fminf(m0, fabsf(__uint_as_float(va[e])));
+                            m1 = fminf(m1, fabsf(__uint_as_float(vb[e])));
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl.tempty[acc_buf]);
+                    const bool z0 = m0 < 0.5f, z1 = m1 < 0.5f;
+                    if (is_upper) {
+                        mU0 |= z0;
+                        mU1 |= z1;
+                    } else {
+                        mL0 |= z0;
+                        mL1 |= z1;
+                    }
+                    if (!p.dense && !warp_resolved) {
+                        // resolved: any lower match, or an upper match that precedence cannot overturn
+                        const bool l_done = !upper_first ? (j + 1 >= tiles_first) : true;
+                        const bool r0 = !v0 || mL0 || (mU0 && (!overlap || l_done));
+                        const bool r1 = !v1 || mL1 || (mU1 && (!overlap || l_done));
+                        // resolution is monotone: each warp reports once; the fourth report ends the block
+                        if (__all_sync(0xffffffffu, r0 && r1)) {
+                            warp_resolved = true;
+                            if (lane == 0 && atomicAdd(&ctl.nres, 1) == 3) *((volatile int *)&ctl.done) = 1;
+                        }
+                    }
+                } else {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl.tempty[acc_buf]);
+                }
+                if (++acc_buf == 2) {
+                    acc_buf = 0;
+                    acc_phase ^= 1u;
+                }
+                if (j < 0) break;
+            }
+            const int lab0 = mL0 ? 0 : (mU0 ? 1 : 2);
+            const int lab1 = mL1 ? 0 : (mU1 ? 1 : 2);
+            if (v0) {
+                if (p.labels) p.labels[h0] = (uint8_t)lab0;
+                c0 += lab0 == 0; c1 += lab0 == 1; c2 += lab0 == 2;
+            }
+            if (v1) {
+                if (p.labels) p.labels[h1] = (uint8_t)lab1;
+                c0 += lab1 == 0; c1 += lab1 == 1; c2 += lab1 == 2;
+            }
+            if (p.grad_counts) {
+                // per-bit counts of I^L rows, from the thermometer scratch
+                const bool L0 = v0 && lab0 == 0, L1 = v1 && lab1 == 0;
+                const int kw = (p.kenc + 31) / 32;
+                for (int half = 0; half < 2; ++half) {
+                    const bool isL = half ? L1 : L0;
+                    if (!__ballot_sync(0xffffffffu, isL)) continue;
+                    const int row = row0 + half * 128;
+                    for (int w = 0; w < kw; ++w) {
+                        const uint32_t tw = isL ? sTw[w * kThreads + row] : 0u;
+                        uint32_t mine = 0;
+#pragma unroll 4
+                        for (int b = 0; b < 32; ++b) {
+                            const uint32_t m = __ballot_sync(0xffffffffu, (tw >> b) & 1u);
+                            if (lane == b) mine = __popc(m);
+                        }
+                        if (mine) atomicAdd(&sCum[w * 32 + lane], mine);
+                    }
+                }
+            }
+        }
+        // Each role advanced its private copy of the ring positions by the same
+        // number of entries (issued tiles + the sentinel), so the copies agree.
+        if (warp == 0 && lane == 0 && *abort_flag) {
+            // let bulk copies that may still be in flight land before the CTA exits
+            const long long t0 = clock64();
+            while (clock64() - t0 < 2000000ll) {
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+    }
+
+    // ---- totals -------------------------------------------------------------
+    if (warp >= 4) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&ctl.cnt[0], c0);
+            atomicAdd(&ctl.cnt[1], c1);
+            atomicAdd(&ctl.cnt[2], c2);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        if (*abort_flag && lane == 0) {
+            // after a timeout, give MMAs that may still be running time to finish
+            const long long t0 = clock64();
+            while (clock64() - t0 < 2000000ll) {
+            }
+        }
+        __syncwarp();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+    if (tid < 3 && ctl.cnt[tid]) atomicAdd(&p.counts3[tid], ctl.cnt[tid]);
+    if (tid == 0 && p.exec_tests && ctl.exec) atomicAdd(p.exec_tests, ctl.exec);
+    if (p.grad_counts && ctl.cnt[0]) {
+        for (int i = tid; i < p.n; i += kThreads) {
+            long long prev = (long long)ctl.cnt[0];
+            for (int k = 1; k <= p.km1; ++k) {
+                const long long cum = (long long)sCum[i * p.km1 + (k - 1)];
+                const long long d = prev - cum;
+                if (d) atomicAdd(&p.grad_counts[(size_t)i * p.K + (k - 1)], (unsigned long long)d);
+                prev = cum;
+            }
+            if (prev) atomicAdd(&p.grad_counts[(size_t)i * p.K + p.km1], (unsigned long long)prev);
+        }
+    }
+}
+
+// Reference rows in the MMA layout: tile t = r / 128 holds rows r in
+// [128 t, 128 t + 128), each KP bytes, core-matrix blocked (tile_off).
+__global__ void encode_tc_kernel(const uint8_t *__restrict__ refs, int64_t R, int64_t rows, int n, int km1,
+                                 int kp, int upper, uint8_t *__restrict__ out) {
+    const int chunks = kp / 16;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= rows * chunks) return;
+    const int64_t r = gid / chunks;
+    const int c = (int)(gid % chunks);
+    const int kenc = n * km1;
+    const int bias_cols = (kenc + 15) / 16;
+    int total = 0;  // sum_i r_i, the number of thermometer ones of an upper reference
+    if (r < R && upper)
+        for (int i = 0; i < n; ++i) total += refs[r * n + i];
+    uint8_t bytes[16];
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+        const int j = c * 16 + e;
+        float v = 0.0f;
+        if (r >= R) {
+            v = (j == kenc) ? 1.0f : 0.0f;  // padding: never zero
+        } else if (j < kenc) {
+            const int i = j / km1, k = j % km1 + 1;
+            const bool a = refs[r * n + i] >= k;
+            v = upper ? (a ? 1.0f : 0.0f) : (a ? 0.0f : 1.0f);
+        } else if (j < kenc + bias_cols && upper) {
+            const int used = (j - kenc) * 16;
+            const int rem = total - used;
+            v = rem <= 0 ? 0.0f : -(float)(rem < 16 ? rem : 16);
+        }
+        // e4m3 encodings of the integers -16..1 used here
+        uint8_t b = 0;
+        if (v == 1.0f) b = 0x38;
+        else if (v < 0.0f) {
+            const int m = (int)(-v);  // 1..16
+            // exponent e, mantissa f: m = (1 + f/8) 2^e
+            int e2 = 0;
+            while ((m >> (e2 + 1)) != 0) ++e2;
+            const int f = ((m << 3) >> e2) & 7;
+            b = (uint8_t)(0x80 | ((e2 + 7) << 3) | f);
+        }
+        bytes[e] = b;
+    }
+    const int64_t t = r / kRefTile;
+    const int rr = (int)(r % kRefTile);
+    uint8_t *dst = out + (size_t)t * kRefTile * kp + tile_off(rr, c, kp);
+    uint4 v;
+    v.x = (uint32_t)bytes[0] | ((uint32_t)bytes[1] << 8) | ((uint32_t)bytes[2] << 16) | ((uint32_t)bytes[3] << 24);
+    v.y = (uint32_t)bytes[4] | ((uint32_t)bytes[5] << 8) | ((uint32_t)bytes[6] << 16) | ((uint32_t)bytes[7] << 24);
+    v.z = (uint32_t)bytes[8] | ((uint32_t)bytes[9] << 8) | ((uint32_t)bytes[10] << 16) | ((uint32_t)bytes[11] << 24);
+    v.w = (uint32_t)bytes[12] | ((uint32_t)bytes[13] << 8) | ((uint32_t)bytes[14] << 16) | ((uint32_t)bytes[15] << 24);
+    *reinterpret_cast<uint4 *>(dst) = v;
+}
+
+}  // namespace
+
+bool tc_supported() {
+    static int cached = -1;
+    if (cached < 0) {
+        int dev = 0, major = 0, minor = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        cached = (major == 10 && minor == 3) ? 1 : 0;
+    }
+    return cached == 1;
+}
+
+int tc_max_kpad() { return 416; }  // two B stages still fit next to the A tiles
+
+cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded, int n, int km1, int kpad,
+                             bool upper, uint8_t *out, cudaStream_t s) {
+    if (rows_padded <= 0) return cudaSuccess;
+    const int64_t total = rows_padded * (kpad / 16);
+    encode_tc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(refs, R, rows_padded, n, km1, kpad,
+                                                                     upper ? 1 : 0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s) {
+    if (p.tc_kpad > tc_max_kpad() || p.tc_kpad % 32 != 0) return cudaErrorNotSupported;
+    const TcSmem plan = tc_smem_plan(p.tc_kpad, p.n * p.km1, kMaxStages);
+    if (plan.nstages < 2) return cudaErrorNotSupported;
+    // at least 120 KB so that two CTAs never share an SM (each takes all 512 TMEM columns)
+    const size_t smem = plan.total > 122880u ? plan.total : 122880u;
+    cudaError_t e = cudaFuncSetAttribute(classify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t nblocks = (p.N + kRows - 1) / kRows;
+    const int64_t grid = std::min<int64_t>(nblocks, (int64_t)device_sm_count());
+    if (grid <= 0) return cudaSuccess;
+    classify_tc_kernel<<<(unsigned)grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
 }  // namespace rsr

@@ -160,7 +160,9 @@ ClassifyParams make_params(const rsr_problem *p, const WsLayout &L, void *ws) {
 // sets are large enough to keep 128x128 MMA tiles busy.
 int choose_path(const rsr_problem *p) {
     if (p->path != RSR_PATH_AUTO) return p->path;
-    if (tc_supported() && (p->R_L + p->R_U) >= 8192 && (p->flags & RSR_FLAG_DENSE)) return RSR_PATH_TC;
+    const WsLayout L = layout_of(p);
+    if (tc_supported() && L.tc_kpad <= tc_max_kpad() && (p->R_L + p->R_U) >= 8192 && (p->flags & RSR_FLAG_DENSE))
+        return RSR_PATH_TC;
     return RSR_PATH_POPC;
 }
 
@@ -197,7 +199,7 @@ int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_strea
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
     const int path = choose_path(problem);
-    if (path == RSR_PATH_TC && !tc_supported()) return RSR_ERR_UNSUPPORTED;
+    if (path == RSR_PATH_TC && (!tc_supported() || L.tc_kpad > tc_max_kpad())) return RSR_ERR_UNSUPPORTED;
     RSR_CUDA(cudaMemsetAsync(base, 0, sizeof(WsHeader), s));
     if ((st = upload_thresholds(problem, L, ws, s)) != RSR_OK) return st;
     const int km1 = problem->K - 1;
@@ -206,7 +208,7 @@ int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_strea
     RSR_CUDA(launch_encode_popc(problem->ref_L, problem->R_L, problem->n, km1, L.words, true, pL, s));
     RSR_CUDA(launch_encode_popc(problem->ref_U, problem->R_U, problem->n, km1, L.words, false, pU, s));
     RSR_CUDA(launch_overlap(pL, problem->R_L, pU, problem->R_U, L.words, reinterpret_cast<WsHeader *>(base), s));
-    if (tc_supported()) {
+    if (tc_supported() && L.tc_kpad <= tc_max_kpad()) {
         RSR_CUDA(launch_encode_tc(problem->ref_L, problem->R_L, L.tc_rows_L, problem->n, km1, L.tc_kpad, false,
                                   reinterpret_cast<uint8_t *>(base + L.off_tc_L), s));
         RSR_CUDA(launch_encode_tc(problem->ref_U, problem->R_U, L.tc_rows_U, problem->n, km1, L.tc_kpad, true,
@@ -261,7 +263,7 @@ int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t offset, int
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int path = choose_path(problem);
     if (path == RSR_PATH_TC) {
-        if (!tc_supported()) return RSR_ERR_UNSUPPORTED;
+        if (!tc_supported() || L.tc_kpad > tc_max_kpad()) return RSR_ERR_UNSUPPORTED;
         RSR_CUDA(launch_classify_tc(c, s));
     } else {
         RSR_CUDA(launch_classify_popc(c, s));

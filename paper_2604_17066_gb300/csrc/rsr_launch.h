@@ -26,6 +26,7 @@ cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded
                              int kpad, bool upper, uint8_t *out, cudaStream_t s);
 cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s);
 bool tc_supported();
+int tc_max_kpad();
 
 int device_sm_count();
 

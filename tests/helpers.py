@@ -1,0 +1,42 @@
+"""Shared helpers of the GPU parity tests (no GPU needed to import)."""
+import numpy as np
+
+import workloads as W
+
+POPC, TC = 1, 2
+
+
+def random_refs_problem(n, K, R_L, R_U, seed):
+    """Partial, random (not boundary) references with a mix of outcomes: lower
+    references sit near the top state with a few low entries, upper references
+    near state 0 with a few high entries."""
+    rng = np.random.default_rng(seed)
+    pmf = rng.dirichlet(np.ones(K) * 0.5, size=n)
+    pmf[:, -1] += 2.0
+    pmf /= pmf.sum(1, keepdims=True)
+    ref_L = np.full((R_L, n), K - 1, dtype=np.uint8)
+    for r in range(R_L):
+        idx = rng.choice(n, size=min(n, int(rng.integers(1, 4))), replace=False)
+        ref_L[r, idx] = rng.integers(0, K - 1, size=idx.size)
+    ref_U = np.zeros((R_U, n), dtype=np.uint8)
+    for r in range(R_U):
+        idx = rng.choice(n, size=min(n, int(rng.integers(3, 12))), replace=False)
+        ref_U[r, idx] = rng.integers(1, K, size=idx.size)
+    return W.Problem("random_refs", pmf, ref_L, ref_U)
+
+
+def tc_kpad(n, K):
+    kenc = n * (K - 1)
+    return ((kenc + (kenc + 15) // 16 + 31) // 32) * 32
+
+
+def make_session(rsr, prob, path=POPC, dense=False):
+    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=dense)
+    return rsr.Session(P)
+
+
+def run(sess, seed, offset, N, samples=None, grad=True):
+    import torch
+    out = sess.classify(seed, offset, N, samples=samples, labels=True, grad=grad, count_tests=True)
+    torch.cuda.synchronize()
+    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}

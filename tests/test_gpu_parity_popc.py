@@ -15,37 +15,7 @@ from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
-POPC = 1
-
-
-def make_session(rsr, prob, path=POPC, dense=False):
-    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=dense)
-    return rsr.Session(P)
-
-
-def random_refs_problem(n, K, R_L, R_U, seed, p_top=0.9):
-    """Partial, random (not boundary) references with a mix of outcomes: lower
-    references sit near the top state with a few low entries, upper references
-    near state 0 with a few high entries."""
-    rng = np.random.default_rng(seed)
-    pmf = rng.dirichlet(np.ones(K) * 0.5, size=n)
-    pmf[:, -1] += 2.0
-    pmf /= pmf.sum(1, keepdims=True)
-    ref_L = np.full((R_L, n), K - 1, dtype=np.uint8)
-    for r in range(R_L):
-        idx = rng.choice(n, size=min(n, int(rng.integers(1, 4))), replace=False)
-        ref_L[r, idx] = rng.integers(0, K - 1, size=idx.size)
-    ref_U = np.zeros((R_U, n), dtype=np.uint8)
-    for r in range(R_U):
-        idx = rng.choice(n, size=min(n, int(rng.integers(3, 12))), replace=False)
-        ref_U[r, idx] = rng.integers(1, K, size=idx.size)
-    return W.Problem("random_refs", pmf, ref_L, ref_U)
-
-
-def run(sess, seed, offset, N, samples=None, grad=True):
-    out = sess.classify(seed, offset, N, samples=samples, labels=True, grad=grad, count_tests=True)
-    torch.cuda.synchronize()
-    return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+from helpers import POPC, make_session, random_refs_problem, run  # noqa: E402
 
 
 @pytest.mark.parametrize("n,K,N,offset", [(17, 2, 777, 0), (100, 4, 1025, 1 << 40), (68, 16, 300, 5),
@@ -129,7 +99,7 @@ def test_multistate_complete_and_inconsistent_refs(rsr, seed):
 
 
 def test_grad_correction_with_resolved_unclassified(rsr):
-    prob = random_refs_problem(60, 3, 40, 40, seed=5)
+    prob = random_refs_problem(60, 3, 6, 3, seed=5)   # labels 790 / 1860 / 350 (oracle)
     N = 3000
     sess = make_session(rsr, prob)
     got = run(sess, 9, 0, N)

@@ -1,0 +1,69 @@
+"""GPU parity of the tensor-core (tcgen05 FP8 contraction) path against the
+oracle: labels, counts and gradient counts bit-exact on the same seeded
+samples, in dense (every reference) and early-exit modes, across several
+128-reference tiles, several 256-sample blocks and ragged tails, for binary
+and multi-state encodings, with and without overlapping reference pairs."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from helpers import TC, make_session, random_refs_problem, run, tc_kpad
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def check(rsr, prob, seed, offset, N, dense, samples=None):
+    sess = make_session(rsr, prob, path=TC, dense=dense)
+    got = run(sess, seed, offset, N, samples=None if samples is None else torch.from_numpy(samples).cuda())
+    X = O.sample(prob.pmf, seed, offset, N) if samples is None else samples
+    lab, cnt = O.classify(X, prob.ref_L, prob.ref_U)
+    assert np.array_equal(got["counts3"], cnt), (got["counts3"], cnt)
+    assert np.array_equal(got["labels"], lab)
+    assert np.array_equal(got["grad_counts"].reshape(prob.n, prob.K), O.grad_counts(X, lab, prob.K))
+    tiles = (-(-prob.R_L // 128)) + (-(-prob.R_U // 128))
+    blocks = -(-N // 256)
+    if dense:
+        assert got["exec_tests"][0] == tiles * blocks * 128 * 256
+    else:
+        assert got["exec_tests"][0] <= tiles * blocks * 128 * 256
+    return got
+
+
+@pytest.mark.parametrize("dense", [True, False])
+def test_tc_grid_philox(rsr, dense):
+    check(rsr, W.c1_grid(), 1, 0, 100000, dense)
+
+
+def test_tc_grid_exhaustive(rsr):
+    p = W.c1_grid()
+    check(rsr, p, 0, 0, 1 << p.n, True, samples=O.all_states(p.n, 2))
+
+
+@pytest.mark.parametrize("n,K,R_L,R_U,N", [(295, 2, 300, 700, 5000), (100, 4, 600, 300, 3001),
+                                           (40, 5, 1, 513, 2049), (300, 2, 0, 257, 1000),
+                                           (300, 2, 300, 0, 1000), (3, 3, 2, 2, 1), (120, 3, 130, 129, 257)])
+@pytest.mark.parametrize("dense", [True, False])
+def test_tc_random_refs(rsr, n, K, R_L, R_U, N, dense):
+    assert tc_kpad(n, K) <= 416
+    check(rsr, random_refs_problem(n, K, R_L, R_U, seed=n * 7 + K), 77, 1000, N, dense)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+@pytest.mark.parametrize("dense", [True, False])
+def test_tc_multistate_with_overlaps(rsr, seed, dense):
+    prob = W.random_small_system(n=6, K=4, M_S=3, seed=seed)
+    extra_U = prob.ref_L[:1].copy()
+    extra_U[0, 0] = 0
+    bad = W.Problem("bad", prob.pmf, prob.ref_L, np.concatenate([prob.ref_U, extra_U]))
+    for pr in (prob, bad):
+        check(rsr, pr, seed, 3, 4099, dense)
+
+
+def test_tc_rejects_too_wide_encodings(rsr):
+    prob = random_refs_problem(68, 16, 3, 3, seed=1)   # 1020 thermometer bits
+    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=TC)
+    with pytest.raises(rsr.RSRError) as e:
+        rsr.Session(P)
+    assert e.value.status == -5
