@@ -179,6 +179,54 @@ RSR_API int rsr_sample(const rsr_problem *problem, uint64_t seed, uint64_t offse
  */
 RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t stream);
 
+/*
+ * Batched launch (many problems, e.g. hazard scenarios, in one persistent
+ * kernel).  Arrays of length S describe the scenarios; scenario s classifies
+ * samples offsets[s] + r*Ns[s] .. offsets[s] + (r+1)*Ns[s] - 1 of its own
+ * Philox stream (key seeds[s]) on the r-th launch after rsr_batch_prepare
+ * (r = 0 first), with the bit-packed test of Algorithm 1 (Sec. 3.3).
+ *   labels_or_null       : host array of S device pointers (N_s uint8 each, NULL entries
+ *                          allowed), or NULL.
+ *   counts3xS            : device int64[S*3]; counts are ADDED.
+ *   grad_counts_or_null  : host array of S device pointers (n_s*K_s int64 each, NULL entries
+ *                          allowed), or NULL; per-state I^L counts are ADDED.
+ * Limits: every scenario within the rsr_problem limits and n*(K-1) <= 512.
+ *
+ * rsr_batch_workspace_size : bytes of the batch workspace (0 on invalid input).
+ * rsr_batch_prepare        : thresholds, reference encodings, precedence pre-checks and the work
+ *                            list (longest scenarios first) into `ws`; not capturable.
+ * rsr_batch                : ONE persistent kernel launch over every (scenario, 256-sample tile);
+ *                            the arguments must equal those given to rsr_batch_prepare (else
+ *                            RSR_ERR_NOT_PREPARED).  The launch re-arms its own counters, so it
+ *                            can be captured once in a CUDA graph and replayed.
+ * rsr_batch_autotune       : times grid sizes and work orders on the prepared batch (writing only
+ *                            into the workspace's scratch, never the caller's outputs), keeps the
+ *                            fastest for later rsr_batch calls and resets the round to 0;
+ *                            chosen[0] = grid, chosen[1] = order (0 = longest first, 1 = as given).
+ *                            Synchronises `stream`.
+ */
+RSR_API size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S);
+RSR_API int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
+                              const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
+                              int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws,
+                              size_t ws_bytes, rsr_stream_t stream);
+RSR_API int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+                      const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
+                      int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream);
+RSR_API int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
+                               const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
+                               int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws,
+                               size_t ws_bytes, rsr_stream_t stream, int32_t chosen[2]);
+
+/*
+ * Time both classifier paths on a 65536-sample slice of `problem` (prepared in
+ * `ws`) and remember the faster one for RSR_PATH_AUTO on problems with the
+ * same n, K, density flag and reference-count bucket (power of two).
+ * *chosen_path receives it.  Synchronises `stream`.
+ */
+RSR_API int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream,
+                         int32_t *chosen_path);
+
 /* Message for a status code (static storage). */
 RSR_API const char *rsr_status_string(int status);
 

@@ -55,6 +55,11 @@ SIGNATURES = {
     "rsr_grad": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _I64, _P, _P, _P, _S, _P]),
     "rsr_sample": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _S, _P]),
     "rsr_workspace_status": (ctypes.c_int, [_P, _P, _P]),
+    "rsr_batch_workspace_size": (ctypes.c_size_t, [_PROB, _I32]),
+    "rsr_batch_prepare": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P]),
+    "rsr_batch": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P]),
+    "rsr_batch_autotune": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P, _P]),
+    "rsr_autotune": (ctypes.c_int, [_PROB, _P, _S, _P, _P]),
     "rsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rsr_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -207,3 +207,71 @@ class RSRProb(torch.autograd.Function):
         g, _ = rsr_grad(ctx.session.problem, ctx.seed, ctx.offset, ctx.N, ctx.grad_counts, ctx.session.ws,
                         stream=ctx.session.stream)
         return grad_output * torch.from_numpy(g), None, None, None, None
+
+
+# ---------------------------------------------------------------------------
+# batched launch
+# ---------------------------------------------------------------------------
+class Batch:
+    """S problems (scenarios) prepared in one workspace and classified by one
+    persistent launch per rsr_batch call.  Outputs live on the device:
+    labels[s] (N_s uint8, optional), counts3 (S x 3 int64) and grad_counts[s]
+    (n_s*K_s int64, optional); counts are accumulated (zero them between
+    launches if needed)."""
+
+    def __init__(self, problems, seeds, offsets, Ns, labels: bool = True, grad: bool = True, stream=None):
+        self.problems = list(problems)
+        S = len(self.problems)
+        self.S = S
+        self.stream = stream
+        self._structs = (rsr_problem * S)(*[p.struct() for p in self.problems])
+        self.seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        self.Ns = np.ascontiguousarray(Ns, dtype=np.int64)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.counts3 = torch.zeros((S, 3), dtype=torch.int64, device=dev)
+        self.labels = [torch.empty(int(n), dtype=torch.uint8, device=dev) for n in self.Ns] if labels else None
+        self.grad_counts = ([torch.zeros(p.n * p.K, dtype=torch.int64, device=dev) for p in self.problems]
+                            if grad else None)
+        self._lab_ptrs = (ctypes.c_void_p * S)(*[t.data_ptr() for t in self.labels]) if labels else None
+        self._grad_ptrs = (ctypes.c_void_p * S)(*[t.data_ptr() for t in self.grad_counts]) if grad else None
+        size = _lib.load().rsr_batch_workspace_size(self._structs, S)
+        if size == 0:
+            raise RSRError(_lib.RSR_ERR_INVALID_ARG, "rsr_batch_workspace_size")
+        raw = torch.empty(size + 256, dtype=torch.uint8, device=dev)
+        off = (-raw.data_ptr()) % 256
+        self.ws = raw[off:off + size]
+        self._args = None
+        rsr_batch_prepare(self)
+
+    def args(self):
+        return (self._structs, self.S, self.seeds.ctypes.data, self.offsets.ctypes.data, self.Ns.ctypes.data,
+                ctypes.cast(self._lab_ptrs, ctypes.c_void_p) if self._lab_ptrs is not None else None,
+                self.counts3.data_ptr(),
+                ctypes.cast(self._grad_ptrs, ctypes.c_void_p) if self._grad_ptrs is not None else None,
+                self.ws.data_ptr(), self.ws.numel())
+
+
+def rsr_batch_prepare(batch: Batch, stream=None) -> None:
+    check(_lib.load().rsr_batch_prepare(*batch.args(), _stream(stream if stream is not None else batch.stream)),
+          "rsr_batch_prepare")
+
+
+def rsr_batch(batch: Batch, stream=None) -> None:
+    check(_lib.load().rsr_batch(*batch.args(), _stream(stream if stream is not None else batch.stream)),
+          "rsr_batch")
+
+
+def rsr_batch_autotune(batch: Batch, stream=None):
+    chosen = np.zeros(2, dtype=np.int32)
+    check(_lib.load().rsr_batch_autotune(*batch.args(), _stream(stream if stream is not None else batch.stream),
+                                         chosen.ctypes.data), "rsr_batch_autotune")
+    return int(chosen[0]), int(chosen[1])
+
+
+def rsr_autotune(problem: Problem, ws: torch.Tensor, stream=None) -> int:
+    s = problem.struct()
+    chosen = ctypes.c_int32(0)
+    check(_lib.load().rsr_autotune(ctypes.byref(s), _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(chosen)),
+          "rsr_autotune")
+    return int(chosen.value)

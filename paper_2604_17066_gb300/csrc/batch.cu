@@ -1,0 +1,263 @@
+// batch.cu -- many classification problems (hazard scenarios) in one
+// persistent launch.
+//
+// Each scenario s has its own n, K, pmf thresholds, reference sets, sample
+// count N_s, seed and offset.  Work items are (scenario, 256-sample tile),
+// enumerated scenario by scenario in the order the host chose (longest
+// scenarios first); a persistent grid pulls items from an atomic counter, so
+// short and long scenarios share the machine without per-scenario launch
+// tails.  Per item the block runs the same bit-packed test as classify_popc.cu
+// (Sec. 3.3, Algorithm 1) for the scenario's word count.  Counts go to the
+// scenario's counts3; I^L per-bit counts go to a scenario scratch counter, and
+// the last block to finish converts them into the per-state gradient counts,
+// zeroes the scratch, resets the work counter and advances the round, so the
+// same launch can be replayed (e.g. from a CUDA graph) on the next N_s samples
+// of every scenario without any host work.
+#include <cuda_runtime.h>
+
+#include "rsr_batch.h"
+#include "rsr_internal.cuh"
+#include "rsr_launch.h"
+
+namespace rsr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 256;
+constexpr int kMaxWB = 16;  // batch path: n*(K-1) <= 512
+
+struct Shared {
+    BatchDesc d;
+    int scenario;
+    long long item;
+    unsigned long long cnt[3];
+    int last;
+};
+
+template <int WB>
+__device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, const unsigned long long *s_thr,
+                              uint32_t *s_tw, uint32_t *s_ref, uint32_t *s_cum, Shared &sh) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t hl = tile * kThreads + tid;
+    const bool valid = hl < d.N;
+    const uint32_t key0 = (uint32_t)d.seed, key1 = (uint32_t)(d.seed >> 32);
+    // ---- sample and encode (thermometer words, one column per thread) ----
+    {
+        uint32_t *col = s_tw + tid;
+        int w = 0, pos = 0;
+        uint32_t cur = 0;
+        if (valid) {
+            const uint64_t h = d.offset + round * (uint64_t)d.N + (uint64_t)hl;
+            for (int q = 0; 4 * q < d.n; ++q) {
+                const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+                const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int i = 4 * q + c;
+                    if (i >= d.n) break;
+                    const uint32_t x = state_from_uniform(us[c], s_thr + (size_t)i * d.km1, d.km1);
+                    const uint32_t bits = (1u << x) - 1u;
+                    cur |= bits << pos;
+                    const int np = pos + d.km1;
+                    if (np >= 32) {
+                        col[w * kThreads] = cur;
+                        ++w;
+                        cur = (np > 32) ? (bits >> (32 - pos)) : 0u;
+                        pos = np - 32;
+                    } else {
+                        pos = np;
+                    }
+                }
+            }
+            if (pos > 0) {
+                col[w * kThreads] = cur;
+                ++w;
+            }
+        }
+        for (; w < WB; ++w) col[w * kThreads] = 0u;
+    }
+    uint32_t t[WB];
+#pragma unroll
+    for (int w = 0; w < WB; ++w) t[w] = s_tw[w * kThreads + tid];
+
+    const bool overlap = *((volatile const int32_t *)d.overlap) != 0;
+    bool mL = false, mU = false, done = !valid;
+    for (int phase = 0; phase < 2; ++phase) {
+        const bool upper = (phase == 0) != overlap;
+        const uint32_t *refs = upper ? d.popc_U : d.popc_L;
+        const int64_t R = upper ? d.R_U : d.R_L;
+        for (int64_t base = 0; base < R; base += kChunk) {
+            if (__syncthreads_and(done)) break;
+            const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
+            for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+            __syncthreads();
+            if (!done) {
+                bool m = false;
+                if (upper) {
+                    for (int r = 0; r < cnt; ++r) {
+                        uint32_t acc = 0;
+#pragma unroll
+                        for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
+                        if (acc == 0u) { m = true; break; }
+                    }
+                } else {
+                    for (int r = 0; r < cnt; ++r) {
+                        uint32_t acc = 0;
+#pragma unroll
+                        for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
+                        if (acc == 0u) { m = true; break; }
+                    }
+                }
+                if (m) {
+                    if (upper) mU = true; else mL = true;
+                    done = true;
+                }
+            }
+        }
+    }
+    const int label = mL ? 0 : (mU ? 1 : 2);
+    if (valid && d.labels) d.labels[hl] = (uint8_t)label;
+    // counts
+    const unsigned b0 = __ballot_sync(0xffffffffu, valid && label == 0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, valid && label == 1);
+    const unsigned b2 = __ballot_sync(0xffffffffu, valid && label == 2);
+    if (lane == 0) {
+        if (b0) atomicAdd(&sh.cnt[0], (unsigned long long)__popc(b0));
+        if (b1) atomicAdd(&sh.cnt[1], (unsigned long long)__popc(b1));
+        if (b2) atomicAdd(&sh.cnt[2], (unsigned long long)__popc(b2));
+    }
+    // per-bit counts of I^L samples
+    if (d.bitcnt && b0) {
+        const bool isL = valid && label == 0;
+#pragma unroll
+        for (int w = 0; w < WB; ++w) {
+            const uint32_t tw = isL ? t[w] : 0u;
+            uint32_t mine = 0;
+#pragma unroll 4
+            for (int b = 0; b < 32; ++b) {
+                const uint32_t m = __ballot_sync(0xffffffffu, (tw >> b) & 1u);
+                if (lane == b) mine = __popc(m);
+            }
+            if (mine) atomicAdd(&s_cum[w * 32 + lane], mine);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchDesc *__restrict__ descs,
+                                                             const int64_t *__restrict__ item_begin, int S,
+                                                             int64_t total_items, BatchHeader *hdr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared sh;
+    const int tid = threadIdx.x;
+    unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);        // [512]
+    uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + 512 * 8);                     // [kMaxWB][256]
+    uint32_t *s_ref = s_tw + kMaxWB * kThreads;                                         // [kChunk * kMaxWB]
+    uint32_t *s_cum = s_ref + kChunk * kMaxWB;                                          // [kMaxWB * 32]
+    const uint64_t round = *((volatile unsigned long long *)&hdr->round);
+    if (tid == 0) sh.scenario = -1;
+    __syncthreads();
+    while (true) {
+        if (tid == 0) sh.item = (long long)atomicAdd(&hdr->next_item, 1ull);
+        __syncthreads();
+        const long long item = sh.item;
+        if (item >= total_items) break;
+        // scenario of this item: last s with item_begin[s] <= item
+        if (tid == 0) {
+            int lo = 0, hi = S - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (item_begin[mid] <= item) lo = mid; else hi = mid - 1;
+            }
+            if (lo != sh.scenario) {
+                sh.scenario = lo;
+                sh.d = descs[lo];
+            }
+            sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0ull;
+        }
+        __syncthreads();
+        const BatchDesc &d = sh.d;
+        const int nthr = d.n * d.km1;
+        for (int i = tid; i < nthr; i += kThreads) s_thr[i] = d.thr[i];
+        for (int j = tid; j < d.words_b * 32; j += kThreads) s_cum[j] = 0u;
+        __syncthreads();
+        const int64_t tile = item - item_begin[sh.scenario];
+        switch (d.words_b) {
+            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+        }
+        __syncthreads();
+        if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);
+        if (d.bitcnt && sh.cnt[0]) {
+            if (tid == 0) atomicAdd(d.lcount, sh.cnt[0]);
+            for (int j = tid; j < nthr; j += kThreads)
+                if (s_cum[j]) atomicAdd(&d.bitcnt[j], s_cum[j]);
+        }
+        __syncthreads();
+    }
+    // ---- the last block converts bit counts to per-state counts and re-arms ----
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh.last = (atomicAdd(&hdr->blocks_done, 1u) == gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (!sh.last) return;
+    __threadfence();
+    for (int s = 0; s < S; ++s) {
+        const BatchDesc &d = descs[s];
+        if (!d.bitcnt) continue;
+        const unsigned long long F = *((volatile unsigned long long *)d.lcount);
+        if (F) {
+            for (int i = tid; i < d.n; i += kThreads) {
+                long long prev = (long long)F;
+                for (int k = 1; k <= d.km1; ++k) {
+                    const long long cum = (long long)((volatile uint32_t *)d.bitcnt)[i * d.km1 + (k - 1)];
+                    const long long delta = prev - cum;
+                    if (delta) atomicAdd(&d.grad_counts[(size_t)i * d.K + (k - 1)], (unsigned long long)delta);
+                    prev = cum;
+                }
+                if (prev) atomicAdd(&d.grad_counts[(size_t)i * d.K + d.km1], (unsigned long long)prev);
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < d.n * d.km1; j += kThreads) d.bitcnt[j] = 0u;
+        if (tid == 0) *d.lcount = 0ull;
+    }
+    if (tid == 0) {
+        hdr->next_item = 0ull;
+        hdr->blocks_done = 0u;
+        hdr->round = round + 1ull;
+    }
+}
+
+}  // namespace
+
+size_t batch_kernel_smem() {
+    return 512 * 8 + sizeof(uint32_t) * ((size_t)kMaxWB * kThreads + (size_t)kChunk * kMaxWB + (size_t)kMaxWB * 32);
+}
+
+int batch_max_words() { return kMaxWB; }
+
+cudaError_t batch_max_grid(int *blocks_per_sm) {
+    const size_t smem = batch_kernel_smem();
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, kThreads, smem);
+}
+
+// The shared-memory attribute is set by batch_max_grid() (called when a batch
+// is prepared), so a launch issues nothing but the kernel and can be captured.
+cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
+                         BatchHeader *hdr, int grid, cudaStream_t s) {
+    const size_t smem = batch_kernel_smem();
+    if (grid <= 0 || total_items <= 0) return cudaSuccess;
+    batch_kernel<<<grid, kThreads, smem, s>>>(descs, item_begin, S, total_items, hdr);
+    return cudaGetLastError();
+}
+
+}  // namespace rsr

@@ -18,6 +18,8 @@
 // Fused in the same pass: Philox sampling (or a read of given states), the
 // label write, the three counts, and the per-bit counts of I^L samples that the
 // score-function gradient needs.  A persistent grid walks 256-sample tiles.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "rsr_internal.cuh"
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const Classi
     const int lane = tid & 31;
     const int nthr = p.n * p.km1;
     unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);
-    uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + ((size_t)nthr * 8 + 15) / 16 * 16);
+    uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + (size_t)kMaxKenc * 8);
     uint32_t *s_ref = s_tw + WB * kThreads;
     uint32_t *s_cum = s_ref + kChunk * WB;  // per thermometer bit: # I^L samples with the bit set
     __shared__ unsigned long long s_cnt[3];
@@ -242,15 +244,24 @@ __global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const Classi
 
 template <int WB>
 cudaError_t launch_wb(const ClassifyParams &p, cudaStream_t s) {
-    const size_t smem = ((size_t)p.n * p.km1 * 8 + 15) / 16 * 16 +
+    // dynamic shared memory for the largest threshold table; the attribute and
+    // the occupancy are queried once per device so that launches made during
+    // stream capture issue nothing but the kernel
+    const size_t smem = (size_t)kMaxKenc * 8 +
                         sizeof(uint32_t) * ((size_t)WB * kThreads + (size_t)kChunk * WB + (size_t)WB * 32);
-    cudaError_t e = cudaFuncSetAttribute(classify_popc_kernel<WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    static int occ_cache[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_popc_kernel<WB>, kThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
+    int occ = (dev >= 0 && dev < 64) ? occ_cache[dev] : 0;
+    if (occ == 0) {
+        e = cudaFuncSetAttribute(classify_popc_kernel<WB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_popc_kernel<WB>, kThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+        if (dev >= 0 && dev < 64) occ_cache[dev] = occ;
+    }
     const int64_t ntiles = (p.N + kThreads - 1) / kThreads;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)device_sm_count() * occ);
     if (grid <= 0) return cudaSuccess;

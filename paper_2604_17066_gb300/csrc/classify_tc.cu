@@ -31,6 +31,8 @@
 // sentinel that walks through the same rings, so every barrier phase stays
 // consistent.  Every wait is bounded; on timeout the kernel records
 // RSR_ERR_TIMEOUT in the workspace header, frees its TMEM and returns.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -657,12 +659,20 @@ cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded
 
 cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s) {
     if (p.tc_kpad > tc_max_kpad() || p.tc_kpad % 32 != 0) return cudaErrorNotSupported;
+    // the largest plan for the widest supported row, so the attribute is set once per device
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(classify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
     const TcSmem plan = tc_smem_plan(p.tc_kpad, p.n * p.km1, kMaxStages);
     if (plan.nstages < 2) return cudaErrorNotSupported;
     // at least 120 KB so that two CTAs never share an SM (each takes all 512 TMEM columns)
     const size_t smem = plan.total > 122880u ? plan.total : 122880u;
-    cudaError_t e = cudaFuncSetAttribute(classify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int64_t nblocks = (p.N + kRows - 1) / kRows;
     const int64_t grid = std::min<int64_t>(nblocks, (int64_t)device_sm_count());
     if (grid <= 0) return cudaSuccess;

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "rsr.h"
+#include "rsr_batch.h"
 #include "rsr_internal.cuh"
 #include "rsr_launch.h"
 
@@ -57,6 +58,15 @@ struct Prepared {
 
 std::mutex g_mu;
 std::unordered_map<const void *, Prepared> g_prepared;
+std::unordered_map<uint64_t, int> g_tuned;  // rsr_autotune decisions for RSR_PATH_AUTO
+
+// Problems that share n, K, density and a reference-count bucket (powers of 2) share a decision.
+uint64_t tune_key(const rsr_problem *p) {
+    int64_t R = p->R_L + p->R_U;
+    int bucket = 0;
+    while ((int64_t(1) << bucket) < R) ++bucket;
+    return ((uint64_t)p->n << 32) ^ ((uint64_t)p->K << 24) ^ ((uint64_t)bucket << 8) ^ (uint64_t)(p->flags & 1u);
+}
 
 int current_device() {
     int d = 0;
@@ -160,6 +170,11 @@ ClassifyParams make_params(const rsr_problem *p, const WsLayout &L, void *ws) {
 // sets are large enough to keep 128x128 MMA tiles busy.
 int choose_path(const rsr_problem *p) {
     if (p->path != RSR_PATH_AUTO) return p->path;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        auto it = g_tuned.find(tune_key(p));
+        if (it != g_tuned.end()) return it->second;
+    }
     const WsLayout L = layout_of(p);
     if (tc_supported() && L.tc_kpad <= tc_max_kpad() && (p->R_L + p->R_U) >= 8192 && (p->flags & RSR_FLAG_DENSE))
         return RSR_PATH_TC;
@@ -363,5 +378,365 @@ const char *rsr_status_string(int status) {
 }
 
 const char *rsr_last_cuda_error(void) { return g_last_cuda_error.c_str(); }
+
+}  // extern "C"
+
+// ============================================================================
+// Batched launch (many scenarios, one persistent kernel) and autotuning.
+// ============================================================================
+namespace rsr {
+namespace {
+
+struct BatchLayout {
+    size_t off_descs = 0, off_begin = 0, off_tune = 0, total = 0;
+    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_bit, off_lc, off_tgrad;
+    std::vector<int> words_b;
+};
+
+BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
+    BatchLayout B;
+    size_t off = align256(sizeof(BatchHeader));
+    B.off_descs = off;
+    off = align256(off + sizeof(BatchDesc) * (size_t)S);
+    B.off_begin = off;
+    off = align256(off + sizeof(int64_t) * (size_t)(S + 1));
+    B.off_tune = off;  // tuning scratch: counts3 per scenario
+    off = align256(off + sizeof(int64_t) * 3 * (size_t)S);
+    for (int s = 0; s < S; ++s) {
+        const rsr_problem &p = probs[s];
+        const int km1 = p.K - 1;
+        const int wb = popc_word_bucket((p.n * km1 + 31) / 32);
+        B.words_b.push_back(wb);
+        B.off_hdr.push_back(off);
+        off = align256(off + sizeof(WsHeader));
+        B.off_thr.push_back(off);
+        off = align256(off + 8 * (size_t)p.n * km1);
+        B.off_pL.push_back(off);
+        off = align256(off + 4 * (size_t)p.R_L * wb);
+        B.off_pU.push_back(off);
+        off = align256(off + 4 * (size_t)p.R_U * wb);
+        B.off_bit.push_back(off);
+        off = align256(off + 4 * (size_t)p.n * km1);
+        B.off_lc.push_back(off);
+        off = align256(off + 8);
+        B.off_tgrad.push_back(off);  // tuning scratch: gradient counts
+        off = align256(off + 8 * (size_t)p.n * p.K);
+    }
+    B.total = off;
+    return B;
+}
+
+struct BatchPrepared {
+    uint64_t fingerprint;
+    int S;
+    int64_t total_items;
+    int grid;
+    int device;
+    std::vector<BatchDesc> descs;     // the caller's outputs
+    std::vector<int64_t> begin;
+};
+std::unordered_map<const void *, BatchPrepared> g_batches;
+
+uint64_t batch_fingerprint(const rsr_problem *probs, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+                           const int64_t *Ns, uint8_t *const *labels, int64_t *counts3xS,
+                           int64_t *const *grad_counts) {
+    uint64_t h = 1469598103934665603ull;
+    for (int s = 0; s < S; ++s) {
+        const rsr_problem &p = probs[s];
+        h = fnv1a(&p.n, sizeof(p.n), h);
+        h = fnv1a(&p.K, sizeof(p.K), h);
+        h = fnv1a(&p.R_L, sizeof(p.R_L), h);
+        h = fnv1a(&p.R_U, sizeof(p.R_U), h);
+        h = fnv1a(&p.ref_L, sizeof(p.ref_L), h);
+        h = fnv1a(&p.ref_U, sizeof(p.ref_U), h);
+        h = fnv1a(p.pmf, sizeof(double) * (size_t)p.n * p.K, h);
+        h = fnv1a(&seeds[s], 8, h);
+        h = fnv1a(&offsets[s], 8, h);
+        h = fnv1a(&Ns[s], 8, h);
+        const void *lp = labels ? (const void *)labels[s] : nullptr;
+        const void *gp = grad_counts ? (const void *)grad_counts[s] : nullptr;
+        h = fnv1a(&lp, sizeof(lp), h);
+        h = fnv1a(&gp, sizeof(gp), h);
+    }
+    h = fnv1a(&counts3xS, sizeof(counts3xS), h);
+    return h;
+}
+
+int validate_batch(const rsr_problem *probs, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+                   const int64_t *Ns, int64_t *counts3xS) {
+    if (!probs || S < 1 || !seeds || !offsets || !Ns || !counts3xS) return RSR_ERR_INVALID_ARG;
+    for (int s = 0; s < S; ++s) {
+        int st = validate(&probs[s]);
+        if (st != RSR_OK) return st;
+        if (Ns[s] < 0) return RSR_ERR_INVALID_ARG;
+        if (popc_word_bucket((probs[s].n * (probs[s].K - 1) + 31) / 32) > batch_max_words()) return RSR_ERR_UNSUPPORTED;
+    }
+    return RSR_OK;
+}
+
+// Upload descriptors in the given scenario order (order[k] = scenario run k-th).
+int upload_schedule(void *ws, const BatchLayout &B, const std::vector<BatchDesc> &descs,
+                    const std::vector<int> &order, std::vector<int64_t> &begin, int64_t &total, cudaStream_t s) {
+    const int S = (int)descs.size();
+    std::vector<BatchDesc> ordered(S);
+    begin.assign(S + 1, 0);
+    total = 0;
+    for (int k = 0; k < S; ++k) {
+        ordered[k] = descs[order[k]];
+        begin[k] = total;
+        total += (ordered[k].N + 255) / 256;
+    }
+    begin[S] = total;
+    char *base = static_cast<char *>(ws);
+    RSR_CUDA(cudaMemcpyAsync(base + B.off_descs, ordered.data(), sizeof(BatchDesc) * S, cudaMemcpyHostToDevice, s));
+    RSR_CUDA(cudaMemcpyAsync(base + B.off_begin, begin.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    return RSR_OK;
+}
+
+std::vector<int> lpt_order(const std::vector<BatchDesc> &d) {
+    // longest first by a work proxy: samples x words x log(2 + references)
+    std::vector<int> order(d.size());
+    std::vector<double> cost(d.size());
+    for (size_t s = 0; s < d.size(); ++s) {
+        order[s] = (int)s;
+        cost[s] = (double)d[s].N * (double)d[s].words_b * std::log(2.0 + (double)(d[s].R_L + d[s].R_U));
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    return order;
+}
+
+}  // namespace
+}  // namespace rsr
+
+extern "C" {
+
+size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S) {
+    if (!problems || S < 1) return 0;
+    for (int s = 0; s < S; ++s)
+        if (validate(&problems[s]) != RSR_OK) return 0;
+    return batch_layout(problems, S).total;
+}
+
+int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+                      const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
+                      int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream) {
+    int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
+    if (st != RSR_OK) return st;
+    const BatchLayout B = batch_layout(problems, S);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < B.total) return RSR_ERR_WORKSPACE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(ws);
+    RSR_CUDA(cudaMemsetAsync(base, 0, B.total, s));
+    std::vector<BatchDesc> descs(S);
+    for (int k = 0; k < S; ++k) {
+        const rsr_problem &p = problems[k];
+        const int km1 = p.K - 1;
+        std::vector<unsigned long long> T;
+        host_thresholds(&p, T);
+        RSR_CUDA(cudaMemcpyAsync(base + B.off_thr[k], T.data(), T.size() * 8, cudaMemcpyHostToDevice, s));
+        uint32_t *pL = reinterpret_cast<uint32_t *>(base + B.off_pL[k]);
+        uint32_t *pU = reinterpret_cast<uint32_t *>(base + B.off_pU[k]);
+        RSR_CUDA(launch_encode_popc(p.ref_L, p.R_L, p.n, km1, B.words_b[k], true, pL, s));
+        RSR_CUDA(launch_encode_popc(p.ref_U, p.R_U, p.n, km1, B.words_b[k], false, pU, s));
+        WsHeader *hs = reinterpret_cast<WsHeader *>(base + B.off_hdr[k]);
+        RSR_CUDA(launch_overlap(pL, p.R_L, pU, p.R_U, B.words_b[k], hs, s));
+        BatchDesc &d = descs[k];
+        d.n = p.n;
+        d.K = p.K;
+        d.km1 = km1;
+        d.words_b = B.words_b[k];
+        d.R_L = p.R_L;
+        d.R_U = p.R_U;
+        d.seed = seeds[k];
+        d.offset = offsets[k];
+        d.N = Ns[k];
+        d.thr = reinterpret_cast<const unsigned long long *>(base + B.off_thr[k]);
+        d.popc_L = pL;
+        d.popc_U = pU;
+        d.overlap = &hs->overlap;
+        d.labels = labels_or_null ? labels_or_null[k] : nullptr;
+        d.counts3 = reinterpret_cast<unsigned long long *>(counts3xS + 3 * (size_t)k);
+        d.grad_counts = grad_counts_or_null ? reinterpret_cast<unsigned long long *>(grad_counts_or_null[k]) : nullptr;
+        d.bitcnt = d.grad_counts ? reinterpret_cast<uint32_t *>(base + B.off_bit[k]) : nullptr;
+        d.lcount = reinterpret_cast<unsigned long long *>(base + B.off_lc[k]);
+    }
+    std::vector<int64_t> begin;
+    int64_t total = 0;
+    if ((st = upload_schedule(ws, B, descs, lpt_order(descs), begin, total, s)) != RSR_OK) return st;
+    int occ = 0;
+    RSR_CUDA(batch_max_grid(&occ));
+    if (occ < 1) occ = 1;
+    BatchPrepared bp;
+    bp.fingerprint = batch_fingerprint(problems, S, seeds, offsets, Ns, labels_or_null, counts3xS, grad_counts_or_null);
+    bp.S = S;
+    bp.total_items = total;
+    bp.grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)device_sm_count() * occ);
+    bp.device = current_device();
+    bp.descs = descs;
+    bp.begin = begin;
+    std::lock_guard<std::mutex> g(g_mu);
+    g_batches[ws] = bp;
+    return RSR_OK;
+}
+
+int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+              const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
+              int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream) {
+    int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
+    if (st != RSR_OK) return st;
+    const BatchLayout B = batch_layout(problems, S);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < B.total) return RSR_ERR_WORKSPACE;
+    BatchPrepared bp;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        auto it = g_batches.find(ws);
+        if (it == g_batches.end()) return RSR_ERR_NOT_PREPARED;
+        bp = it->second;
+    }
+    if (bp.fingerprint != batch_fingerprint(problems, S, seeds, offsets, Ns, labels_or_null, counts3xS,
+                                            grad_counts_or_null) ||
+        bp.device != current_device())
+        return RSR_ERR_NOT_PREPARED;
+    char *base = static_cast<char *>(ws);
+    RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
+                          reinterpret_cast<const int64_t *>(base + B.off_begin), S, bp.total_items,
+                          reinterpret_cast<BatchHeader *>(base), bp.grid, reinterpret_cast<cudaStream_t>(stream)));
+    return RSR_OK;
+}
+
+int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+                       const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
+                       int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream,
+                       int32_t *chosen) {
+    int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
+    if (st != RSR_OK) return st;
+    const BatchLayout B = batch_layout(problems, S);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < B.total) return RSR_ERR_WORKSPACE;
+    BatchPrepared bp;
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        auto it = g_batches.find(ws);
+        if (it == g_batches.end()) return RSR_ERR_NOT_PREPARED;
+        bp = it->second;
+    }
+    if (bp.fingerprint != batch_fingerprint(problems, S, seeds, offsets, Ns, labels_or_null, counts3xS,
+                                            grad_counts_or_null))
+        return RSR_ERR_NOT_PREPARED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    char *base = static_cast<char *>(ws);
+    // tuning runs write into the workspace's own scratch, never the caller's outputs
+    std::vector<BatchDesc> scratch = bp.descs;
+    for (int k = 0; k < S; ++k) {
+        scratch[k].labels = nullptr;
+        scratch[k].counts3 = reinterpret_cast<unsigned long long *>(base + B.off_tune + 24 * (size_t)k);
+        if (scratch[k].grad_counts)
+            scratch[k].grad_counts = reinterpret_cast<unsigned long long *>(base + B.off_tgrad[k]);
+    }
+    int occ = 0;
+    RSR_CUDA(batch_max_grid(&occ));
+    if (occ < 1) occ = 1;
+    const int sms = device_sm_count();
+    std::vector<int> natural(S);
+    for (int k = 0; k < S; ++k) natural[k] = k;
+    const std::vector<int> lpt = lpt_order(bp.descs);
+    cudaEvent_t e0, e1;
+    RSR_CUDA(cudaEventCreate(&e0));
+    RSR_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_grid = bp.grid, best_order = 0;
+    for (int ord = 0; ord < 2; ++ord) {
+        std::vector<int64_t> begin;
+        int64_t total = 0;
+        if ((st = upload_schedule(ws, B, scratch, ord ? natural : lpt, begin, total, s)) != RSR_OK) return st;
+        for (int bps = 1; bps <= occ; bps *= 2) {
+            const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)sms * bps);
+            float ms_sum = 0.0f;
+            for (int rep = 0; rep < 3; ++rep) {
+                RSR_CUDA(cudaEventRecord(e0, s));
+                RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
+                                      reinterpret_cast<const int64_t *>(base + B.off_begin), S, total,
+                                      reinterpret_cast<BatchHeader *>(base), grid, s));
+                RSR_CUDA(cudaEventRecord(e1, s));
+                RSR_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.0f;
+                RSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) ms_sum += ms;
+            }
+            if (ms_sum < best) {
+                best = ms_sum;
+                best_grid = grid;
+                best_order = ord;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // restore the caller's descriptors in the chosen order, reset the round counter
+    std::vector<int64_t> begin;
+    int64_t total = 0;
+    if ((st = upload_schedule(ws, B, bp.descs, best_order ? natural : lpt, begin, total, s)) != RSR_OK) return st;
+    RSR_CUDA(cudaMemsetAsync(base, 0, sizeof(BatchHeader), s));
+    for (int k = 0; k < S; ++k) {
+        RSR_CUDA(cudaMemsetAsync(base + B.off_lc[k], 0, 8, s));
+        RSR_CUDA(cudaMemsetAsync(base + B.off_bit[k], 0, 4 * (size_t)problems[k].n * (problems[k].K - 1), s));
+    }
+    RSR_CUDA(cudaStreamSynchronize(s));
+    if (chosen) {
+        chosen[0] = best_grid;
+        chosen[1] = best_order;
+    }
+    std::lock_guard<std::mutex> g(g_mu);
+    BatchPrepared &ref = g_batches[ws];
+    ref.grid = best_grid;
+    ref.total_items = total;
+    ref.begin = begin;
+    return RSR_OK;
+}
+
+int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream, int32_t *chosen_path) {
+    int st = validate(problem);
+    if (st != RSR_OK) return st;
+    const WsLayout L = layout_of(problem);
+    if ((st = check_ws(L, ws, ws_bytes)) != RSR_OK) return st;
+    if ((st = check_prepared(problem, ws)) != RSR_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // time both classifiers on the same slice; counts go to the header's spare words
+    ClassifyParams c = make_params(problem, L, ws);
+    c.N = 1 << 16;
+    c.seed = 0x5EEDull;
+    c.offset = 0;
+    c.counts3 = reinterpret_cast<unsigned long long *>(&reinterpret_cast<WsHeader *>(ws)->reserved[2]);
+    cudaEvent_t e0, e1;
+    RSR_CUDA(cudaEventCreate(&e0));
+    RSR_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_path = RSR_PATH_POPC;
+    const bool tc_ok = tc_supported() && L.tc_kpad <= tc_max_kpad();
+    for (int path = RSR_PATH_POPC; path <= RSR_PATH_TC; ++path) {
+        if (path == RSR_PATH_TC && !tc_ok) continue;
+        float sum = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            RSR_CUDA(cudaEventRecord(e0, s));
+            RSR_CUDA(path == RSR_PATH_TC ? launch_classify_tc(c, s) : launch_classify_popc(c, s));
+            RSR_CUDA(cudaEventRecord(e1, s));
+            RSR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            RSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) sum += ms;
+        }
+        if (sum < best) {
+            best = sum;
+            best_path = path;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_tuned[tune_key(problem)] = best_path;
+    }
+    if (chosen_path) *chosen_path = best_path;
+    return RSR_OK;
+}
 
 }  // extern "C"

@@ -31,7 +31,7 @@ def lib():
 
 def test_header_declares_the_boundary():
     names = set(_header_entry_points())
-    for required in ("rsr_classify", "rsr_estimate", "rsr_grad", "rsr_prepare",
+    for required in ("rsr_classify", "rsr_estimate", "rsr_grad", "rsr_batch", "rsr_prepare",
                      "rsr_workspace_size", "rsr_sample", "rsr_status_string"):
         assert required in names, required
 
