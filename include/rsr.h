@@ -227,6 +227,30 @@ RSR_API int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uin
 RSR_API int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream,
                          int32_t *chosen_path);
 
+/*
+ * Classification for callers that cannot allocate device memory: for example
+ * a plugin inside a host application that owns all device memory through its
+ * own pool and does not let libraries allocate, a real-time loop whose
+ * allocations are fixed at start-up, or a foreign-language caller that reaches
+ * this library only through the C ABI and has no device allocator.  The
+ * paper has no counterpart: this is a deployment variant of rsr_prepare +
+ * rsr_classify on RSR_PATH_POPC (same arguments, same results; problem->path
+ * is ignored, problem->flags honoured), not a step of the method.
+ * The workspace is a library-owned device array of RSR_STATIC_SCRATCH_BYTES
+ * (4 MiB) that every GPU loading librsr holds until the process exits.
+ * Problems whose header + thresholds + bit-packed references exceed it are
+ * rejected with RSR_ERR_WORKSPACE before any GPU work.  The first call on a
+ * device looks up the array's device address once (cudaGetSymbolAddress, with
+ * that device current), so make that first call before any stream capture.
+ * Every call shares the array and re-initialises what it needs; calls whose
+ * GPU work overlaps (other streams, other host threads) race on it, so
+ * serialise them.  The library itself calls no allocation routine here.
+ */
+#define RSR_STATIC_SCRATCH_BYTES (4u << 20)
+RSR_API int rsr_classify_static(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N,
+                                const uint8_t *samples_or_null, uint8_t *labels_or_null, int64_t *counts3,
+                                int64_t *grad_counts_or_null, rsr_stream_t stream);
+
 /* Message for a status code (static storage). */
 RSR_API const char *rsr_status_string(int status);
 

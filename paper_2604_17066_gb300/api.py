@@ -275,3 +275,15 @@ def rsr_autotune(problem: Problem, ws: torch.Tensor, stream=None) -> int:
     check(_lib.load().rsr_autotune(ctypes.byref(s), _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(chosen)),
           "rsr_autotune")
     return int(chosen.value)
+
+
+def rsr_classify_static(problem: Problem, seed: int, offset: int, N: int, counts3: torch.Tensor,
+                        samples: Optional[torch.Tensor] = None, labels: Optional[torch.Tensor] = None,
+                        grad_counts: Optional[torch.Tensor] = None, stream=None) -> None:
+    """rsr_classify_static: classification whose workspace is a 4 MiB device
+    array owned by the library, for callers that cannot allocate device
+    memory (see include/rsr.h)."""
+    s = problem.struct()
+    check(_lib.load().rsr_classify_static(ctypes.byref(s), int(seed), int(offset), int(N), _ptr(samples),
+                                          _ptr(labels), _ptr(counts3), _ptr(grad_counts), _stream(stream)),
+          "rsr_classify_static")
