@@ -153,6 +153,7 @@ def main():
     ap.add_argument("--workload", default="c3", choices=["c3", "c2"])
     ap.add_argument("--ref-samples", type=int, default=8000)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--samples", type=int, default=0, help="override samples per GPU (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -173,6 +174,9 @@ def main():
     rsr_build.build()
 
     prob, N, wname = _workload(args.workload)
+    if args.samples > 0:
+        N = args.samples
+        wname += "_N%d" % N
     path = rsr.RSR_PATH_TC if args.workload == "c3" else rsr.RSR_PATH_POPC
     P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=(args.workload == "c3"))
     stream = torch.cuda.current_stream()

@@ -659,20 +659,30 @@ cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded
 
 cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s) {
     if (p.tc_kpad > tc_max_kpad() || p.tc_kpad % 32 != 0) return cudaErrorNotSupported;
-    // the largest plan for the widest supported row, so the attribute is set once per device
-    static bool attr_set[64] = {false};
+    // dynamic shared memory up to the opt-in limit minus the kernel's static
+    // shared memory; set once per device so that captured launches issue nothing else
+    static size_t max_dyn[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(classify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (max_dyn[dev] == 0) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, classify_tc_kernel);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        int optin = 0;
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        const size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        e = cudaFuncSetAttribute(classify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        if (e != cudaSuccess) return e;
+        max_dyn[dev] = lim;
     }
     const TcSmem plan = tc_smem_plan(p.tc_kpad, p.n * p.km1, kMaxStages);
     if (plan.nstages < 2) return cudaErrorNotSupported;
     // at least 120 KB so that two CTAs never share an SM (each takes all 512 TMEM columns)
     const size_t smem = plan.total > 122880u ? plan.total : 122880u;
+    if (smem > max_dyn[dev]) return cudaErrorNotSupported;
     const int64_t nblocks = (p.N + kRows - 1) / kRows;
     const int64_t grid = std::min<int64_t>(nblocks, (int64_t)device_sm_count());
     if (grid <= 0) return cudaSuccess;

@@ -27,6 +27,9 @@ namespace {
 thread_local std::string g_last_cuda_error;
 
 int cuda_fail(cudaError_t e, const char *where) {
+    // consume the runtime's last-error state so that a later, unrelated
+    // cudaGetLastError() does not report this failure again
+    (void)cudaGetLastError();
     char buf[256];
     snprintf(buf, sizeof(buf), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
     g_last_cuda_error = buf;
