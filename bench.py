@@ -103,6 +103,59 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def bench_batch(rsr, torch, reps=5):
+    """256 hazard scenarios (n = 50..300 edges, 1e2..1e5 references, N = 2e5 each):
+    one persistent launch replayed from a CUDA graph vs the per-scenario path
+    (one rsr_classify per scenario on prepared workspaces)."""
+    import workloads.large as L
+    probs = L.c5_batch()
+    S, N = len(probs), 200_000
+    P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_POPC) for p in probs]
+    seeds, offsets, Ns = [1000 + s for s in range(S)], [0] * S, [N] * S
+    t0 = time.perf_counter()
+    b = rsr.Batch(P, seeds, offsets, Ns, labels=True, grad=True)
+    grid, order = rsr.rsr_batch_autotune(b)
+    prep_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        rsr.rsr_batch(b, stream=torch.cuda.current_stream())
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(reps):
+        g.replay()
+    ev[1].record()
+    torch.cuda.synchronize()
+    batched_ms = ev[0].elapsed_time(ev[1]) / reps
+    # per-scenario path
+    sessions = [rsr.Session(p) for p in P]
+    cur = torch.cuda.current_stream()
+    cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+    lab = torch.empty(N, dtype=torch.uint8, device="cuda")
+    grads = [torch.zeros(p.n * p.K, dtype=torch.int64, device="cuda") for p in P]
+
+    def plain(r):
+        for s_, (p, se) in enumerate(zip(P, sessions)):
+            rsr.rsr_classify(p, seeds[s_], offsets[s_] + r * N, N, se.ws, cnt, None, lab, grads[s_], None, cur)
+
+    plain(0)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for r in range(reps):
+        plain(1 + r)
+    ev[1].record()
+    torch.cuda.synchronize()
+    plain_ms = ev[0].elapsed_time(ev[1]) / reps
+    R = [p.R_L + p.R_U for p in P]
+    return {"workload": "c5_256_scenarios_N2e5", "scenarios": S, "refs_total": int(sum(R)),
+            "batched_ms": batched_ms, "per_scenario_ms": plain_ms, "speedup": plain_ms / batched_ms,
+            "samples_per_s": S * N / (batched_ms / 1000.0), "autotune_grid": grid,
+            "autotune_order": "longest-first" if order == 0 else "as-given", "prepare_s": prep_s}
+
+
 def cpu_baseline(prob, seed, n_sample, offset=0):
     """The oracle as it stands, single-threaded, on a bounded sample."""
     from oracle import oracle as O
@@ -153,6 +206,7 @@ def main():
     ap.add_argument("--workload", default="c3", choices=["c3", "c2"])
     ap.add_argument("--ref-samples", type=int, default=8000)
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-scenario batched comparison")
     ap.add_argument("--samples", type=int, default=0, help="override samples per GPU (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -298,6 +352,8 @@ def main():
             del s2
         extras["prepare_ms"] = prep_ms
         extras["overlap_pairs"] = bool(overlap)
+        if args.workload == "c3" and not args.no_batch:
+            extras["batch_c5"] = bench_batch(rsr, torch)
 
     # end to end through the public API: pmf -> thresholds (H2D), classify, results (D2H)
     e2e = None

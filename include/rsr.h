@@ -67,6 +67,11 @@ typedef enum rsr_path {
 
 /* rsr_problem.flags */
 #define RSR_FLAG_DENSE 1u  /* test every sample against every reference (no early exit) */
+/* Failure-detection test hook (tensor-core path only): the reference producer
+ * never starts, so the kernel's bounded waits run out after about 10 ms; the
+ * kernel records RSR_ERR_TIMEOUT in the workspace header (rsr_workspace_status),
+ * frees its tensor memory and returns, leaving the context usable. */
+#define RSR_FLAG_TEST_STALL 0x100u
 
 /*
  * One classification problem for a threshold m' (Sec. 3.2-3.3).

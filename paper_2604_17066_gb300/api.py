@@ -50,6 +50,7 @@ class Problem:
         self.ref_U = torch.as_tensor(np.asarray(ref_U, dtype=np.uint8).reshape(-1, n)).to(dev).contiguous()
         self.path = int(path)
         self.dense = bool(dense)
+        self.extra_flags = 0   # further RSR_FLAG_* bits (e.g. the failure-detection test hook)
 
     @property
     def n(self) -> int:
@@ -75,7 +76,7 @@ class Problem:
         s.ref_L = self.ref_L.data_ptr() if self.R_L else None
         s.ref_U = self.ref_U.data_ptr() if self.R_U else None
         s.path = self.path
-        s.flags = RSR_FLAG_DENSE if self.dense else 0
+        s.flags = (RSR_FLAG_DENSE if self.dense else 0) | int(self.extra_flags)
         return s
 
 

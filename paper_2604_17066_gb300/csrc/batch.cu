@@ -83,36 +83,38 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
 
     const bool overlap = *((volatile const int32_t *)d.overlap) != 0;
     bool mL = false, mU = false, done = !valid;
-    for (int phase = 0; phase < 2; ++phase) {
-        const bool upper = (phase == 0) != overlap;
+    const int64_t nU = (d.R_U + kChunk - 1) / kChunk, nL = (d.R_L + kChunk - 1) / kChunk;
+    for (int64_t step = 0; step < nU + nL; ++step) {
+        if (__syncthreads_and(done)) break;
+        bool upper;
+        int64_t ci;
+        chunk_at(step, nU, nL, overlap, &upper, &ci);
         const uint32_t *refs = upper ? d.popc_U : d.popc_L;
         const int64_t R = upper ? d.R_U : d.R_L;
-        for (int64_t base = 0; base < R; base += kChunk) {
-            if (__syncthreads_and(done)) break;
-            const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
-            for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
-            __syncthreads();
-            if (!done) {
-                bool m = false;
-                if (upper) {
-                    for (int r = 0; r < cnt; ++r) {
-                        uint32_t acc = 0;
+        const int64_t base = ci * kChunk;
+        const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
+        for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+        __syncthreads();
+        if (!done) {
+            bool m = false;
+            if (upper) {
+                for (int r = 0; r < cnt; ++r) {
+                    uint32_t acc = 0;
 #pragma unroll
-                        for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
-                        if (acc == 0u) { m = true; break; }
-                    }
-                } else {
-                    for (int r = 0; r < cnt; ++r) {
-                        uint32_t acc = 0;
+                    for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
+                    if (acc == 0u) { m = true; break; }
+                }
+            } else {
+                for (int r = 0; r < cnt; ++r) {
+                    uint32_t acc = 0;
 #pragma unroll
-                        for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
-                        if (acc == 0u) { m = true; break; }
-                    }
+                    for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
+                    if (acc == 0u) { m = true; break; }
                 }
-                if (m) {
-                    if (upper) mU = true; else mL = true;
-                    done = true;
-                }
+            }
+            if (m) {
+                if (upper) mU = true; else mL = true;
+                done = true;
             }
         }
     }

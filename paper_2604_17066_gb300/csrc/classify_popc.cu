@@ -81,9 +81,8 @@ __global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const Classi
     if (tid == 0) s_exec = 0ull;
     __syncthreads();
 
-    // Without overlapping reference pairs a sample matches at most one set, so
-    // the likelier set (upper) goes first and any match is final.  With
-    // overlaps, every lower reference is tried first (Algorithm 1 precedence).
+    // Set order: see chunk_at() (alternating without overlapping pairs, lower
+    // first with them, as Algorithm 1's precedence requires).
     const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     unsigned long long my_cnt0 = 0, my_cnt1 = 0, my_cnt2 = 0, my_exec = 0;
@@ -120,66 +119,70 @@ __global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const Classi
         // ---- classify ---------------------------------------------------------
         bool mL = false, mU = false;
         bool done = !valid;
-        for (int phase = 0; phase < 2; ++phase) {
-            const bool upper = (phase == 0) != overlap;
+        const int64_t nU = (p.R_U + kChunk - 1) / kChunk, nL = (p.R_L + kChunk - 1) / kChunk;
+        for (int64_t step = 0; step < nU + nL; ++step) {
+            const bool all_done = __syncthreads_and(done);  // also: previous chunk consumed
+            if (all_done && !p.dense) break;
+            bool upper;
+            int64_t ci;
+            chunk_at(step, nU, nL, overlap, &upper, &ci);
             const uint32_t *refs = upper ? p.popc_U : p.popc_L;
             const int64_t R = upper ? p.R_U : p.R_L;
-            for (int64_t base = 0; base < R; base += kChunk) {
-                const bool all_done = __syncthreads_and(done);  // also: previous chunk consumed
-                if (all_done && !p.dense) break;
-                const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
-                const uint4 *src = reinterpret_cast<const uint4 *>(refs + base * WB);
-                uint4 *dst = reinterpret_cast<uint4 *>(s_ref);
-                if ((WB & 3) == 0) {
-                    for (int idx = tid; idx < cnt * WB / 4; idx += kThreads) dst[idx] = src[idx];
-                } else {
-                    for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
-                }
-                __syncthreads();
-                if (p.dense) {
-                    bool m = false;
-                    if (valid) {
-                        if (upper) {
-                            for (int r = 0; r < cnt; ++r) {
-                                uint32_t acc = 0;
-#pragma unroll
-                                for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
-                                m |= (acc == 0u);
-                            }
-                        } else {
-                            for (int r = 0; r < cnt; ++r) {
-                                uint32_t acc = 0;
-#pragma unroll
-                                for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
-                                m |= (acc == 0u);
-                            }
-                        }
-                        my_exec += (unsigned long long)cnt;
-                    }
-                    if (upper) mU |= m; else mL |= m;
-                } else if (!done) {
-                    int r = 0;
-                    bool m = false;
+            const int64_t base = ci * kChunk;
+            const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
+            const uint4 *src = reinterpret_cast<const uint4 *>(refs + base * WB);
+            uint4 *dst = reinterpret_cast<uint4 *>(s_ref);
+            if ((WB & 3) == 0) {
+                for (int idx = tid; idx < cnt * WB / 4; idx += kThreads) dst[idx] = src[idx];
+            } else {
+                for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+            }
+            __syncthreads();
+            if (p.dense) {
+                bool m = false;
+                if (valid) {
                     if (upper) {
-                        for (; r < cnt; ++r) {
+                        for (int r = 0; r < cnt; ++r) {
                             uint32_t acc = 0;
 #pragma unroll
                             for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
-                            if (acc == 0u) { m = true; ++r; break; }
+                            m |= (acc == 0u);
                         }
                     } else {
-                        for (; r < cnt; ++r) {
+                        for (int r = 0; r < cnt; ++r) {
                             uint32_t acc = 0;
 #pragma unroll
                             for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
-                            if (acc == 0u) { m = true; ++r; break; }
+                            m |= (acc == 0u);
                         }
                     }
-                    my_exec += (unsigned long long)r;
-                    if (m) {
-                        if (upper) mU = true; else mL = true;
-                        done = true;
+                    my_exec += (unsigned long long)cnt;
+                }
+                if (upper) mU |= m; else mL |= m;
+            } else if (!done) {
+                int r = 0;
+                bool m = false;
+                if (upper) {
+                    for (; r < cnt; ++r) {
+                        uint32_t acc = 0;
+#pragma unroll
+                        for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
+                        if (acc == 0u) { m = true; ++r; break; }
                     }
+                } else {
+                    for (; r < cnt; ++r) {
+                        uint32_t acc = 0;
+#pragma unroll
+                        for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
+                        if (acc == 0u) { m = true; ++r; break; }
+                    }
+                }
+                my_exec += (unsigned long long)r;
+                // a match is final unless precedence can still overturn it: an upper match
+                // with overlapping pairs waits for the lower chunks, which come first then
+                if (m) {
+                    if (upper) mU = true; else mL = true;
+                    done = true;
                 }
             }
         }

@@ -50,6 +50,7 @@ constexpr int kMaxStages = 4;
 constexpr int kSmemLimit = 232448;   // 227 KB opt-in per CTA
 constexpr uint32_t kTmemCols = 512;  // 2 buffers x (2 A tiles x 128 columns)
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at the base clock
+constexpr long long kTestWaitCycles = 20000000ll; // ~10 ms, RSR_FLAG_TEST_STALL
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -80,7 +81,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 
 // Bounded wait: false on timeout or when another role already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                          int32_t *err) {
+                                          int32_t *err, long long budget = kWaitCycles) {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     uint32_t it = 0;
@@ -88,7 +89,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
         if (mbar_test(bar, parity)) return true;
         if ((++it & 255u) == 0u) {
             if (*abort_flag) return false;
-            if (clock64() - t0 > kWaitCycles) {
+            if (clock64() - t0 > budget) {
                 *abort_flag = 1;
                 atomicExch(err, RSR_ERR_TIMEOUT);
                 return false;
@@ -267,6 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
     uint32_t *sCum = reinterpret_cast<uint32_t *>(smem + plan.cum);
     volatile int *abort_flag = &ctl.abort_flag;
     int32_t *err = &p.hdr->error;
+    const long long budget = p.test_stall ? kTestWaitCycles : kWaitCycles;
 
     for (int i = tid; i < nthr; i += kThreads) sThr[i] = p.thr[i];
     for (int j = tid; j < kp; j += kThreads) sCum[j] = 0u;
@@ -295,12 +297,10 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
     const uint32_t tmem = ctl.tmem_base;
 
     const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
-    const bool upper_first = !overlap;
-    const int64_t tiles_first = ((upper_first ? p.R_U : p.R_L) + kRefTile - 1) / kRefTile;
-    const int64_t tiles_second = ((upper_first ? p.R_L : p.R_U) + kRefTile - 1) / kRefTile;
-    const int64_t T = tiles_first + tiles_second;
-    const uint8_t *src_first = upper_first ? p.tc_U : p.tc_L;
-    const uint8_t *src_second = upper_first ? p.tc_L : p.tc_U;
+    // tile order: chunk_at() (alternating without overlapping pairs, lower first with them)
+    const int64_t tiles_U = (p.R_U + kRefTile - 1) / kRefTile;
+    const int64_t tiles_L = (p.R_L + kRefTile - 1) / kRefTile;
+    const int64_t T = tiles_U + tiles_L;
     const uint32_t tile_bytes = (uint32_t)kRefTile * kp;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const int bias_cols = (p.kenc + 15) / 16;
@@ -368,17 +368,19 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
 
         // ---- 2. roles -----------------------------------------------------------
         if (warp == 0) {
-            if (lane == 0) {
+            if (lane == 0 && !p.test_stall) {
                 for (int64_t j = 0; j <= T; ++j) {
                     const bool stop = (j == T) || (!p.dense && *((volatile int *)&ctl.done));
-                    if (!mbar_wait(&ctl.empty[st_stage], st_phase ^ 1u, abort_flag, err)) break;
+                    if (!mbar_wait(&ctl.empty[st_stage], st_phase ^ 1u, abort_flag, err, budget)) break;
                     if (stop) {
                         ctl.stage_tile[st_stage] = -1;
                         mbar_arrive(&ctl.full[st_stage]);
                     } else {
                         ctl.stage_tile[st_stage] = (int)j;
-                        const uint8_t *src = (j < tiles_first) ? src_first + (size_t)j * tile_bytes
-                                                               : src_second + (size_t)(j - tiles_first) * tile_bytes;
+                        bool up;
+                        int64_t ti;
+                        chunk_at(j, tiles_U, tiles_L, overlap, &up, &ti);
+                        const uint8_t *src = (up ? p.tc_U : p.tc_L) + (size_t)ti * tile_bytes;
                         mbar_arrive_expect_tx(&ctl.full[st_stage], tile_bytes);
                         bulk_g2s(sStage + (size_t)st_stage * tile_bytes, src, tile_bytes, &ctl.full[st_stage]);
                     }
@@ -395,9 +397,9 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                 const uint32_t sbo = (uint32_t)kp * 8u;
                 unsigned long long issued = 0;
                 while (true) {
-                    if (!mbar_wait(&ctl.full[st_stage], st_phase, abort_flag, err)) break;
+                    if (!mbar_wait(&ctl.full[st_stage], st_phase, abort_flag, err, budget)) break;
                     const int j = ctl.stage_tile[st_stage];
-                    if (!mbar_wait(&ctl.tempty[acc_buf], acc_phase ^ 1u, abort_flag, err)) break;
+                    if (!mbar_wait(&ctl.tempty[acc_buf], acc_phase ^ 1u, abort_flag, err, budget)) break;
                     ctl.acc_tile[acc_buf] = j;
                     if (j < 0) {
                         mbar_arrive(&ctl.empty[st_stage]);
@@ -441,11 +443,13 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
             bool mL0 = false, mU0 = false, mL1 = false, mU1 = false;
             bool warp_resolved = false;
             while (true) {
-                if (!mbar_wait(&ctl.tfull[acc_buf], acc_phase, abort_flag, err)) break;
+                if (!mbar_wait(&ctl.tfull[acc_buf], acc_phase, abort_flag, err, budget)) break;
                 const int j = ctl.acc_tile[acc_buf];
                 if (j >= 0) {
                     tc_fence_after();
-                    const bool is_upper = (j < tiles_first) == upper_first;
+                    bool is_upper;
+                    int64_t ti;
+                    chunk_at(j, tiles_U, tiles_L, overlap, &is_upper, &ti);
                     float m0 = 1.0f, m1 = 1.0f;
                     const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc_buf * 256);
 #pragma unroll 1
@@ -472,8 +476,9 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                         mL1 |= z1;
                     }
                     if (!p.dense && !warp_resolved) {
-                        // resolved: any lower match, or an upper match that precedence cannot overturn
-                        const bool l_done = !upper_first ? (j + 1 >= tiles_first) : true;
+                        // resolved: any lower match, or an upper match that precedence cannot
+                        // overturn (with overlaps the lower tiles come first)
+                        const bool l_done = overlap ? (j + 1 >= tiles_L) : true;
                         const bool r0 = !v0 || mL0 || (mU0 && (!overlap || l_done));
                         const bool r1 = !v1 || mL1 || (mU1 && (!overlap || l_done));
                         // resolution is monotone: each warp reports once; the fourth report ends the block
@@ -580,18 +585,19 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
 
 // Reference rows in the MMA layout: tile t = r / 128 holds rows r in
 // [128 t, 128 t + 128), each KP bytes, core-matrix blocked (tile_off).
-__global__ void encode_tc_kernel(const uint8_t *__restrict__ refs, int64_t R, int64_t rows, int n, int km1,
-                                 int kp, int upper, uint8_t *__restrict__ out) {
+__global__ void encode_tc_kernel(const uint8_t *__restrict__ refs, const int32_t *__restrict__ perm, int64_t R,
+                                 int64_t rows, int n, int km1, int kp, int upper, uint8_t *__restrict__ out) {
     const int chunks = kp / 16;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= rows * chunks) return;
-    const int64_t r = gid / chunks;
+    const int64_t r = gid / chunks;                                        // slot (row of the tile matrix)
+    const int64_t src = (r < R && perm) ? (int64_t)perm[r] : r;            // reference stored in it
     const int c = (int)(gid % chunks);
     const int kenc = n * km1;
     const int bias_cols = (kenc + 15) / 16;
     int total = 0;  // sum_i r_i, the number of thermometer ones of an upper reference
     if (r < R && upper)
-        for (int i = 0; i < n; ++i) total += refs[r * n + i];
+        for (int i = 0; i < n; ++i) total += refs[src * n + i];
     uint8_t bytes[16];
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
@@ -601,7 +607,7 @@ __global__ void encode_tc_kernel(const uint8_t *__restrict__ refs, int64_t R, in
             v = (j == kenc) ? 1.0f : 0.0f;  // padding: never zero
         } else if (j < kenc) {
             const int i = j / km1, k = j % km1 + 1;
-            const bool a = refs[r * n + i] >= k;
+            const bool a = refs[src * n + i] >= k;
             v = upper ? (a ? 1.0f : 0.0f) : (a ? 0.0f : 1.0f);
         } else if (j < kenc + bias_cols && upper) {
             const int used = (j - kenc) * 16;
@@ -649,10 +655,10 @@ bool tc_supported() {
 int tc_max_kpad() { return 416; }  // two B stages still fit next to the A tiles
 
 cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded, int n, int km1, int kpad,
-                             bool upper, uint8_t *out, cudaStream_t s) {
+                             bool upper, uint8_t *out, cudaStream_t s, const int32_t *perm) {
     if (rows_padded <= 0) return cudaSuccess;
     const int64_t total = rows_padded * (kpad / 16);
-    encode_tc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(refs, R, rows_padded, n, km1, kpad,
+    encode_tc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(refs, perm, R, rows_padded, n, km1, kpad,
                                                                      upper ? 1 : 0, out);
     return cudaGetLastError();
 }

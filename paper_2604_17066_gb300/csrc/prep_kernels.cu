@@ -15,11 +15,12 @@ namespace {
 // lower references are stored complemented (within the n*(K-1) valid bits) so
 // that the classifier's failure test is t(x) AND stored == 0 (Sec. 3.3: the
 // subset test H . Rbar = 0).
-__global__ void encode_popc_kernel(const uint8_t *__restrict__ refs, int64_t R, int n, int km1, int words_b,
-                                   int complement, uint32_t *__restrict__ out) {
+__global__ void encode_popc_kernel(const uint8_t *__restrict__ refs, const int32_t *__restrict__ perm, int64_t R,
+                                   int n, int km1, int words_b, int complement, uint32_t *__restrict__ out) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= R * words_b) return;
-    const int64_t r = gid / words_b;
+    const int64_t slot = gid / words_b;
+    const int64_t r = perm ? (int64_t)perm[slot] : slot;  // reference stored in this slot
     const int w = (int)(gid % words_b);
     const int kenc = n * km1;
     uint32_t word = 0;
@@ -76,6 +77,18 @@ cudaError_t launch_overlap_wb(const uint32_t *popc_L, int64_t R_L, const uint32_
     return cudaGetLastError();
 }
 
+// Reference score for ordering: sum over components of a per-(component,
+// state) table (log P(X_i <= v) for lower references, log P(X_i >= v) for
+// upper ones), i.e. the log-probability of the reference's dominated region.
+__global__ void score_refs_kernel(const uint8_t *__restrict__ refs, int64_t R, int n, int K,
+                                  const float *__restrict__ table, float *__restrict__ score) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    float acc = 0.0f;
+    for (int i = 0; i < n; ++i) acc += table[i * K + refs[r * n + i]];
+    score[r] = acc;
+}
+
 // Materialised samples: thread per sample, same Philox layout and thresholds
 // as the classifiers.
 __global__ void sample_kernel(const ClassifyParams p, uint8_t *__restrict__ states) {
@@ -120,11 +133,18 @@ __global__ void grad_correction_kernel(const ClassifyParams p, const int64_t *__
 }  // namespace
 
 cudaError_t launch_encode_popc(const uint8_t *refs, int64_t R, int n, int km1, int words_b, bool complement,
-                               uint32_t *out, cudaStream_t s) {
+                               uint32_t *out, cudaStream_t s, const int32_t *perm) {
     const int64_t total = R * words_b;
     if (total <= 0) return cudaSuccess;
-    encode_popc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(refs, R, n, km1, words_b,
+    encode_popc_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(refs, perm, R, n, km1, words_b,
                                                                         complement ? 1 : 0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_refs(const uint8_t *refs, int64_t R, int n, int K, const float *table, float *score,
+                              cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    score_refs_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(refs, R, n, K, table, score);
     return cudaGetLastError();
 }
 

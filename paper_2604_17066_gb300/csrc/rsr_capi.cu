@@ -166,6 +166,7 @@ ClassifyParams make_params(const rsr_problem *p, const WsLayout &L, void *ws) {
     c.tc_kpad = L.tc_kpad;
     c.hdr = reinterpret_cast<WsHeader *>(base);
     c.dense = (p->flags & RSR_FLAG_DENSE) ? 1 : 0;
+    c.test_stall = (p->flags & RSR_FLAG_TEST_STALL) ? 1 : 0;
     return c;
 }
 
@@ -182,6 +183,45 @@ int choose_path(const rsr_problem *p) {
     if (tc_supported() && L.tc_kpad <= tc_max_kpad() && (p->R_L + p->R_U) >= 8192 && (p->flags & RSR_FLAG_DENSE))
         return RSR_PATH_TC;
     return RSR_PATH_POPC;
+}
+
+
+// Per-(component, state) log-probability tables of the dominated regions:
+// [0][i*K+v] = log P(X_i <= v) (lower references), [1][i*K+v] = log P(X_i >= v)
+// (upper references).
+void ordering_tables(const rsr_problem *p, std::vector<float> &tab) {
+    const int n = p->n, K = p->K;
+    tab.assign(2 * (size_t)n * K, 0.0f);
+    for (int i = 0; i < n; ++i) {
+        double c = 0.0;
+        for (int v = 0; v < K; ++v) {
+            c += p->pmf[(size_t)i * K + v];
+            tab[(size_t)i * K + v] = (float)std::log(c);
+        }
+        double sfx = 0.0;
+        for (int v = K - 1; v >= 0; --v) {
+            sfx += p->pmf[(size_t)i * K + v];
+            tab[(size_t)n * K + (size_t)i * K + v] = (float)std::log(sfx);
+        }
+    }
+}
+
+// Reference order: decreasing probability of the region each reference
+// dominates under the current pmf, so that early exit meets a match sooner.
+// Labels do not depend on the order.  Writes the permutation to d_perm;
+// synchronises the stream (the scores come back to the host for sorting).
+int order_references(const uint8_t *refs, int64_t R, int n, int K, const float *d_table, float *d_score,
+                     int32_t *d_perm, cudaStream_t s) {
+    if (R <= 0) return RSR_OK;
+    std::vector<float> sc((size_t)R);
+    RSR_CUDA(launch_score_refs(refs, R, n, K, d_table, d_score, s));
+    RSR_CUDA(cudaMemcpyAsync(sc.data(), d_score, sizeof(float) * (size_t)R, cudaMemcpyDeviceToHost, s));
+    RSR_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> idx((size_t)R);
+    for (int64_t r = 0; r < R; ++r) idx[(size_t)r] = (int32_t)r;
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return sc[(size_t)a] > sc[(size_t)b]; });
+    RSR_CUDA(cudaMemcpyAsync(d_perm, idx.data(), sizeof(int32_t) * (size_t)R, cudaMemcpyHostToDevice, s));
+    return RSR_OK;
 }
 
 }  // namespace
@@ -223,15 +263,30 @@ int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_strea
     const int km1 = problem->K - 1;
     uint32_t *pL = reinterpret_cast<uint32_t *>(base + L.off_popc_L);
     uint32_t *pU = reinterpret_cast<uint32_t *>(base + L.off_popc_U);
-    RSR_CUDA(launch_encode_popc(problem->ref_L, problem->R_L, problem->n, km1, L.words, true, pL, s));
-    RSR_CUDA(launch_encode_popc(problem->ref_U, problem->R_U, problem->n, km1, L.words, false, pU, s));
-    RSR_CUDA(launch_overlap(pL, problem->R_L, pU, problem->R_U, L.words, reinterpret_cast<WsHeader *>(base), s));
-    if (tc_supported() && L.tc_kpad <= tc_max_kpad()) {
+    float *d_table = reinterpret_cast<float *>(base + L.off_table);
+    float *d_score = reinterpret_cast<float *>(base + L.off_score);
+    int32_t *d_perm = reinterpret_cast<int32_t *>(base + L.off_perm);
+    std::vector<float> tab;
+    ordering_tables(problem, tab);
+    RSR_CUDA(cudaMemcpyAsync(d_table, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s));
+    const bool tc_enc = tc_supported() && L.tc_kpad <= tc_max_kpad();
+    // lower set: order, then encode through the order (the next ordering waits for these encodes)
+    if ((st = order_references(problem->ref_L, problem->R_L, problem->n, problem->K, d_table, d_score, d_perm, s)) !=
+        RSR_OK)
+        return st;
+    RSR_CUDA(launch_encode_popc(problem->ref_L, problem->R_L, problem->n, km1, L.words, true, pL, s, d_perm));
+    if (tc_enc)
         RSR_CUDA(launch_encode_tc(problem->ref_L, problem->R_L, L.tc_rows_L, problem->n, km1, L.tc_kpad, false,
-                                  reinterpret_cast<uint8_t *>(base + L.off_tc_L), s));
+                                  reinterpret_cast<uint8_t *>(base + L.off_tc_L), s, d_perm));
+    // upper set
+    if ((st = order_references(problem->ref_U, problem->R_U, problem->n, problem->K,
+                               d_table + (size_t)problem->n * problem->K, d_score, d_perm, s)) != RSR_OK)
+        return st;
+    RSR_CUDA(launch_encode_popc(problem->ref_U, problem->R_U, problem->n, km1, L.words, false, pU, s, d_perm));
+    if (tc_enc)
         RSR_CUDA(launch_encode_tc(problem->ref_U, problem->R_U, L.tc_rows_U, problem->n, km1, L.tc_kpad, true,
-                                  reinterpret_cast<uint8_t *>(base + L.off_tc_U), s));
-    }
+                                  reinterpret_cast<uint8_t *>(base + L.off_tc_U), s, d_perm));
+    RSR_CUDA(launch_overlap(pL, problem->R_L, pU, problem->R_U, L.words, reinterpret_cast<WsHeader *>(base), s));
     std::lock_guard<std::mutex> g(g_mu);
     g_prepared[ws] = Prepared{problem->n, problem->K, problem->R_L, problem->R_U, problem->ref_L, problem->ref_U,
                               pmf_hash(problem), current_device()};
@@ -391,7 +446,7 @@ namespace rsr {
 namespace {
 
 struct BatchLayout {
-    size_t off_descs = 0, off_begin = 0, off_tune = 0, total = 0;
+    size_t off_descs = 0, off_begin = 0, off_tune = 0, off_table = 0, off_score = 0, off_perm = 0, total = 0;
     std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_bit, off_lc, off_tgrad;
     std::vector<int> words_b;
 };
@@ -405,6 +460,17 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
     off = align256(off + sizeof(int64_t) * (size_t)(S + 1));
     B.off_tune = off;  // tuning scratch: counts3 per scenario
     off = align256(off + sizeof(int64_t) * 3 * (size_t)S);
+    size_t max_nk = 1, max_r = 1;  // reference-ordering scratch, shared by the scenarios in turn
+    for (int s = 0; s < S; ++s) {
+        max_nk = std::max(max_nk, (size_t)probs[s].n * probs[s].K);
+        max_r = std::max(max_r, (size_t)std::max(probs[s].R_L, probs[s].R_U));
+    }
+    B.off_table = off;
+    off = align256(off + sizeof(float) * 2 * max_nk);
+    B.off_score = off;
+    off = align256(off + sizeof(float) * max_r);
+    B.off_perm = off;
+    off = align256(off + sizeof(int32_t) * max_r);
     for (int s = 0; s < S; ++s) {
         const rsr_problem &p = probs[s];
         const int km1 = p.K - 1;
@@ -539,8 +605,20 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         RSR_CUDA(cudaMemcpyAsync(base + B.off_thr[k], T.data(), T.size() * 8, cudaMemcpyHostToDevice, s));
         uint32_t *pL = reinterpret_cast<uint32_t *>(base + B.off_pL[k]);
         uint32_t *pU = reinterpret_cast<uint32_t *>(base + B.off_pU[k]);
-        RSR_CUDA(launch_encode_popc(p.ref_L, p.R_L, p.n, km1, B.words_b[k], true, pL, s));
-        RSR_CUDA(launch_encode_popc(p.ref_U, p.R_U, p.n, km1, B.words_b[k], false, pU, s));
+        float *d_table = reinterpret_cast<float *>(base + B.off_table);
+        float *d_score = reinterpret_cast<float *>(base + B.off_score);
+        int32_t *d_perm = reinterpret_cast<int32_t *>(base + B.off_perm);
+        std::vector<float> tab;
+        ordering_tables(&p, tab);
+        // the previous scenario's encodes read the shared scratch: the ordering below syncs first
+        RSR_CUDA(cudaStreamSynchronize(s));
+        RSR_CUDA(cudaMemcpyAsync(d_table, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s));
+        if ((st = order_references(p.ref_L, p.R_L, p.n, p.K, d_table, d_score, d_perm, s)) != RSR_OK) return st;
+        RSR_CUDA(launch_encode_popc(p.ref_L, p.R_L, p.n, km1, B.words_b[k], true, pL, s, d_perm));
+        if ((st = order_references(p.ref_U, p.R_U, p.n, p.K, d_table + (size_t)p.n * p.K, d_score, d_perm, s)) !=
+            RSR_OK)
+            return st;
+        RSR_CUDA(launch_encode_popc(p.ref_U, p.R_U, p.n, km1, B.words_b[k], false, pU, s, d_perm));
         WsHeader *hs = reinterpret_cast<WsHeader *>(base + B.off_hdr[k]);
         RSR_CUDA(launch_overlap(pL, p.R_L, pU, p.R_U, B.words_b[k], hs, s));
         BatchDesc &d = descs[k];

@@ -56,6 +56,32 @@ __device__ __forceinline__ uint32_t state_from_uniform(uint32_t u, const unsigne
 }
 
 // ---------------------------------------------------------------------------
+// Visiting order of the two reference sets, in chunks (tiles) of references.
+// Without an overlapping pair (no upper reference below a lower one) a sample
+// matches at most one set and any match is final, so the sets alternate chunk
+// by chunk, upper first, until one runs out: a sample that belongs to either
+// set meets its set within the first chunks.  With an overlapping pair every
+// lower chunk comes first (Algorithm 1: lower takes precedence).
+// step in [0, nU + nL) -> (*upper, *idx = chunk index within that set).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ void chunk_at(int64_t step, int64_t nU, int64_t nL, bool overlap, bool *upper,
+                                                  int64_t *idx) {
+    if (overlap) {
+        *upper = step >= nL;
+        *idx = *upper ? step - nL : step;
+        return;
+    }
+    const int64_t m = nU < nL ? nU : nL;
+    if (step < 2 * m) {
+        *upper = (step & 1) == 0;
+        *idx = step >> 1;
+        return;
+    }
+    *upper = nU > nL;
+    *idx = m + (step - 2 * m);
+}
+
+// ---------------------------------------------------------------------------
 // Workspace layout.  The caller passes one 256-byte aligned buffer; offsets
 // below are derived from the problem sizes only (rsr_workspace_size()).
 // ---------------------------------------------------------------------------
@@ -77,6 +103,9 @@ struct WsLayout {
     size_t off_popc_U = 0;      // uint32 [R_U][words]  (reference thermometer)
     size_t off_tc_L = 0;        // FP8 tiles of the lower references
     size_t off_tc_U = 0;        // FP8 tiles of the upper references
+    size_t off_table = 0;       // float [2][n*K]: per-state log-probability tables (reference ordering)
+    size_t off_score = 0;       // float [max(R_L, R_U)]: reference scores (ordering)
+    size_t off_perm = 0;        // int32 [max(R_L, R_U)]: reference order (ordering)
     size_t total = 0;
 };
 
@@ -109,6 +138,13 @@ inline WsLayout make_layout(int32_t n, int32_t K, int64_t R_L, int64_t R_U, int3
     off = align256(off + (size_t)L.tc_rows_L * L.tc_kpad);
     L.off_tc_U = off;
     off = align256(off + (size_t)L.tc_rows_U * L.tc_kpad);
+    const size_t rmax = (size_t)(R_L > R_U ? R_L : R_U) + 1;
+    L.off_table = off;
+    off = align256(off + sizeof(float) * 2 * (size_t)n * K);
+    L.off_score = off;
+    off = align256(off + sizeof(float) * rmax);
+    L.off_perm = off;
+    off = align256(off + sizeof(int32_t) * rmax);
     L.total = off;
     return L;
 }
@@ -130,6 +166,7 @@ struct ClassifyParams {
     unsigned long long *exec_tests;    // [1] or NULL
     WsHeader *hdr;
     int32_t dense;
+    int32_t test_stall;                // RSR_FLAG_TEST_STALL: the producer never starts
 };
 
 }  // namespace rsr

@@ -13,7 +13,9 @@ int popc_word_bucket(int words);
 
 // Preparation (prep_kernels.cu).
 cudaError_t launch_encode_popc(const uint8_t *refs, int64_t R, int n, int km1, int words_b,
-                               bool complement, uint32_t *out, cudaStream_t s);
+                               bool complement, uint32_t *out, cudaStream_t s, const int32_t *perm = nullptr);
+cudaError_t launch_score_refs(const uint8_t *refs, int64_t R, int n, int K, const float *table, float *score,
+                              cudaStream_t s);
 cudaError_t launch_overlap(const uint32_t *popc_L, int64_t R_L, const uint32_t *popc_U, int64_t R_U,
                            int words_b, WsHeader *hdr, cudaStream_t s);
 cudaError_t launch_sample(const ClassifyParams &p, uint8_t *states, cudaStream_t s);
@@ -23,7 +25,7 @@ cudaError_t launch_grad_correction(const ClassifyParams &p, const int64_t *idx, 
 // Classification (classify_popc.cu, classify_tc.cu).
 cudaError_t launch_classify_popc(const ClassifyParams &p, cudaStream_t s);
 cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded, int n, int km1,
-                             int kpad, bool upper, uint8_t *out, cudaStream_t s);
+                             int kpad, bool upper, uint8_t *out, cudaStream_t s, const int32_t *perm = nullptr);
 cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s);
 bool tc_supported();
 int tc_max_kpad();

@@ -67,3 +67,21 @@ def test_tc_rejects_too_wide_encodings(rsr):
     with pytest.raises(rsr.RSRError) as e:
         rsr.Session(P)
     assert e.value.status == -5
+
+
+def test_tc_bounded_waits_time_out_and_leave_the_context_usable(rsr):
+    """Failure detection on the device without a fault: with the test hook the
+    reference producer never starts, every bounded wait runs out (about 10 ms),
+    the kernel records RSR_ERR_TIMEOUT, frees its tensor memory and returns."""
+    from paper_2604_17066_gb300._lib import RSR_FLAG_TEST_STALL
+    prob = random_refs_problem(120, 3, 130, 129, seed=2)
+    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=TC)
+    sess = rsr.Session(P)
+    P.extra_flags = RSR_FLAG_TEST_STALL
+    sess.classify(1, 0, 4096)
+    torch.cuda.synchronize()
+    overlap, err = rsr.rsr_workspace_status(sess.ws)
+    assert err == -4
+    # the context still works: a normal run on a fresh workspace matches the oracle
+    P.extra_flags = 0
+    check(rsr, prob, 1, 0, 4096, dense=False)
