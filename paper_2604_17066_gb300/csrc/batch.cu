@@ -26,6 +26,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChunk = 256;
 constexpr int kMaxWB = 16;  // batch path: n*(K-1) <= 512
+constexpr int kCoopLanes = 8;  // at most this many unresolved lanes: cooperative warp scan
 
 struct Shared {
     BatchDesc d;
@@ -49,11 +50,13 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         uint32_t cur = 0;
         if (valid) {
             const uint64_t h = d.offset + round * (uint64_t)d.N + (uint64_t)hl;
-            for (int q = 0; 4 * q < d.n; ++q) {
-                const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
-                const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+            // two independent Philox blocks per iteration (instruction-level parallelism)
+            for (int q = 0; 4 * q < d.n; q += 2) {
+                const U32x4 ra = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+                const U32x4 rb = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)(q + 1), 0u, key0, key1);
+                const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < 8; ++c) {
                     const int i = 4 * q + c;
                     if (i >= d.n) break;
                     const uint32_t x = state_from_uniform(us[c], s_thr + (size_t)i * d.km1, d.km1);
@@ -95,26 +98,60 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
         for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
         __syncthreads();
-        if (!done) {
-            bool m = false;
-            if (upper) {
-                for (int r = 0; r < cnt; ++r) {
-                    uint32_t acc = 0;
+        // per-lane scan while many lanes are unresolved, cooperative warp scan otherwise
+        const unsigned active = __ballot_sync(0xffffffffu, !done);
+        if (__popc(active) > kCoopLanes) {
+            if (!done) {
+                bool m = false;
+                if (upper) {
+                    for (int r = 0; r < cnt; ++r) {
+                        uint32_t acc = 0;
 #pragma unroll
-                    for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
-                    if (acc == 0u) { m = true; break; }
+                        for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
+                        if (acc == 0u) { m = true; break; }
+                    }
+                } else {
+                    for (int r = 0; r < cnt; ++r) {
+                        uint32_t acc = 0;
+#pragma unroll
+                        for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
+                        if (acc == 0u) { m = true; break; }
+                    }
                 }
-            } else {
-                for (int r = 0; r < cnt; ++r) {
-                    uint32_t acc = 0;
-#pragma unroll
-                    for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
-                    if (acc == 0u) { m = true; break; }
+                if (m) {
+                    if (upper) mU = true; else mL = true;
+                    done = true;
                 }
             }
-            if (m) {
-                if (upper) mU = true; else mL = true;
-                done = true;
+        } else {
+            unsigned rem = active;
+            while (rem) {
+                const int src = __ffs(rem) - 1;
+                rem &= rem - 1;
+                uint32_t ts[WB];
+#pragma unroll
+                for (int w = 0; w < WB; ++w) ts[w] = __shfl_sync(0xffffffffu, t[w], src);
+                bool found = false;
+                for (int r0 = 0; r0 < cnt && !found; r0 += 32) {
+                    const int r = r0 + lane;
+                    bool m = false;
+                    if (r < cnt) {
+                        uint32_t acc = 0;
+                        if (upper) {
+#pragma unroll
+                            for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~ts[w];
+                        } else {
+#pragma unroll
+                            for (int w = 0; w < WB; ++w) acc |= ts[w] & s_ref[r * WB + w];
+                        }
+                        m = (acc == 0u);
+                    }
+                    found = __any_sync(0xffffffffu, m);
+                }
+                if (lane == src && found) {
+                    if (upper) mU = true; else mL = true;
+                    done = true;
+                }
             }
         }
     }

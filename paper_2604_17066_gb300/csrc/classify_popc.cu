@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kThreads = 256;   // one sample per thread
 constexpr int kChunk = 256;     // references per shared-memory chunk
+constexpr int kCoopLanes = 8;   // at most this many unresolved lanes: cooperative warp scan
 
 struct WordWriter {
     // Appends per-component thermometer runs to a column of 32-bit words in
@@ -101,13 +102,16 @@ __global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const Classi
             } else {
                 const uint64_t h = p.offset + (uint64_t)hl;
                 const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
-                for (int q = 0; 4 * q < p.n; ++q) {
-                    const U32x4 r = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
-                    const int i0 = 4 * q;
-                    ww.put(state_from_uniform(r.x, s_thr + (size_t)i0 * p.km1, p.km1));
-                    if (i0 + 1 < p.n) ww.put(state_from_uniform(r.y, s_thr + (size_t)(i0 + 1) * p.km1, p.km1));
-                    if (i0 + 2 < p.n) ww.put(state_from_uniform(r.z, s_thr + (size_t)(i0 + 2) * p.km1, p.km1));
-                    if (i0 + 3 < p.n) ww.put(state_from_uniform(r.w, s_thr + (size_t)(i0 + 3) * p.km1, p.km1));
+                // two independent Philox blocks per iteration (instruction-level parallelism)
+                for (int q = 0; 4 * q < p.n; q += 2) {
+                    const U32x4 ra = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
+                    const U32x4 rb = philox4x32_10(h0, h1, (uint32_t)(q + 1), 0u, key0, key1);
+                    const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int i = 4 * q + c;
+                        if (i < p.n) ww.put(state_from_uniform(us[c], s_thr + (size_t)i * p.km1, p.km1));
+                    }
                 }
             }
         }
@@ -159,30 +163,71 @@ __global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const Classi
                     my_exec += (unsigned long long)cnt;
                 }
                 if (upper) mU |= m; else mL |= m;
-            } else if (!done) {
-                int r = 0;
-                bool m = false;
-                if (upper) {
-                    for (; r < cnt; ++r) {
-                        uint32_t acc = 0;
+            } else {
+                // Early-exit mode.  While many lanes of the warp are unresolved each lane
+                // scans for its own sample; once few remain, the warp scans cooperatively,
+                // one unresolved sample at a time, 32 references per step.
+                const unsigned active = __ballot_sync(0xffffffffu, !done);
+                if (__popc(active) > kCoopLanes) {
+                    if (!done) {
+                        int r = 0;
+                        bool m = false;
+                        if (upper) {
+                            for (; r < cnt; ++r) {
+                                uint32_t acc = 0;
 #pragma unroll
-                        for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
-                        if (acc == 0u) { m = true; ++r; break; }
+                                for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~t[w];
+                                if (acc == 0u) { m = true; ++r; break; }
+                            }
+                        } else {
+                            for (; r < cnt; ++r) {
+                                uint32_t acc = 0;
+#pragma unroll
+                                for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
+                                if (acc == 0u) { m = true; ++r; break; }
+                            }
+                        }
+                        my_exec += (unsigned long long)r;
+                        if (m) {
+                            if (upper) mU = true; else mL = true;
+                            done = true;
+                        }
                     }
                 } else {
-                    for (; r < cnt; ++r) {
-                        uint32_t acc = 0;
+                    unsigned rem = active;
+                    while (rem) {
+                        const int src = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        uint32_t ts[WB];
 #pragma unroll
-                        for (int w = 0; w < WB; ++w) acc |= t[w] & s_ref[r * WB + w];
-                        if (acc == 0u) { m = true; ++r; break; }
+                        for (int w = 0; w < WB; ++w) ts[w] = __shfl_sync(0xffffffffu, t[w], src);
+                        bool found = false;
+                        int tested = 0;
+                        for (int r0 = 0; r0 < cnt && !found; r0 += 32) {
+                            const int r = r0 + lane;
+                            bool m = false;
+                            if (r < cnt) {
+                                uint32_t acc = 0;
+                                if (upper) {
+#pragma unroll
+                                    for (int w = 0; w < WB; ++w) acc |= s_ref[r * WB + w] & ~ts[w];
+                                } else {
+#pragma unroll
+                                    for (int w = 0; w < WB; ++w) acc |= ts[w] & s_ref[r * WB + w];
+                                }
+                                m = (acc == 0u);
+                            }
+                            found = __any_sync(0xffffffffu, m);
+                            tested = (cnt < r0 + 32) ? cnt : r0 + 32;
+                        }
+                        if (lane == src) {
+                            my_exec += (unsigned long long)tested;
+                            if (found) {
+                                if (upper) mU = true; else mL = true;
+                                done = true;
+                            }
+                        }
                     }
-                }
-                my_exec += (unsigned long long)r;
-                // a match is final unless precedence can still overturn it: an upper match
-                // with overlapping pairs waits for the lower chunks, which come first then
-                if (m) {
-                    if (upper) mU = true; else mL = true;
-                    done = true;
                 }
             }
         }

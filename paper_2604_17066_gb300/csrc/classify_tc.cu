@@ -326,11 +326,14 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                     for (int i = 0; i < p.n; ++i) bw.put((1u << row[i]) - 1u, p.km1);
                 } else {
                     const uint64_t h = p.offset + (uint64_t)hl;
-                    for (int q = 0; 4 * q < p.n; ++q) {
-                        const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
-                        const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+                    // two independent Philox blocks per iteration (instruction-level parallelism)
+                    for (int q = 0; 4 * q < p.n; q += 2) {
+                        const U32x4 ra = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+                        const U32x4 rb =
+                            philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)(q + 1), 0u, key0, key1);
+                        const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
+                        for (int c = 0; c < 8; ++c) {
                             const int i = 4 * q + c;
                             if (i < p.n) {
                                 const uint32_t x = state_from_uniform(us[c], sThr + (size_t)i * p.km1, p.km1);
