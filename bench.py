@@ -103,13 +103,16 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def bench_batch(rsr, torch, reps=5):
-    """256 hazard scenarios (n = 50..300 edges, 1e2..1e5 references, N = 2e5 each):
-    one persistent launch replayed from a CUDA graph vs the per-scenario path
-    (one rsr_classify per scenario on prepared workspaces)."""
+def bench_batch(rsr, torch, N=200_000, reps=5):
+    """256 hazard scenarios (n = 50..300 edges, 1e2..1e5 references, N samples
+    each): one persistent launch replayed from a CUDA graph vs the per-scenario
+    path on prepared workspaces.  Two comparisons: kernels only (one batched
+    launch vs one rsr_classify per scenario), and a forward+gradient round
+    (batched launch + rsr_batch_grad vs rsr_classify + rsr_grad per scenario,
+    each rsr_grad reading its counts back)."""
     import workloads.large as L
     probs = L.c5_batch()
-    S, N = len(probs), 200_000
+    S = len(probs)
     P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_POPC) for p in probs]
     seeds, offsets, Ns = [1000 + s for s in range(S)], [0] * S, [N] * S
     t0 = time.perf_counter()
@@ -130,6 +133,11 @@ def bench_batch(rsr, torch, reps=5):
     ev[1].record()
     torch.cuda.synchronize()
     batched_ms = ev[0].elapsed_time(ev[1]) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g.replay()
+        rsr.rsr_batch_grad(b)
+    batched_round_ms = 1000 * (time.perf_counter() - t0) / reps
     # per-scenario path
     sessions = [rsr.Session(p) for p in P]
     cur = torch.cuda.current_stream()
@@ -137,21 +145,30 @@ def bench_batch(rsr, torch, reps=5):
     lab = torch.empty(N, dtype=torch.uint8, device="cuda")
     grads = [torch.zeros(p.n * p.K, dtype=torch.int64, device="cuda") for p in P]
 
-    def plain(r):
+    def plain(r, with_grad):
         for s_, (p, se) in enumerate(zip(P, sessions)):
             rsr.rsr_classify(p, seeds[s_], offsets[s_] + r * N, N, se.ws, cnt, None, lab, grads[s_], None, cur)
+            if with_grad:
+                rsr.rsr_grad(p, seeds[s_], offsets[s_] + r * N, N, grads[s_], se.ws, stream=cur)
 
-    plain(0)
+    plain(0, False)
     torch.cuda.synchronize()
     ev[0].record()
     for r in range(reps):
-        plain(1 + r)
+        plain(1 + r, False)
     ev[1].record()
     torch.cuda.synchronize()
     plain_ms = ev[0].elapsed_time(ev[1]) / reps
+    t0 = time.perf_counter()
+    for r in range(reps):
+        plain(10 + r, True)
+    torch.cuda.synchronize()
+    plain_round_ms = 1000 * (time.perf_counter() - t0) / reps
     R = [p.R_L + p.R_U for p in P]
-    return {"workload": "c5_256_scenarios_N2e5", "scenarios": S, "refs_total": int(sum(R)),
-            "batched_ms": batched_ms, "per_scenario_ms": plain_ms, "speedup": plain_ms / batched_ms,
+    return {"workload": "c5_256_scenarios_N%d" % N, "scenarios": S, "refs_total": int(sum(R)),
+            "batched_ms": batched_ms, "per_scenario_ms": plain_ms, "speedup_kernels": plain_ms / batched_ms,
+            "batched_fwd_grad_round_ms": batched_round_ms, "per_scenario_fwd_grad_round_ms": plain_round_ms,
+            "speedup_fwd_grad_round": plain_round_ms / batched_round_ms,
             "samples_per_s": S * N / (batched_ms / 1000.0), "autotune_grid": grid,
             "autotune_order": "longest-first" if order == 0 else "as-given", "prepare_s": prep_s}
 
@@ -353,7 +370,8 @@ def main():
         extras["prepare_ms"] = prep_ms
         extras["overlap_pairs"] = bool(overlap)
         if args.workload == "c3" and not args.no_batch:
-            extras["batch_c5"] = bench_batch(rsr, torch)
+            extras["batch_c5"] = bench_batch(rsr, torch, N=200_000)
+            extras["batch_c5_N2e4"] = bench_batch(rsr, torch, N=20_000)
 
     # end to end through the public API: pmf -> thresholds (H2D), classify, results (D2H)
     e2e = None

@@ -224,6 +224,16 @@ RSR_API int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uin
                                size_t ws_bytes, rsr_stream_t stream, int32_t chosen[2]);
 
 /*
+ * Gradients of every scenario of a batch from its per-state I^L counts (the
+ * same arithmetic as rsr_grad, without Stage-2 corrections): grad_counts[s]
+ * (device int64[n_s*K_s], e.g. filled by rsr_batch), Ns[s] samples;
+ * grad_out[s], se_out[s] host fp64[n_s*K_s].  One device->host transfer per
+ * scenario on `stream`, one synchronisation for the whole batch.
+ */
+RSR_API int rsr_batch_grad(const rsr_problem *problems, int32_t S, const int64_t *Ns, int64_t *const *grad_counts,
+                           double *const *grad_out, double *const *se_out, rsr_stream_t stream);
+
+/*
  * Time both classifier paths on a 65536-sample slice of `problem` (prepared in
  * `ws`) and remember the faster one for RSR_PATH_AUTO on problems with the
  * same n, K, density flag and reference-count bucket (power of two).

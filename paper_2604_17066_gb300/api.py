@@ -270,6 +270,22 @@ def rsr_batch_autotune(batch: Batch, stream=None):
     return int(chosen[0]), int(chosen[1])
 
 
+def rsr_batch_grad(batch: Batch, stream=None):
+    """FP64 gradients and standard errors of every scenario from the batch's
+    gradient counts: lists of n_s x K_s arrays."""
+    if batch.grad_counts is None:
+        raise ValueError("batch was built without gradient counts")
+    g = [np.zeros((p.n, p.K), dtype=np.float64) for p in batch.problems]
+    se = [np.zeros_like(x) for x in g]
+    gp = (ctypes.c_void_p * batch.S)(*[x.ctypes.data for x in g])
+    sp = (ctypes.c_void_p * batch.S)(*[x.ctypes.data for x in se])
+    check(_lib.load().rsr_batch_grad(batch._structs, batch.S, batch.Ns.ctypes.data,
+                                     ctypes.cast(batch._grad_ptrs, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
+                                     ctypes.cast(sp, ctypes.c_void_p),
+                                     _stream(stream if stream is not None else batch.stream)), "rsr_batch_grad")
+    return g, se
+
+
 def rsr_autotune(problem: Problem, ws: torch.Tensor, stream=None) -> int:
     s = problem.struct()
     chosen = ctypes.c_int32(0)

@@ -19,13 +19,17 @@
 // is an integer far below 2^24, so FP32 accumulation is exact.  Padding
 // references carry a +1 in the first bias column and never give 0.
 //
-// Kernel structure (one CTA per SM, persistent over 256-sample blocks):
-//   all 8 warps : Philox-sample the block's 256 states into two FP8 A tiles
-//   warp 0      : producer, one cp.async.bulk per 128-reference tile into a
-//                 ring of shared-memory stages (references are pre-encoded in
-//                 global memory in the MMA's shared-memory layout)
-//   warp 1      : TMEM owner and MMA issuer (2 A tiles x KP/32 MMAs per stage)
-//   warps 4-7   : epilogue, each thread owns one TMEM lane = two sample rows
+// Kernel structure (one CTA per SM, persistent over 128-sample blocks):
+//   all 8 warps : Philox-sample the block's 128 states (two threads per row,
+//                 half of the components each) into the FP8 A tile (128 x KP)
+//   warp 0      : producer, one cp.async.bulk per B tile of BN references
+//                 (BN = 256, the MMA's N; 128 for rows wider than 320 bytes)
+//                 into a ring of shared-memory stages; references are
+//                 pre-encoded in global memory in the MMA's shared-memory
+//                 layout, so BN/128 consecutive encoded tiles are one copy
+//   warp 1      : TMEM owner and MMA issuer (KP/32 MMAs of 128 x BN x 32 per
+//                 stage into one of two accumulator buffers of BN columns)
+//   warps 4-7   : epilogue, the thread of TMEM lane r owns sample row r
 // Early exit: the epilogue raises a flag once every row of the block is
 // resolved; the producer stops issuing and closes the block with an in-band
 // sentinel that walks through the same rings, so every barrier phase stays
@@ -44,11 +48,11 @@ namespace rsr {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRows = 256;           // samples per block (two 128-row A tiles)
-constexpr int kRefTile = kTcRefTile; // references per B tile (MMA N)
+constexpr int kRows = 128;           // samples per block: one A tile, the MMA's M
+constexpr int kEncTile = kTcRefTile; // rows per encoded reference tile in global memory (128)
 constexpr int kMaxStages = 4;
 constexpr int kSmemLimit = 232448;   // 227 KB opt-in per CTA
-constexpr uint32_t kTmemCols = 512;  // 2 buffers x (2 A tiles x 128 columns)
+// tensor memory: two FP32 accumulator buffers of BN columns each (BN = MMA N)
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at the base clock
 constexpr long long kTestWaitCycles = 20000000ll; // ~10 ms, RSR_FLAG_TEST_STALL
 
@@ -169,8 +173,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major,
-// N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kRefTile >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// M = 128, N = BN.
+template <int BN>
+__host__ __device__ constexpr uint32_t tc_idesc() {
+    return (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+}
 
 // Byte offset of (row, 16-byte chunk c) inside a tile of KP-byte rows.
 __device__ __forceinline__ uint32_t tile_off(int row, int c, int kp) {
@@ -214,7 +221,7 @@ struct TcSmem {
     int nstages;
 };
 
-__host__ __device__ inline TcSmem tc_smem_plan(int kp, int nthr, int stages_cap) {
+__host__ __device__ inline TcSmem tc_smem_plan(int kp, int nthr, int bn, int stages_cap) {
     TcSmem s{};
     uint32_t off = 0;
     s.a = off;
@@ -227,7 +234,7 @@ __host__ __device__ inline TcSmem tc_smem_plan(int kp, int nthr, int stages_cap)
     off += (uint32_t)kp * 4;
     off = (off + 1023) & ~1023u;
     s.stages = off;
-    const uint32_t stage_bytes = (uint32_t)kRefTile * kp;
+    const uint32_t stage_bytes = (uint32_t)bn * kp;
     int ns = 0;
     while (ns < stages_cap && off + (ns + 1) * stage_bytes + 1024 <= (uint32_t)kSmemLimit) ++ns;
     s.nstages = ns;
@@ -250,16 +257,23 @@ struct TcCtl {
     unsigned long long cnt[3];
 };
 
+// BN = references per B tile = MMA N (256, or 128 for rows too wide for two
+// 256-row stages).  A block is 128 samples: thread t and t + 128 each sample
+// half of row t's components (Philox blocks are independent), so all 8 warps
+// generate; the epilogue thread of TMEM lane r owns sample row r.
+template <int BN>
 __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const ClassifyParams p) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ TcCtl ctl;
+    constexpr uint32_t kTmemCols = 2 * BN;
+    constexpr uint32_t kIdesc = tc_idesc<BN>();
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int kp = p.tc_kpad;
     const int kwords = kp / 32;
     const int nthr = p.n * p.km1;
-    const TcSmem plan = tc_smem_plan(kp, nthr, kMaxStages);
+    const TcSmem plan = tc_smem_plan(kp, nthr, BN, kMaxStages);
     const int S = plan.nstages;
     uint8_t *sA = smem + plan.a;
     uint8_t *sStage = smem + plan.stages;
@@ -298,12 +312,14 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
 
     const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
     // tile order: chunk_at() (alternating without overlapping pairs, lower first with them)
-    const int64_t tiles_U = (p.R_U + kRefTile - 1) / kRefTile;
-    const int64_t tiles_L = (p.R_L + kRefTile - 1) / kRefTile;
+    const int64_t tiles_U = (p.R_U + BN - 1) / BN;
+    const int64_t tiles_L = (p.R_L + BN - 1) / BN;
     const int64_t T = tiles_U + tiles_L;
-    const uint32_t tile_bytes = (uint32_t)kRefTile * kp;
+    const uint32_t tile_bytes = (uint32_t)BN * kp;   // BN/128 consecutive encoded tiles
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     const int bias_cols = (p.kenc + 15) / 16;
+    // component split between the two threads that sample one row (a multiple of 4: whole Philox blocks)
+    const int n_half = ((p.n + 7) / 8) * 4;
 
     // ring state (continuous across blocks)
     int st_stage = 0;
@@ -316,18 +332,24 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
 
     const int64_t nblocks = (p.N + kRows - 1) / kRows;
     for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
-        // ---- 1. sample the block into the thermometer scratch and the A tiles --
+        // ---- 1. sample the block into the thermometer scratch and the A tile -----
         {
-            const int64_t hl = blk * kRows + tid;
-            Bits bw{sTw + tid, 0, 0, 0u};
+            const int row = tid & (kRows - 1), half = tid >> 7;
+            const int64_t hl = blk * kRows + row;
+            const int i_lo = half ? (n_half < p.n ? n_half : p.n) : 0;
+            const int i_hi = half ? p.n : (n_half < p.n ? n_half : p.n);
+            // this thread's bits start at bit i_lo*(K-1) of the row; earlier words stay zero
+            const int start = i_lo * p.km1;
+            Bits bw{sTw + tid, start >> 5, start & 31, 0u};
+            for (int w = 0; w < (start >> 5); ++w) sTw[w * kThreads + tid] = 0u;
             if (hl < p.N) {
                 if (p.samples) {
-                    const uint8_t *row = p.samples + hl * (int64_t)p.n;
-                    for (int i = 0; i < p.n; ++i) bw.put((1u << row[i]) - 1u, p.km1);
+                    const uint8_t *srow = p.samples + hl * (int64_t)p.n;
+                    for (int i = i_lo; i < i_hi; ++i) bw.put((1u << srow[i]) - 1u, p.km1);
                 } else {
                     const uint64_t h = p.offset + (uint64_t)hl;
                     // two independent Philox blocks per iteration (instruction-level parallelism)
-                    for (int q = 0; 4 * q < p.n; q += 2) {
+                    for (int q = i_lo / 4; 4 * q < i_hi; q += 2) {
                         const U32x4 ra = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
                         const U32x4 rb =
                             philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)(q + 1), 0u, key0, key1);
@@ -335,31 +357,38 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
 #pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             const int i = 4 * q + c;
-                            if (i < p.n) {
+                            if (i < i_hi) {
                                 const uint32_t x = state_from_uniform(us[c], sThr + (size_t)i * p.km1, p.km1);
                                 bw.put((1u << x) - 1u, p.km1);
                             }
                         }
                     }
                 }
-                for (int b = bias_cols; b > 0; b -= 16) {
-                    const int len = b < 16 ? b : 16;
-                    bw.put((1u << len) - 1u, len);
+                if (half) {  // the constant-one bias columns follow the last component
+                    for (int b = bias_cols; b > 0; b -= 16) {
+                        const int len = b < 16 ? b : 16;
+                        bw.put((1u << len) - 1u, len);
+                    }
                 }
             }
             bw.finish(kwords);
-            // expand to FP8 bytes in the MMA layout
-            const int a_tile = tid >> 7, rr = tid & 127;
-            uint8_t *tileA = sA + (size_t)a_tile * 128 * kp;
-            for (int c = 0; c < kp / 16; ++c) {
-                const uint32_t w = sTw[(c >> 1) * kThreads + tid];
-                const uint32_t b16 = (w >> ((c & 1) * 16)) & 0xFFFFu;
+        }
+        __syncthreads();
+        {
+            // expand the row's bits (the OR of its two halves) to FP8 bytes in the MMA layout;
+            // thread t does chunks [0, kp/32) of row t, thread t + 128 the rest
+            const int row = tid & (kRows - 1), half = tid >> 7;
+            const int c_lo = half ? kp / 32 : 0, c_hi = half ? kp / 16 : kp / 32;
+            for (int c = c_lo; c < c_hi; ++c) {
+                const int w = c >> 1;
+                const uint32_t word = sTw[w * kThreads + row] | sTw[w * kThreads + row + kRows];
+                const uint32_t b16 = (word >> ((c & 1) * 16)) & 0xFFFFu;
                 uint4 v;
                 v.x = nibble_to_fp8(b16 & 0xF);
                 v.y = nibble_to_fp8((b16 >> 4) & 0xF);
                 v.z = nibble_to_fp8((b16 >> 8) & 0xF);
                 v.w = nibble_to_fp8((b16 >> 12) & 0xF);
-                *reinterpret_cast<uint4 *>(tileA + tile_off(rr, c, kp)) = v;
+                *reinterpret_cast<uint4 *>(sA + tile_off(row, c, kp)) = v;
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -410,16 +439,12 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                     } else {
                         tc_fence_after();
                         const uint32_t b_base = smem_u32(sStage + (size_t)st_stage * tile_bytes);
+                        const uint32_t d = tmem + (uint32_t)(acc_buf * BN);
 #pragma unroll 1
-                        for (int a = 0; a < 2; ++a) {
-                            const uint32_t d = tmem + (uint32_t)(acc_buf * 256 + a * 128);
-                            const uint32_t at = a_base + (uint32_t)(a * 128 * kp);
-#pragma unroll 1
-                            for (int kk = 0; kk < kp / 32; ++kk) {
-                                const uint64_t ad = smem_desc(at + kk * 256, 128, sbo);
-                                const uint64_t bd = smem_desc(b_base + kk * 256, 128, sbo);
-                                mma_f8(d, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
-                            }
+                        for (int kk = 0; kk < kp / 32; ++kk) {
+                            const uint64_t ad = smem_desc(a_base + kk * 256, 128, sbo);
+                            const uint64_t bd = smem_desc(b_base + kk * 256, 128, sbo);
+                            mma_f8(d, ad, bd, kIdesc, kk > 0 ? 1u : 0u);
                         }
                         mma_commit(&ctl.empty[st_stage]);
                         mma_commit(&ctl.tfull[acc_buf]);
@@ -436,14 +461,14 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                     }
                     if (j < 0) break;
                 }
-                ctl.exec += issued * (unsigned long long)(kRefTile * kRows);
+                ctl.exec += issued * (unsigned long long)(BN * kRows);
             }
         } else if (warp >= 4) {
-            const int q = warp & 3;                   // TMEM lane quarter
-            const int row0 = q * 32 + lane;           // row in A tile 0; row0 + 128 in A tile 1
-            const int64_t h0 = blk * kRows + row0, h1 = h0 + 128;
-            const bool v0 = h0 < p.N, v1 = h1 < p.N;
-            bool mL0 = false, mU0 = false, mL1 = false, mU1 = false;
+            const int q = warp & 3;              // TMEM lane quarter
+            const int row = q * 32 + lane;       // sample row of this thread
+            const int64_t h = blk * kRows + row;
+            const bool v = h < p.N;
+            bool mL = false, mU = false;
             bool warp_resolved = false;
             while (true) {
                 if (!mbar_wait(&ctl.tfull[acc_buf], acc_phase, abort_flag, err, budget)) break;
@@ -453,39 +478,30 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                     bool is_upper;
                     int64_t ti;
                     chunk_at(j, tiles_U, tiles_L, overlap, &is_upper, &ti);
-                    float m0 = 1.0f, m1 = 1.0f;
-                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc_buf * 256);
+                    float m = 1.0f;
+                    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc_buf * BN);
 #pragma unroll 1
-                    for (int c = 0; c < 4; ++c) {
+                    for (int c = 0; c < BN / 64; ++c) {
                         uint32_t va[32], vb[32];
-                        tmem_ld32(tbase + c * 32, va);
-                        tmem_ld32(tbase + 128 + c * 32, vb);
+                        tmem_ld32(tbase + c * 64, va);
+                        tmem_ld32(tbase + c * 64 + 32, vb);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) {
-                            m0 = fminf(m0, fabsf(__uint_as_float(va[e])));
-                            m1 = fminf(m1, fabsf(__uint_as_float(vb[e])));
-                        }
+                        for (int e = 0; e < 32; ++e)
+                            m = fminf(m, fminf(fabsf(__uint_as_float(va[e])), fabsf(__uint_as_float(vb[e]))));
                     }
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&ctl.tempty[acc_buf]);
-                    const bool z0 = m0 < 0.5f, z1 = m1 < 0.5f;
-                    if (is_upper) {
-                        mU0 |= z0;
-                        mU1 |= z1;
-                    } else {
-                        mL0 |= z0;
-                        mL1 |= z1;
-                    }
+                    const bool z = m < 0.5f;
+                    if (is_upper) mU |= z; else mL |= z;
                     if (!p.dense && !warp_resolved) {
                         // resolved: any lower match, or an upper match that precedence cannot
                         // overturn (with overlaps the lower tiles come first)
                         const bool l_done = overlap ? (j + 1 >= tiles_L) : true;
-                        const bool r0 = !v0 || mL0 || (mU0 && (!overlap || l_done));
-                        const bool r1 = !v1 || mL1 || (mU1 && (!overlap || l_done));
+                        const bool r = !v || mL || (mU && (!overlap || l_done));
                         // resolution is monotone: each warp reports once; the fourth report ends the block
-                        if (__all_sync(0xffffffffu, r0 && r1)) {
+                        if (__all_sync(0xffffffffu, r)) {
                             warp_resolved = true;
                             if (lane == 0 && atomicAdd(&ctl.nres, 1) == 3) *((volatile int *)&ctl.done) = 1;
                         }
@@ -500,31 +516,24 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                 }
                 if (j < 0) break;
             }
-            const int lab0 = mL0 ? 0 : (mU0 ? 1 : 2);
-            const int lab1 = mL1 ? 0 : (mU1 ? 1 : 2);
-            if (v0) {
-                if (p.labels) p.labels[h0] = (uint8_t)lab0;
-                c0 += lab0 == 0; c1 += lab0 == 1; c2 += lab0 == 2;
-            }
-            if (v1) {
-                if (p.labels) p.labels[h1] = (uint8_t)lab1;
-                c0 += lab1 == 0; c1 += lab1 == 1; c2 += lab1 == 2;
+            const int lab = mL ? 0 : (mU ? 1 : 2);
+            if (v) {
+                if (p.labels) p.labels[h] = (uint8_t)lab;
+                c0 += lab == 0; c1 += lab == 1; c2 += lab == 2;
             }
             if (p.grad_counts) {
-                // per-bit counts of I^L rows, from the thermometer scratch
-                const bool L0 = v0 && lab0 == 0, L1 = v1 && lab1 == 0;
-                const int kw = (p.kenc + 31) / 32;
-                for (int half = 0; half < 2; ++half) {
-                    const bool isL = half ? L1 : L0;
-                    if (!__ballot_sync(0xffffffffu, isL)) continue;
-                    const int row = row0 + half * 128;
+                // per-bit counts of I^L rows, from the thermometer scratch (OR of the two halves)
+                const bool isL = v && lab == 0;
+                if (__ballot_sync(0xffffffffu, isL)) {
+                    const int kw = (p.kenc + 31) / 32;
                     for (int w = 0; w < kw; ++w) {
-                        const uint32_t tw = isL ? sTw[w * kThreads + row] : 0u;
+                        const uint32_t tw =
+                            isL ? (sTw[w * kThreads + row] | sTw[w * kThreads + row + kRows]) : 0u;
                         uint32_t mine = 0;
 #pragma unroll 4
                         for (int b = 0; b < 32; ++b) {
-                            const uint32_t m = __ballot_sync(0xffffffffu, (tw >> b) & 1u);
-                            if (lane == b) mine = __popc(m);
+                            const uint32_t mm = __ballot_sync(0xffffffffu, (tw >> b) & 1u);
+                            if (lane == b) mine = __popc(mm);
                         }
                         if (mine) atomicAdd(&sCum[w * 32 + lane], mine);
                     }
@@ -577,8 +586,8 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
             long long prev = (long long)ctl.cnt[0];
             for (int k = 1; k <= p.km1; ++k) {
                 const long long cum = (long long)sCum[i * p.km1 + (k - 1)];
-                const long long d = prev - cum;
-                if (d) atomicAdd(&p.grad_counts[(size_t)i * p.K + (k - 1)], (unsigned long long)d);
+                const long long dd = prev - cum;
+                if (dd) atomicAdd(&p.grad_counts[(size_t)i * p.K + (k - 1)], (unsigned long long)dd);
                 prev = cum;
             }
             if (prev) atomicAdd(&p.grad_counts[(size_t)i * p.K + p.km1], (unsigned long long)prev);
@@ -630,9 +639,9 @@ __global__ void encode_tc_kernel(const uint8_t *__restrict__ refs, const int32_t
         }
         bytes[e] = b;
     }
-    const int64_t t = r / kRefTile;
-    const int rr = (int)(r % kRefTile);
-    uint8_t *dst = out + (size_t)t * kRefTile * kp + tile_off(rr, c, kp);
+    const int64_t t = r / kEncTile;
+    const int rr = (int)(r % kEncTile);
+    uint8_t *dst = out + (size_t)t * kEncTile * kp + tile_off(rr, c, kp);
     uint4 v;
     v.x = (uint32_t)bytes[0] | ((uint32_t)bytes[1] << 8) | ((uint32_t)bytes[2] << 16) | ((uint32_t)bytes[3] << 24);
     v.y = (uint32_t)bytes[4] | ((uint32_t)bytes[5] << 8) | ((uint32_t)bytes[6] << 16) | ((uint32_t)bytes[7] << 24);
@@ -655,7 +664,7 @@ bool tc_supported() {
     return cached == 1;
 }
 
-int tc_max_kpad() { return 416; }  // two B stages still fit next to the A tiles
+int tc_max_kpad() { return 512; }  // widest row whose A tile and two 128-wide B stages fit
 
 cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded, int n, int km1, int kpad,
                              bool upper, uint8_t *out, cudaStream_t s, const int32_t *perm) {
@@ -666,8 +675,10 @@ cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded
     return cudaGetLastError();
 }
 
-cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s) {
-    if (p.tc_kpad > tc_max_kpad() || p.tc_kpad % 32 != 0) return cudaErrorNotSupported;
+namespace {
+
+template <int BN>
+cudaError_t launch_tc_bn(const ClassifyParams &p, cudaStream_t s) {
     // dynamic shared memory up to the opt-in limit minus the kernel's static
     // shared memory; set once per device so that captured launches issue nothing else
     static size_t max_dyn[64] = {0};
@@ -677,26 +688,36 @@ cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (max_dyn[dev] == 0) {
         cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, classify_tc_kernel);
+        e = cudaFuncGetAttributes(&fa, classify_tc_kernel<BN>);
         if (e != cudaSuccess) return e;
         int optin = 0;
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return e;
         const size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-        e = cudaFuncSetAttribute(classify_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        e = cudaFuncSetAttribute(classify_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
         if (e != cudaSuccess) return e;
         max_dyn[dev] = lim;
     }
-    const TcSmem plan = tc_smem_plan(p.tc_kpad, p.n * p.km1, kMaxStages);
+    const TcSmem plan = tc_smem_plan(p.tc_kpad, p.n * p.km1, BN, kMaxStages);
     if (plan.nstages < 2) return cudaErrorNotSupported;
-    // at least 120 KB so that two CTAs never share an SM (each takes all 512 TMEM columns)
+    // at least 120 KB so that two CTAs never share an SM (each takes 2*BN TMEM columns)
     const size_t smem = plan.total > 122880u ? plan.total : 122880u;
     if (smem > max_dyn[dev]) return cudaErrorNotSupported;
     const int64_t nblocks = (p.N + kRows - 1) / kRows;
     const int64_t grid = std::min<int64_t>(nblocks, (int64_t)device_sm_count());
     if (grid <= 0) return cudaSuccess;
-    classify_tc_kernel<<<(unsigned)grid, kThreads, smem, s>>>(p);
+    classify_tc_kernel<BN><<<(unsigned)grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+// MMA N = 256 (one instruction covers 256 references) whenever two 256-row
+// B stages fit next to the A tile; narrower 128-row tiles for wider rows.
+cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s) {
+    if (p.tc_kpad > tc_max_kpad() || p.tc_kpad % 32 != 0) return cudaErrorNotSupported;
+    if (tc_smem_plan(p.tc_kpad, p.n * p.km1, 256, kMaxStages).nstages >= 2) return launch_tc_bn<256>(p, s);
+    return launch_tc_bn<128>(p, s);
 }
 
 }  // namespace rsr

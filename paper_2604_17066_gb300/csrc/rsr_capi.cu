@@ -774,6 +774,41 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     return RSR_OK;
 }
 
+int rsr_batch_grad(const rsr_problem *problems, int32_t S, const int64_t *Ns, int64_t *const *grad_counts,
+                   double *const *grad_out, double *const *se_out, rsr_stream_t stream) {
+    if (!problems || S < 1 || !Ns || !grad_counts || !grad_out || !se_out) return RSR_ERR_INVALID_ARG;
+    size_t total = 0;
+    for (int s = 0; s < S; ++s) {
+        int st = validate(&problems[s]);
+        if (st != RSR_OK) return st;
+        if (Ns[s] <= 0 || !grad_counts[s] || !grad_out[s] || !se_out[s]) return RSR_ERR_INVALID_ARG;
+        total += (size_t)problems[s].n * problems[s].K;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::vector<int64_t> C(total);
+    size_t off = 0;
+    for (int s = 0; s < S; ++s) {
+        const size_t nk = (size_t)problems[s].n * problems[s].K;
+        RSR_CUDA(cudaMemcpyAsync(C.data() + off, grad_counts[s], nk * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        off += nk;
+    }
+    RSR_CUDA(cudaStreamSynchronize(st));
+    off = 0;
+    for (int s = 0; s < S; ++s) {
+        const rsr_problem &p = problems[s];
+        const size_t nk = (size_t)p.n * p.K;
+        const double H = (double)Ns[s];
+        for (size_t j = 0; j < nk; ++j) {
+            const double pj = (double)C[off + j] / H;
+            const double q = p.pmf[j];
+            grad_out[s][j] = pj / q;
+            se_out[s][j] = std::sqrt(pj * (1.0 - pj) / H) / q;
+        }
+        off += nk;
+    }
+    return RSR_OK;
+}
+
 int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream, int32_t *chosen_path) {
     int st = validate(problem);
     if (st != RSR_OK) return st;

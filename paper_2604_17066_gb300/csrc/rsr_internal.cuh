@@ -109,7 +109,8 @@ struct WsLayout {
     size_t total = 0;
 };
 
-constexpr int kTcRefTile = 128;  // references per tensor-core B tile (N of the MMA)
+constexpr int kTcRefTile = 128;  // rows per encoded reference tile (the MMA's B is 128 or 256 rows)
+constexpr int kTcRowPad = 256;   // encoded reference rows are padded to this multiple
 
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -125,8 +126,8 @@ inline WsLayout make_layout(int32_t n, int32_t K, int64_t R_L, int64_t R_U, int3
     // survival bias (see classify_tc.cu); rounded up to the 32-byte MMA K step.
     const int bias_cols = (L.kenc + 15) / 16;
     L.tc_kpad = ((L.kenc + bias_cols + kTcKPad - 1) / kTcKPad) * kTcKPad;
-    L.tc_rows_L = ((R_L + kTcRefTile - 1) / kTcRefTile) * kTcRefTile;
-    L.tc_rows_U = ((R_U + kTcRefTile - 1) / kTcRefTile) * kTcRefTile;
+    L.tc_rows_L = ((R_L + kTcRowPad - 1) / kTcRowPad) * kTcRowPad;
+    L.tc_rows_U = ((R_U + kTcRowPad - 1) / kTcRowPad) * kTcRowPad;
     size_t off = align256(sizeof(WsHeader));
     L.off_thr = off;
     off = align256(off + sizeof(unsigned long long) * (size_t)n * (K - 1));

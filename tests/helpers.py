@@ -40,3 +40,12 @@ def run(sess, seed, offset, N, samples=None, grad=True):
     out = sess.classify(seed, offset, N, samples=samples, labels=True, grad=grad, count_tests=True)
     torch.cuda.synchronize()
     return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
+
+
+def tc_executed_tests(n, K, R_L, R_U, N):
+    """Reference tests the tensor-core path executes in dense mode: 128-sample
+    blocks times BN-reference tiles (BN = 256 when a row fits in 320 bytes,
+    else 128), padding included."""
+    bn = 256 if tc_kpad(n, K) <= 320 else 128
+    tiles = -(-R_L // bn) + -(-R_U // bn)
+    return (-(-N // 128)) * 128 * tiles * bn

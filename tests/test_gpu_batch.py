@@ -45,6 +45,20 @@ def test_batch_matches_oracle_and_single_path(rsr):
         assert np.array_equal(single["labels"], lab)
 
 
+def test_batch_grad_matches_oracle(rsr):
+    probs, seeds, offsets, Ns = scenarios()
+    b = make_batch(rsr, probs, seeds, offsets, Ns)
+    rsr.rsr_batch(b)
+    torch.cuda.synchronize()
+    g, se = rsr.rsr_batch_grad(b)
+    for s, p in enumerate(probs):
+        X = O.sample(p.pmf, seeds[s], offsets[s], Ns[s])
+        lab, _ = O.classify(X, p.ref_L, p.ref_U)
+        g_o, se_o = O.grad(O.grad_counts(X, lab, p.K), Ns[s], p.pmf)
+        np.testing.assert_allclose(g[s], g_o, rtol=1e-12, atol=0, equal_nan=True)
+        np.testing.assert_allclose(se[s], se_o, rtol=1e-12, atol=0, equal_nan=True)
+
+
 def test_batch_replay_and_graph_capture(rsr):
     probs, seeds, offsets, Ns = scenarios()
     b = make_batch(rsr, probs, seeds, offsets, Ns)

@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import workloads as W
-from helpers import TC, make_session, random_refs_problem, run, tc_kpad
+from helpers import TC, make_session, random_refs_problem, run, tc_executed_tests, tc_kpad
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -22,12 +22,11 @@ def check(rsr, prob, seed, offset, N, dense, samples=None):
     assert np.array_equal(got["counts3"], cnt), (got["counts3"], cnt)
     assert np.array_equal(got["labels"], lab)
     assert np.array_equal(got["grad_counts"].reshape(prob.n, prob.K), O.grad_counts(X, lab, prob.K))
-    tiles = (-(-prob.R_L // 128)) + (-(-prob.R_U // 128))
-    blocks = -(-N // 256)
+    full = tc_executed_tests(prob.n, prob.K, prob.R_L, prob.R_U, N)
     if dense:
-        assert got["exec_tests"][0] == tiles * blocks * 128 * 256
+        assert got["exec_tests"][0] == full
     else:
-        assert got["exec_tests"][0] <= tiles * blocks * 128 * 256
+        assert got["exec_tests"][0] <= full
     return got
 
 
@@ -43,10 +42,11 @@ def test_tc_grid_exhaustive(rsr):
 
 @pytest.mark.parametrize("n,K,R_L,R_U,N", [(295, 2, 300, 700, 5000), (100, 4, 600, 300, 3001),
                                            (40, 5, 1, 513, 2049), (300, 2, 0, 257, 1000),
-                                           (300, 2, 300, 0, 1000), (3, 3, 2, 2, 1), (120, 3, 130, 129, 257)])
+                                           (300, 2, 300, 0, 1000), (3, 3, 2, 2, 1), (120, 3, 130, 129, 257),
+                                           (120, 4, 300, 600, 3001)])   # 384-byte rows: 128-wide B tiles
 @pytest.mark.parametrize("dense", [True, False])
 def test_tc_random_refs(rsr, n, K, R_L, R_U, N, dense):
-    assert tc_kpad(n, K) <= 416
+    assert tc_kpad(n, K) <= 512
     check(rsr, random_refs_problem(n, K, R_L, R_U, seed=n * 7 + K), 77, 1000, N, dense)
 
 
