@@ -38,6 +38,23 @@ def _peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def _captured_traffic(workload_tag):
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
+    record, if the kernel source is unchanged since the capture (else None)."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "classify_tc_c3_dense_traffic.json")
+    src = os.path.join(ROOT, "paper_2604_17066_gb300", "csrc", "classify_tc.cu")
+    try:
+        d = json.load(open(rec))
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() != d["source_sha1"]:
+            return None
+        if not workload_tag.startswith(d["workload"].split()[0]) or "_N" in workload_tag.split("p0.9")[-1]:
+            return None
+        return float(d["dram_bytes_read"]) + float(d["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def _workload(name):
     import workloads.large as L
     if name == "c3":
@@ -327,7 +344,7 @@ def main():
         achieved = flops / (kern_avg / 1000.0) / 1e12
         peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": _captured_traffic(wname) if P.dense else None,
                 "note": "FP8 dense peak = 2 x bf16 sustained (%s); algorithmic flops = 2*n(K-1)*N*(R_L+R_U)"
                         % peak_src}
     else:
@@ -349,24 +366,30 @@ def main():
         extras["fwd_ms"] = sum(fw) / len(fw)
         extras["fwd_grad_ms"] = ms_step
         extras["fwd_grad_over_fwd"] = ms_step / extras["fwd_ms"]
-        # early exit (production mode) on the same references
+        # early exit (production mode) on the same references, both classifier paths
         if args.workload == "c3":
-            P2 = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=rsr.RSR_PATH_TC, dense=False)
-            s2 = rsr.Session(P2)
-            ee = []
-            for k in range(4):
-                flush.fill_(k)
-                counts.zero_()
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-                e[0].record(stream)
-                rsr.rsr_classify(P2, 1, 7 * N + k * N, N, s2.ws, counts, None, labels, gcounts, None, stream)
-                e[1].record(stream)
-                torch.cuda.synchronize()
-                ee.append(e[0].elapsed_time(e[1]))
-            ee_ms = statistics.median(ee[1:])
-            extras["early_exit"] = {"ms": ee_ms, "samples_per_s": N / (ee_ms / 1000.0),
-                                    "nominal_tests_per_s": N * R / (ee_ms / 1000.0)}
-            del s2
+            ee_all = {}
+            for pname, pth in (("tc", rsr.RSR_PATH_TC), ("popc", rsr.RSR_PATH_POPC)):
+                P2 = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=pth, dense=False)
+                s2 = rsr.Session(P2)
+                ee = []
+                ex = torch.zeros(1, dtype=torch.int64, device=dev)
+                for k in range(4):
+                    flush.fill_(k)
+                    counts.zero_()
+                    ex.zero_()
+                    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                    e[0].record(stream)
+                    rsr.rsr_classify(P2, 1, 7 * N + k * N, N, s2.ws, counts, None, labels, gcounts, ex, stream)
+                    e[1].record(stream)
+                    torch.cuda.synchronize()
+                    ee.append(e[0].elapsed_time(e[1]))
+                ee_ms = statistics.median(ee[1:])
+                ee_all[pname] = {"ms": ee_ms, "samples_per_s": N / (ee_ms / 1000.0),
+                                 "nominal_tests_per_s": N * R / (ee_ms / 1000.0),
+                                 "executed_tests_per_sample": int(ex.item()) / N}
+                del s2
+            extras["early_exit"] = ee_all
         extras["prepare_ms"] = prep_ms
         extras["overlap_pairs"] = bool(overlap)
         if args.workload == "c3" and not args.no_batch:
