@@ -58,6 +58,12 @@ def _load():
             lib.orc_grad.argtypes = [i32, i32, i64, P, P, P, P]
             lib.orc_count_overlaps.argtypes = [i32, i64, P, i64, P]
             lib.orc_count_overlaps.restype = i64
+            lib.orc_phi.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, P, P]
+            lib.orc_phi.restype = ctypes.c_int
+            lib.orc_resolve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, P, ctypes.c_int, i64, P, P]
+            lib.orc_resolve.restype = i64
             _lib = lib
     return _lib
 
@@ -154,6 +160,39 @@ def count_overlaps(ref_L: np.ndarray, ref_U: np.ndarray) -> int:
     ref_U = np.ascontiguousarray(ref_U, dtype=np.uint8)
     n = ref_L.shape[1] if ref_L.ndim == 2 else ref_U.shape[1]
     return int(_load().orc_count_overlaps(n, ref_L.shape[0], _p(ref_L), ref_U.shape[0], _p(ref_U)))
+
+
+# --------------------------------------------------------------------------
+# Stage 2: Phi on the unclassified samples (Sec. 3.5)
+# --------------------------------------------------------------------------
+PHI_ST_CONNECTIVITY = 0
+PHI_ST_MAXFLOW_LEVELS = 1
+
+
+def _graph_args(edges, thresholds):
+    e = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
+    src = np.ascontiguousarray(e[:, 0])
+    dst = np.ascontiguousarray(e[:, 1])
+    thr = np.ascontiguousarray([] if thresholds is None else thresholds, dtype=np.int32)
+    return src, dst, thr
+
+
+def phi(kind: int, n_nodes: int, edges, s: int, t: int, x, thresholds=None) -> int:
+    """System function of one state: s-t connectivity (kind 0) or the s-t
+    max-flow level #{l : flow >= thresholds[l]} (kind 1)."""
+    src, dst, thr = _graph_args(edges, thresholds)
+    xs = np.ascontiguousarray(x, dtype=np.uint8)
+    return int(_load().orc_phi(kind, n_nodes, src.size, _p(src), _p(dst), s, t, thr.size, _p(thr), _p(xs)))
+
+
+def resolve(kind: int, n_nodes: int, edges, s: int, t: int, X, labels, m_prime: int = 0, thresholds=None):
+    """Stage 2: labels 2 become 3 (Phi <= m') or 4; returns (new labels, #3)."""
+    src, dst, thr = _graph_args(edges, thresholds)
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    lab = np.array(labels, dtype=np.uint8, copy=True)
+    lower = _load().orc_resolve(kind, n_nodes, src.size, _p(src), _p(dst), s, t, thr.size, _p(thr), m_prime,
+                                X.shape[0], _p(X), _p(lab))
+    return lab, int(lower)
 
 
 # --------------------------------------------------------------------------

@@ -26,6 +26,7 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
@@ -250,4 +251,123 @@ int64_t orc_count_overlaps(int32_t n, int64_t R_L, const uint8_t *ref_L,
             if (orc_leq(n, ref_U + (size_t)b * n, ref_L + (size_t)a * n))
                 c += 1;
     return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stage 2 (Sec. 3.5): the system function Phi is evaluated for the          */
+/* unclassified samples, and P(S <= m') is estimated from |I^L| plus the      */
+/* unclassified samples with Phi <= m'.  Two system functions of the paper's  */
+/* experiments:                                                               */
+/*   kind 0, s-t connectivity (Sec. 2.2 example, Sec. 4.1): component e is an */
+/*     undirected edge (src[e], dst[e]) that works when x_e = 1;              */
+/*     Phi = 1 if s reaches t over working edges, else 0;                     */
+/*   kind 1, s-t maximum flow (Sec. 2.2, d-MC/d-MP systems): component a is a */
+/*     directed arc src[a] -> dst[a] with capacity x_a; f = max flow s -> t;  */
+/*     Phi = #{ l : f >= thr[l] } for the level thresholds thr[0..L-1].       */
+/* Labels 2 are rewritten to 3 (Phi <= m') or 4 (Phi >= m'+1); the function   */
+/* returns the number of 3s.                                                  */
+/* ------------------------------------------------------------------------ */
+static int orc_st_connected(int n_nodes, int n_edges, const int32_t *src, const int32_t *dst, int s, int t,
+                            const uint8_t *x, int32_t *queue, uint8_t *seen)
+{
+    for (int v = 0; v < n_nodes; ++v) seen[v] = 0;
+    int head = 0, tail = 0;
+    queue[tail++] = s;
+    seen[s] = 1;
+    while (head < tail) {
+        int v = queue[head++];
+        if (v == t) return 1;
+        for (int e = 0; e < n_edges; ++e) {
+            if (!x[e]) continue;
+            int w = -1;
+            if (src[e] == v) w = dst[e];
+            else if (dst[e] == v) w = src[e];
+            if (w >= 0 && !seen[w]) {
+                seen[w] = 1;
+                queue[tail++] = w;
+            }
+        }
+    }
+    return 0;
+}
+
+/* Ford-Fulkerson with breadth-first augmenting paths (Edmonds-Karp). */
+static int orc_max_flow(int n_nodes, int n_arcs, const int32_t *src, const int32_t *dst, int s, int t,
+                        const uint8_t *cap, int32_t *flow, int32_t *queue, int32_t *parent_arc, int8_t *parent_dir)
+{
+    for (int a = 0; a < n_arcs; ++a) flow[a] = 0;
+    int total = 0;
+    while (1) {
+        for (int v = 0; v < n_nodes; ++v) parent_arc[v] = -2;
+        parent_arc[s] = -1;
+        int head = 0, tail = 0;
+        queue[tail++] = s;
+        while (head < tail && parent_arc[t] == -2) {
+            int v = queue[head++];
+            for (int a = 0; a < n_arcs; ++a) {
+                if (src[a] == v && parent_arc[dst[a]] == -2 && flow[a] < cap[a]) {
+                    parent_arc[dst[a]] = a;
+                    parent_dir[dst[a]] = 1;
+                    queue[tail++] = dst[a];
+                } else if (dst[a] == v && parent_arc[src[a]] == -2 && flow[a] > 0) {
+                    parent_arc[src[a]] = a;
+                    parent_dir[src[a]] = -1;
+                    queue[tail++] = src[a];
+                }
+            }
+        }
+        if (parent_arc[t] == -2) break;
+        int bottleneck = 1 << 30;
+        for (int v = t; v != s;) {
+            int a = parent_arc[v];
+            int r = parent_dir[v] > 0 ? cap[a] - flow[a] : flow[a];
+            if (r < bottleneck) bottleneck = r;
+            v = parent_dir[v] > 0 ? src[a] : dst[a];
+        }
+        for (int v = t; v != s;) {
+            int a = parent_arc[v];
+            flow[a] += parent_dir[v] > 0 ? bottleneck : -bottleneck;
+            v = parent_dir[v] > 0 ? src[a] : dst[a];
+        }
+        total += bottleneck;
+    }
+    return total;
+}
+
+int orc_phi(int kind, int n_nodes, int n, const int32_t *src, const int32_t *dst, int s, int t,
+            int n_thr, const int32_t *thr, const uint8_t *x)
+{
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n_nodes + n + 1));
+    uint8_t *seen = (uint8_t *)malloc((size_t)n_nodes + 1);
+    int32_t *flow = (int32_t *)malloc(sizeof(int32_t) * (size_t)n + 4);
+    int32_t *parent_arc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n_nodes + 4);
+    int8_t *parent_dir = (int8_t *)malloc((size_t)n_nodes + 4);
+    int phi;
+    if (kind == 0) {
+        phi = orc_st_connected(n_nodes, n, src, dst, s, t, x, queue, seen);
+    } else {
+        int f = orc_max_flow(n_nodes, n, src, dst, s, t, x, flow, queue, parent_arc, parent_dir);
+        phi = 0;
+        for (int l = 0; l < n_thr; ++l)
+            if (f >= thr[l]) phi += 1;
+    }
+    free(queue); free(seen); free(flow); free(parent_arc); free(parent_dir);
+    return phi;
+}
+
+int64_t orc_resolve(int kind, int n_nodes, int n, const int32_t *src, const int32_t *dst, int s, int t,
+                    int n_thr, const int32_t *thr, int m_prime, int64_t N, const uint8_t *X, uint8_t *labels)
+{
+    int64_t lower = 0;
+    for (int64_t h = 0; h < N; ++h) {
+        if (labels[h] != 2) continue;
+        int phi = orc_phi(kind, n_nodes, n, src, dst, s, t, n_thr, thr, X + (size_t)h * n);
+        if (phi <= m_prime) {
+            labels[h] = 3;
+            lower += 1;
+        } else {
+            labels[h] = 4;
+        }
+    }
+    return lower;
 }
