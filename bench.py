@@ -63,6 +63,9 @@ def _workload(name):
     if name == "c2":
         p = L.c2_rgg()
         return p, 1_000_000, "c2_rgg119n295e_N1e6"
+    if name == "c4":
+        p = L.c4_flow(0)
+        return p, 1_000_000, "c4_flow40n100a_K4_m0_N1e6"
     raise ValueError(name)
 
 
@@ -237,7 +240,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4"])
     ap.add_argument("--ref-samples", type=int, default=8000)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-scenario batched comparison")
@@ -267,6 +270,13 @@ def main():
         wname += "_N%d" % N
     path = rsr.RSR_PATH_TC if args.workload == "c3" else rsr.RSR_PATH_POPC
     P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=(args.workload == "c3"))
+    if args.workload == "c4":
+        # multi-state: let the autotuner pick the classifier path for this problem
+        P.path = rsr.RSR_PATH_AUTO
+        probe = rsr.Session(P)
+        path = rsr.rsr_autotune(P, probe.ws)
+        P.path = path
+        del probe
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     sess = rsr.Session(P)
@@ -281,18 +291,39 @@ def main():
     exec_t = torch.zeros(1, dtype=torch.int64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
+    # Stage 2 (Sec. 3.5) for the graph workloads: Phi on the unclassified samples, on the device
+    system = None
+    if args.workload == "c2":
+        system = rsr.System(rsr.RSR_PHI_ST_CONNECTIVITY, prob.meta["n_nodes"], prob.meta["edges"],
+                            prob.meta["s"], prob.meta["t"])
+    elif args.workload == "c4":
+        system = rsr.System(rsr.RSR_PHI_ST_MAXFLOW_LEVELS, prob.meta["n_nodes"], prob.meta["arcs"],
+                            prob.meta["s"], prob.meta["t"], (prob.meta["l1"], prob.meta["l2"]), prob.meta["m_prime"])
+    uidx = torch.empty(n_rank, dtype=torch.int64, device=dev)
+    c2 = torch.zeros(2, dtype=torch.int64, device=dev)
+    stage2_ms = []
+
     def step(k, grad=True, ev=None):
         counts.zero_()
         gcounts.zero_()
+        off = offset + k * N * world
         if ev is not None:
             ev[0].record(stream)
-        rsr.rsr_classify(P, 1, offset + k * N * world, n_rank, sess.ws, counts, None, labels,
+        rsr.rsr_classify(P, 1, off, n_rank, sess.ws, counts, None, labels,
                          gcounts if grad else None, exec_t, stream)
         if ev is not None:
             ev[1].record(stream)
+        n_ul = 0
+        if system is not None:
+            c2.zero_()
+            rsr.rsr_resolve(P, system, 1, off, n_rank, labels, sess.ws, u_lower_idx=uidx, counts2=c2, stream=stream)
+            if ev is not None:
+                ev[4].record(stream)
+            n_ul = int(c2[0].item())
         if grad:
-            rsr.rsr_grad(P, 1, offset + k * N * world, n_rank, gcounts, sess.ws, stream=stream)
-        est = rsr.rsr_estimate(counts.cpu().numpy(), n_rank)
+            rsr.rsr_grad(P, 1, off, n_rank, gcounts, sess.ws, u_lower_idx=uidx[:n_ul] if n_ul else None,
+                         stream=stream)
+        est = rsr.rsr_estimate(counts.cpu().numpy(), n_rank, n_ul)
         return est
 
     for k in range(args.warmup):
@@ -314,14 +345,16 @@ def main():
         torch.cuda.synchronize()
         for k in range(args.steps):
             flush.fill_(k & 0xFF)                      # L2 flush between timed steps (not timed)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             ev[2].record(stream)
             est = step(args.warmup + k, grad=True, ev=ev)
             ev[3].record(stream)
             torch.cuda.synchronize()
-            launches += 1
+            launches += 2 if system is not None else 1
             kern_ms.append(ev[0].elapsed_time(ev[1]))
             step_ms.append(ev[2].elapsed_time(ev[3]))
+            if system is not None:
+                stage2_ms.append(ev[1].elapsed_time(ev[4]))
     torch.cuda.synchronize()
     exec_tests = int(exec_t.item())
     total_ms = sum(step_ms)
@@ -333,23 +366,35 @@ def main():
     ms_step = total_ms / args.steps
     value = world * n_rank / (ms_step / 1000.0)
 
-    # roofline of the classifier kernel: algorithmic flops (tensor path) or tests
+    # roofline of the classifier kernel.  Tensor path: algorithmic flops 2*n(K-1) per
+    # dominance test (all N*(R_L+R_U) tests in dense mode, the executed ones otherwise).
+    # Bit-packed path: an integer-op model, 80 ops per Philox4x32-10 block (10 rounds of two
+    # 32x32->64 products, two 3-input xors, two key adds), n(K-1) threshold compares per
+    # sample, ceil(n(K-1)/32) + 1 ops per executed test; peak = SMs x 128 lanes x max clock.
     peaks, peak_src = _peaks()
     R = P.R_L + P.R_U
     kenc = P.n * (P.K - 1)
     kern_avg = sum(kern_ms) / len(kern_ms)
     tests_per_launch = n_rank * R
+    exec_per_launch = exec_tests / args.steps
     if path == rsr.RSR_PATH_TC:
-        flops = 2.0 * kenc * tests_per_launch
+        work_tests = tests_per_launch if P.dense else exec_per_launch
+        flops = 2.0 * kenc * work_tests
         achieved = flops / (kern_avg / 1000.0) / 1e12
         peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _captured_traffic(wname) if P.dense else None,
-                "note": "FP8 dense peak = 2 x bf16 sustained (%s); algorithmic flops = 2*n(K-1)*N*(R_L+R_U)"
-                        % peak_src}
+                "note": "FP8 dense peak = 2 x bf16 sustained (%s); flops = 2*n(K-1)*%s tests"
+                        % (peak_src, "N*(R_L+R_U)" if P.dense else "executed")}
     else:
-        roof = {"bound": "alu", "achieved": tests_per_launch / (kern_avg / 1000.0) / 1e12, "peak": None,
-                "unit": "Ttests/s", "frac": None, "traffic": None}
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        ops = n_rank * (((P.n + 3) // 4) * 80 + kenc) + exec_per_launch * ((kenc + 31) // 32 + 1)
+        achieved = ops / (kern_avg / 1000.0) / 1e12
+        peak = sms * 128 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": None, "note": "integer-op model (80 per Philox block, n(K-1) compares per sample, "
+                                         "ceil(n(K-1)/32)+1 per executed test); peak = SMs x 128 x max SM clock"}
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -392,6 +437,10 @@ def main():
             extras["early_exit"] = ee_all
         extras["prepare_ms"] = prep_ms
         extras["overlap_pairs"] = bool(overlap)
+        if stage2_ms:
+            extras["stage2"] = {"resolve_ms": sum(stage2_ms) / len(stage2_ms), "n_u": int(c2.sum().item()),
+                                "note": "Phi evaluated on the device for every unclassified sample; the step "
+                                        "estimate is the Stage-2 P(S<=m')"}
         if args.workload == "c3" and not args.no_batch:
             extras["batch_c5"] = bench_batch(rsr, torch, N=200_000)
             extras["batch_c5_N2e4"] = bench_batch(rsr, torch, N=20_000)
@@ -409,15 +458,23 @@ def main():
             sess.set_pmf(prob.pmf)                     # host thresholds -> device
             counts.zero_()
             gcounts.zero_()
-            rsr.rsr_classify(P, 1, 11 * N + k * N, n_rank, sess.ws, counts, None, labels, gcounts, None, stream)
+            off_k = 11 * N + k * N
+            rsr.rsr_classify(P, 1, off_k, n_rank, sess.ws, counts, None, labels, gcounts, None, stream)
+            n_ul = 0
+            if system is not None:
+                c2.zero_()
+                rsr.rsr_resolve(P, system, 1, off_k, n_rank, labels, sess.ws, u_lower_idx=uidx, counts2=c2,
+                                stream=stream)
+                n_ul = int(c2[0].item())
             lab_host.copy_(labels, non_blocking=True)
             cnt_host.copy_(counts, non_blocking=True)
-            g, se = rsr.rsr_grad(P, 1, 11 * N + k * N, n_rank, gcounts, sess.ws, stream=stream)   # syncs
-            rsr.rsr_estimate(cnt_host.numpy(), n_rank)
+            g, se = rsr.rsr_grad(P, 1, off_k, n_rank, gcounts, sess.ws,
+                                 u_lower_idx=uidx[:n_ul] if n_ul else None, stream=stream)   # syncs
+            rsr.rsr_estimate(cnt_host.numpy(), n_rank, n_ul)
             times.append(time.perf_counter() - t0)
         e2e_s = statistics.median(times)
         e2e = {"value": n_rank / e2e_s, "unit": UNIT, "h2d_bytes_per_step": P.n * (P.K - 1) * 8,
-               "d2h_bytes_per_step": n_rank + 3 * 8 + P.n * P.K * 8}
+               "d2h_bytes_per_step": n_rank + 3 * 8 + P.n * P.K * 8 + (16 if system is not None else 0)}
 
     cpu = None
     if rank == 0:

@@ -266,6 +266,48 @@ RSR_API int rsr_classify_static(const rsr_problem *problem, uint64_t seed, uint6
                                 const uint8_t *samples_or_null, uint8_t *labels_or_null, int64_t *counts3,
                                 int64_t *grad_counts_or_null, rsr_stream_t stream);
 
+/*
+ * Stage 2 on the device (Sec. 3.5): evaluate the system function Phi for the
+ * unclassified samples so that P(S <= m') is estimated without the host.
+ * Built-in system functions (the families of the paper's experiments):
+ *   RSR_PHI_ST_CONNECTIVITY   K = 2; component i is the undirected edge
+ *                             (src[i], dst[i]), working when x_i = 1;
+ *                             Phi = 1 iff s reaches t over working edges.
+ *   RSR_PHI_ST_MAXFLOW_LEVELS component i is the directed arc src[i] -> dst[i]
+ *                             with capacity x_i; Phi = #{l : maxflow(s->t) >= level_thr[l]}
+ *                             (level_thr ascending, n_levels <= 8).
+ * Limits: n_nodes <= 1024.  src/dst: device int32[n].
+ */
+#define RSR_PHI_ST_CONNECTIVITY 0
+#define RSR_PHI_ST_MAXFLOW_LEVELS 1
+
+typedef struct rsr_system {
+    int32_t kind;
+    int32_t n_nodes;
+    const int32_t *src;
+    const int32_t *dst;
+    int32_t s, t;
+    int32_t n_levels;
+    int32_t level_thr[8];
+    int32_t m_prime;
+} rsr_system;
+
+/*
+ * For every sample with label 2 in labels[0..N) (device, from rsr_classify on
+ * samples offset..offset+N-1 of `seed`), regenerate its states, evaluate Phi
+ * and relabel it 3 (Phi <= m', i.e. S <= m') or 4 (S >= m'+1).
+ *   u_lower_idx : device int64[cap]; the local indices of the 3s are appended in
+ *                 no particular order (pass them to rsr_grad).  If more than cap
+ *                 samples resolve lower, the extra indices are dropped and the
+ *                 workspace error word is set (rsr_workspace_status); counts stay exact.
+ *   counts2     : device int64[2], += (#3, #4); n_u_lower for rsr_estimate is counts2[0].
+ * Bad node indices in src/dst are dropped and flagged in the error word.
+ * Asynchronous on `stream`; `ws` must be prepared for `problem`.
+ */
+RSR_API int rsr_resolve(const rsr_problem *problem, const rsr_system *system, uint64_t seed, uint64_t offset,
+                        int64_t N, uint8_t *labels, int64_t *u_lower_idx, int64_t cap, int64_t *counts2,
+                        void *ws, size_t ws_bytes, rsr_stream_t stream);
+
 /* Message for a status code (static storage). */
 RSR_API const char *rsr_status_string(int status);
 

@@ -13,7 +13,8 @@ __all__ = [
     "rsr_workspace_size", "rsr_prepare", "rsr_update_pmf", "rsr_classify", "rsr_estimate",
     "rsr_grad", "rsr_sample", "rsr_workspace_status",
     "Batch", "rsr_batch_prepare", "rsr_batch", "rsr_batch_autotune", "rsr_autotune",
-    "rsr_classify_static", "rsr_batch_grad",
+    "rsr_classify_static", "rsr_batch_grad", "System", "rsr_resolve",
+    "RSR_PHI_ST_CONNECTIVITY", "RSR_PHI_ST_MAXFLOW_LEVELS",
     "RSR_PATH_AUTO", "RSR_PATH_POPC", "RSR_PATH_TC", "RSR_FLAG_DENSE",
 ]
 

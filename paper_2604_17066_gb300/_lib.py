@@ -38,6 +38,24 @@ class rsr_problem(ctypes.Structure):
     ]
 
 
+RSR_PHI_ST_CONNECTIVITY = 0
+RSR_PHI_ST_MAXFLOW_LEVELS = 1
+
+
+class rsr_system(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("n_nodes", ctypes.c_int32),
+        ("src", ctypes.c_void_p),
+        ("dst", ctypes.c_void_p),
+        ("s", ctypes.c_int32),
+        ("t", ctypes.c_int32),
+        ("n_levels", ctypes.c_int32),
+        ("level_thr", ctypes.c_int32 * 8),
+        ("m_prime", ctypes.c_int32),
+    ]
+
+
 class rsr_estimate_out(ctypes.Structure):
     _fields_ = [(name, ctypes.c_double) for name in (
         "pL", "pU", "pu", "P_lower", "P_upper", "cov_pL", "cov_pU", "cov_pu", "cov_lower", "cov_upper")]
@@ -63,6 +81,8 @@ SIGNATURES = {
     "rsr_autotune": (ctypes.c_int, [_PROB, _P, _S, _P, _P]),
     "rsr_batch_grad": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P]),
     "rsr_classify_static": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _P, _P, _P]),
+    "rsr_resolve": (ctypes.c_int, [_PROB, ctypes.POINTER(rsr_system), _U64, _U64, _I64, _P, _P, _I64, _P, _P, _S,
+                                   _P]),
     "rsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rsr_last_cuda_error": (ctypes.c_char_p, []),
 }

@@ -15,7 +15,8 @@ import torch
 
 from . import _lib
 from ._lib import (RSR_FLAG_DENSE, RSR_PATH_AUTO, RSR_PATH_POPC, RSR_PATH_TC,  # noqa: F401
-                   RSRError, check, rsr_estimate_out, rsr_problem)
+                   RSR_PHI_ST_CONNECTIVITY, RSR_PHI_ST_MAXFLOW_LEVELS, RSRError, check, rsr_estimate_out,
+                   rsr_problem, rsr_system)
 
 
 def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
@@ -304,3 +305,49 @@ def rsr_classify_static(problem: Problem, seed: int, offset: int, N: int, counts
     check(_lib.load().rsr_classify_static(ctypes.byref(s), int(seed), int(offset), int(N), _ptr(samples),
                                           _ptr(labels), _ptr(counts3), _ptr(grad_counts), _stream(stream)),
           "rsr_classify_static")
+
+
+class System:
+    """A built-in system function for Stage 2: s-t connectivity over undirected
+    edges (binary components) or s-t max-flow levels over directed arcs
+    (component state = capacity).  edges: n x 2 node indices, one row per
+    component."""
+
+    def __init__(self, kind: int, n_nodes: int, edges, s: int, t: int, level_thr=(), m_prime: int = 0,
+                 device: Optional[torch.device] = None):
+        e = np.asarray(edges, dtype=np.int32).reshape(-1, 2)
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.src = torch.from_numpy(np.ascontiguousarray(e[:, 0])).to(dev)
+        self.dst = torch.from_numpy(np.ascontiguousarray(e[:, 1])).to(dev)
+        self.kind, self.n_nodes, self.s, self.t = int(kind), int(n_nodes), int(s), int(t)
+        self.level_thr = [int(v) for v in level_thr]
+        self.m_prime = int(m_prime)
+
+    def struct(self) -> rsr_system:
+        st = rsr_system()
+        st.kind, st.n_nodes = self.kind, self.n_nodes
+        st.src, st.dst = self.src.data_ptr(), self.dst.data_ptr()
+        st.s, st.t = self.s, self.t
+        st.n_levels = len(self.level_thr)
+        for i, v in enumerate(self.level_thr):
+            st.level_thr[i] = v
+        st.m_prime = self.m_prime
+        return st
+
+
+def rsr_resolve(problem: Problem, system: System, seed: int, offset: int, N: int, labels: torch.Tensor,
+                ws: torch.Tensor, u_lower_idx: Optional[torch.Tensor] = None, counts2: Optional[torch.Tensor] = None,
+                stream=None):
+    """Stage 2: relabel unclassified samples 3 (S <= m') or 4 by evaluating Phi
+    on the device; returns (u_lower_idx, counts2) device tensors."""
+    dev = labels.device
+    if u_lower_idx is None:
+        u_lower_idx = torch.empty(max(int(N), 1), dtype=torch.int64, device=dev)
+    if counts2 is None:
+        counts2 = torch.zeros(2, dtype=torch.int64, device=dev)
+    s = problem.struct()
+    g = system.struct()
+    check(_lib.load().rsr_resolve(ctypes.byref(s), ctypes.byref(g), int(seed), int(offset), int(N), _ptr(labels),
+                                  _ptr(u_lower_idx), u_lower_idx.numel(), _ptr(counts2), _ptr(ws), ws.numel(),
+                                  _stream(stream)), "rsr_resolve")
+    return u_lower_idx, counts2

@@ -398,6 +398,35 @@ int rsr_grad(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t
     return RSR_OK;
 }
 
+int rsr_resolve(const rsr_problem *problem, const rsr_system *system, uint64_t seed, uint64_t offset, int64_t N,
+                uint8_t *labels, int64_t *u_lower_idx, int64_t cap, int64_t *counts2, void *ws, size_t ws_bytes,
+                rsr_stream_t stream) {
+    int st = validate(problem);
+    if (st != RSR_OK) return st;
+    if (!system || N < 0 || !labels || !counts2 || cap < 0 || (cap > 0 && !u_lower_idx)) return RSR_ERR_INVALID_ARG;
+    if (system->kind != RSR_PHI_ST_CONNECTIVITY && system->kind != RSR_PHI_ST_MAXFLOW_LEVELS)
+        return RSR_ERR_INVALID_ARG;
+    if (system->n_nodes < 1 || system->n_nodes > resolve_max_nodes()) return RSR_ERR_UNSUPPORTED;
+    if (!system->src || !system->dst || system->s < 0 || system->s >= system->n_nodes || system->t < 0 ||
+        system->t >= system->n_nodes)
+        return RSR_ERR_INVALID_ARG;
+    if (system->kind == RSR_PHI_ST_CONNECTIVITY && problem->K != 2) return RSR_ERR_INVALID_ARG;
+    if (system->n_levels < 0 || system->n_levels > 8 || system->m_prime < 0) return RSR_ERR_INVALID_ARG;
+    for (int l = 1; l < system->n_levels; ++l)
+        if (system->level_thr[l] < system->level_thr[l - 1]) return RSR_ERR_INVALID_ARG;
+    const WsLayout L = layout_of(problem);
+    if ((st = check_ws(L, ws, ws_bytes)) != RSR_OK) return st;
+    if ((st = check_prepared(problem, ws)) != RSR_OK) return st;
+    if (N == 0) return RSR_OK;
+    ClassifyParams c = make_params(problem, L, ws);
+    c.N = N;
+    c.seed = seed;
+    c.offset = offset;
+    RSR_CUDA(launch_resolve(c, *system, labels, u_lower_idx, cap, reinterpret_cast<unsigned long long *>(counts2),
+                            reinterpret_cast<cudaStream_t>(stream)));
+    return RSR_OK;
+}
+
 int rsr_sample(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N, uint8_t *states, void *ws,
                size_t ws_bytes, rsr_stream_t stream) {
     int st = validate(problem);

@@ -30,6 +30,11 @@ cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s);
 bool tc_supported();
 int tc_max_kpad();
 
+// Stage 2 (resolve.cu).
+cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8_t *labels, int64_t *u_lower_idx,
+                           int64_t cap, unsigned long long *counts2, cudaStream_t s);
+int resolve_max_nodes();
+
 int device_sm_count();
 
 }  // namespace rsr
