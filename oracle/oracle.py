@@ -64,6 +64,10 @@ def _load():
             lib.orc_resolve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, P, ctypes.c_int, i64, P, P]
             lib.orc_resolve.restype = i64
+            lib.orc_boundary_search.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int,
+                                                ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P]
+            lib.orc_boundary_search.restype = ctypes.c_int
+            lib.orc_nondominated.argtypes = [ctypes.c_int, i64, P, ctypes.c_int, P]
             _lib = lib
     return _lib
 
@@ -167,6 +171,8 @@ def count_overlaps(ref_L: np.ndarray, ref_U: np.ndarray) -> int:
 # --------------------------------------------------------------------------
 PHI_ST_CONNECTIVITY = 0
 PHI_ST_MAXFLOW_LEVELS = 1
+PHI_GLOBAL_CONNECTIVITY = 2
+PHI_GLOBAL_CONN_LEVEL = 3
 
 
 def _graph_args(edges, thresholds):
@@ -193,6 +199,84 @@ def resolve(kind: int, n_nodes: int, edges, s: int, t: int, X, labels, m_prime: 
     lower = _load().orc_resolve(kind, n_nodes, src.size, _p(src), _p(dst), s, t, thr.size, _p(thr), m_prime,
                                 X.shape[0], _p(X), _p(lab))
     return lab, int(lower)
+
+
+# --------------------------------------------------------------------------
+# Stage 1: reference-state search (Sec. 3.4, 3.5)
+# --------------------------------------------------------------------------
+def boundary_search(kind: int, n_nodes: int, edges, s: int, t: int, x, K: int, m_prime: int = 0,
+                    thresholds=None):
+    """Componentwise boundary search from state x: (side, reference, #Phi evaluations),
+    side 0 = lower reference (Phi(x) <= m'), 1 = upper."""
+    src, dst, thr = _graph_args(edges, thresholds)
+    xs = np.ascontiguousarray(x, dtype=np.uint8)
+    out = np.zeros_like(xs)
+    ev = np.zeros(1, dtype=np.int64)
+    side = _load().orc_boundary_search(kind, n_nodes, src.size, _p(src), _p(dst), s, t, thr.size, _p(thr),
+                                       m_prime, K, _p(xs), _p(out), _p(ev))
+    return int(side), out, int(ev[0])
+
+
+def nondominated(refs, upper: bool) -> np.ndarray:
+    """keep mask of the non-dominated references of one side (first of equal ones kept)."""
+    refs = np.ascontiguousarray(refs, dtype=np.uint8)
+    R = refs.shape[0]
+    keep = np.zeros(R, dtype=np.uint8)
+    if R:
+        _load().orc_nondominated(refs.shape[1], R, _p(refs), 1 if upper else 0, _p(keep))
+    return keep.astype(bool)
+
+
+def stage1(pmf, kind: int, n_nodes: int, edges, s: int, t: int, seed: int, N: int, max_starts: int,
+           eps_u: float, R_max: int, max_rounds: int, m_prime: int = 0, thresholds=None,
+           ref_L=None, ref_U=None):
+    """Stage 1 of the RSR workflow (Sec. 3.5), with many searches per round.
+
+    Round r draws samples r*N .. r*N+N-1 (Philox stream `seed`) and classifies
+    them against the current references.  It stops when the unclassified
+    fraction is below eps_u, when R_L + R_U >= R_max, or after max_rounds.
+    Otherwise the first min(max_starts, #unclassified, R_max - R) unclassified
+    samples in index order (a uniform random choice, the samples being i.i.d.)
+    each start a componentwise boundary search.  The new references are
+    appended to their side in start order, and each side is reduced to its
+    non-dominated elements (order kept).
+
+    Returns dict(ref_L, ref_U, history=[(n_unclassified, R_L, R_U, n_starts)],
+    stop=0 converged | 1 R_max | 2 max_rounds, phi_evals)."""
+    pmf = np.asarray(pmf, dtype=np.float64)
+    n, K = pmf.shape
+    L = np.zeros((0, n), np.uint8) if ref_L is None else np.array(ref_L, dtype=np.uint8).reshape(-1, n)
+    U = np.zeros((0, n), np.uint8) if ref_U is None else np.array(ref_U, dtype=np.uint8).reshape(-1, n)
+    hist = []
+    evals = 0
+    stop = 2
+    for r in range(max_rounds):
+        X = sample(pmf, seed, r * N, N)
+        lab, cnt = classify(X, L, U)
+        n_u = int(cnt[2])
+        R = L.shape[0] + U.shape[0]
+        if n_u < eps_u * N:
+            hist.append((n_u, L.shape[0], U.shape[0], 0))
+            stop = 0
+            break
+        if R >= R_max:
+            hist.append((n_u, L.shape[0], U.shape[0], 0))
+            stop = 1
+            break
+        starts = np.flatnonzero(lab == 2)[:min(max_starts, R_max - R)]
+        hist.append((n_u, L.shape[0], U.shape[0], int(starts.size)))
+        newL, newU = [], []
+        for h in starts:
+            side, ref, ev = boundary_search(kind, n_nodes, edges, s, t, X[h], K, m_prime, thresholds)
+            evals += ev
+            (newL if side == 0 else newU).append(ref)
+        if newL:
+            L = np.concatenate([L, np.array(newL, dtype=np.uint8)])
+            L = L[nondominated(L, upper=False)]
+        if newU:
+            U = np.concatenate([U, np.array(newU, dtype=np.uint8)])
+            U = U[nondominated(U, upper=True)]
+    return dict(ref_L=L, ref_U=U, history=hist, stop=stop, phi_evals=evals)
 
 
 # --------------------------------------------------------------------------

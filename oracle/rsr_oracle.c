@@ -17,6 +17,11 @@
  *     the p^L / p^U / p^u definitions and Algorithm 1
  *   - count estimators p_hat = |I|/H and c.o.v. sqrt((1-p)/(H p)): Sec. 3.3
  *   - Stage 2 estimate of P(S <= m') after resolving I^u with Phi: Sec. 3.5
+ *   - componentwise boundary search for new reference states: Sec. 3.4
+ *   - non-dominated reference sets: Sec. 2.2, Eqs. (2)-(3)
+ *   - system functions of the experiments: s-t connectivity (Sec. 4.1-4.2),
+ *     global connectivity (Sec. 4.3), s-t maximum-flow levels (d-MC / d-MP
+ *     systems, Sec. 2.2) and the three-state global connectivity level (Sec. 4.6)
  * Not in the paper (defined by this build, see the function comments):
  *   - the sampler (Philox4x32-10 counter layout and integer inverse-CDF
  *     thresholds); the paper only states that P(X) is available (Sec. 3.1)
@@ -334,6 +339,39 @@ static int orc_max_flow(int n_nodes, int n_arcs, const int32_t *src, const int32
     return total;
 }
 
+/* Number of nodes reached from node 0 over working edges, edge `skip` left out
+ * (skip = -1: none).  Breadth-first search over the undirected edge list. */
+static int orc_reached_from_0(int n_nodes, int n_edges, const int32_t *src, const int32_t *dst,
+                              const uint8_t *x, int skip, int32_t *queue, uint8_t *seen)
+{
+    for (int v = 0; v < n_nodes; ++v) seen[v] = 0;
+    int head = 0, tail = 0;
+    queue[tail++] = 0;
+    seen[0] = 1;
+    while (head < tail) {
+        int v = queue[head++];
+        for (int e = 0; e < n_edges; ++e) {
+            if (!x[e] || e == skip) continue;
+            int w = -1;
+            if (src[e] == v) w = dst[e];
+            else if (dst[e] == v) w = src[e];
+            if (w >= 0 && !seen[w]) {
+                seen[w] = 1;
+                queue[tail++] = w;
+            }
+        }
+    }
+    return tail;
+}
+
+/* Further system functions (binary components = undirected edges):
+ *   kind 2, global connectivity (Sec. 4.3): Phi = 1 if every node is
+ *     connected to every other over working edges, else 0;
+ *   kind 3, global connectivity level (Sec. 4.6): Phi = 0 if disconnected,
+ *     1 if connected but some pair of nodes has only one edge-disjoint path,
+ *     2 if every pair has two or more.  By Menger's theorem the last case is
+ *     "no single working edge disconnects the graph", which is tested here by
+ *     removing each working edge in turn. */
 int orc_phi(int kind, int n_nodes, int n, const int32_t *src, const int32_t *dst, int s, int t,
             int n_thr, const int32_t *thr, const uint8_t *x)
 {
@@ -345,11 +383,18 @@ int orc_phi(int kind, int n_nodes, int n, const int32_t *src, const int32_t *dst
     int phi;
     if (kind == 0) {
         phi = orc_st_connected(n_nodes, n, src, dst, s, t, x, queue, seen);
-    } else {
+    } else if (kind == 1) {
         int f = orc_max_flow(n_nodes, n, src, dst, s, t, x, flow, queue, parent_arc, parent_dir);
         phi = 0;
         for (int l = 0; l < n_thr; ++l)
             if (f >= thr[l]) phi += 1;
+    } else {
+        phi = orc_reached_from_0(n_nodes, n, src, dst, x, -1, queue, seen) == n_nodes ? 1 : 0;
+        if (kind == 3 && phi == 1) {
+            phi = 2;
+            for (int e = 0; e < n && phi == 2; ++e)
+                if (x[e] && orc_reached_from_0(n_nodes, n, src, dst, x, e, queue, seen) < n_nodes) phi = 1;
+        }
     }
     free(queue); free(seen); free(flow); free(parent_arc); free(parent_dir);
     return phi;
@@ -370,4 +415,72 @@ int64_t orc_resolve(int kind, int n_nodes, int n, const int32_t *src, const int3
         }
     }
     return lower;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Componentwise boundary search (Sec. 3.4).  From a state x with           */
+/* Phi(x) <= m', the components are visited in index order; each is raised  */
+/* one state at a time, Phi re-evaluated after every step, until it reaches */
+/* the top state K-1 or the step makes Phi > m', in which case that step is */
+/* undone and the next component is visited.  A state with Phi(x) >= m'+1  */
+/* is lowered in the same way.  The final state is a lower (side 0) or      */
+/* upper (side 1) boundary reference state.  *phi_evals receives the number */
+/* of Phi evaluations, the first one included.                              */
+/* ------------------------------------------------------------------------ */
+int orc_boundary_search(int kind, int n_nodes, int n, const int32_t *src, const int32_t *dst, int s, int t,
+                        int n_thr, const int32_t *thr, int m_prime, int K, const uint8_t *x_in, uint8_t *x_out,
+                        int64_t *phi_evals)
+{
+    int64_t evals = 0;
+    for (int i = 0; i < n; ++i) x_out[i] = x_in[i];
+    const int lower = orc_phi(kind, n_nodes, n, src, dst, s, t, n_thr, thr, x_out) <= m_prime;
+    evals += 1;
+    for (int i = 0; i < n; ++i) {
+        if (lower) {
+            while (x_out[i] < K - 1) {
+                x_out[i] += 1;
+                evals += 1;
+                if (orc_phi(kind, n_nodes, n, src, dst, s, t, n_thr, thr, x_out) > m_prime) {
+                    x_out[i] -= 1;
+                    break;
+                }
+            }
+        } else {
+            while (x_out[i] > 0) {
+                x_out[i] -= 1;
+                evals += 1;
+                if (orc_phi(kind, n_nodes, n, src, dst, s, t, n_thr, thr, x_out) <= m_prime) {
+                    x_out[i] += 1;
+                    break;
+                }
+            }
+        }
+    }
+    if (phi_evals) *phi_evals = evals;
+    return lower ? 0 : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Non-dominated references (Sec. 2.2, Eqs. (2)-(3)).  A lower reference    */
+/* r_j is redundant when another lower reference r_i satisfies r_j <= r_i   */
+/* componentwise; an upper reference r_j when another upper reference r_i   */
+/* satisfies r_j >= r_i.  Of identical references only the first (lowest    */
+/* index) is kept.  keep[j] = 1 for the references that remain.             */
+/* ------------------------------------------------------------------------ */
+void orc_nondominated(int n, int64_t R, const uint8_t *refs, int upper, uint8_t *keep)
+{
+    for (int64_t j = 0; j < R; ++j) {
+        const uint8_t *rj = refs + (size_t)j * n;
+        keep[j] = 1;
+        for (int64_t i = 0; i < R && keep[j]; ++i) {
+            if (i == j) continue;
+            const uint8_t *ri = refs + (size_t)i * n;
+            int dominated = 1, equal = 1;
+            for (int k = 0; k < n; ++k) {
+                if (upper ? (rj[k] < ri[k]) : (rj[k] > ri[k])) dominated = 0;
+                if (rj[k] != ri[k]) equal = 0;
+            }
+            if (dominated && (!equal || i < j)) keep[j] = 0;
+        }
+    }
 }
