@@ -276,10 +276,19 @@ RSR_API int rsr_classify_static(const rsr_problem *problem, uint64_t seed, uint6
  *   RSR_PHI_ST_MAXFLOW_LEVELS component i is the directed arc src[i] -> dst[i]
  *                             with capacity x_i; Phi = #{l : maxflow(s->t) >= level_thr[l]}
  *                             (level_thr ascending, n_levels <= 8).
- * Limits: n_nodes <= 1024.  src/dst: device int32[n].
+ *   RSR_PHI_GLOBAL_CONNECTIVITY  K = 2; edges as for s-t connectivity; Phi = 1 iff
+ *                             the working edges connect all n_nodes nodes (Sec. 4.3).
+ *   RSR_PHI_GLOBAL_CONN_LEVEL K = 2; Phi = 0 if the working edges leave the nodes
+ *                             disconnected, 1 if connected but some working edge is
+ *                             a bridge (some pair of nodes has a single
+ *                             edge-disjoint path), 2 otherwise (Sec. 4.6).
+ * s and t are read by the s-t kinds only but must lie in [0, n_nodes) for every
+ * kind.  Limits: n_nodes <= 1024.  src/dst: device int32[n].
  */
 #define RSR_PHI_ST_CONNECTIVITY 0
 #define RSR_PHI_ST_MAXFLOW_LEVELS 1
+#define RSR_PHI_GLOBAL_CONNECTIVITY 2
+#define RSR_PHI_GLOBAL_CONN_LEVEL 3
 
 typedef struct rsr_system {
     int32_t kind;
@@ -307,6 +316,88 @@ typedef struct rsr_system {
 RSR_API int rsr_resolve(const rsr_problem *problem, const rsr_system *system, uint64_t seed, uint64_t offset,
                         int64_t N, uint8_t *labels, int64_t *u_lower_idx, int64_t cap, int64_t *counts2,
                         void *ws, size_t ws_bytes, rsr_stream_t stream);
+
+/*
+ * Stage 1 building block (Sec. 3.4): componentwise boundary search.  For each
+ * j < n_starts, sample offset + starts[j] of `seed` is regenerated (same
+ * sampler as rsr_classify).  If Phi(x) <= m' its components are raised in
+ * index order, one state at a time with Phi re-evaluated after each step, until
+ * the top state or until a step makes Phi > m' (that step is undone); otherwise
+ * they are lowered in the same way while Phi >= m'+1 holds.  The final state is
+ * a boundary reference state.
+ *   problem   : n, K, pmf are read (references are not).
+ *   starts    : device int64[n_starts], sample indices relative to offset.
+ *   refs_out  : device uint8[n_starts*n], row j = the reference found from start j.
+ *   side_out  : device uint8[n_starts], 0 = lower reference (S <= m'), 1 = upper.
+ *   phi_evals : device int64[1], += number of Phi evaluations (NULL: not counted).
+ *   ws        : device, rsr_search_workspace_size(problem) bytes, 256-byte aligned;
+ *               the call writes the sampler thresholds into it (not prepared).
+ * Asynchronous on `stream`.  Bad node indices set the error word of `ws`.
+ */
+RSR_API size_t rsr_search_workspace_size(const rsr_problem *problem);
+RSR_API int rsr_boundary_search(const rsr_problem *problem, const rsr_system *system, uint64_t seed,
+                                uint64_t offset, const int64_t *starts, int64_t n_starts, uint8_t *refs_out,
+                                uint8_t *side_out, int64_t *phi_evals, void *ws, size_t ws_bytes,
+                                rsr_stream_t stream);
+
+/*
+ * Reference-set maintenance (Sec. 2.2, Eqs. (2)-(3): reference sets hold only
+ * non-dominated states).  keep[j] = 1 iff no other reference of the set
+ * dominates refs[j]: for a lower set (upper = 0) no r_i with r_j <= r_i
+ * componentwise, for an upper set no r_i with r_j >= r_i.  Of equal references
+ * only the first (lowest index) is kept.
+ *   refs    : device uint8[R*n], states in [0, K).
+ *   keep    : device uint8[R].   n_keep : device int64[1], += number kept.
+ *   scratch : device, rsr_nondominated_scratch_size(n, K, R) bytes, 256-byte aligned.
+ * Asynchronous on `stream`.
+ */
+RSR_API size_t rsr_nondominated_scratch_size(int32_t n, int32_t K, int64_t R);
+RSR_API int rsr_nondominated(int32_t n, int32_t K, int64_t R, const uint8_t *refs, int32_t upper, uint8_t *keep,
+                             int64_t *n_keep, void *scratch, size_t scratch_bytes, rsr_stream_t stream);
+
+/*
+ * Stage 1 on the device (Sec. 3.5, with many searches per round).  Round r
+ * classifies samples r*N .. r*N+N-1 of `seed` against the current references
+ * and stops when (double)n_u < eps_u * (double)N (n_u = unclassified count),
+ * else when R_L + R_U >= R_max, else after max_rounds rounds.  Otherwise the
+ * first min(max_starts, n_u, R_max - R_L - R_U) unclassified samples in index
+ * order start boundary searches (rsr_boundary_search); the references found are
+ * appended to their set in start order and each set is reduced to its
+ * non-dominated elements, order kept (rsr_nondominated).
+ */
+typedef struct rsr_stage1_opts {
+    uint64_t seed;          /* Philox stream of the rounds                          */
+    int64_t N;              /* samples per round (the paper's H)                     */
+    int64_t max_starts;     /* boundary searches per round, >= 1                     */
+    double eps_u;           /* target unclassified fraction                          */
+    int64_t R_max;          /* reference limit; each buffer holds R_max rows         */
+    int32_t max_rounds;     /* >= 1                                                  */
+} rsr_stage1_opts;
+
+typedef struct rsr_stage1_result {
+    int32_t rounds;         /* rounds classified                                     */
+    int32_t stop;           /* 0 = eps_u reached, 1 = R_max reached, 2 = max_rounds  */
+    int64_t R_L, R_U;       /* rows now held in ref_L_buf / ref_U_buf                */
+    int64_t n_u_last;       /* unclassified samples of the last round                */
+    int64_t phi_evals;      /* Phi evaluations of all searches                       */
+} rsr_stage1_result;
+
+/*
+ *   problem   : n, K, pmf, path, flags; R_L / R_U = rows already in the buffers
+ *               (initial references, may be 0); problem->ref_L / ref_U are ignored.
+ *   system    : Phi and m' (system->m_prime).
+ *   ref_L_buf, ref_U_buf : device uint8[R_max*n] each, updated in place.
+ *   history_or_null : host int64[4*max_rounds]; row r = (n_u, R_L, R_U, starts)
+ *               at the start of round r.
+ *   ws        : device, rsr_stage1_workspace_size(problem, opts) bytes, 256-aligned.
+ * Synchronous: returns when Stage 1 has stopped.  Returns RSR_ERR_TIMEOUT if a
+ * classification round reported a device timeout, RSR_ERR_INVALID_ARG if a system
+ * kernel reported bad input (error word of the workspace).
+ */
+RSR_API size_t rsr_stage1_workspace_size(const rsr_problem *problem, const rsr_stage1_opts *opts);
+RSR_API int rsr_stage1(const rsr_problem *problem, const rsr_system *system, const rsr_stage1_opts *opts,
+                       uint8_t *ref_L_buf, uint8_t *ref_U_buf, int64_t *history_or_null,
+                       rsr_stage1_result *result, void *ws, size_t ws_bytes, rsr_stream_t stream);
 
 /* Message for a status code (static storage). */
 RSR_API const char *rsr_status_string(int status);

@@ -40,6 +40,8 @@ class rsr_problem(ctypes.Structure):
 
 RSR_PHI_ST_CONNECTIVITY = 0
 RSR_PHI_ST_MAXFLOW_LEVELS = 1
+RSR_PHI_GLOBAL_CONNECTIVITY = 2
+RSR_PHI_GLOBAL_CONN_LEVEL = 3
 
 
 class rsr_system(ctypes.Structure):
@@ -53,6 +55,28 @@ class rsr_system(ctypes.Structure):
         ("n_levels", ctypes.c_int32),
         ("level_thr", ctypes.c_int32 * 8),
         ("m_prime", ctypes.c_int32),
+    ]
+
+
+class rsr_stage1_opts(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("N", ctypes.c_int64),
+        ("max_starts", ctypes.c_int64),
+        ("eps_u", ctypes.c_double),
+        ("R_max", ctypes.c_int64),
+        ("max_rounds", ctypes.c_int32),
+    ]
+
+
+class rsr_stage1_result(ctypes.Structure):
+    _fields_ = [
+        ("rounds", ctypes.c_int32),
+        ("stop", ctypes.c_int32),
+        ("R_L", ctypes.c_int64),
+        ("R_U", ctypes.c_int64),
+        ("n_u_last", ctypes.c_int64),
+        ("phi_evals", ctypes.c_int64),
     ]
 
 
@@ -83,6 +107,14 @@ SIGNATURES = {
     "rsr_classify_static": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _P, _P, _P]),
     "rsr_resolve": (ctypes.c_int, [_PROB, ctypes.POINTER(rsr_system), _U64, _U64, _I64, _P, _P, _I64, _P, _P, _S,
                                    _P]),
+    "rsr_search_workspace_size": (ctypes.c_size_t, [_PROB]),
+    "rsr_boundary_search": (ctypes.c_int, [_PROB, ctypes.POINTER(rsr_system), _U64, _U64, _P, _I64, _P, _P, _P,
+                                           _P, _S, _P]),
+    "rsr_nondominated_scratch_size": (ctypes.c_size_t, [_I32, _I32, _I64]),
+    "rsr_nondominated": (ctypes.c_int, [_I32, _I32, _I64, _P, _I32, _P, _P, _P, _S, _P]),
+    "rsr_stage1_workspace_size": (ctypes.c_size_t, [_PROB, ctypes.POINTER(rsr_stage1_opts)]),
+    "rsr_stage1": (ctypes.c_int, [_PROB, ctypes.POINTER(rsr_system), ctypes.POINTER(rsr_stage1_opts), _P, _P, _P,
+                                  ctypes.POINTER(rsr_stage1_result), _P, _S, _P]),
     "rsr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rsr_last_cuda_error": (ctypes.c_char_p, []),
 }

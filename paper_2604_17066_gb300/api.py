@@ -15,7 +15,8 @@ import torch
 
 from . import _lib
 from ._lib import (RSR_FLAG_DENSE, RSR_PATH_AUTO, RSR_PATH_POPC, RSR_PATH_TC,  # noqa: F401
-                   RSR_PHI_ST_CONNECTIVITY, RSR_PHI_ST_MAXFLOW_LEVELS, RSRError, check, rsr_estimate_out,
+                   RSR_PHI_GLOBAL_CONN_LEVEL, RSR_PHI_GLOBAL_CONNECTIVITY, RSR_PHI_ST_CONNECTIVITY,
+                   RSR_PHI_ST_MAXFLOW_LEVELS, RSRError, check, rsr_estimate_out,
                    rsr_problem, rsr_system)
 
 
@@ -308,10 +309,10 @@ def rsr_classify_static(problem: Problem, seed: int, offset: int, N: int, counts
 
 
 class System:
-    """A built-in system function for Stage 2: s-t connectivity over undirected
-    edges (binary components) or s-t max-flow levels over directed arcs
-    (component state = capacity).  edges: n x 2 node indices, one row per
-    component."""
+    """A built-in system function Phi with its threshold m': s-t connectivity
+    or global connectivity (level) over undirected edges (binary components),
+    or s-t max-flow levels over directed arcs (component state = capacity).
+    edges: n x 2 node indices, one row per component."""
 
     def __init__(self, kind: int, n_nodes: int, edges, s: int, t: int, level_thr=(), m_prime: int = 0,
                  device: Optional[torch.device] = None):
@@ -351,3 +352,92 @@ def rsr_resolve(problem: Problem, system: System, seed: int, offset: int, N: int
                                   _ptr(u_lower_idx), u_lower_idx.numel(), _ptr(counts2), _ptr(ws), ws.numel(),
                                   _stream(stream)), "rsr_resolve")
     return u_lower_idx, counts2
+
+
+# ---------------------------------------------------------------------------
+# Stage 1: boundary search, reference-set maintenance, the round loop
+# ---------------------------------------------------------------------------
+def _aligned(nbytes: int, device) -> torch.Tensor:
+    buf = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    return buf[off:off + int(nbytes)]
+
+
+def rsr_boundary_search(problem: Problem, system: System, seed: int, offset: int, starts: torch.Tensor,
+                        ws: Optional[torch.Tensor] = None, phi_evals: Optional[torch.Tensor] = None, stream=None):
+    """Componentwise boundary search from samples offset + starts[j]; returns
+    (refs [n_starts x n] uint8, side [n_starts] uint8, phi_evals [1] int64) on the device."""
+    dev = starts.device
+    s = problem.struct()
+    lib = _lib.load()
+    if ws is None:
+        size = lib.rsr_search_workspace_size(ctypes.byref(s))
+        if size == 0:
+            raise RSRError(_lib.RSR_ERR_INVALID_ARG, "rsr_search_workspace_size")
+        ws = _aligned(size, dev)
+    S = int(starts.numel())
+    refs = torch.empty((S, problem.n), dtype=torch.uint8, device=dev)
+    side = torch.empty(S, dtype=torch.uint8, device=dev)
+    if phi_evals is None:
+        phi_evals = torch.zeros(1, dtype=torch.int64, device=dev)
+    g = system.struct()
+    check(lib.rsr_boundary_search(ctypes.byref(s), ctypes.byref(g), int(seed), int(offset), _ptr(starts), S,
+                                  _ptr(refs), _ptr(side), _ptr(phi_evals), _ptr(ws), ws.numel(), _stream(stream)),
+          "rsr_boundary_search")
+    return refs, side, phi_evals
+
+
+def rsr_nondominated(refs: torch.Tensor, K: int, upper: bool, stream=None):
+    """keep mask (uint8) of the non-dominated references of one set, and the kept count (device int64[1])."""
+    R, n = (int(v) for v in refs.shape)
+    lib = _lib.load()
+    size = lib.rsr_nondominated_scratch_size(n, int(K), R)
+    if size == 0:
+        raise RSRError(_lib.RSR_ERR_INVALID_ARG, "rsr_nondominated_scratch_size")
+    scratch = _aligned(size, refs.device)
+    keep = torch.empty(R, dtype=torch.uint8, device=refs.device)
+    n_keep = torch.zeros(1, dtype=torch.int64, device=refs.device)
+    check(lib.rsr_nondominated(n, int(K), R, _ptr(refs) if R else None, 1 if upper else 0,
+                               _ptr(keep) if R else None, _ptr(n_keep), _ptr(scratch), scratch.numel(),
+                               _stream(stream)), "rsr_nondominated")
+    return keep, n_keep
+
+
+def rsr_stage1(pmf, system: System, seed: int, N: int, max_starts: int, eps_u: float, R_max: int,
+               max_rounds: int, ref_L=None, ref_U=None, path: int = RSR_PATH_POPC, stream=None,
+               device: Optional[torch.device] = None):
+    """Stage 1 on the device.  Returns dict(ref_L, ref_U (device uint8),
+    history (rounds x 4 int64: n_u, R_L, R_U, starts), rounds, stop, n_u_last,
+    phi_evals)."""
+    pmf = np.ascontiguousarray(pmf, dtype=np.float64)
+    n = pmf.shape[0]
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    L0 = np.zeros((0, n), np.uint8) if ref_L is None else np.asarray(ref_L, dtype=np.uint8).reshape(-1, n)
+    U0 = np.zeros((0, n), np.uint8) if ref_U is None else np.asarray(ref_U, dtype=np.uint8).reshape(-1, n)
+    bufL = torch.zeros((int(R_max), n), dtype=torch.uint8, device=dev)
+    bufU = torch.zeros((int(R_max), n), dtype=torch.uint8, device=dev)
+    if L0.shape[0]:
+        bufL[:L0.shape[0]] = torch.from_numpy(np.ascontiguousarray(L0)).to(dev)
+    if U0.shape[0]:
+        bufU[:U0.shape[0]] = torch.from_numpy(np.ascontiguousarray(U0)).to(dev)
+    prob = rsr_problem()
+    prob.n, prob.K = n, pmf.shape[1]
+    prob.pmf = pmf.ctypes.data
+    prob.R_L, prob.R_U = L0.shape[0], U0.shape[0]
+    prob.ref_L = prob.ref_U = None
+    prob.path, prob.flags = int(path), 0
+    opts = _lib.rsr_stage1_opts()
+    opts.seed, opts.N, opts.max_starts = int(seed), int(N), int(max_starts)
+    opts.eps_u, opts.R_max, opts.max_rounds = float(eps_u), int(R_max), int(max_rounds)
+    lib = _lib.load()
+    size = lib.rsr_stage1_workspace_size(ctypes.byref(prob), ctypes.byref(opts))
+    if size == 0:
+        raise RSRError(_lib.RSR_ERR_INVALID_ARG, "rsr_stage1_workspace_size")
+    ws = _aligned(size, dev)
+    hist = np.zeros((int(max_rounds), 4), dtype=np.int64)
+    res = _lib.rsr_stage1_result()
+    g = system.struct()
+    check(lib.rsr_stage1(ctypes.byref(prob), ctypes.byref(g), ctypes.byref(opts), _ptr(bufL), _ptr(bufU),
+                         hist.ctypes.data, ctypes.byref(res), _ptr(ws), ws.numel(), _stream(stream)), "rsr_stage1")
+    return dict(ref_L=bufL[:res.R_L], ref_U=bufU[:res.R_U], history=hist[:res.rounds], rounds=res.rounds,
+                stop=res.stop, n_u_last=res.n_u_last, phi_evals=res.phi_evals)

@@ -1,0 +1,201 @@
+// maintain.cu -- reference-set maintenance and order-preserving selection.
+//
+// * Non-dominance (Sec. 2.2, Eqs. (2)-(3)): a reference set keeps only states
+//   that no other state of the set dominates.  On thermometer words t(r)
+//   (bit (i,k) = [r_i >= k]) the tests are word-wise: r_j <= r_i iff
+//   t(r_j) AND NOT t(r_i) = 0, and r_j = r_i iff the words are equal.  One
+//   reference per thread against the set streamed through shared memory (the
+//   same shape as the bit-packed classifier), a block leaving as soon as all
+//   of its references are known to be dominated.
+// * Selection: the first `limit` indices i (ascending) with flags[i] == value,
+//   in three launches (per-tile counts, one-block exclusive scan of the
+//   counts, ballot-ranked scatter).  Stage 1 uses it to pick unclassified
+//   samples as search starts and to compact reference rows in order.
+#include <cuda_runtime.h>
+
+#include "rsr_internal.cuh"
+#include "rsr_launch.h"
+
+namespace rsr {
+
+namespace {
+
+constexpr int kNdThreads = 256;
+constexpr int kSelTile = 4096;
+constexpr int kSelThreads = 256;
+constexpr int kScanThreads = 1024;
+
+template <int WB>
+__global__ void __launch_bounds__(kNdThreads) nondominated_kernel(const uint32_t *__restrict__ enc, int64_t R,
+                                                                  int upper, uint8_t *__restrict__ keep,
+                                                                  unsigned long long *n_keep) {
+    __shared__ __align__(16) uint32_t s_ref[kNdThreads * WB];
+    const int64_t j = (int64_t)blockIdx.x * kNdThreads + threadIdx.x;
+    uint32_t a[WB];
+#pragma unroll
+    for (int w = 0; w < WB; ++w) a[w] = (j < R) ? enc[j * WB + w] : 0u;
+    bool done = !(j < R);      // dominated, or no reference in this slot
+    for (int64_t base = 0; base < R; base += kNdThreads) {
+        if (__syncthreads_and(done)) break;
+        const int cnt = (int)((R - base) < kNdThreads ? (R - base) : kNdThreads);
+        for (int idx = threadIdx.x; idx < cnt * WB; idx += kNdThreads) s_ref[idx] = enc[base * WB + idx];
+        __syncthreads();
+        if (!done) {
+            for (int r = 0; r < cnt; ++r) {
+                const int64_t i = base + r;
+                if (i == j) continue;
+                uint32_t viol = 0u, diff = 0u;
+#pragma unroll
+                for (int w = 0; w < WB; ++w) {
+                    const uint32_t b = s_ref[r * WB + w];
+                    viol |= upper ? (b & ~a[w]) : (a[w] & ~b);
+                    diff |= a[w] ^ b;
+                }
+                if (viol == 0u && (diff != 0u || i < j)) {
+                    done = true;
+                    break;
+                }
+            }
+        }
+    }
+    if (j < R) {
+        keep[j] = done ? 0 : 1;
+        if (!done) atomicAdd(n_keep, 1ull);
+    }
+}
+
+template <int WB>
+cudaError_t launch_nd_wb(const uint32_t *enc, int64_t R, bool upper, uint8_t *keep, unsigned long long *n_keep,
+                         cudaStream_t s) {
+    const int64_t blocks = (R + kNdThreads - 1) / kNdThreads;
+    nondominated_kernel<WB><<<(unsigned)blocks, kNdThreads, 0, s>>>(enc, R, upper ? 1 : 0, keep, n_keep);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kSelThreads) select_count_kernel(const uint8_t *__restrict__ flags, uint8_t value,
+                                                                   int64_t N, int64_t *__restrict__ tile_cnt) {
+    __shared__ int s_warp[kSelThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kSelTile;
+    int c = 0;
+    for (int i = threadIdx.x; i < kSelTile; i += kSelThreads) {
+        const int64_t g = base + i;
+        if (g < N && flags[g] == value) ++c;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kSelThreads / 32; ++w) t += s_warp[w];
+        tile_cnt[blockIdx.x] = t;
+    }
+}
+
+// One block: tile counts -> exclusive offsets, in place; *n_out = min(total, limit).
+__global__ void __launch_bounds__(kScanThreads) select_scan_kernel(int64_t *tile_cnt, int64_t n_tiles, int64_t limit,
+                                                                   int64_t *n_out) {
+    __shared__ int64_t s[kScanThreads];
+    int64_t carry = 0;
+    for (int64_t base = 0; base < n_tiles; base += kScanThreads) {
+        const int64_t g = base + threadIdx.x;
+        const int64_t v = g < n_tiles ? tile_cnt[g] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int d = 1; d < kScanThreads; d <<= 1) {
+            const int64_t add = threadIdx.x >= (unsigned)d ? s[threadIdx.x - d] : 0;
+            __syncthreads();
+            s[threadIdx.x] += add;
+            __syncthreads();
+        }
+        if (g < n_tiles) tile_cnt[g] = carry + s[threadIdx.x] - v;
+        carry += s[kScanThreads - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_out = carry < limit ? carry : limit;
+}
+
+__global__ void __launch_bounds__(kSelThreads) select_scatter_kernel(const uint8_t *__restrict__ flags, uint8_t value,
+                                                                     int64_t N, const int64_t *__restrict__ tile_off,
+                                                                     int64_t limit, int64_t *__restrict__ out_idx) {
+    __shared__ int s_warp[kSelThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kSelTile;
+    int64_t off = tile_off[blockIdx.x];
+    if (off >= limit) return;   // block-uniform
+    for (int chunk = 0; chunk < kSelTile; chunk += kSelThreads) {
+        const int64_t g = base + chunk + threadIdx.x;
+        const bool f = g < N && flags[g] == value;
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_warp[warp] = __popc(m);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < kSelThreads / 32; ++w) {
+            before += w < warp ? s_warp[w] : 0;
+            total += s_warp[w];
+        }
+        if (f) {
+            const int64_t pos = off + before + __popc(m & ((1u << lane) - 1u));
+            if (pos < limit) out_idx[pos] = g;
+        }
+        off += total;
+        __syncthreads();
+    }
+}
+
+__global__ void gather_rows_kernel(const uint8_t *__restrict__ src, const int64_t *__restrict__ idx, int64_t count,
+                                   int n, uint8_t *__restrict__ dst) {
+    const int64_t total = count * n;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = g / n;
+        const int i = (int)(g - k * n);
+        dst[g] = src[idx[k] * n + i];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_nondominated(const uint32_t *enc, int64_t R, int words_b, bool upper, uint8_t *keep,
+                                unsigned long long *n_keep, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    switch (words_b) {
+        case 1: return launch_nd_wb<1>(enc, R, upper, keep, n_keep, s);
+        case 2: return launch_nd_wb<2>(enc, R, upper, keep, n_keep, s);
+        case 4: return launch_nd_wb<4>(enc, R, upper, keep, n_keep, s);
+        case 6: return launch_nd_wb<6>(enc, R, upper, keep, n_keep, s);
+        case 8: return launch_nd_wb<8>(enc, R, upper, keep, n_keep, s);
+        case 10: return launch_nd_wb<10>(enc, R, upper, keep, n_keep, s);
+        case 12: return launch_nd_wb<12>(enc, R, upper, keep, n_keep, s);
+        case 16: return launch_nd_wb<16>(enc, R, upper, keep, n_keep, s);
+        case 24: return launch_nd_wb<24>(enc, R, upper, keep, n_keep, s);
+        case 32: return launch_nd_wb<32>(enc, R, upper, keep, n_keep, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t select_scratch_bytes(int64_t N) {
+    const int64_t tiles = (N + kSelTile - 1) / kSelTile;
+    return (size_t)(tiles + 1) * sizeof(int64_t);
+}
+
+cudaError_t launch_select(const uint8_t *flags, uint8_t value, int64_t N, int64_t limit, int64_t *out_idx,
+                          int64_t *n_out, int64_t *scratch, cudaStream_t s) {
+    if (N <= 0 || limit <= 0) return cudaMemsetAsync(n_out, 0, sizeof(int64_t), s);
+    const int64_t tiles = (N + kSelTile - 1) / kSelTile;
+    select_count_kernel<<<(unsigned)tiles, kSelThreads, 0, s>>>(flags, value, N, scratch);
+    select_scan_kernel<<<1, kScanThreads, 0, s>>>(scratch, tiles, limit, n_out);
+    select_scatter_kernel<<<(unsigned)tiles, kSelThreads, 0, s>>>(flags, value, N, scratch, limit, out_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const uint8_t *src, const int64_t *idx, int64_t count, int n, uint8_t *dst,
+                               cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    const int64_t total = count * n;
+    int64_t blocks = (total + 255) / 256;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    if (blocks > cap) blocks = cap;
+    gather_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(src, idx, count, n, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace rsr

@@ -1,23 +1,40 @@
-// resolve.cu -- Stage 2 on the device (Sec. 3.5): the system function Phi is
+// resolve.cu -- system-function kernels: Stage 2 (Sec. 3.5), where Phi is
 // evaluated for every unclassified sample, which closes the estimate of
-// P(S <= m') without the host.
+// P(S <= m') without the host; and the componentwise boundary search of
+// Stage 1 (Sec. 3.4), which turns unclassified samples into new reference
+// states.
 //
-// Built-in system functions (the two families of the paper's experiments):
+// Built-in system functions (the families of the paper's experiments):
 //   RSR_PHI_ST_CONNECTIVITY   binary components are undirected edges; Phi = 1
 //                             iff s reaches t over working edges (x_e = 1)
 //   RSR_PHI_ST_MAXFLOW_LEVELS components are directed arcs with capacity x_a;
 //                             Phi = #{l : maxflow(s -> t) >= thr_l}
-// One warp per unclassified sample: its states are regenerated from Philox
-// (lane-strided blocks), then
-//   connectivity: label propagation over a shared-memory bitset, one edge per
-//                 lane per sweep, until t is reached or nothing changes;
+//   RSR_PHI_GLOBAL_CONNECTIVITY  Phi = 1 iff the working edges connect all
+//                             nodes (Sec. 4.3)
+//   RSR_PHI_GLOBAL_CONN_LEVEL Phi = 0 disconnected, 1 connected with a bridge
+//                             (some pair has one edge-disjoint path), 2 no
+//                             bridge (Sec. 4.6; Menger)
+// One warp per sample: its states are regenerated from Philox (lane-strided
+// blocks), then
+//   s-t connectivity: label propagation over a shared-memory bitset, one edge
+//                 per lane per sweep, until t is reached or nothing changes;
 //   max flow:     Ford-Fulkerson; each augmenting path is found by a
 //                 warp-parallel search of the residual graph (parents claimed
 //                 with atomicCAS, so they form a tree rooted at s) and pushed
 //                 by one lane; it stops as soon as the flow reaches the
-//                 threshold that decides S <= m'.
-// Labels 2 become 3 (Phi <= m') or 4 (Phi >= m'+1); the local indices of the
-// 3s are appended to u_lower_idx (in no particular order) for rsr_grad.
+//                 threshold that decides S <= m';
+//   global:       a level-synchronous breadth-first tree from node 0 (parent
+//                 word = depth << 16 | edge); bridges by covering: every
+//                 non-tree working edge walks its two ends up to their common
+//                 ancestor and marks the tree edges it passes, and a tree edge
+//                 left unmarked is a bridge.
+// Stage 2 rewrites labels 2 to 3 (Phi <= m') or 4 (Phi >= m'+1) and appends
+// the local indices of the 3s to u_lower_idx (in no particular order) for
+// rsr_grad.  The search raises (Phi <= m') or lowers (Phi >= m'+1) the
+// components in index order one state at a time, undoing the step that
+// crosses the boundary, exactly as Sec. 3.4 describes.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "rsr.h"
@@ -46,12 +63,93 @@ struct WarpScratch {
 
 __device__ __forceinline__ bool bit(const uint32_t *v, int i) { return (v[i >> 5] >> (i & 31)) & 1u; }
 
-// Phi(x) <= m' ?
-__device__ bool resolve_lower(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
-                              int32_t *err) {
+__device__ __forceinline__ int vload(const int32_t *p) { return *(const volatile int32_t *)p; }
+
+// Breadth-first tree from node 0 over working edges, level by level: in sweep d
+// only nodes of depth d-1 expand, so depths are exact.  parent[v] = depth << 16
+// | edge (0xFFFF at the root), -1 unreached.  Returns the number of reached nodes.
+__device__ int bfs_tree(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst) {
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < g.n_nodes; v += 32) w.parent[v] = -1;
+    __syncwarp();
+    if (lane == 0) w.parent[0] = 0xFFFF;
+    __syncwarp();
+    int reached = 1;
+    for (int d = 1; d < g.n_nodes; ++d) {
+        int claimed = 0;
+        for (int e = lane; e < n; e += 32) {
+            if (!w.x[e]) continue;
+            const int u = s_src[e], v = s_dst[e];
+            const int pu = vload(&w.parent[u]), pv = vload(&w.parent[v]);
+            if (pu != -1 && (pu >> 16) == d - 1 && pv == -1) {
+                if (atomicCAS(&w.parent[v], -1, (d << 16) | e) == -1) ++claimed;
+            } else if (pv != -1 && (pv >> 16) == d - 1 && pu == -1) {
+                if (atomicCAS(&w.parent[u], -1, (d << 16) | e) == -1) ++claimed;
+            }
+        }
+        claimed = __reduce_add_sync(0xffffffffu, claimed);
+        __syncwarp();
+        if (claimed == 0) break;
+        reached += claimed;
+    }
+    return reached;
+}
+
+// With a spanning tree from bfs_tree that reached every node: true iff no
+// working edge is a bridge.
+__device__ bool bridgeless(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
+                           int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < n; e += 32) w.flow[e] = 0;   // "covered" marks of tree edges
+    __syncwarp();
+    for (int e = lane; e < n; e += 32) {
+        if (!w.x[e]) continue;
+        int a = s_src[e], b = s_dst[e];
+        if (a == b || (w.parent[a] & 0xFFFF) == e || (w.parent[b] & 0xFFFF) == e) continue;   // loop / tree edge
+        for (int guard = 0; a != b && guard < 2 * g.n_nodes; ++guard) {
+            const int qa = w.parent[a], qb = w.parent[b];
+            if ((qa & 0xFFFF) >= n && (qb & 0xFFFF) >= n) {
+                atomicMax(err, 3);   // both at the root yet apart: cannot happen; recorded, walk stopped
+                break;
+            }
+            if ((qa >> 16) >= (qb >> 16) && (qa & 0xFFFF) < n) {
+                const int ea = qa & 0xFFFF;
+                w.flow[ea] = 1;
+                a = s_src[ea] == a ? s_dst[ea] : s_src[ea];
+            } else if ((qb & 0xFFFF) < n) {
+                const int eb = qb & 0xFFFF;
+                w.flow[eb] = 1;
+                b = s_src[eb] == b ? s_dst[eb] : s_src[eb];
+            } else {
+                const int ea = qa & 0xFFFF;   // b is the root, a is not
+                w.flow[ea] = 1;
+                a = s_src[ea] == a ? s_dst[ea] : s_src[ea];
+            }
+        }
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int v = lane + 1; v < g.n_nodes; v += 32) {
+        const int e = w.parent[v] & 0xFFFF;
+        if (e >= n || w.flow[e] == 0) ok = false;
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Phi(x) <= m' ?  (warp-uniform result; x in w.x)
+__device__ bool phi_le(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
+                       int32_t *err) {
     const int lane = threadIdx.x & 31;
     const int nw = (g.n_nodes + 31) / 32;
+    if (g.kind == RSR_PHI_GLOBAL_CONNECTIVITY || g.kind == RSR_PHI_GLOBAL_CONN_LEVEL) {
+        const int top = g.kind == RSR_PHI_GLOBAL_CONNECTIVITY ? 1 : 2;
+        if (g.m_prime >= top) return true;
+        if (bfs_tree(g, n, w, s_src, s_dst) < g.n_nodes) return true;        // Phi = 0
+        if (g.m_prime == 0) return false;                                    // Phi >= 1
+        return !bridgeless(g, n, w, s_src, s_dst, err);                      // m' = 1: Phi = 1 ?
+    }
     if (g.kind == RSR_PHI_ST_CONNECTIVITY) {
+        if (g.m_prime >= 1) return true;
         for (int i = lane; i < nw; i += 32) w.vis[i] = 0u;
         __syncwarp();
         if (lane == 0) w.vis[g.s >> 5] |= 1u << (g.s & 31);
@@ -89,7 +187,7 @@ __device__ bool resolve_lower(const Sys &g, int n, WarpScratch &w, const int32_t
             bool changed = false;
             for (int a = lane; a < n; a += 32) {
                 const int u = s_src[a], v = s_dst[a];
-                const int pu = ((volatile int32_t *)w.parent)[u], pv = ((volatile int32_t *)w.parent)[v];
+                const int pu = vload(&w.parent[u]), pv = vload(&w.parent[v]);
                 if (pu != -1 && pv == -1 && w.flow[a] < (int)w.x[a]) {
                     if (atomicCAS(&w.parent[v], -1, 2 * a) == -1) changed = true;
                 } else if (pv != -1 && pu == -1 && w.flow[a] > 0) {
@@ -97,7 +195,7 @@ __device__ bool resolve_lower(const Sys &g, int n, WarpScratch &w, const int32_t
                 }
             }
             __syncwarp();
-            if (((volatile int32_t *)w.parent)[g.t] != -1) {
+            if (vload(&w.parent[g.t]) != -1) {
                 reached = true;
                 break;
             }
@@ -134,15 +232,10 @@ __device__ bool resolve_lower(const Sys &g, int n, WarpScratch &w, const int32_t
     return total < target;
 }
 
-__global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyParams p, const Sys g, uint8_t *labels,
-                                                              int64_t *u_lower_idx, int64_t cap,
-                                                              unsigned long long *counts2) {
-    __shared__ WarpScratch ws[kWarps];
-    __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
-    __shared__ unsigned long long s_thr[kMaxKenc];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int32_t *err = &p.hdr->error;
-    for (int i = tid; i < p.n; i += blockDim.x) {
+// Graph and sampler thresholds into shared memory (whole block).
+__device__ void stage_system(const ClassifyParams &p, const Sys &g, int32_t *s_src, int32_t *s_dst,
+                             unsigned long long *s_thr, int32_t *err) {
+    for (int i = threadIdx.x; i < p.n; i += blockDim.x) {
         int u = g.src[i], v = g.dst[i];
         if (u < 0 || u >= g.n_nodes || v < 0 || v >= g.n_nodes) {
             atomicMax(err, 2);  // node index out of range: the edge is dropped
@@ -151,10 +244,37 @@ __global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyPara
         s_src[i] = u;
         s_dst[i] = v;
     }
-    for (int i = tid; i < p.n * p.km1; i += blockDim.x) s_thr[i] = p.thr[i];
+    for (int i = threadIdx.x; i < p.n * p.km1; i += blockDim.x) s_thr[i] = p.thr[i];
     __syncthreads();
-    WarpScratch &w = ws[warp];
+}
+
+// States of sample offset + hl into w.x (whole warp).
+__device__ void regen_sample(const ClassifyParams &p, int64_t hl, WarpScratch &w, const unsigned long long *s_thr) {
+    const int lane = threadIdx.x & 31;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    const uint64_t h = p.offset + (uint64_t)hl;
+    for (int q = lane; 4 * q < p.n; q += 32) {
+        const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+        const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = 4 * q + c;
+            if (i < p.n) w.x[i] = (uint8_t)state_from_uniform(us[c], s_thr + (size_t)i * p.km1, p.km1);
+        }
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyParams p, const Sys g, uint8_t *labels,
+                                                              int64_t *u_lower_idx, int64_t cap,
+                                                              unsigned long long *counts2) {
+    __shared__ WarpScratch ws[kWarps];
+    __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
+    __shared__ unsigned long long s_thr[kMaxKenc];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *err = &p.hdr->error;
+    stage_system(p, g, s_src, s_dst, s_thr, err);
+    WarpScratch &w = ws[warp];
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
     for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < p.N; base += warps_total * 32) {
         const int64_t mine = base + lane;
@@ -164,18 +284,8 @@ __global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyPara
             const int src_lane = __ffs(todo) - 1;
             todo &= todo - 1;
             const int64_t hl = base + src_lane;
-            const uint64_t h = p.offset + (uint64_t)hl;
-            for (int q = lane; 4 * q < p.n; q += 32) {
-                const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
-                const uint32_t us[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const int i = 4 * q + c;
-                    if (i < p.n) w.x[i] = (uint8_t)state_from_uniform(us[c], s_thr + (size_t)i * p.km1, p.km1);
-                }
-            }
-            __syncwarp();
-            const bool lower = resolve_lower(g, p.n, w, s_src, s_dst, err);
+            regen_sample(p, hl, w, s_thr);
+            const bool lower = phi_le(g, p.n, w, s_src, s_dst, err);
             if (lane == 0) {
                 labels[hl] = lower ? 3 : 4;
                 if (lower) {
@@ -191,11 +301,66 @@ __global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyPara
     }
 }
 
+// Componentwise boundary search (Sec. 3.4) from samples offset + starts[j].
+__global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParams p, const Sys g,
+                                                             const int64_t *starts, int64_t n_starts,
+                                                             uint8_t *refs_out, uint8_t *side_out,
+                                                             unsigned long long *evals) {
+    __shared__ WarpScratch ws[kWarps];
+    __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
+    __shared__ unsigned long long s_thr[kMaxKenc];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *err = &p.hdr->error;
+    stage_system(p, g, s_src, s_dst, s_thr, err);
+    WarpScratch &w = ws[warp];
+    const int top = p.K - 1;
+    for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < n_starts; j += (int64_t)gridDim.x * kWarps) {
+        regen_sample(p, starts[j], w, s_thr);
+        const bool lower = phi_le(g, p.n, w, s_src, s_dst, err);
+        unsigned long long ev = 1;
+        for (int i = 0; i < p.n; ++i) {
+            if (lower) {
+                while (w.x[i] < top) {
+                    __syncwarp();
+                    if (lane == 0) w.x[i] += 1;
+                    __syncwarp();
+                    ++ev;
+                    if (!phi_le(g, p.n, w, s_src, s_dst, err)) {
+                        __syncwarp();
+                        if (lane == 0) w.x[i] -= 1;
+                        __syncwarp();
+                        break;
+                    }
+                }
+            } else {
+                while (w.x[i] > 0) {
+                    __syncwarp();
+                    if (lane == 0) w.x[i] -= 1;
+                    __syncwarp();
+                    ++ev;
+                    if (phi_le(g, p.n, w, s_src, s_dst, err)) {
+                        __syncwarp();
+                        if (lane == 0) w.x[i] += 1;
+                        __syncwarp();
+                        break;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        for (int i = lane; i < p.n; i += 32) refs_out[(size_t)j * p.n + i] = w.x[i];
+        if (lane == 0) {
+            side_out[j] = lower ? 0 : 1;
+            atomicAdd(evals, ev);
+        }
+        __syncwarp();
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8_t *labels, int64_t *u_lower_idx,
-                           int64_t cap, unsigned long long *counts2, cudaStream_t s) {
-    if (p.N <= 0) return cudaSuccess;
+namespace {
+Sys make_sys(const rsr_system &sys) {
     Sys g{};
     g.kind = sys.kind;
     g.n_nodes = sys.n_nodes;
@@ -206,9 +371,26 @@ cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8
     for (int l = 0; l < 8; ++l) g.thr[l] = sys.level_thr[l];
     g.src = sys.src;
     g.dst = sys.dst;
+    return g;
+}
+}  // namespace
+
+cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8_t *labels, int64_t *u_lower_idx,
+                           int64_t cap, unsigned long long *counts2, cudaStream_t s) {
+    if (p.N <= 0) return cudaSuccess;
+    const Sys g = make_sys(sys);
     const int64_t warps = (p.N + 31) / 32;
     const int64_t grid = std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
     resolve_kernel<<<(unsigned)grid, kWarps * 32, 0, s>>>(p, g, labels, u_lower_idx, cap, counts2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const int64_t *starts, int64_t n_starts,
+                          uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, cudaStream_t s) {
+    if (n_starts <= 0) return cudaSuccess;
+    const Sys g = make_sys(sys);
+    const int64_t grid = std::min<int64_t>((n_starts + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
+    search_kernel<<<(unsigned)grid, kWarps * 32, 0, s>>>(p, g, starts, n_starts, refs_out, side_out, evals);
     return cudaGetLastError();
 }
 

@@ -26,16 +26,6 @@ namespace {
 
 thread_local std::string g_last_cuda_error;
 
-int cuda_fail(cudaError_t e, const char *where) {
-    // consume the runtime's last-error state so that a later, unrelated
-    // cudaGetLastError() does not report this failure again
-    (void)cudaGetLastError();
-    char buf[256];
-    snprintf(buf, sizeof(buf), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
-    g_last_cuda_error = buf;
-    return RSR_ERR_CUDA;
-}
-
 #define RSR_CUDA(call)                                             \
     do {                                                           \
         cudaError_t e_ = (call);                                   \
@@ -79,22 +69,11 @@ int current_device() {
 
 int validate(const rsr_problem *p) {
     if (!p) return RSR_ERR_INVALID_ARG;
-    if (p->n < 1 || p->K < 2 || p->R_L < 0 || p->R_U < 0 || p->R_L + p->R_U < 1) return RSR_ERR_INVALID_ARG;
-    if (p->K > kMaxK || (int64_t)p->n * (p->K - 1) > kMaxKenc) return RSR_ERR_UNSUPPORTED;
+    if (p->R_L < 0 || p->R_U < 0 || p->R_L + p->R_U < 1) return RSR_ERR_INVALID_ARG;
     if (p->R_L >= (int64_t(1) << 31) || p->R_U >= (int64_t(1) << 31)) return RSR_ERR_UNSUPPORTED;
-    if (!p->pmf) return RSR_ERR_INVALID_ARG;
     if ((p->R_L > 0 && !p->ref_L) || (p->R_U > 0 && !p->ref_U)) return RSR_ERR_INVALID_ARG;
     if (p->path < RSR_PATH_AUTO || p->path > RSR_PATH_TC) return RSR_ERR_INVALID_ARG;
-    for (int i = 0; i < p->n; ++i) {
-        double s = 0.0;
-        for (int k = 0; k < p->K; ++k) {
-            const double q = p->pmf[(size_t)i * p->K + k];
-            if (!(q >= 0.0 && q <= 1.0)) return RSR_ERR_INVALID_ARG;
-            s += q;
-        }
-        if (std::fabs(s - 1.0) > 1e-9) return RSR_ERR_INVALID_ARG;
-    }
-    return RSR_OK;
+    return validate_states(p->n, p->K, p->pmf);
 }
 
 int check_ws(const WsLayout &L, const void *ws, size_t ws_bytes) {
@@ -107,23 +86,9 @@ WsLayout layout_of(const rsr_problem *p) {
     return make_layout(p->n, p->K, p->R_L, p->R_U, popc_word_bucket(words));
 }
 
-// Sampler thresholds T_{i,k} = min(2^32, floor(2^32 * c_{i,k})), c_{i,k} the
-// fp64 left-to-right sum of q_{i,0..k-1}.
 void host_thresholds(const rsr_problem *p, std::vector<unsigned long long> &T) {
-    const int km1 = p->K - 1;
-    T.assign((size_t)p->n * km1, 0ull);
-    for (int i = 0; i < p->n; ++i) {
-        double c = 0.0;
-        for (int k = 1; k <= km1; ++k) {
-            c += p->pmf[(size_t)i * p->K + (k - 1)];
-            const double v = std::floor(std::ldexp(c, 32));
-            unsigned long long t;
-            if (v <= 0.0) t = 0ull;
-            else if (v >= 4294967296.0) t = 4294967296ull;
-            else t = (unsigned long long)v;
-            T[(size_t)i * km1 + (k - 1)] = t;
-        }
-    }
+    T.assign((size_t)p->n * (p->K - 1), 0ull);
+    rsr::host_thresholds(p->n, p->K, p->pmf, T.data());
 }
 
 uint64_t pmf_hash(const rsr_problem *p) { return fnv1a(p->pmf, sizeof(double) * (size_t)p->n * p->K); }
@@ -225,6 +190,65 @@ int order_references(const uint8_t *refs, int64_t R, int n, int K, const float *
 }
 
 }  // namespace
+
+int cuda_fail(cudaError_t e, const char *where) {
+    // consume the runtime's last-error state so that a later, unrelated
+    // cudaGetLastError() does not report this failure again
+    (void)cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+    g_last_cuda_error = buf;
+    return RSR_ERR_CUDA;
+}
+
+int validate_system(const rsr_system *system, int K) {
+    if (!system) return RSR_ERR_INVALID_ARG;
+    const int kind = system->kind;
+    if (kind < RSR_PHI_ST_CONNECTIVITY || kind > RSR_PHI_GLOBAL_CONN_LEVEL) return RSR_ERR_INVALID_ARG;
+    if (system->n_nodes < 1 || system->n_nodes > resolve_max_nodes()) return RSR_ERR_UNSUPPORTED;
+    if (!system->src || !system->dst || system->s < 0 || system->s >= system->n_nodes || system->t < 0 ||
+        system->t >= system->n_nodes)
+        return RSR_ERR_INVALID_ARG;
+    if (kind != RSR_PHI_ST_MAXFLOW_LEVELS && K != 2) return RSR_ERR_INVALID_ARG;
+    if (system->n_levels < 0 || system->n_levels > 8 || system->m_prime < 0) return RSR_ERR_INVALID_ARG;
+    for (int l = 1; l < system->n_levels; ++l)
+        if (system->level_thr[l] < system->level_thr[l - 1]) return RSR_ERR_INVALID_ARG;
+    return RSR_OK;
+}
+
+int validate_states(int n, int K, const double *pmf) {
+    if (n < 1 || K < 2) return RSR_ERR_INVALID_ARG;
+    if (K > kMaxK || (int64_t)n * (K - 1) > kMaxKenc) return RSR_ERR_UNSUPPORTED;
+    if (!pmf) return RSR_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            const double q = pmf[(size_t)i * K + k];
+            if (!(q >= 0.0 && q <= 1.0)) return RSR_ERR_INVALID_ARG;
+            s += q;
+        }
+        if (std::fabs(s - 1.0) > 1e-9) return RSR_ERR_INVALID_ARG;
+    }
+    return RSR_OK;
+}
+
+// Sampler thresholds T_{i,k} = min(2^32, floor(2^32 * c_{i,k})), c_{i,k} the
+// fp64 left-to-right sum of q_{i,0..k-1}.
+void host_thresholds(int n, int K, const double *pmf, unsigned long long *T) {
+    const int km1 = K - 1;
+    for (int i = 0; i < n; ++i) {
+        double c = 0.0;
+        for (int k = 1; k <= km1; ++k) {
+            c += pmf[(size_t)i * K + (k - 1)];
+            const double v = std::floor(std::ldexp(c, 32));
+            unsigned long long t;
+            if (v <= 0.0) t = 0ull;
+            else if (v >= 4294967296.0) t = 4294967296ull;
+            else t = (unsigned long long)v;
+            T[(size_t)i * km1 + (k - 1)] = t;
+        }
+    }
+}
 
 int device_sm_count() {
     static int cached[64] = {0};
@@ -404,16 +428,7 @@ int rsr_resolve(const rsr_problem *problem, const rsr_system *system, uint64_t s
     int st = validate(problem);
     if (st != RSR_OK) return st;
     if (!system || N < 0 || !labels || !counts2 || cap < 0 || (cap > 0 && !u_lower_idx)) return RSR_ERR_INVALID_ARG;
-    if (system->kind != RSR_PHI_ST_CONNECTIVITY && system->kind != RSR_PHI_ST_MAXFLOW_LEVELS)
-        return RSR_ERR_INVALID_ARG;
-    if (system->n_nodes < 1 || system->n_nodes > resolve_max_nodes()) return RSR_ERR_UNSUPPORTED;
-    if (!system->src || !system->dst || system->s < 0 || system->s >= system->n_nodes || system->t < 0 ||
-        system->t >= system->n_nodes)
-        return RSR_ERR_INVALID_ARG;
-    if (system->kind == RSR_PHI_ST_CONNECTIVITY && problem->K != 2) return RSR_ERR_INVALID_ARG;
-    if (system->n_levels < 0 || system->n_levels > 8 || system->m_prime < 0) return RSR_ERR_INVALID_ARG;
-    for (int l = 1; l < system->n_levels; ++l)
-        if (system->level_thr[l] < system->level_thr[l - 1]) return RSR_ERR_INVALID_ARG;
+    if ((st = validate_system(system, problem->K)) != RSR_OK) return st;
     const WsLayout L = layout_of(problem);
     if ((st = check_ws(L, ws, ws_bytes)) != RSR_OK) return st;
     if ((st = check_prepared(problem, ws)) != RSR_OK) return st;

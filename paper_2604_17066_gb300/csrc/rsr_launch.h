@@ -34,6 +34,23 @@ int tc_max_kpad();
 cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8_t *labels, int64_t *u_lower_idx,
                            int64_t cap, unsigned long long *counts2, cudaStream_t s);
 int resolve_max_nodes();
+cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const int64_t *starts, int64_t n_starts,
+                          uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, cudaStream_t s);
+
+// Reference-set maintenance and order-preserving selection (maintain.cu).
+cudaError_t launch_nondominated(const uint32_t *enc, int64_t R, int words_b, bool upper, uint8_t *keep,
+                                unsigned long long *n_keep, cudaStream_t s);
+size_t select_scratch_bytes(int64_t N);
+cudaError_t launch_select(const uint8_t *flags, uint8_t value, int64_t N, int64_t limit, int64_t *out_idx,
+                          int64_t *n_out, int64_t *scratch, cudaStream_t s);
+cudaError_t launch_gather_rows(const uint8_t *src, const int64_t *idx, int64_t count, int n, uint8_t *dst,
+                               cudaStream_t s);
+
+// Host helpers of the C ABI (rsr_capi.cu).
+int validate_states(int n, int K, const double *pmf);   // sizes and pmf rows; RSR_OK or an error code
+int validate_system(const rsr_system *system, int K);    // built-in Phi arguments
+void host_thresholds(int n, int K, const double *pmf, unsigned long long *T);   // n*(K-1) values
+int cuda_fail(cudaError_t e, const char *where);          // records the error, returns RSR_ERR_CUDA
 
 int device_sm_count();
 

@@ -97,3 +97,55 @@ def test_estimate_rejects_inconsistent_counts(lib):
         api.rsr_estimate((1, 2, 3), 7)          # counts do not sum to N
     with pytest.raises(RSRError):
         api.rsr_estimate((1, 2, 3), 6, 4)       # more resolved than unclassified
+
+
+def _system_struct(kind=0, n_nodes=4, s=0, t=3, levels=(), m_prime=0):
+    from paper_2604_17066_gb300._lib import rsr_system
+    g = rsr_system()
+    g.kind, g.n_nodes, g.s, g.t, g.m_prime = kind, n_nodes, s, t, m_prime
+    g.src, g.dst = 0x3000, 0x4000            # never dereferenced on the host
+    g.n_levels = len(levels)
+    for i, v in enumerate(levels):
+        g.level_thr[i] = v
+    return g
+
+
+def test_stage1_entry_points_reject_bad_arguments(lib):
+    from paper_2604_17066_gb300 import _lib
+    E_ARG, E_WS, E_UNS = _lib.RSR_ERR_INVALID_ARG, _lib.RSR_ERR_WORKSPACE, _lib.RSR_ERR_UNSUPPORTED
+    s, pmf = _problem_struct(n=4, K=2, R_L=0, R_U=0)
+    P = ctypes.c_void_p
+    # search workspace: header + counter (512 B) + thresholds rounded to 256 B
+    assert lib.rsr_search_workspace_size(ctypes.byref(s)) == 512 + 256
+    good = _system_struct()
+    fake = P(0x10000)                                 # 256-aligned, never dereferenced
+    args = lambda g, ws_bytes=4096: (ctypes.byref(s), ctypes.byref(g), 1, 0, fake, 2, fake, fake, None, fake,
+                                     ws_bytes, None)
+    assert lib.rsr_boundary_search(*args(_system_struct(kind=7))) == E_ARG            # unknown Phi
+    assert lib.rsr_boundary_search(*args(_system_struct(n_nodes=2000))) == E_UNS      # too many nodes
+    assert lib.rsr_boundary_search(*args(_system_struct(t=4))) == E_ARG               # t out of range
+    assert lib.rsr_boundary_search(*args(_system_struct(kind=1, levels=(3, 2)))) == E_ARG   # not ascending
+    assert lib.rsr_boundary_search(*args(good, ws_bytes=100)) == E_WS
+    s3, _ = _problem_struct(n=4, K=3, R_L=0, R_U=0)
+    assert lib.rsr_boundary_search(ctypes.byref(s3), ctypes.byref(good), 1, 0, fake, 2, fake, fake, None, fake,
+                                   4096, None) == E_ARG                               # connectivity needs K = 2
+    # non-dominance scratch: one 32-bit word bucket per reference, 256-byte rounded
+    assert lib.rsr_nondominated_scratch_size(4, 2, 100) == 512
+    assert lib.rsr_nondominated_scratch_size(300, 2, 1000) == 40192   # 1000 x 10 words x 4 B, rounded
+    assert lib.rsr_nondominated_scratch_size(0, 2, 10) == 0
+    assert lib.rsr_nondominated(4, 2, 10, fake, 0, fake, None, fake, 4096, None) == E_ARG     # n_keep NULL
+    assert lib.rsr_nondominated(4, 2, 10, fake, 0, fake, fake, fake, 16, None) == E_WS
+    # Stage 1 options
+    opts = _lib.rsr_stage1_opts()
+    opts.seed, opts.N, opts.max_starts, opts.eps_u, opts.R_max, opts.max_rounds = 1, 1000, 8, 1e-5, 64, 10
+    assert lib.rsr_stage1_workspace_size(ctypes.byref(s), ctypes.byref(opts)) > 0
+    for field, bad in (("N", 0), ("max_starts", 0), ("R_max", 0), ("max_rounds", 0), ("eps_u", -1.0)):
+        old = getattr(opts, field)
+        setattr(opts, field, bad)
+        assert lib.rsr_stage1_workspace_size(ctypes.byref(s), ctypes.byref(opts)) == 0, field
+        setattr(opts, field, old)
+    s_big, _ = _problem_struct(n=4, K=2, R_L=65, R_U=0)   # more initial rows than R_max
+    assert lib.rsr_stage1_workspace_size(ctypes.byref(s_big), ctypes.byref(opts)) == 0
+    res = _lib.rsr_stage1_result()
+    assert lib.rsr_stage1(ctypes.byref(s), ctypes.byref(good), ctypes.byref(opts), fake, fake, None,
+                          ctypes.byref(res), fake, 16, None) == E_WS

@@ -18,6 +18,8 @@ from __future__ import annotations
 
 from .systems import (  # noqa: F401
     Problem,
+    binary_pmf,
+    all_states,
     grid_graph,
     st_connectivity_all_states,
     reference_sets_from_phi,
