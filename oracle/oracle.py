@@ -68,6 +68,8 @@ def _load():
                                                 ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P]
             lib.orc_boundary_search.restype = ctypes.c_int
             lib.orc_nondominated.argtypes = [ctypes.c_int, i64, P, ctypes.c_int, P]
+            lib.orc_levels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, P, i64, P, P]
             _lib = lib
     return _lib
 
@@ -199,6 +201,25 @@ def resolve(kind: int, n_nodes: int, edges, s: int, t: int, X, labels, m_prime: 
     lower = _load().orc_resolve(kind, n_nodes, src.size, _p(src), _p(dst), s, t, thr.size, _p(thr), m_prime,
                                 X.shape[0], _p(X), _p(lab))
     return lab, int(lower)
+
+
+def levels(kind: int, n_nodes: int, edges, s: int, t: int, X, thresholds=None) -> np.ndarray:
+    """Phi(x_h) for every row of X (uint8 system levels)."""
+    src, dst, thr = _graph_args(edges, thresholds)
+    X = np.ascontiguousarray(X, dtype=np.uint8)
+    out = np.zeros(X.shape[0], dtype=np.uint8)
+    if X.shape[0]:
+        _load().orc_levels(kind, n_nodes, src.size, _p(src), _p(dst), s, t, thr.size, _p(thr), X.shape[0], _p(X),
+                           _p(out))
+    return out
+
+
+def level_pmf(pmf, kind: int, n_nodes: int, edges, s: int, t: int, seed: int, offset: int, N: int, n_levels: int,
+              thresholds=None):
+    """(counts[m] = #{h : Phi(x_h) = m}, levels) for samples offset .. offset+N-1."""
+    X = sample(pmf, seed, offset, N)
+    lv = levels(kind, n_nodes, edges, s, t, X, thresholds)
+    return np.bincount(lv, minlength=n_levels).astype(np.int64), lv
 
 
 # --------------------------------------------------------------------------

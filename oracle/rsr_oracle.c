@@ -484,3 +484,15 @@ void orc_nondominated(int n, int64_t R, const uint8_t *refs, int upper, uint8_t 
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* System-state pmf over all levels (Sec. 3.5 applied at every boundary,    */
+/* Sec. 4.5-4.6): P(S = m) is estimated by #{h : Phi(x_h) = m} / H.  The    */
+/* oracle takes the definition directly: Phi of every sample.               */
+/* ------------------------------------------------------------------------ */
+void orc_levels(int kind, int n_nodes, int n, const int32_t *src, const int32_t *dst, int s, int t, int n_thr,
+                const int32_t *thr, int64_t N, const uint8_t *X, uint8_t *levels)
+{
+    for (int64_t h = 0; h < N; ++h)
+        levels[h] = (uint8_t)orc_phi(kind, n_nodes, n, src, dst, s, t, n_thr, thr, X + (size_t)h * n);
+}

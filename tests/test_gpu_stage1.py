@@ -42,12 +42,8 @@ def _random_graph(seed, n_nodes=30, n_edges=80):
 
 
 def _small_flow(K=3):
-    rng = np.random.default_rng(21)
-    n_nodes, arcs = 5, []
-    while len(arcs) < 7:
-        a, b = (int(v) for v in rng.integers(0, n_nodes, 2))
-        if a != b and (a, b) not in arcs:
-            arcs.append((a, b))
+    # two routes s=0 -> t=4 with a cross arc: flows 0..4 all occur
+    n_nodes, arcs = 5, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2), (3, 4), (2, 4)]
     pmf = np.random.default_rng(2).dirichlet(np.ones(K), size=len(arcs))
     return n_nodes, arcs, 0, 4, pmf, (2, 4)
 

@@ -94,12 +94,8 @@ def test_boundary_search_visits_components_in_index_order_on_the_grid():
 
 
 def _small_flow_system(K=3, thresholds=(2, 4)):
-    rng = np.random.default_rng(21)
-    n_nodes, arcs = 5, []
-    while len(arcs) < 7:
-        a, b = (int(v) for v in rng.integers(0, n_nodes, 2))
-        if a != b and (a, b) not in arcs:
-            arcs.append((a, b))
+    # two routes s=0 -> t=4 with a cross arc: flows 0..4 all occur
+    n_nodes, arcs = 5, [(0, 1), (0, 2), (1, 3), (2, 3), (1, 2), (3, 4), (2, 4)]
     s, t = 0, 4
     X = W.all_states(len(arcs), K)
     phi = np.zeros(X.shape[0], dtype=np.int64)
@@ -119,6 +115,7 @@ def test_boundary_search_multistate_flow_from_every_state(m_prime):
     n_nodes, arcs, s, t, X, phi, thr = _small_flow_system(K)
     n = len(arcs)
     ref_L, ref_U = W.reference_sets_from_phi(phi, n, K, m_prime)
+    assert set(np.unique(phi)) == {0, 1, 2} and len(ref_L) >= 3 and len(ref_U) >= 3
     Lset = {bytes(r) for r in ref_L}
     Uset = {bytes(r) for r in ref_U}
     for j, x in enumerate(X):
