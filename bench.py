@@ -123,6 +123,65 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def bench_pipeline(rsr, torch, reps=5):
+    """The paper's whole workflow on a 119-node / 295-edge graph with every
+    edge failing with probability 0.05 (Sec. 2.4, 4.1): Stage 1 from no
+    references to an unclassified fraction below 1e-5 (rounds of 10^6 samples,
+    64 searches per round, at most 10^4 references), then Stage 2 on a fresh
+    10^6 samples with the references found (classification + Phi of the
+    unclassified samples on the device).  Timed with CUDA events (Stage 2) and
+    the host clock around the synchronous Stage 1 call."""
+    import workloads.large as L
+    from workloads.systems import binary_pmf
+    p = L.c2_rgg()
+    m = p.meta
+    pmf = binary_pmf(np.full(p.n, 0.05))
+    system = rsr.System(rsr.RSR_PHI_ST_CONNECTIVITY, m["n_nodes"], m["edges"], m["s"], m["t"])
+    rsr.rsr_stage1(pmf, system, 99, 10000, 16, 1e-5, 64, 2)              # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s1 = rsr.rsr_stage1(pmf, system, 2, 1_000_000, 64, 1e-5, 10_000, 2000)
+    torch.cuda.synchronize()
+    t_s1 = time.perf_counter() - t0
+    P = rsr.Problem(pmf, s1["ref_L"].cpu().numpy(), s1["ref_U"].cpu().numpy(), path=rsr.RSR_PATH_POPC)
+    sess = rsr.Session(P)
+    N = 1_000_000
+    dev = torch.device("cuda")
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    labels = torch.empty(N, dtype=torch.uint8, device=dev)
+    uidx = torch.empty(N, dtype=torch.int64, device=dev)
+    c2 = torch.zeros(2, dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    times, est = [], None
+    for k in range(reps + 2):
+        flush.fill_(k)
+        counts.zero_()
+        c2.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        off = (1000 + k) * N
+        e[0].record(stream)
+        rsr.rsr_classify(P, 7, off, N, sess.ws, counts, None, labels, None, None, stream)
+        rsr.rsr_resolve(P, system, 7, off, N, labels, sess.ws, u_lower_idx=uidx, counts2=c2, stream=stream)
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            times.append(e[0].elapsed_time(e[1]))
+        est = rsr.rsr_estimate(counts.cpu().numpy(), N, int(c2[0].item()))
+    h = s1["history"]
+    return {
+        "graph": "119 nodes / 295 edges, p_f = 0.05 (synthetic stand-in; reference counts are a property "
+                 "of this graph and of the component order, not comparable with the paper's)",
+        "stage1_s": t_s1, "stage1_rounds": int(s1["rounds"]), "stage1_stop": int(s1["stop"]),
+        "stage1_refs": [int(s1["ref_L"].shape[0]), int(s1["ref_U"].shape[0])],
+        "stage1_final_pu": float(h[-1][0]) / 1e6, "stage1_phi_evals": int(s1["phi_evals"]),
+        "stage2_ms_1e6_samples": sum(times) / len(times), "stage2_P_S_le_0": est["P_lower"],
+        "stage2_unclassified": est["pu"],
+        "paper_context": "Table 3, Graph 2 (another graph and machine): reference search 0.0571 h, "
+                         "probability evaluation 9.33 s",
+    }
+
+
 def bench_batch(rsr, torch, N=200_000, reps=5):
     """256 hazard scenarios (n = 50..300 edges, 1e2..1e5 references, N samples
     each): one persistent launch replayed from a CUDA graph vs the per-scenario
@@ -441,6 +500,7 @@ def main():
             extras["stage2"] = {"resolve_ms": sum(stage2_ms) / len(stage2_ms), "n_u": int(c2.sum().item()),
                                 "note": "Phi evaluated on the device for every unclassified sample; the step "
                                         "estimate is the Stage-2 P(S<=m')"}
+        extras["pipeline_119_295"] = bench_pipeline(rsr, torch)
         if args.workload == "c3" and not args.no_batch:
             extras["batch_c5"] = bench_batch(rsr, torch, N=200_000)
             extras["batch_c5_N2e4"] = bench_batch(rsr, torch, N=20_000)

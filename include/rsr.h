@@ -318,6 +318,35 @@ RSR_API int rsr_resolve(const rsr_problem *problem, const rsr_system *system, ui
                         void *ws, size_t ws_bytes, rsr_stream_t stream);
 
 /*
+ * System-state pmf over all levels in one call (Sec. 3.5 applied at every
+ * boundary; the multi-state examples of Sec. 4.5-4.6): counts of S = m for
+ * m = 0..n_boundaries over samples offset..offset+N-1 of `seed`.
+ * Each boundary b (m' = b) classifies every sample against its own reference
+ * sets: a lower match bounds S <= b, an upper match S >= b+1.  A sample whose
+ * bounds meet is counted directly; for the others Phi is evaluated on the
+ * device (decisions Phi <= m' for the open boundaries, lowest first).
+ *   problems        : host array[n_boundaries]; problem b holds the references
+ *                     of boundary m' = b; all share n, K and the pmf.
+ *   ws, ws_bytes    : host arrays[n_boundaries]; ws[b] prepared for problems[b].
+ *   system          : Phi (system->m_prime is ignored).  The number of
+ *                     boundaries must match Phi: 1 for the binary kinds, 2 for
+ *                     RSR_PHI_GLOBAL_CONN_LEVEL, n_levels for max-flow levels.
+ *   labels_scratch  : device uint8[n_boundaries*N] (per-boundary labels, 0/1/2).
+ *   levels_or_null  : device uint8[N], S of every sample.
+ *   counts3_per_boundary : device int64[3*n_boundaries], += the classification
+ *                     counts (I^L, I^U, I^u) of each boundary.
+ *   level_counts    : device int64[n_boundaries+1], += #{h : S_h = m}.
+ *   n_phi_or_null   : device int64[1], += samples that needed Phi.
+ * Asynchronous on `stream`.  Inconsistent references (a lower bound below an
+ * upper bound for one sample) set the error word of ws[0]; the sample is not counted.
+ */
+RSR_API int rsr_level_pmf(const rsr_problem *problems, int32_t n_boundaries, void *const *ws,
+                          const size_t *ws_bytes, const rsr_system *system, uint64_t seed, uint64_t offset,
+                          int64_t N, uint8_t *labels_scratch, uint8_t *levels_or_null,
+                          int64_t *counts3_per_boundary, int64_t *level_counts, int64_t *n_phi_or_null,
+                          rsr_stream_t stream);
+
+/*
  * Stage 1 building block (Sec. 3.4): componentwise boundary search.  For each
  * j < n_starts, sample offset + starts[j] of `seed` is regenerated (same
  * sampler as rsr_classify).  If Phi(x) <= m' its components are raised in

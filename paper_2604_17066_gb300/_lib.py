@@ -107,6 +107,8 @@ SIGNATURES = {
     "rsr_classify_static": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _P, _P, _P]),
     "rsr_resolve": (ctypes.c_int, [_PROB, ctypes.POINTER(rsr_system), _U64, _U64, _I64, _P, _P, _I64, _P, _P, _S,
                                    _P]),
+    "rsr_level_pmf": (ctypes.c_int, [_PROB, _I32, _P, _P, ctypes.POINTER(rsr_system), _U64, _U64, _I64, _P, _P, _P,
+                                     _P, _P, _P]),
     "rsr_search_workspace_size": (ctypes.c_size_t, [_PROB]),
     "rsr_boundary_search": (ctypes.c_int, [_PROB, ctypes.POINTER(rsr_system), _U64, _U64, _P, _I64, _P, _P, _P,
                                            _P, _S, _P]),

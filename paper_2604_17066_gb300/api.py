@@ -441,3 +441,25 @@ def rsr_stage1(pmf, system: System, seed: int, N: int, max_starts: int, eps_u: f
                          hist.ctypes.data, ctypes.byref(res), _ptr(ws), ws.numel(), _stream(stream)), "rsr_stage1")
     return dict(ref_L=bufL[:res.R_L], ref_U=bufU[:res.R_U], history=hist[:res.rounds], rounds=res.rounds,
                 stop=res.stop, n_u_last=res.n_u_last, phi_evals=res.phi_evals)
+
+
+def rsr_level_pmf(sessions, system: System, seed: int, offset: int, N: int, levels: bool = True, stream=None):
+    """System-state pmf over all levels in one call: sessions[b] is a prepared
+    Session of boundary m' = b.  Returns dict(level_counts [M_S], levels [N] or
+    None, counts3 [n_boundaries x 3], n_phi) as device tensors."""
+    nb = len(sessions)
+    dev = sessions[0].ws.device
+    structs = (rsr_problem * nb)(*[S.problem.struct() for S in sessions])
+    ws_ptrs = (ctypes.c_void_p * nb)(*[_ptr(S.ws) for S in sessions])
+    ws_sizes = (ctypes.c_size_t * nb)(*[S.ws.numel() for S in sessions])
+    scratch = torch.empty(max(nb * int(N), 1), dtype=torch.uint8, device=dev)
+    lv = torch.empty(max(int(N), 1), dtype=torch.uint8, device=dev) if levels else None
+    counts3 = torch.zeros((nb, 3), dtype=torch.int64, device=dev)
+    level_counts = torch.zeros(nb + 1, dtype=torch.int64, device=dev)
+    n_phi = torch.zeros(1, dtype=torch.int64, device=dev)
+    g = system.struct()
+    check(_lib.load().rsr_level_pmf(structs, nb, ws_ptrs, ws_sizes, ctypes.byref(g), int(seed), int(offset), int(N),
+                                    _ptr(scratch), _ptr(lv), _ptr(counts3), _ptr(level_counts), _ptr(n_phi),
+                                    _stream(stream)), "rsr_level_pmf")
+    return dict(level_counts=level_counts, levels=None if lv is None else lv[:int(N)], counts3=counts3,
+                n_phi=n_phi)

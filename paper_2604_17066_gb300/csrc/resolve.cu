@@ -47,6 +47,7 @@ namespace {
 
 constexpr int kWarps = 4;          // warps per block, one sample each at a time
 constexpr int kMaxNodes = 1024;
+constexpr int kMaxLevels = 9;      // system levels: at most 8 boundaries
 
 struct Sys {
     int32_t kind, n_nodes, s, t, n_levels, m_prime;
@@ -357,6 +358,72 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
     }
 }
 
+// System-state level of every sample from the labels of nb boundaries
+// (labels[b*N + h], boundary m' = b): a lower match at b bounds S <= b, an
+// upper match S >= b+1.  Where the bounds meet the level is known; otherwise
+// Phi decides, boundary by boundary from the lowest open one.
+__global__ void __launch_bounds__(kWarps * 32) levels_kernel(const ClassifyParams p, const Sys g, int nb,
+                                                             const uint8_t *labels, uint8_t *levels_out,
+                                                             unsigned long long *level_counts,
+                                                             unsigned long long *n_phi) {
+    __shared__ WarpScratch ws[kWarps];
+    __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
+    __shared__ unsigned long long s_thr[kMaxKenc];
+    __shared__ unsigned long long s_hist[kMaxLevels];
+    __shared__ unsigned long long s_phi;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *err = &p.hdr->error;
+    if (threadIdx.x < kMaxLevels) s_hist[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) s_phi = 0ull;
+    stage_system(p, g, s_src, s_dst, s_thr, err);
+    WarpScratch &w = ws[warp];
+    const int64_t warps_total = (int64_t)gridDim.x * kWarps;
+    for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < p.N; base += warps_total * 32) {
+        const int64_t h = base + lane;
+        const bool valid = h < p.N;
+        int lo = 0, hi = nb;
+        if (valid) {
+            for (int b = 0; b < nb; ++b) {
+                const uint8_t lab = labels[(size_t)b * p.N + h];
+                if (lab == 0) hi = b < hi ? b : hi;
+                else if (lab == 1) lo = b + 1 > lo ? b + 1 : lo;
+            }
+            if (lo > hi) {
+                atomicMax(err, 5);   // a lower and an upper bound that exclude each other: inconsistent references
+            } else if (lo == hi) {
+                if (levels_out) levels_out[h] = (uint8_t)lo;
+                atomicAdd(&s_hist[lo], 1ull);
+            }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, valid && lo < hi);
+        while (todo) {
+            const int src_lane = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t hs = base + src_lane;
+            const int slo = __shfl_sync(0xffffffffu, lo, src_lane), shi = __shfl_sync(0xffffffffu, hi, src_lane);
+            regen_sample(p, hs, w, s_thr);
+            int S = shi;
+            for (int m = slo; m < shi; ++m) {
+                Sys gm = g;
+                gm.m_prime = m;
+                if (phi_le(gm, p.n, w, s_src, s_dst, err)) {
+                    S = m;
+                    break;
+                }
+            }
+            if (lane == 0) {
+                if (levels_out) levels_out[hs] = (uint8_t)S;
+                atomicAdd(&s_hist[S], 1ull);
+                atomicAdd(&s_phi, 1ull);
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x <= nb && s_hist[threadIdx.x]) atomicAdd(&level_counts[threadIdx.x], s_hist[threadIdx.x]);
+    if (threadIdx.x == 0 && n_phi && s_phi) atomicAdd(n_phi, s_phi);
+}
+
 }  // namespace
 
 namespace {
@@ -391,6 +458,18 @@ cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const 
     const Sys g = make_sys(sys);
     const int64_t grid = std::min<int64_t>((n_starts + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
     search_kernel<<<(unsigned)grid, kWarps * 32, 0, s>>>(p, g, starts, n_starts, refs_out, side_out, evals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_levels(const ClassifyParams &p, const rsr_system &sys, int nb, const uint8_t *labels,
+                          uint8_t *levels_out, unsigned long long *level_counts, unsigned long long *n_phi,
+                          cudaStream_t s) {
+    if (p.N <= 0) return cudaSuccess;
+    if (nb < 1 || nb >= kMaxLevels) return cudaErrorInvalidValue;
+    const Sys g = make_sys(sys);
+    const int64_t warps = (p.N + 31) / 32;
+    const int64_t grid = std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
+    levels_kernel<<<(unsigned)grid, kWarps * 32, 0, s>>>(p, g, nb, labels, levels_out, level_counts, n_phi);
     return cudaGetLastError();
 }
 

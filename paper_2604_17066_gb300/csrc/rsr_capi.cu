@@ -442,6 +442,53 @@ int rsr_resolve(const rsr_problem *problem, const rsr_system *system, uint64_t s
     return RSR_OK;
 }
 
+int rsr_level_pmf(const rsr_problem *problems, int32_t n_boundaries, void *const *ws, const size_t *ws_bytes,
+                  const rsr_system *system, uint64_t seed, uint64_t offset, int64_t N, uint8_t *labels_scratch,
+                  uint8_t *levels_or_null, int64_t *counts3_per_boundary, int64_t *level_counts,
+                  int64_t *n_phi_or_null, rsr_stream_t stream) {
+    if (!problems || !ws || !ws_bytes || n_boundaries < 1 || n_boundaries > 8 || N < 0 || !labels_scratch ||
+        !counts3_per_boundary || !level_counts)
+        return RSR_ERR_INVALID_ARG;
+    int st;
+    for (int b = 0; b < n_boundaries; ++b) {
+        if ((st = validate(&problems[b])) != RSR_OK) return st;
+        if (problems[b].n != problems[0].n || problems[b].K != problems[0].K ||
+            pmf_hash(&problems[b]) != pmf_hash(&problems[0]))
+            return RSR_ERR_INVALID_ARG;
+        if ((st = check_ws(layout_of(&problems[b]), ws[b], ws_bytes[b])) != RSR_OK) return st;
+        if ((st = check_prepared(&problems[b], ws[b])) != RSR_OK) return st;
+    }
+    if ((st = validate_system(system, problems[0].K)) != RSR_OK) return st;
+    const int want = system->kind == RSR_PHI_ST_MAXFLOW_LEVELS ? system->n_levels
+                     : system->kind == RSR_PHI_GLOBAL_CONN_LEVEL ? 2 : 1;
+    if (n_boundaries != want) return RSR_ERR_INVALID_ARG;
+    if (N == 0) return RSR_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int b = 0; b < n_boundaries; ++b) {
+        const WsLayout L = layout_of(&problems[b]);
+        ClassifyParams c = make_params(&problems[b], L, ws[b]);
+        c.N = N;
+        c.seed = seed;
+        c.offset = offset;
+        c.labels = labels_scratch + (size_t)b * N;
+        c.counts3 = reinterpret_cast<unsigned long long *>(counts3_per_boundary + 3 * b);
+        if (choose_path(&problems[b]) == RSR_PATH_TC) {
+            if (!tc_supported() || L.tc_kpad > tc_max_kpad()) return RSR_ERR_UNSUPPORTED;
+            RSR_CUDA(launch_classify_tc(c, s));
+        } else {
+            RSR_CUDA(launch_classify_popc(c, s));
+        }
+    }
+    ClassifyParams c0 = make_params(&problems[0], layout_of(&problems[0]), ws[0]);
+    c0.N = N;
+    c0.seed = seed;
+    c0.offset = offset;
+    RSR_CUDA(launch_levels(c0, *system, n_boundaries, labels_scratch, levels_or_null,
+                           reinterpret_cast<unsigned long long *>(level_counts),
+                           reinterpret_cast<unsigned long long *>(n_phi_or_null), s));
+    return RSR_OK;
+}
+
 int rsr_sample(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N, uint8_t *states, void *ws,
                size_t ws_bytes, rsr_stream_t stream) {
     int st = validate(problem);

@@ -34,6 +34,9 @@ int tc_max_kpad();
 cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8_t *labels, int64_t *u_lower_idx,
                            int64_t cap, unsigned long long *counts2, cudaStream_t s);
 int resolve_max_nodes();
+cudaError_t launch_levels(const ClassifyParams &p, const rsr_system &sys, int nb, const uint8_t *labels,
+                          uint8_t *levels_out, unsigned long long *level_counts, unsigned long long *n_phi,
+                          cudaStream_t s);
 cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const int64_t *starts, int64_t n_starts,
                           uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, cudaStream_t s);
 
