@@ -65,7 +65,8 @@ def _load():
                                         ctypes.c_int, P, ctypes.c_int, i64, P, P]
             lib.orc_resolve.restype = i64
             lib.orc_boundary_search.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int,
-                                                ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P]
+                                                ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P, P]
+            lib.orc_search_order.argtypes = [u64, u64, ctypes.c_int, P]
             lib.orc_boundary_search.restype = ctypes.c_int
             lib.orc_nondominated.argtypes = [ctypes.c_int, i64, P, ctypes.c_int, P]
             lib.orc_levels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int,
@@ -225,16 +226,29 @@ def level_pmf(pmf, kind: int, n_nodes: int, edges, s: int, t: int, seed: int, of
 # --------------------------------------------------------------------------
 # Stage 1: reference-state search (Sec. 3.4, 3.5)
 # --------------------------------------------------------------------------
+SEARCH_INDEX_ORDER = 0
+SEARCH_PERMUTED = 1
+
+
+def search_order(seed: int, h: int, n: int) -> np.ndarray:
+    """Visiting order of the permuted search from (global) sample h."""
+    out = np.zeros(n, dtype=np.int32)
+    _load().orc_search_order(int(seed), int(h), n, _p(out))
+    return out
+
+
 def boundary_search(kind: int, n_nodes: int, edges, s: int, t: int, x, K: int, m_prime: int = 0,
-                    thresholds=None):
+                    thresholds=None, order=None):
     """Componentwise boundary search from state x: (side, reference, #Phi evaluations),
-    side 0 = lower reference (Phi(x) <= m'), 1 = upper."""
+    side 0 = lower reference (Phi(x) <= m'), 1 = upper.  order: None = index order,
+    else the visiting order of the components."""
     src, dst, thr = _graph_args(edges, thresholds)
     xs = np.ascontiguousarray(x, dtype=np.uint8)
     out = np.zeros_like(xs)
     ev = np.zeros(1, dtype=np.int64)
+    od = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
     side = _load().orc_boundary_search(kind, n_nodes, src.size, _p(src), _p(dst), s, t, thr.size, _p(thr),
-                                       m_prime, K, _p(xs), _p(out), _p(ev))
+                                       m_prime, K, _p(xs), _p(out), _p(ev), None if od is None else _p(od))
     return int(side), out, int(ev[0])
 
 
@@ -250,7 +264,7 @@ def nondominated(refs, upper: bool) -> np.ndarray:
 
 def stage1(pmf, kind: int, n_nodes: int, edges, s: int, t: int, seed: int, N: int, max_starts: int,
            eps_u: float, R_max: int, max_rounds: int, m_prime: int = 0, thresholds=None,
-           ref_L=None, ref_U=None):
+           ref_L=None, ref_U=None, order: int = SEARCH_INDEX_ORDER):
     """Stage 1 of the RSR workflow (Sec. 3.5), with many searches per round.
 
     Round r draws samples r*N .. r*N+N-1 (Philox stream `seed`) and classifies
@@ -260,7 +274,8 @@ def stage1(pmf, kind: int, n_nodes: int, edges, s: int, t: int, seed: int, N: in
     samples in index order (a uniform random choice, the samples being i.i.d.)
     each start a componentwise boundary search.  The new references are
     appended to their side in start order, and each side is reduced to its
-    non-dominated elements (order kept).
+    non-dominated elements (order kept).  order = SEARCH_PERMUTED visits the
+    components of the search from sample h (global index) in search_order(seed, h).
 
     Returns dict(ref_L, ref_U, history=[(n_unclassified, R_L, R_U, n_starts)],
     stop=0 converged | 1 R_max | 2 max_rounds, phi_evals)."""
@@ -288,7 +303,8 @@ def stage1(pmf, kind: int, n_nodes: int, edges, s: int, t: int, seed: int, N: in
         hist.append((n_u, L.shape[0], U.shape[0], int(starts.size)))
         newL, newU = [], []
         for h in starts:
-            side, ref, ev = boundary_search(kind, n_nodes, edges, s, t, X[h], K, m_prime, thresholds)
+            od = search_order(seed, r * N + int(h), n) if order == SEARCH_PERMUTED else None
+            side, ref, ev = boundary_search(kind, n_nodes, edges, s, t, X[h], K, m_prime, thresholds, od)
             evals += ev
             (newL if side == 0 else newU).append(ref)
         if newL:

@@ -427,15 +427,40 @@ int64_t orc_resolve(int kind, int n_nodes, int n, const int32_t *src, const int3
 /* upper (side 1) boundary reference state.  *phi_evals receives the number */
 /* of Phi evaluations, the first one included.                              */
 /* ------------------------------------------------------------------------ */
+/* Visiting order of the permuted search (not in the paper, which visits in   */
+/* index order): a Fisher-Yates shuffle of 0..n-1 driven by Philox4x32-10    */
+/* with key = seed and counter (h lo, h hi, floor(i/4), 1) -- counter word 3  */
+/* = 1 keeps it apart from the sampler's words (word 3 = 0).  For i = n-1    */
+/* down to 1: u = word (i mod 4) of block floor(i/4), j = (u * (i+1)) >> 32  */
+/* (an exact integer multiply-shift), swap order[i] and order[j].            */
+void orc_search_order(uint64_t seed, uint64_t h, int n, int32_t *order)
+{
+    for (int i = 0; i < n; ++i) order[i] = i;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int i = n - 1; i >= 1; --i) {
+        const uint32_t ctr[4] = {(uint32_t)h, (uint32_t)(h >> 32), (uint32_t)(i / 4), 1u};
+        uint32_t words[4];
+        orc_philox4x32_10(ctr, key, words);
+        const uint32_t u = words[i % 4];
+        const int j = (int)(((uint64_t)u * (uint64_t)(i + 1)) >> 32);
+        const int32_t tmp = order[i];
+        order[i] = order[j];
+        order[j] = tmp;
+    }
+}
+
+/* order = NULL: index order 0..n-1 (Sec. 3.4); otherwise the components are
+ * visited as order[0], order[1], ... */
 int orc_boundary_search(int kind, int n_nodes, int n, const int32_t *src, const int32_t *dst, int s, int t,
                         int n_thr, const int32_t *thr, int m_prime, int K, const uint8_t *x_in, uint8_t *x_out,
-                        int64_t *phi_evals)
+                        int64_t *phi_evals, const int32_t *order)
 {
     int64_t evals = 0;
     for (int i = 0; i < n; ++i) x_out[i] = x_in[i];
     const int lower = orc_phi(kind, n_nodes, n, src, dst, s, t, n_thr, thr, x_out) <= m_prime;
     evals += 1;
-    for (int i = 0; i < n; ++i) {
+    for (int step = 0; step < n; ++step) {
+        const int i = order ? order[step] : step;
         if (lower) {
             while (x_out[i] < K - 1) {
                 x_out[i] += 1;

@@ -190,3 +190,48 @@ def test_stage1_multistate_flow_finds_complete_set_elements():
     assert res["stop"] == 0
     assert {bytes(r) for r in res["ref_L"]} <= {bytes(r) for r in ref_L}
     assert {bytes(r) for r in res["ref_U"]} <= {bytes(r) for r in ref_U}
+
+
+def test_search_order_is_a_uniform_permutation():
+    seen = {}
+    for h in range(24000):
+        o = O.search_order(7, h, 4)
+        assert sorted(o.tolist()) == [0, 1, 2, 3]
+        seen[tuple(o)] = seen.get(tuple(o), 0) + 1
+    assert len(seen) == 24
+    counts = np.array(list(seen.values()), dtype=np.float64)
+    chi2 = ((counts - 1000.0) ** 2 / 1000.0).sum()
+    assert chi2 < 49.7                     # 99.9% quantile of chi^2 with 23 degrees of freedom
+    big = O.search_order(3, 12345, 300)
+    assert sorted(big.tolist()) == list(range(300))
+    assert not np.array_equal(big, O.search_order(3, 12346, 300))
+    assert not np.array_equal(big, O.search_order(4, 12345, 300))
+
+
+def test_permuted_search_is_the_lexicographic_extreme_in_the_visiting_order():
+    p, n_nodes, edges, s, t, phi_all = _grid()
+    X = W.all_states(p.n, 2)
+    rng = np.random.default_rng(16)
+    for k, x in enumerate((rng.random((40, p.n)) < 0.75).astype(np.uint8)):
+        order = O.search_order(9, k, p.n)
+        side, r, _ = O.boundary_search(O.PHI_ST_CONNECTIVITY, n_nodes, edges, s, t, x, 2, order=order)
+        # component order[0] is the most significant: relabel and reuse the index-order characterisation
+        Xp = X[:, order]
+        key = Xp.astype(np.int64) @ (2 ** np.arange(p.n - 1, -1, -1)).astype(np.int64)
+        if side == 0:
+            ok = np.all(X >= x, axis=1) & (phi_all <= 0)
+            want = X[np.flatnonzero(ok)[np.argmax(key[ok])]]
+        else:
+            ok = np.all(X <= x, axis=1) & (phi_all >= 1)
+            want = X[np.flatnonzero(ok)[np.argmin(key[ok])]]
+        assert np.array_equal(r, want)
+
+
+def test_stage1_permuted_order_converges_to_boundary_states():
+    p, n_nodes, edges, s, t, _ = _grid()
+    N = 4000
+    res = O.stage1(p.pmf, O.PHI_ST_CONNECTIVITY, n_nodes, edges, s, t, seed=3, N=N, max_starts=4,
+                   eps_u=0.5 / N, R_max=1000, max_rounds=200, order=O.SEARCH_PERMUTED)
+    assert res["stop"] == 0
+    assert all(bytes(r) in {bytes(q) for q in p.ref_L} for r in res["ref_L"])
+    assert all(bytes(r) in {bytes(q) for q in p.ref_U} for r in res["ref_U"])
