@@ -349,11 +349,19 @@ RSR_API int rsr_level_pmf(const rsr_problem *problems, int32_t n_boundaries, voi
 /*
  * Stage 1 building block (Sec. 3.4): componentwise boundary search.  For each
  * j < n_starts, sample offset + starts[j] of `seed` is regenerated (same
- * sampler as rsr_classify).  If Phi(x) <= m' its components are raised in
- * index order, one state at a time with Phi re-evaluated after each step, until
- * the top state or until a step makes Phi > m' (that step is undone); otherwise
- * they are lowered in the same way while Phi >= m'+1 holds.  The final state is
- * a boundary reference state.
+ * sampler as rsr_classify).  If Phi(x) <= m' its components are raised one at a
+ * time in the visiting order, one state at a time with Phi re-evaluated after
+ * each step, until the top state or until a step makes Phi > m' (that step is
+ * undone); otherwise they are lowered in the same way while Phi >= m'+1 holds.
+ * The final state is a boundary reference state.
+ *   order     : RSR_SEARCH_INDEX_ORDER visits components 0, 1, ..., n-1, as the
+ *               paper does; RSR_SEARCH_PERMUTED visits them in a per-start
+ *               pseudo-random order (not in the paper): a Fisher-Yates shuffle,
+ *               for i = n-1 down to 1 swapping i with j = (u*(i+1)) >> 32, u = word
+ *               (i mod 4) of Philox4x32-10(key = seed, counter = (h lo, h hi,
+ *               floor(i/4), 1)), h = offset + starts[j].  Searches from different
+ *               samples then spread over the boundary instead of concentrating on
+ *               the states that are extreme in index order.
  *   problem   : n, K, pmf are read (references are not).
  *   starts    : device int64[n_starts], sample indices relative to offset.
  *   refs_out  : device uint8[n_starts*n], row j = the reference found from start j.
@@ -364,9 +372,11 @@ RSR_API int rsr_level_pmf(const rsr_problem *problems, int32_t n_boundaries, voi
  * Asynchronous on `stream`.  Bad node indices set the error word of `ws`.
  */
 RSR_API size_t rsr_search_workspace_size(const rsr_problem *problem);
+#define RSR_SEARCH_INDEX_ORDER 0
+#define RSR_SEARCH_PERMUTED 1
 RSR_API int rsr_boundary_search(const rsr_problem *problem, const rsr_system *system, uint64_t seed,
                                 uint64_t offset, const int64_t *starts, int64_t n_starts, uint8_t *refs_out,
-                                uint8_t *side_out, int64_t *phi_evals, void *ws, size_t ws_bytes,
+                                uint8_t *side_out, int64_t *phi_evals, int32_t order, void *ws, size_t ws_bytes,
                                 rsr_stream_t stream);
 
 /*
@@ -401,6 +411,7 @@ typedef struct rsr_stage1_opts {
     double eps_u;           /* target unclassified fraction                          */
     int64_t R_max;          /* reference limit; each buffer holds R_max rows         */
     int32_t max_rounds;     /* >= 1                                                  */
+    int32_t search_order;   /* RSR_SEARCH_INDEX_ORDER or RSR_SEARCH_PERMUTED         */
 } rsr_stage1_opts;
 
 typedef struct rsr_stage1_result {

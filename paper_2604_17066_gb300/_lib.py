@@ -43,6 +43,9 @@ RSR_PHI_ST_MAXFLOW_LEVELS = 1
 RSR_PHI_GLOBAL_CONNECTIVITY = 2
 RSR_PHI_GLOBAL_CONN_LEVEL = 3
 
+RSR_SEARCH_INDEX_ORDER = 0
+RSR_SEARCH_PERMUTED = 1
+
 
 class rsr_system(ctypes.Structure):
     _fields_ = [
@@ -66,6 +69,7 @@ class rsr_stage1_opts(ctypes.Structure):
         ("eps_u", ctypes.c_double),
         ("R_max", ctypes.c_int64),
         ("max_rounds", ctypes.c_int32),
+        ("search_order", ctypes.c_int32),
     ]
 
 
@@ -111,7 +115,7 @@ SIGNATURES = {
                                      _P, _P, _P]),
     "rsr_search_workspace_size": (ctypes.c_size_t, [_PROB]),
     "rsr_boundary_search": (ctypes.c_int, [_PROB, ctypes.POINTER(rsr_system), _U64, _U64, _P, _I64, _P, _P, _P,
-                                           _P, _S, _P]),
+                                           _I32, _P, _S, _P]),
     "rsr_nondominated_scratch_size": (ctypes.c_size_t, [_I32, _I32, _I64]),
     "rsr_nondominated": (ctypes.c_int, [_I32, _I32, _I64, _P, _I32, _P, _P, _P, _S, _P]),
     "rsr_stage1_workspace_size": (ctypes.c_size_t, [_PROB, ctypes.POINTER(rsr_stage1_opts)]),

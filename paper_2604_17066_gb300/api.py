@@ -364,7 +364,8 @@ def _aligned(nbytes: int, device) -> torch.Tensor:
 
 
 def rsr_boundary_search(problem: Problem, system: System, seed: int, offset: int, starts: torch.Tensor,
-                        ws: Optional[torch.Tensor] = None, phi_evals: Optional[torch.Tensor] = None, stream=None):
+                        ws: Optional[torch.Tensor] = None, phi_evals: Optional[torch.Tensor] = None,
+                        order: int = _lib.RSR_SEARCH_INDEX_ORDER, stream=None):
     """Componentwise boundary search from samples offset + starts[j]; returns
     (refs [n_starts x n] uint8, side [n_starts] uint8, phi_evals [1] int64) on the device."""
     dev = starts.device
@@ -382,7 +383,8 @@ def rsr_boundary_search(problem: Problem, system: System, seed: int, offset: int
         phi_evals = torch.zeros(1, dtype=torch.int64, device=dev)
     g = system.struct()
     check(lib.rsr_boundary_search(ctypes.byref(s), ctypes.byref(g), int(seed), int(offset), _ptr(starts), S,
-                                  _ptr(refs), _ptr(side), _ptr(phi_evals), _ptr(ws), ws.numel(), _stream(stream)),
+                                  _ptr(refs), _ptr(side), _ptr(phi_evals), int(order), _ptr(ws), ws.numel(),
+                                  _stream(stream)),
           "rsr_boundary_search")
     return refs, side, phi_evals
 
@@ -405,7 +407,7 @@ def rsr_nondominated(refs: torch.Tensor, K: int, upper: bool, stream=None):
 
 def rsr_stage1(pmf, system: System, seed: int, N: int, max_starts: int, eps_u: float, R_max: int,
                max_rounds: int, ref_L=None, ref_U=None, path: int = RSR_PATH_POPC, stream=None,
-               device: Optional[torch.device] = None):
+               device: Optional[torch.device] = None, order: int = _lib.RSR_SEARCH_INDEX_ORDER):
     """Stage 1 on the device.  Returns dict(ref_L, ref_U (device uint8),
     history (rounds x 4 int64: n_u, R_L, R_U, starts), rounds, stop, n_u_last,
     phi_evals)."""
@@ -429,6 +431,7 @@ def rsr_stage1(pmf, system: System, seed: int, N: int, max_starts: int, eps_u: f
     opts = _lib.rsr_stage1_opts()
     opts.seed, opts.N, opts.max_starts = int(seed), int(N), int(max_starts)
     opts.eps_u, opts.R_max, opts.max_rounds = float(eps_u), int(R_max), int(max_rounds)
+    opts.search_order = int(order)
     lib = _lib.load()
     size = lib.rsr_stage1_workspace_size(ctypes.byref(prob), ctypes.byref(opts))
     if size == 0:

@@ -302,24 +302,53 @@ __global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyPara
     }
 }
 
-// Componentwise boundary search (Sec. 3.4) from samples offset + starts[j].
+// Permuted visiting order from sample h: Fisher-Yates over 0..n-1 driven by
+// Philox4x32-10 (key = seed, counter (h lo, h hi, floor(i/4), 1)); for
+// i = n-1 down to 1, j = (u * (i+1)) >> 32 with u = word (i mod 4).  One lane.
+__device__ void search_order(const ClassifyParams &p, uint64_t h, int16_t *ord) {
+    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
+    for (int i = 0; i < p.n; ++i) ord[i] = (int16_t)i;
+    U32x4 blk{0u, 0u, 0u, 0u};
+    int cur = -1;
+    for (int i = p.n - 1; i >= 1; --i) {
+        if ((i >> 2) != cur) {
+            cur = i >> 2;
+            blk = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)cur, 1u, key0, key1);
+        }
+        const uint32_t u = (i & 3) == 0 ? blk.x : (i & 3) == 1 ? blk.y : (i & 3) == 2 ? blk.z : blk.w;
+        const int j = (int)(((unsigned long long)u * (unsigned long long)(i + 1)) >> 32);
+        const int16_t tmp = ord[i];
+        ord[i] = ord[j];
+        ord[j] = tmp;
+    }
+}
+
+// Componentwise boundary search (Sec. 3.4) from samples offset + starts[j];
+// order_mode 0 visits components in index order, 1 in search_order.
 __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParams p, const Sys g,
                                                              const int64_t *starts, int64_t n_starts,
                                                              uint8_t *refs_out, uint8_t *side_out,
-                                                             unsigned long long *evals) {
+                                                             unsigned long long *evals, int order_mode) {
     __shared__ WarpScratch ws[kWarps];
     __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
     __shared__ unsigned long long s_thr[kMaxKenc];
+    extern __shared__ int16_t s_order[];     // kWarps * kMaxKenc (dynamic)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *err = &p.hdr->error;
     stage_system(p, g, s_src, s_dst, s_thr, err);
     WarpScratch &w = ws[warp];
+    int16_t *ord = s_order + warp * kMaxKenc;
     const int top = p.K - 1;
     for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < n_starts; j += (int64_t)gridDim.x * kWarps) {
         regen_sample(p, starts[j], w, s_thr);
+        if (order_mode) {
+            if (lane == 0) search_order(p, p.offset + (uint64_t)starts[j], ord);
+            __syncwarp();
+        }
         const bool lower = phi_le(g, p.n, w, s_src, s_dst, err);
         unsigned long long ev = 1;
-        for (int i = 0; i < p.n; ++i) {
+        for (int step = 0; step < p.n; ++step) {
+            const int i = order_mode ? (int)ord[step] : step;
             if (lower) {
                 while (w.x[i] < top) {
                     __syncwarp();
@@ -453,11 +482,21 @@ cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8
 }
 
 cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const int64_t *starts, int64_t n_starts,
-                          uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, cudaStream_t s) {
+                          uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, int order_mode,
+                          cudaStream_t s) {
     if (n_starts <= 0) return cudaSuccess;
+    constexpr int kDyn = kWarps * kMaxKenc * (int)sizeof(int16_t);
+    static int attr_set[64] = {0};
+    const int d = [] { int v = 0; cudaGetDevice(&v); return v; }();
+    if (d >= 0 && d < 64 && !attr_set[d]) {
+        const cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+        if (e != cudaSuccess) return e;
+        attr_set[d] = 1;
+    }
     const Sys g = make_sys(sys);
     const int64_t grid = std::min<int64_t>((n_starts + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
-    search_kernel<<<(unsigned)grid, kWarps * 32, 0, s>>>(p, g, starts, n_starts, refs_out, side_out, evals);
+    search_kernel<<<(unsigned)grid, kWarps * 32, kDyn, s>>>(p, g, starts, n_starts, refs_out, side_out, evals,
+                                                             order_mode);
     return cudaGetLastError();
 }
 

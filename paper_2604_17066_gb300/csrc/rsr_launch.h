@@ -38,7 +38,8 @@ cudaError_t launch_levels(const ClassifyParams &p, const rsr_system &sys, int nb
                           uint8_t *levels_out, unsigned long long *level_counts, unsigned long long *n_phi,
                           cudaStream_t s);
 cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const int64_t *starts, int64_t n_starts,
-                          uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, cudaStream_t s);
+                          uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, int order_mode,
+                          cudaStream_t s);
 
 // Reference-set maintenance and order-preserving selection (maintain.cu).
 cudaError_t launch_nondominated(const uint32_t *enc, int64_t R, int words_b, bool upper, uint8_t *keep,

@@ -95,6 +95,8 @@ int check_opts(const rsr_problem *p, const rsr_stage1_opts *o) {
     if (!p || !o) return RSR_ERR_INVALID_ARG;
     if (o->N < 1 || o->max_starts < 1 || o->R_max < 1 || o->max_rounds < 1 || !(o->eps_u >= 0.0))
         return RSR_ERR_INVALID_ARG;
+    if (o->search_order != RSR_SEARCH_INDEX_ORDER && o->search_order != RSR_SEARCH_PERMUTED)
+        return RSR_ERR_INVALID_ARG;
     if (o->R_max >= (int64_t(1) << 31)) return RSR_ERR_UNSUPPORTED;
     if (p->R_L < 0 || p->R_U < 0 || p->R_L > o->R_max || p->R_U > o->R_max) return RSR_ERR_INVALID_ARG;
     if (p->path < RSR_PATH_AUTO || p->path > RSR_PATH_TC) return RSR_ERR_INVALID_ARG;
@@ -115,8 +117,9 @@ size_t rsr_search_workspace_size(const rsr_problem *problem) {
 
 int rsr_boundary_search(const rsr_problem *problem, const rsr_system *system, uint64_t seed, uint64_t offset,
                         const int64_t *starts, int64_t n_starts, uint8_t *refs_out, uint8_t *side_out,
-                        int64_t *phi_evals, void *ws, size_t ws_bytes, rsr_stream_t stream) {
+                        int64_t *phi_evals, int32_t order, void *ws, size_t ws_bytes, rsr_stream_t stream) {
     if (!problem) return RSR_ERR_INVALID_ARG;
+    if (order != RSR_SEARCH_INDEX_ORDER && order != RSR_SEARCH_PERMUTED) return RSR_ERR_INVALID_ARG;
     int st = validate_states(problem->n, problem->K, problem->pmf);
     if (st != RSR_OK) return st;
     if ((st = validate_system(system, problem->K)) != RSR_OK) return st;
@@ -141,7 +144,7 @@ int rsr_boundary_search(const rsr_problem *problem, const rsr_system *system, ui
     c.offset = offset;
     unsigned long long *ev = phi_evals ? reinterpret_cast<unsigned long long *>(phi_evals)
                                        : reinterpret_cast<unsigned long long *>(base + kSearchOffEvals);
-    S1_CUDA(launch_search(c, *system, starts, n_starts, refs_out, side_out, ev, s));
+    S1_CUDA(launch_search(c, *system, starts, n_starts, refs_out, side_out, ev, order, s));
     return RSR_OK;
 }
 
@@ -255,8 +258,8 @@ int rsr_stage1(const rsr_problem *problem, const rsr_system *system, const rsr_s
             break;
         }
         S1_CUDA(launch_select(labels, 2, N, S, starts, &scal[0], selscr, s));
-        if ((st = rsr_boundary_search(problem, system, opts->seed, off, starts, S, fresh, side, &scal[2], ws_search,
-                                      Lw.search_bytes, stream)) != RSR_OK)
+        if ((st = rsr_boundary_search(problem, system, opts->seed, off, starts, S, fresh, side, &scal[2],
+                                      opts->search_order, ws_search, Lw.search_bytes, stream)) != RSR_OK)
             return st;
         for (int v = 0; v < 2; ++v) {
             int64_t c = 0;

@@ -119,15 +119,16 @@ def test_stage1_entry_points_reject_bad_arguments(lib):
     assert lib.rsr_search_workspace_size(ctypes.byref(s)) == 512 + 256
     good = _system_struct()
     fake = P(0x10000)                                 # 256-aligned, never dereferenced
-    args = lambda g, ws_bytes=4096: (ctypes.byref(s), ctypes.byref(g), 1, 0, fake, 2, fake, fake, None, fake,
-                                     ws_bytes, None)
+    args = lambda g, ws_bytes=4096, order=0: (ctypes.byref(s), ctypes.byref(g), 1, 0, fake, 2, fake, fake, None,
+                                              order, fake, ws_bytes, None)
+    assert lib.rsr_boundary_search(*args(good, order=2)) == E_ARG                   # unknown visiting order
     assert lib.rsr_boundary_search(*args(_system_struct(kind=7))) == E_ARG            # unknown Phi
     assert lib.rsr_boundary_search(*args(_system_struct(n_nodes=2000))) == E_UNS      # too many nodes
     assert lib.rsr_boundary_search(*args(_system_struct(t=4))) == E_ARG               # t out of range
     assert lib.rsr_boundary_search(*args(_system_struct(kind=1, levels=(3, 2)))) == E_ARG   # not ascending
     assert lib.rsr_boundary_search(*args(good, ws_bytes=100)) == E_WS
     s3, _ = _problem_struct(n=4, K=3, R_L=0, R_U=0)
-    assert lib.rsr_boundary_search(ctypes.byref(s3), ctypes.byref(good), 1, 0, fake, 2, fake, fake, None, fake,
+    assert lib.rsr_boundary_search(ctypes.byref(s3), ctypes.byref(good), 1, 0, fake, 2, fake, fake, None, 0, fake,
                                    4096, None) == E_ARG                               # connectivity needs K = 2
     # non-dominance scratch: one 32-bit word bucket per reference, 256-byte rounded
     assert lib.rsr_nondominated_scratch_size(4, 2, 100) == 512
@@ -139,7 +140,8 @@ def test_stage1_entry_points_reject_bad_arguments(lib):
     opts = _lib.rsr_stage1_opts()
     opts.seed, opts.N, opts.max_starts, opts.eps_u, opts.R_max, opts.max_rounds = 1, 1000, 8, 1e-5, 64, 10
     assert lib.rsr_stage1_workspace_size(ctypes.byref(s), ctypes.byref(opts)) > 0
-    for field, bad in (("N", 0), ("max_starts", 0), ("R_max", 0), ("max_rounds", 0), ("eps_u", -1.0)):
+    for field, bad in (("N", 0), ("max_starts", 0), ("R_max", 0), ("max_rounds", 0), ("eps_u", -1.0),
+                       ("search_order", 5)):
         old = getattr(opts, field)
         setattr(opts, field, bad)
         assert lib.rsr_stage1_workspace_size(ctypes.byref(s), ctypes.byref(opts)) == 0, field

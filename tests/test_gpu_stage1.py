@@ -74,51 +74,57 @@ def test_resolve_global_connectivity_kinds(rsr, kind, m_prime, n_edges, p_f):
 
 
 # ---------------------------------------------------------------- boundary search
-def _check_search(rsr, pmf, kind, nn, edges, s, t, seed, offset, starts, m_prime=0, thr=()):
+def _check_search(rsr, pmf, kind, nn, edges, s, t, seed, offset, starts, m_prime=0, thr=(), order=0):
     K = pmf.shape[1]
     P = rsr.Problem(pmf, np.zeros((0, pmf.shape[0]), np.uint8), np.ones((1, pmf.shape[0]), np.uint8) * (K - 1))
     sys_ = rsr.System(kind, nn, edges, s, t, thr, m_prime)
     st = torch.as_tensor(np.asarray(starts, dtype=np.int64), device="cuda")
-    refs, side, ev = rsr.rsr_boundary_search(P, sys_, seed, offset, st)
+    refs, side, ev = rsr.rsr_boundary_search(P, sys_, seed, offset, st, order=order)
     torch.cuda.synchronize()
     refs, side, ev = refs.cpu().numpy(), side.cpu().numpy(), int(ev.item())
     total = 0
     for j, h in enumerate(starts):
         x = O.sample(pmf, seed, offset + int(h), 1)[0]
-        sd, r, e = O.boundary_search(kind, nn, edges, s, t, x, K, m_prime, list(thr) if thr else None)
+        od = O.search_order(seed, offset + int(h), pmf.shape[0]) if order else None
+        sd, r, e = O.boundary_search(kind, nn, edges, s, t, x, K, m_prime, list(thr) if thr else None, od)
         assert side[j] == sd, j
         assert np.array_equal(refs[j], r), j
         total += e
     assert ev == total
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("kind", [0, 2, 3])
-def test_boundary_search_grid(rsr, kind):
+def test_boundary_search_grid(rsr, kind, order):
     p, nn, edges, s, t = _grid()
     pmf = W.binary_pmf(np.full(p.n, 0.3))
     m_prime = 1 if kind == 3 else 0
-    _check_search(rsr, pmf, kind, nn, edges, s, t, 11, 7, np.arange(0, 600, 3), m_prime)
+    _check_search(rsr, pmf, kind, nn, edges, s, t, 11, 7, np.arange(0, 600, 3), m_prime, order=order)
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("m_prime", [0, 1])
-def test_boundary_search_small_flow(rsr, m_prime):
+def test_boundary_search_small_flow(rsr, m_prime, order):
     nn, arcs, s, t, pmf, thr = _small_flow()
-    _check_search(rsr, pmf, 1, nn, arcs, s, t, 3, 0, np.arange(257), m_prime, thr)
+    _check_search(rsr, pmf, 1, nn, arcs, s, t, 3, 0, np.arange(257), m_prime, thr, order=order)
 
 
-def test_boundary_search_c4_flow(rsr):
+@pytest.mark.parametrize("order", [0, 1])
+def test_boundary_search_c4_flow(rsr, order):
     import workloads.large as L
     p = L.c4_flow(0)
     m = p.meta
     _check_search(rsr, p.pmf, 1, m["n_nodes"], m["arcs"], m["s"], m["t"], 4, 5000, np.arange(0, 130 * 7, 7), 0,
-                  (m["l1"], m["l2"]))
+                  (m["l1"], m["l2"]), order=order)
 
 
-def test_boundary_search_c2_graph(rsr):
+@pytest.mark.parametrize("order", [0, 1])
+def test_boundary_search_c2_graph(rsr, order):
     import workloads.large as L
     p = L.c2_rgg()
     m = p.meta
-    _check_search(rsr, p.pmf, 0, m["n_nodes"], m["edges"], m["s"], m["t"], 1, 0, np.arange(0, 200 * 13, 13))
+    _check_search(rsr, p.pmf, 0, m["n_nodes"], m["edges"], m["s"], m["t"], 1, 0, np.arange(0, 200 * 13, 13),
+                  order=order)
 
 
 # ---------------------------------------------------------------- non-dominance
@@ -152,11 +158,12 @@ def test_nondominated_empty_and_single(rsr):
 
 # ---------------------------------------------------------------- Stage 1 loop
 def _check_stage1(rsr, pmf, kind, nn, edges, s, t, seed, N, B, eps_u, R_max, rounds, m_prime=0, thr=(),
-                  path=POPC, ref_L=None, ref_U=None):
+                  path=POPC, ref_L=None, ref_U=None, order=0):
     sys_ = rsr.System(kind, nn, edges, s, t, thr, m_prime)
-    got = rsr.rsr_stage1(pmf, sys_, seed, N, B, eps_u, R_max, rounds, ref_L=ref_L, ref_U=ref_U, path=path)
+    got = rsr.rsr_stage1(pmf, sys_, seed, N, B, eps_u, R_max, rounds, ref_L=ref_L, ref_U=ref_U, path=path,
+                         order=order)
     want = O.stage1(pmf, kind, nn, edges, s, t, seed, N, B, eps_u, R_max, rounds, m_prime=m_prime,
-                    thresholds=list(thr) if thr else None, ref_L=ref_L, ref_U=ref_U)
+                    thresholds=list(thr) if thr else None, ref_L=ref_L, ref_U=ref_U, order=order)
     assert got["stop"] == want["stop"]
     assert np.array_equal(got["history"], np.array(want["history"], dtype=np.int64).reshape(-1, 4))
     assert np.array_equal(got["ref_L"].cpu().numpy(), want["ref_L"])
@@ -200,18 +207,26 @@ def test_stage1_multistate_flow(rsr, m_prime):
     _check_stage1(rsr, pmf, 1, nn, arcs, s, t, 9, 3000, 3, 0.5 / 3000, 10000, 300, m_prime, thr)
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("kind,m_prime", [(2, 0), (3, 1)])
-def test_stage1_global_connectivity_grid(rsr, kind, m_prime):
+def test_stage1_global_connectivity_grid(rsr, kind, m_prime, order):
     p, nn, edges, s, t = _grid()
     pmf = W.binary_pmf(np.full(p.n, 0.05))
-    _check_stage1(rsr, pmf, kind, nn, edges, s, t, 12, 5000, 16, 1e-3, 3000, 25, m_prime)
+    _check_stage1(rsr, pmf, kind, nn, edges, s, t, 12, 5000, 16, 1e-3, 3000, 25, m_prime, order=order)
 
 
-def test_stage1_c2_graph_parity(rsr):
+@pytest.mark.parametrize("order", [0, 1])
+def test_stage1_c2_graph_parity(rsr, order):
     import workloads.large as L
     p = L.c2_rgg()
     m = p.meta
-    _check_stage1(rsr, p.pmf, 0, m["n_nodes"], m["edges"], m["s"], m["t"], 2, 20000, 64, 1e-4, 2000, 6)
+    _check_stage1(rsr, p.pmf, 0, m["n_nodes"], m["edges"], m["s"], m["t"], 2, 20000, 64, 1e-4, 2000, 6,
+                  order=order)
+
+
+def test_stage1_multistate_flow_permuted(rsr):
+    nn, arcs, s, t, pmf, thr = _small_flow()
+    _check_stage1(rsr, pmf, 1, nn, arcs, s, t, 9, 3000, 3, 0.5 / 3000, 10000, 300, 1, thr, order=1)
 
 
 def test_stage1_c2_full_size_finds_boundary_states(rsr):
