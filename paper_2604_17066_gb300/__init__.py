@@ -16,7 +16,7 @@ __all__ = [
     "rsr_classify_static", "rsr_batch_grad", "System", "rsr_resolve",
     "rsr_boundary_search", "rsr_nondominated", "rsr_stage1", "rsr_level_pmf",
     "RSR_PHI_ST_CONNECTIVITY", "RSR_PHI_ST_MAXFLOW_LEVELS", "RSR_PHI_GLOBAL_CONNECTIVITY",
-    "RSR_PHI_GLOBAL_CONN_LEVEL",
+    "RSR_PHI_GLOBAL_CONN_LEVEL", "RSR_SEARCH_INDEX_ORDER", "RSR_SEARCH_PERMUTED",
     "RSR_PATH_AUTO", "RSR_PATH_POPC", "RSR_PATH_TC", "RSR_FLAG_DENSE",
 ]
 

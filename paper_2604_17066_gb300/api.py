@@ -16,7 +16,8 @@ import torch
 from . import _lib
 from ._lib import (RSR_FLAG_DENSE, RSR_PATH_AUTO, RSR_PATH_POPC, RSR_PATH_TC,  # noqa: F401
                    RSR_PHI_GLOBAL_CONN_LEVEL, RSR_PHI_GLOBAL_CONNECTIVITY, RSR_PHI_ST_CONNECTIVITY,
-                   RSR_PHI_ST_MAXFLOW_LEVELS, RSRError, check, rsr_estimate_out,
+                   RSR_PHI_ST_MAXFLOW_LEVELS, RSR_SEARCH_INDEX_ORDER, RSR_SEARCH_PERMUTED, RSRError, check,
+                   rsr_estimate_out,
                    rsr_problem, rsr_system)
 
 
