@@ -311,18 +311,46 @@ def run_reference(args):
     return 0
 
 
+def run_pipeline(args):
+    """--workload pipeline: the whole workflow of bench_pipeline as its own line
+    (value = seconds of Stage 1 + Stage 2 on the 119/295 graph, permuted
+    visiting order).  Used for the kernel launch lists of Stage 1 / Stage 2."""
+    import torch
+    from paper_2604_17066_gb300 import api as rsr
+    from paper_2604_17066_gb300 import build as rsr_build
+    rsr_build.build()
+    torch.cuda.set_device(0)
+    res = None
+    with Clocks(None) as clk:
+        res = bench_pipeline(rsr, torch, reps=max(1, args.steps))
+    total = res["stage1"]["s"] + res["stage2_ms_1e6_samples"] / 1000.0
+    line = {"metric": "RSR workflow time: Stage 1 to p_u < 1e-5 from no references + Stage 2 on 1e6 samples",
+            "value": total, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-packed",
+            "data": "synthetic", "config": {"workload": "pipeline_rgg119n295e_pf0.05"},
+            "clocks": clk.summary(), "pipeline": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "pipeline"])
     ap.add_argument("--ref-samples", type=int, default=8000)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-scenario batched comparison")
     ap.add_argument("--samples", type=int, default=0, help="override samples per GPU (profiling runs)")
     args = ap.parse_args()
+    if args.workload == "pipeline":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the workflow line has no oracle arm; "
+                              "the oracle's Stage 1 is timed by the tests only"}), flush=True)
+            return 0
+        return run_pipeline(args)
     if args.impl == "reference":
         return run_reference(args)
 
