@@ -66,17 +66,20 @@ __device__ __forceinline__ bool bit(const uint32_t *v, int i) { return (v[i >> 5
 
 __device__ __forceinline__ int vload(const int32_t *p) { return *(const volatile int32_t *)p; }
 
-// Breadth-first tree from node 0 over working edges, level by level: in sweep d
+// Breadth-first tree from `root` over working edges, level by level: in sweep d
 // only nodes of depth d-1 expand, so depths are exact.  parent[v] = depth << 16
-// | edge (0xFFFF at the root), -1 unreached.  Returns the number of reached nodes.
-__device__ int bfs_tree(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst) {
+// | edge (0xFFFF at the root), -1 unreached.  Stops early once `stop` (>= 0) is
+// reached.  Returns the number of reached nodes.
+__device__ int bfs_tree(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
+                        int root = 0, int stop = -1) {
     const int lane = threadIdx.x & 31;
     for (int v = lane; v < g.n_nodes; v += 32) w.parent[v] = -1;
     __syncwarp();
-    if (lane == 0) w.parent[0] = 0xFFFF;
+    if (lane == 0) w.parent[root] = 0xFFFF;
     __syncwarp();
     int reached = 1;
     for (int d = 1; d < g.n_nodes; ++d) {
+        if (stop >= 0 && vload(&w.parent[stop]) != -1) break;
         int claimed = 0;
         for (int e = lane; e < n; e += 32) {
             if (!w.x[e]) continue;
@@ -137,6 +140,89 @@ __device__ bool bridgeless(const Sys &g, int n, WarpScratch &w, const int32_t *s
     return __all_sync(0xffffffffu, ok);
 }
 
+// One augmenting path s -> t in the residual graph of the flow in w.flow
+// (capacities w.x), found by a warp-parallel search; parents (2a forward,
+// 2a+1 backward arc) are claimed with atomicCAS, so they form a tree rooted at
+// s.  True if t was reached.
+__device__ bool residual_path(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst) {
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < g.n_nodes; v += 32) w.parent[v] = -1;
+    __syncwarp();
+    if (lane == 0) w.parent[g.s] = -2;
+    __syncwarp();
+    for (int sweep = 0; sweep <= g.n_nodes; ++sweep) {
+        bool changed = false;
+        for (int a = lane; a < n; a += 32) {
+            const int u = s_src[a], v = s_dst[a];
+            const int pu = vload(&w.parent[u]), pv = vload(&w.parent[v]);
+            if (pu != -1 && pv == -1 && w.flow[a] < (int)w.x[a]) {
+                if (atomicCAS(&w.parent[v], -1, 2 * a) == -1) changed = true;
+            } else if (pv != -1 && pu == -1 && w.flow[a] > 0) {
+                if (atomicCAS(&w.parent[u], -1, 2 * a + 1) == -1) changed = true;
+            }
+        }
+        __syncwarp();
+        if (vload(&w.parent[g.t]) != -1) return true;
+        if (!__any_sync(0xffffffffu, changed)) return false;
+    }
+    return vload(&w.parent[g.t]) != -1;
+}
+
+// Push `amount` (> 0: the bottleneck is computed; < 0: exactly -amount is
+// taken back) along the path of residual_path.  Lane 0 works; returns the
+// amount pushed (warp-uniform), 0 on a broken chain (recorded).
+__device__ int push_path(const Sys &g, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst, int amount,
+                         int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    int pushed = 0;
+    if (lane == 0) {
+        int b = amount;
+        int v = g.t, guard = 0;
+        if (amount > 0) {
+            b = 0x7fffffff;
+            while (v != g.s && guard++ <= g.n_nodes) {
+                const int pa = w.parent[v], a = pa >> 1;
+                const int r = (pa & 1) ? (int)w.flow[a] : (int)w.x[a] - (int)w.flow[a];
+                b = r < b ? r : b;
+                v = (pa & 1) ? s_dst[a] : s_src[a];
+            }
+            if (v != g.s) {
+                atomicMax(err, 3);  // a broken parent chain cannot happen; recorded, not pushed
+                b = 0;
+            }
+            if (amount < b) b = amount;
+        }
+        v = g.t;
+        guard = 0;
+        while (b != 0 && v != g.s && guard++ <= g.n_nodes) {
+            const int pa = w.parent[v], a = pa >> 1;
+            w.flow[a] += (pa & 1) ? -b : b;
+            v = (pa & 1) ? s_dst[a] : s_src[a];
+        }
+        pushed = b;
+    }
+    pushed = __shfl_sync(0xffffffffu, pushed, 0);
+    __syncwarp();
+    return pushed;
+}
+
+// Ford-Fulkerson from zero flow, stopping once the flow reaches `target`.
+// Returns the flow value; w.flow holds the flow.
+__device__ int maxflow_to(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
+                          int target, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    for (int a = lane; a < n; a += 32) w.flow[a] = 0;
+    __syncwarp();
+    int total = 0;
+    while (total < target) {
+        if (!residual_path(g, n, w, s_src, s_dst)) break;
+        const int push = push_path(g, w, s_src, s_dst, 0x7fffffff, err);
+        if (push <= 0) break;
+        total += push;
+    }
+    return total;
+}
+
 // Phi(x) <= m' ?  (warp-uniform result; x in w.x)
 __device__ bool phi_le(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
                        int32_t *err) {
@@ -175,62 +261,7 @@ __device__ bool phi_le(const Sys &g, int n, WarpScratch &w, const int32_t *s_src
     }
     // max flow; the decision needs only whether the flow reaches thr[m'] (ascending thresholds)
     const int target = g.m_prime < g.n_levels ? g.thr[g.m_prime] : 0x7fffffff;
-    for (int a = lane; a < n; a += 32) w.flow[a] = 0;
-    __syncwarp();
-    int total = 0;
-    while (total < target) {
-        for (int v = lane; v < g.n_nodes; v += 32) w.parent[v] = -1;
-        __syncwarp();
-        if (lane == 0) w.parent[g.s] = -2;
-        __syncwarp();
-        bool reached = false;
-        for (int sweep = 0; sweep <= g.n_nodes; ++sweep) {
-            bool changed = false;
-            for (int a = lane; a < n; a += 32) {
-                const int u = s_src[a], v = s_dst[a];
-                const int pu = vload(&w.parent[u]), pv = vload(&w.parent[v]);
-                if (pu != -1 && pv == -1 && w.flow[a] < (int)w.x[a]) {
-                    if (atomicCAS(&w.parent[v], -1, 2 * a) == -1) changed = true;
-                } else if (pv != -1 && pu == -1 && w.flow[a] > 0) {
-                    if (atomicCAS(&w.parent[u], -1, 2 * a + 1) == -1) changed = true;
-                }
-            }
-            __syncwarp();
-            if (vload(&w.parent[g.t]) != -1) {
-                reached = true;
-                break;
-            }
-            if (!__any_sync(0xffffffffu, changed)) break;
-        }
-        if (!reached) break;
-        int push = 0;
-        if (lane == 0) {
-            int b = 0x7fffffff, v = g.t, guard = 0;
-            while (v != g.s && guard++ <= g.n_nodes) {
-                const int pa = w.parent[v], a = pa >> 1;
-                const int r = (pa & 1) ? (int)w.flow[a] : (int)w.x[a] - (int)w.flow[a];
-                b = r < b ? r : b;
-                v = (pa & 1) ? s_dst[a] : s_src[a];
-            }
-            if (v != g.s) {
-                atomicMax(err, 3);  // a broken parent chain cannot happen; recorded, not pushed
-                b = 0;
-            }
-            v = g.t;
-            guard = 0;
-            while (b > 0 && v != g.s && guard++ <= g.n_nodes) {
-                const int pa = w.parent[v], a = pa >> 1;
-                w.flow[a] += (pa & 1) ? -b : b;
-                v = (pa & 1) ? s_dst[a] : s_src[a];
-            }
-            push = b;
-        }
-        push = __shfl_sync(0xffffffffu, push, 0);
-        __syncwarp();
-        if (push <= 0) break;
-        total += push;
-    }
-    return total < target;
+    return maxflow_to(g, n, w, s_src, s_dst, target, err) < target;
 }
 
 // Graph and sampler thresholds into shared memory (whole block).
@@ -302,6 +333,214 @@ __global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyPara
     }
 }
 
+// ---------------------------------------------------------------------------
+// Incremental Phi for the search.  Every step of the componentwise search asks
+// whether one more raise (lower side) or lowering (upper side) of component i
+// crosses the boundary.  Where the system function allows, the answer comes
+// from state kept across steps instead of a new evaluation from scratch; the
+// answer is the same, so the references and the evaluation counts are too.
+//   s-t / global connectivity, raising (Phi = 0 kept): union-find over the
+//     working edges; an added edge crosses iff it joins s's and t's components
+//     (s-t) or the last two components (global).
+//   s-t / global connectivity, lowering (Phi = 1 kept): a witness (an s-t path,
+//     a spanning tree) in the edge bitmask; deleting an edge outside it keeps
+//     Phi; deleting a witness edge triggers a breadth-first search that also
+//     rebuilds the witness.
+//   max flow, raising (flow < target kept, w.flow a maximum flow): one unit of
+//     capacity raises the maximum flow by at most one, so one residual path
+//     search decides; a path that reaches the target is pushed back.
+//   max flow, lowering (flow >= target kept, w.flow a feasible flow): if the
+//     arc carries less than its capacity the flow stays feasible; otherwise the
+//     flow is recomputed up to the target, from a saved copy if that fails.
+// Other cases (the connectivity grade, m' beyond the levels) evaluate Phi.
+// ---------------------------------------------------------------------------
+enum SearchMode { kGeneric = 0, kDsuSt, kPathSt, kDsuGlobal, kTreeGlobal, kFlowRaise, kFlowLower };
+
+__device__ __forceinline__ int dsu_find(int32_t *par, int v) {
+    while (par[v] != v) {
+        par[v] = par[par[v]];
+        v = par[v];
+    }
+    return v;
+}
+
+__device__ __forceinline__ void set_edge_bit(uint32_t *bits, int e) { atomicOr(&bits[e >> 5], 1u << (e & 31)); }
+
+// Witness bitmask of the tree in w.parent: the path t -> root (s-t) or every tree edge (global).
+__device__ void build_witness(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
+                              bool path_only, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    for (int i = lane; i < (n + 31) / 32; i += 32) w.vis[i] = 0u;
+    __syncwarp();
+    if (path_only) {
+        if (lane == 0) {
+            int v = g.t, guard = 0;
+            while (v != g.s && guard++ <= g.n_nodes) {
+                const int e = w.parent[v] & 0xFFFF;
+                if (e >= n) {
+                    atomicMax(err, 3);
+                    break;
+                }
+                w.vis[e >> 5] |= 1u << (e & 31);
+                v = s_src[e] == v ? s_dst[e] : s_src[e];
+            }
+        }
+    } else {
+        for (int v = lane; v < g.n_nodes; v += 32) {
+            const int e = w.parent[v] & 0xFFFF;
+            if (e < n) set_edge_bit(w.vis, e);
+        }
+    }
+    __syncwarp();
+}
+
+__device__ int search_setup(const Sys &g, int n, bool lower, WarpScratch &w, const int32_t *s_src,
+                            const int32_t *s_dst, int *state, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const bool st = g.kind == RSR_PHI_ST_CONNECTIVITY, gl = g.kind == RSR_PHI_GLOBAL_CONNECTIVITY;
+    if ((st || gl) && g.m_prime == 0) {
+        if (lower) {
+            // union-find over the working edges (lane 0); state = components (global)
+            for (int v = lane; v < g.n_nodes; v += 32) w.parent[v] = v;
+            __syncwarp();
+            int comps = g.n_nodes;
+            if (lane == 0) {
+                for (int e = 0; e < n; ++e) {
+                    if (!w.x[e]) continue;
+                    const int ru = dsu_find(w.parent, s_src[e]), rv = dsu_find(w.parent, s_dst[e]);
+                    if (ru != rv) {
+                        w.parent[ru] = rv;
+                        --comps;
+                    }
+                }
+            }
+            *state = __shfl_sync(0xffffffffu, comps, 0);
+            __syncwarp();
+            return st ? kDsuSt : kDsuGlobal;
+        }
+        if (st) bfs_tree(g, n, w, s_src, s_dst, g.s, g.t);
+        else bfs_tree(g, n, w, s_src, s_dst);
+        build_witness(g, n, w, s_src, s_dst, st, err);
+        return st ? kPathSt : kTreeGlobal;
+    }
+    if (g.kind == RSR_PHI_ST_MAXFLOW_LEVELS && g.m_prime < g.n_levels) {
+        // the decision left w.flow at a maximum flow (< target) or a feasible flow (>= target)
+        int total = 0;
+        if (lane == 0) {
+            for (int a = 0; a < n; ++a) {
+                if (s_src[a] == g.s) total += w.flow[a];
+                if (s_dst[a] == g.s) total -= w.flow[a];
+            }
+        }
+        *state = __shfl_sync(0xffffffffu, total, 0);
+        return lower ? kFlowRaise : kFlowLower;
+    }
+    return kGeneric;
+}
+
+// One search step on component i: raise (lower side) or lower it by one state.
+// Keeps the step and returns true if Phi stays on the start's side; otherwise
+// undoes it and returns false.  Warp-uniform.
+__device__ bool try_step(const Sys &g, int n, int mode, bool lower, int i, WarpScratch &w, int16_t *bak,
+                         const int32_t *s_src, const int32_t *s_dst, int *state, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int d = lower ? 1 : -1;
+    switch (mode) {
+        case kDsuSt:
+        case kDsuGlobal: {
+            int keep = 1, comps = *state;
+            if (lane == 0) {
+                const int ru = dsu_find(w.parent, s_src[i]), rv = dsu_find(w.parent, s_dst[i]);
+                if (ru != rv) {
+                    if (mode == kDsuSt) {
+                        const int rs = dsu_find(w.parent, g.s), rt = dsu_find(w.parent, g.t);
+                        keep = !((ru == rs && rv == rt) || (ru == rt && rv == rs));
+                    } else {
+                        keep = comps > 2;
+                    }
+                    if (keep) {
+                        w.parent[ru] = rv;
+                        --comps;
+                    }
+                }
+                if (keep) w.x[i] = 1;
+            }
+            keep = __shfl_sync(0xffffffffu, keep, 0);
+            *state = __shfl_sync(0xffffffffu, comps, 0);
+            __syncwarp();
+            return keep != 0;
+        }
+        case kPathSt:
+        case kTreeGlobal: {
+            const bool on = (w.vis[i >> 5] >> (i & 31)) & 1u;
+            __syncwarp();
+            if (lane == 0) w.x[i] = 0;
+            __syncwarp();
+            if (!on) return true;
+            bool ok;
+            if (mode == kPathSt) {
+                bfs_tree(g, n, w, s_src, s_dst, g.s, g.t);
+                ok = vload(&w.parent[g.t]) != -1;
+            } else {
+                ok = bfs_tree(g, n, w, s_src, s_dst) == g.n_nodes;
+            }
+            if (ok) {
+                build_witness(g, n, w, s_src, s_dst, mode == kPathSt, err);
+            } else {
+                if (lane == 0) w.x[i] = 1;
+                __syncwarp();
+            }
+            return ok;
+        }
+        case kFlowRaise: {
+            const int target = g.thr[g.m_prime];
+            if (lane == 0) w.x[i] += 1;
+            __syncwarp();
+            if (!residual_path(g, n, w, s_src, s_dst)) return true;     // maximum flow unchanged
+            const int pushed = push_path(g, w, s_src, s_dst, 1, err);
+            if (*state + pushed < target) {
+                *state += pushed;
+                return true;
+            }
+            push_path(g, w, s_src, s_dst, -pushed, err);                 // take the unit back
+            if (lane == 0) w.x[i] -= 1;
+            __syncwarp();
+            return false;
+        }
+        case kFlowLower: {
+            const int target = g.thr[g.m_prime];
+            const bool fits = (int)w.flow[i] < (int)w.x[i];
+            __syncwarp();
+            if (lane == 0) w.x[i] -= 1;
+            __syncwarp();
+            if (fits) return true;                                       // the flow stays feasible
+            for (int a = lane; a < n; a += 32) bak[a] = w.flow[a];
+            __syncwarp();
+            const int tot = maxflow_to(g, n, w, s_src, s_dst, target, err);
+            if (tot >= target) {
+                *state = tot;
+                return true;
+            }
+            for (int a = lane; a < n; a += 32) w.flow[a] = bak[a];
+            if (lane == 0) w.x[i] += 1;
+            __syncwarp();
+            return false;
+        }
+        default: {
+            __syncwarp();
+            if (lane == 0) w.x[i] += d;
+            __syncwarp();
+            const bool ok = phi_le(g, n, w, s_src, s_dst, err) == lower;
+            if (!ok) {
+                __syncwarp();
+                if (lane == 0) w.x[i] -= d;
+                __syncwarp();
+            }
+            return ok;
+        }
+    }
+}
+
 // Permuted visiting order from sample h: Fisher-Yates over 0..n-1 driven by
 // Philox4x32-10 (key = seed, counter (h lo, h hi, floor(i/4), 1)); for
 // i = n-1 down to 1, j = (u * (i+1)) >> 32 with u = word (i mod 4).  One lane.
@@ -332,12 +571,13 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
     __shared__ WarpScratch ws[kWarps];
     __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
     __shared__ unsigned long long s_thr[kMaxKenc];
-    extern __shared__ int16_t s_order[];     // kWarps * kMaxKenc (dynamic)
+    extern __shared__ int16_t s_dyn[];       // per warp: visiting order, saved flow (dynamic)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *err = &p.hdr->error;
     stage_system(p, g, s_src, s_dst, s_thr, err);
     WarpScratch &w = ws[warp];
-    int16_t *ord = s_order + warp * kMaxKenc;
+    int16_t *ord = s_dyn + (size_t)warp * 2 * kMaxKenc;
+    int16_t *bak = ord + kMaxKenc;
     const int top = p.K - 1;
     for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < n_starts; j += (int64_t)gridDim.x * kWarps) {
         regen_sample(p, starts[j], w, s_thr);
@@ -346,34 +586,20 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
             __syncwarp();
         }
         const bool lower = phi_le(g, p.n, w, s_src, s_dst, err);
+        int state = 0;
+        const int mode = search_setup(g, p.n, lower, w, s_src, s_dst, &state, err);
         unsigned long long ev = 1;
         for (int step = 0; step < p.n; ++step) {
             const int i = order_mode ? (int)ord[step] : step;
             if (lower) {
                 while (w.x[i] < top) {
-                    __syncwarp();
-                    if (lane == 0) w.x[i] += 1;
-                    __syncwarp();
                     ++ev;
-                    if (!phi_le(g, p.n, w, s_src, s_dst, err)) {
-                        __syncwarp();
-                        if (lane == 0) w.x[i] -= 1;
-                        __syncwarp();
-                        break;
-                    }
+                    if (!try_step(g, p.n, mode, true, i, w, bak, s_src, s_dst, &state, err)) break;
                 }
             } else {
                 while (w.x[i] > 0) {
-                    __syncwarp();
-                    if (lane == 0) w.x[i] -= 1;
-                    __syncwarp();
                     ++ev;
-                    if (phi_le(g, p.n, w, s_src, s_dst, err)) {
-                        __syncwarp();
-                        if (lane == 0) w.x[i] += 1;
-                        __syncwarp();
-                        break;
-                    }
+                    if (!try_step(g, p.n, mode, false, i, w, bak, s_src, s_dst, &state, err)) break;
                 }
             }
         }
@@ -485,7 +711,7 @@ cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const 
                           uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, int order_mode,
                           cudaStream_t s) {
     if (n_starts <= 0) return cudaSuccess;
-    constexpr int kDyn = kWarps * kMaxKenc * (int)sizeof(int16_t);
+    constexpr int kDyn = kWarps * 2 * kMaxKenc * (int)sizeof(int16_t);
     static int attr_set[64] = {0};
     const int d = [] { int v = 0; cudaGetDevice(&v); return v; }();
     if (d >= 0 && d < 64 && !attr_set[d]) {
