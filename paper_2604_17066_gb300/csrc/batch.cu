@@ -183,7 +183,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2) batch_kernel(const BatchDesc *__restrict__ descs,
+__global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__restrict__ descs,
                                                              const int64_t *__restrict__ item_begin, int S,
                                                              int64_t total_items, BatchHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem[];

@@ -33,6 +33,12 @@ constexpr int kThreads = 256;   // one sample per thread
 constexpr int kChunk = 256;     // references per shared-memory chunk
 constexpr int kCoopLanes = 8;   // at most this many unresolved lanes: cooperative warp scan
 
+// Resident blocks per SM the register budget is sized for: four (64 registers a
+// thread) while a sample's words fit beside the Philox state, fewer for wide
+// encodings, where a tighter budget would spill (C2 at n = 295: 1.30 -> 1.05 ms
+// with four instead of two).
+constexpr int min_blocks(int wb) { return wb <= 12 ? 4 : (wb <= 16 ? 3 : 2); }
+
 struct WordWriter {
     // Appends per-component thermometer runs to a column of 32-bit words in
     // shared memory (word w of thread t at col[w * kThreads]).
@@ -63,7 +69,7 @@ struct WordWriter {
 };
 
 template <int WB>
-__global__ void __launch_bounds__(kThreads, 2) classify_popc_kernel(const ClassifyParams p) {
+__global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel(const ClassifyParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
