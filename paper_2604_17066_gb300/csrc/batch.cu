@@ -26,7 +26,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kChunk = 256;
 constexpr int kMaxWB = 16;  // batch path: n*(K-1) <= 512
-constexpr int kCoopLanes = 8;  // at most this many unresolved lanes: cooperative warp scan
+constexpr int kCoopLanes = 16; // at most this many unresolved lanes: cooperative warp scan
 
 struct Shared {
     BatchDesc d;

@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kThreads = 256;   // one sample per thread
 constexpr int kChunk = 256;     // references per shared-memory chunk
-constexpr int kCoopLanes = 8;   // at most this many unresolved lanes: cooperative warp scan
+constexpr int kCoopLanes = 16;  // at most this many unresolved lanes: cooperative warp scan
 
 // Resident blocks per SM the register budget is sized for: four (64 registers a
 // thread) while a sample's words fit beside the Philox state, fewer for wide
