@@ -139,7 +139,7 @@ def _stage1_summary(s1, dt):
             "final_pu": float(h[-1][0]) / 1e6, "phi_evals": int(s1["phi_evals"])}
 
 
-def bench_pipeline(rsr, torch, reps=5):
+def bench_pipeline(rsr, torch, reps=5, quick=False):
     """The paper's whole workflow on a 119-node / 295-edge graph with every
     edge failing with probability 0.05 (Sec. 2.4, 4.1): Stage 1 from no
     references to an unclassified fraction below 1e-5 (rounds of 10^6 samples,
@@ -155,7 +155,8 @@ def bench_pipeline(rsr, torch, reps=5):
     m = p.meta
     pmf = binary_pmf(np.full(p.n, 0.05))
     system = rsr.System(rsr.RSR_PHI_ST_CONNECTIVITY, m["n_nodes"], m["edges"], m["s"], m["t"])
-    s1_idx, t_idx = _stage1_timed(rsr, torch, pmf, system, 64, 10_000, 2000, rsr.RSR_SEARCH_INDEX_ORDER)
+    s1_idx, t_idx = (None, 0.0) if quick else _stage1_timed(rsr, torch, pmf, system, 64, 10_000, 2000,
+                                                           rsr.RSR_SEARCH_INDEX_ORDER)
     s1, t_s1 = _stage1_timed(rsr, torch, pmf, system, 64, 10_000, 2000, rsr.RSR_SEARCH_PERMUTED)
     P = rsr.Problem(pmf, s1["ref_L"].cpu().numpy(), s1["ref_U"].cpu().numpy(), path=rsr.RSR_PATH_POPC)
     sess = rsr.Session(P)
@@ -182,17 +183,22 @@ def bench_pipeline(rsr, torch, reps=5):
         if k >= 2:
             times.append(e[0].elapsed_time(e[1]))
         est = rsr.rsr_estimate(counts.cpu().numpy(), N, int(c2[0].item()))
+    out = {
+        "graph": "119 nodes / 295 edges, p_f = 0.05 (synthetic stand-in for the paper's Graph 2)",
+        "stage1": _stage1_summary(s1, t_s1),
+        "stage2_ms_1e6_samples": sum(times) / len(times), "stage2_P_S_le_0": est["P_lower"],
+        "stage2_unclassified": est["pu"],
+    }
+    if quick:
+        return out
     # global connectivity of a 59-node / 262-edge graph (Sec. 4.3), permuted order
     _, e1, _, _ = L.rgg_graph(59, 262, 1)
     pmf1 = binary_pmf(np.full(262, 0.05))
     g_sys = rsr.System(rsr.RSR_PHI_GLOBAL_CONNECTIVITY, 59, e1, 0, 0)
     s1g, t_g = _stage1_timed(rsr, torch, pmf1, g_sys, 1024, 100_000, 400, rsr.RSR_SEARCH_PERMUTED)
     return {
-        "graph": "119 nodes / 295 edges, p_f = 0.05 (synthetic stand-in for the paper's Graph 2)",
-        "stage1": _stage1_summary(s1, t_s1),
+        **out,
         "stage1_index_order": _stage1_summary(s1_idx, t_idx),
-        "stage2_ms_1e6_samples": sum(times) / len(times), "stage2_P_S_le_0": est["P_lower"],
-        "stage2_unclassified": est["pu"],
         "global_connectivity_59_262": _stage1_summary(s1g, t_g),
         "paper_context": "Table 3 Graph 2 (another graph, desktop CPU + T400): 288 references, reference "
                          "search 0.0571 h, probability evaluation 9.33 s; Tables 4-5 Graph 1 global "
@@ -322,7 +328,7 @@ def run_pipeline(args):
     torch.cuda.set_device(0)
     res = None
     with Clocks(None) as clk:
-        res = bench_pipeline(rsr, torch, reps=max(1, args.steps))
+        res = bench_pipeline(rsr, torch, reps=max(1, args.steps), quick=args.quick)
     total = res["stage1"]["s"] + res["stage2_ms_1e6_samples"] / 1000.0
     line = {"metric": "RSR workflow time: Stage 1 to p_u < 1e-5 from no references + Stage 2 on 1e6 samples",
             "value": total, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
@@ -344,6 +350,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-scenario batched comparison")
     ap.add_argument("--samples", type=int, default=0, help="override samples per GPU (profiling runs)")
+    ap.add_argument("--quick", action="store_true",
+                    help="--workload pipeline: only the permuted-order Stage 1 and Stage 2 (profiling runs)")
     args = ap.parse_args()
     if args.workload == "pipeline":
         if args.impl == "reference":

@@ -356,6 +356,77 @@ __global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyPara
 // ---------------------------------------------------------------------------
 enum SearchMode { kGeneric = 0, kDsuSt, kPathSt, kDsuGlobal, kTreeGlobal, kFlowRaise, kFlowLower };
 
+// Adjacency of the block's graph (compressed rows in shared memory): the edges
+// of node v are adj[off[v] .. off[v+1]).  Built once per block.
+struct Csr {
+    int32_t *off;     // [n_nodes + 1]
+    int32_t *cur;     // [n_nodes] fill cursors
+    int16_t *adj;     // [2 n]
+};
+
+__device__ void build_csr(const Sys &g, int n, const int32_t *s_src, const int32_t *s_dst, Csr c) {
+    for (int v = threadIdx.x; v <= g.n_nodes; v += blockDim.x) c.off[v] = 0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        atomicAdd(&c.off[s_src[e] + 1], 1);
+        atomicAdd(&c.off[s_dst[e] + 1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int v = 0; v < g.n_nodes; ++v) c.off[v + 1] += c.off[v];
+    __syncthreads();
+    for (int v = threadIdx.x; v < g.n_nodes; v += blockDim.x) c.cur[v] = c.off[v];
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        c.adj[atomicAdd(&c.cur[s_src[e]], 1)] = (int16_t)e;
+        c.adj[atomicAdd(&c.cur[s_dst[e]], 1)] = (int16_t)e;
+    }
+    __syncthreads();
+}
+
+// Breadth-first tree from `root` over working edges, frontier by frontier over
+// the adjacency lists: each level touches only the edges of its frontier, so a
+// search costs O(edges) instead of O(levels x edges).  Same parent encoding as
+// bfs_tree (depth << 16 | edge, 0xFFFF at the root, -1 unreached); stops once
+// `stop` (>= 0) is reached.  qa, qb: per-warp frontier buffers [n_nodes];
+// *cnt: a per-warp counter.  Returns the number of reached nodes.
+__device__ int bfs_csr(const Sys &g, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst, const Csr &c,
+                       int root, int stop, int16_t *qa, int16_t *qb, int *cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < g.n_nodes; v += 32) w.parent[v] = -1;
+    __syncwarp();
+    if (lane == 0) {
+        w.parent[root] = 0xFFFF;
+        qa[0] = (int16_t)root;
+        *cnt = 0;
+    }
+    __syncwarp();
+    int nf = 1, reached = 1;
+    for (int d = 1; nf > 0 && d < g.n_nodes; ++d) {
+        if (stop >= 0 && vload(&w.parent[stop]) != -1) break;
+        for (int f = lane; f < nf; f += 32) {
+            const int v = qa[f];
+            for (int k = c.off[v]; k < c.off[v + 1]; ++k) {
+                const int e = c.adj[k];
+                if (!w.x[e]) continue;
+                const int u = s_src[e] == v ? s_dst[e] : s_src[e];
+                if (vload(&w.parent[u]) == -1 && atomicCAS(&w.parent[u], -1, (d << 16) | e) == -1)
+                    qb[atomicAdd(cnt, 1)] = (int16_t)u;
+            }
+        }
+        __syncwarp();
+        nf = *(volatile int *)cnt;
+        __syncwarp();
+        if (lane == 0) *cnt = 0;
+        reached += nf;
+        int16_t *t = qa;
+        qa = qb;
+        qb = t;
+        __syncwarp();
+    }
+    return reached;
+}
+
 __device__ __forceinline__ int dsu_find(int32_t *par, int v) {
     while (par[v] != v) {
         par[v] = par[par[v]];
@@ -394,8 +465,14 @@ __device__ void build_witness(const Sys &g, int n, WarpScratch &w, const int32_t
     __syncwarp();
 }
 
+struct SearchBufs {
+    Csr csr;
+    int16_t *qa, *qb;   // frontier buffers (the flow arrays; connectivity does not use them)
+    int *cnt;
+};
+
 __device__ int search_setup(const Sys &g, int n, bool lower, WarpScratch &w, const int32_t *s_src,
-                            const int32_t *s_dst, int *state, int32_t *err) {
+                            const int32_t *s_dst, int *state, int32_t *err, const SearchBufs &sb) {
     const int lane = threadIdx.x & 31;
     const bool st = g.kind == RSR_PHI_ST_CONNECTIVITY, gl = g.kind == RSR_PHI_GLOBAL_CONNECTIVITY;
     if ((st || gl) && g.m_prime == 0) {
@@ -418,8 +495,7 @@ __device__ int search_setup(const Sys &g, int n, bool lower, WarpScratch &w, con
             __syncwarp();
             return st ? kDsuSt : kDsuGlobal;
         }
-        if (st) bfs_tree(g, n, w, s_src, s_dst, g.s, g.t);
-        else bfs_tree(g, n, w, s_src, s_dst);
+        bfs_csr(g, w, s_src, s_dst, sb.csr, st ? g.s : 0, st ? g.t : -1, sb.qa, sb.qb, sb.cnt);
         build_witness(g, n, w, s_src, s_dst, st, err);
         return st ? kPathSt : kTreeGlobal;
     }
@@ -442,7 +518,8 @@ __device__ int search_setup(const Sys &g, int n, bool lower, WarpScratch &w, con
 // Keeps the step and returns true if Phi stays on the start's side; otherwise
 // undoes it and returns false.  Warp-uniform.
 __device__ bool try_step(const Sys &g, int n, int mode, bool lower, int i, WarpScratch &w, int16_t *bak,
-                         const int32_t *s_src, const int32_t *s_dst, int *state, int32_t *err) {
+                         const int32_t *s_src, const int32_t *s_dst, int *state, int32_t *err,
+                         const SearchBufs &sb) {
     const int lane = threadIdx.x & 31;
     const int d = lower ? 1 : -1;
     switch (mode) {
@@ -479,10 +556,10 @@ __device__ bool try_step(const Sys &g, int n, int mode, bool lower, int i, WarpS
             if (!on) return true;
             bool ok;
             if (mode == kPathSt) {
-                bfs_tree(g, n, w, s_src, s_dst, g.s, g.t);
+                bfs_csr(g, w, s_src, s_dst, sb.csr, g.s, g.t, sb.qa, sb.qb, sb.cnt);
                 ok = vload(&w.parent[g.t]) != -1;
             } else {
-                ok = bfs_tree(g, n, w, s_src, s_dst) == g.n_nodes;
+                ok = bfs_csr(g, w, s_src, s_dst, sb.csr, 0, -1, sb.qa, sb.qb, sb.cnt) == g.n_nodes;
             }
             if (ok) {
                 build_witness(g, n, w, s_src, s_dst, mode == kPathSt, err);
@@ -571,13 +648,26 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
     __shared__ WarpScratch ws[kWarps];
     __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
     __shared__ unsigned long long s_thr[kMaxKenc];
-    extern __shared__ int16_t s_dyn[];       // per warp: visiting order, saved flow (dynamic)
+    // dynamic: per warp a visiting order and a saved flow (int16 [kMaxKenc] each), then
+    // the block's adjacency (off, cur: int32 [kMaxNodes + 1]; adj: int16 [2 kMaxKenc]) and
+    // one frontier counter per warp
+    extern __shared__ __align__(16) unsigned char s_dyn[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *err = &p.hdr->error;
     stage_system(p, g, s_src, s_dst, s_thr, err);
     WarpScratch &w = ws[warp];
-    int16_t *ord = s_dyn + (size_t)warp * 2 * kMaxKenc;
+    int16_t *ord = reinterpret_cast<int16_t *>(s_dyn) + (size_t)warp * 2 * kMaxKenc;
     int16_t *bak = ord + kMaxKenc;
+    int32_t *csr_base = reinterpret_cast<int32_t *>(s_dyn + (size_t)kWarps * 2 * kMaxKenc * sizeof(int16_t));
+    SearchBufs sb;
+    sb.csr.off = csr_base;
+    sb.csr.cur = csr_base + (kMaxNodes + 1);
+    sb.csr.adj = reinterpret_cast<int16_t *>(csr_base + 2 * (kMaxNodes + 1));
+    sb.cnt = reinterpret_cast<int *>(sb.csr.adj + 2 * kMaxKenc) + warp;
+    sb.qa = w.flow;
+    sb.qb = bak;
+    const bool csr = g.kind == RSR_PHI_ST_CONNECTIVITY || g.kind == RSR_PHI_GLOBAL_CONNECTIVITY;
+    if (csr) build_csr(g, p.n, s_src, s_dst, sb.csr);
     const int top = p.K - 1;
     for (int64_t j = (int64_t)blockIdx.x * kWarps + warp; j < n_starts; j += (int64_t)gridDim.x * kWarps) {
         regen_sample(p, starts[j], w, s_thr);
@@ -587,19 +677,19 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
         }
         const bool lower = phi_le(g, p.n, w, s_src, s_dst, err);
         int state = 0;
-        const int mode = search_setup(g, p.n, lower, w, s_src, s_dst, &state, err);
+        const int mode = search_setup(g, p.n, lower, w, s_src, s_dst, &state, err, sb);
         unsigned long long ev = 1;
         for (int step = 0; step < p.n; ++step) {
             const int i = order_mode ? (int)ord[step] : step;
             if (lower) {
                 while (w.x[i] < top) {
                     ++ev;
-                    if (!try_step(g, p.n, mode, true, i, w, bak, s_src, s_dst, &state, err)) break;
+                    if (!try_step(g, p.n, mode, true, i, w, bak, s_src, s_dst, &state, err, sb)) break;
                 }
             } else {
                 while (w.x[i] > 0) {
                     ++ev;
-                    if (!try_step(g, p.n, mode, false, i, w, bak, s_src, s_dst, &state, err)) break;
+                    if (!try_step(g, p.n, mode, false, i, w, bak, s_src, s_dst, &state, err, sb)) break;
                 }
             }
         }
@@ -711,7 +801,8 @@ cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const 
                           uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, int order_mode,
                           cudaStream_t s) {
     if (n_starts <= 0) return cudaSuccess;
-    constexpr int kDyn = kWarps * 2 * kMaxKenc * (int)sizeof(int16_t);
+    constexpr int kDyn = kWarps * 2 * kMaxKenc * (int)sizeof(int16_t) + 2 * (kMaxNodes + 1) * (int)sizeof(int32_t) +
+                         2 * kMaxKenc * (int)sizeof(int16_t) + kWarps * (int)sizeof(int);
     static int attr_set[64] = {0};
     const int d = [] { int v = 0; cudaGetDevice(&v); return v; }();
     if (d >= 0 && d < 64 && !attr_set[d]) {
