@@ -437,6 +437,7 @@ def main():
             rsr.rsr_grad(P, 1, off, n_rank, gcounts, sess.ws, u_lower_idx=uidx[:n_ul] if n_ul else None,
                          stream=stream)
         est = rsr.rsr_estimate(counts.cpu().numpy(), n_rank, n_ul)
+        step.last_launches = 1 + (system is not None) + (grad and n_ul > 0)   # classify, resolve, correction
         return est
 
     for k in range(args.warmup):
@@ -463,7 +464,7 @@ def main():
             est = step(args.warmup + k, grad=True, ev=ev)
             ev[3].record(stream)
             torch.cuda.synchronize()
-            launches += 2 if system is not None else 1
+            launches += step.last_launches
             kern_ms.append(ev[0].elapsed_time(ev[1]))
             step_ms.append(ev[2].elapsed_time(ev[3]))
             if system is not None:
