@@ -254,3 +254,80 @@ def test_stage1_c2_full_size_finds_boundary_states(rsr):
                 y = r.copy()
                 y[i] = 1 - y[i]
                 assert (O.phi(0, nn, edges, s, t, y) <= 0) != lower
+
+
+# ---------------------------------------------------------------- at the size limits
+def _big_graph(seed, n_nodes, n_edges):
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(n_nodes)
+    edges = [(int(a), int(b)) for a, b in zip(order[:-1], order[1:])]      # spanning path
+    seen = {tuple(sorted(e)) for e in edges}
+    while len(edges) < n_edges:
+        a, b = (int(v) for v in rng.integers(0, n_nodes, 2))
+        if a != b and tuple(sorted((a, b))) not in seen:
+            seen.add(tuple(sorted((a, b))))
+            edges.append((a, b))
+    return edges
+
+
+@pytest.mark.parametrize("kind", [0, 2])
+def test_search_and_resolve_at_1024_nodes_and_components(rsr, kind):
+    """n_nodes = 1024 and n = 1024 edges: the shared-memory graph, node bitsets,
+    parent words and adjacency lists at their limits."""
+    nn = 1024
+    edges = _big_graph(5, nn, 1024)
+    pmf = W.binary_pmf(np.full(len(edges), 0.003))
+    s, t = (0, nn - 1) if kind == 0 else (0, 0)
+    _check_search(rsr, pmf, kind, nn, edges, s, t, 3, 0, np.arange(0, 24 * 5, 5), order=1)
+    prob = W.Problem("big", pmf, np.zeros((1, len(edges)), np.uint8), np.zeros((0, len(edges)), np.uint8))
+    N = 3000
+    sess = make_session(rsr, prob)
+    out = sess.classify(2, 0, N, labels=True, grad=False)
+    _, c2 = rsr.rsr_resolve(sess.problem, rsr.System(kind, nn, edges, s, t), 2, 0, N, out["labels"], sess.ws)
+    torch.cuda.synchronize()
+    X = O.sample(pmf, 2, 0, N)
+    lab, _ = O.classify(X, prob.ref_L, prob.ref_U)
+    res, n_lower = O.resolve(kind, nn, edges, s, t, X, lab)
+    assert np.array_equal(out["labels"].cpu().numpy(), res)
+    assert int(c2[0].item()) == n_lower
+
+
+def test_search_max_flow_at_1024_thermometer_bits(rsr):
+    """K = 3, n = 512 arcs: n(K-1) = 1024 thermometer bits, the sampler's limit."""
+    rng = np.random.default_rng(9)
+    nn = 200
+    arcs = []
+    seen = set()
+    while len(arcs) < 512:
+        a, b = (int(v) for v in rng.integers(0, nn, 2))
+        if a != b and (a, b) not in seen:
+            seen.add((a, b))
+            arcs.append((a, b))
+    pmf = rng.dirichlet(np.ones(3), size=512)
+    deg = np.bincount(np.array(arcs).ravel(), minlength=nn)
+    s = int(np.argmax(deg))
+    t = int(np.argsort(deg)[-2])
+    for m_prime in (0, 1):
+        _check_search(rsr, pmf, 1, nn, arcs, s, t, 6, 0, np.arange(40), m_prime, (2, 4), order=1)
+
+
+@pytest.mark.parametrize("upper", [False, True])
+def test_nondominated_at_32_words(rsr, upper):
+    rng = np.random.default_rng(31)
+    rows = rng.integers(0, 2, size=(700, 1024)).astype(np.uint8)
+    rows[::7] = rows[1::7] if upper else rows[::7]          # duplicates
+    rows[3::11] = np.maximum(rows[3::11], rows[4::11][: rows[3::11].shape[0]]) if not upper else rows[3::11]
+    keep, n_keep = rsr.rsr_nondominated(torch.as_tensor(rows, device="cuda"), 2, upper)
+    torch.cuda.synchronize()
+    want = O.nondominated(rows, upper)
+    assert np.array_equal(keep.cpu().numpy().astype(bool), want)
+    assert int(n_keep.item()) == int(want.sum())
+
+
+def test_boundary_search_without_starts(rsr):
+    p, nn, edges, s, t = _grid()
+    P = rsr.Problem(p.pmf, p.ref_L, p.ref_U)
+    refs, side, ev = rsr.rsr_boundary_search(P, rsr.System(0, nn, edges, s, t), 1, 0,
+                                             torch.zeros(0, dtype=torch.int64, device="cuda"))
+    torch.cuda.synchronize()
+    assert refs.shape == (0, p.n) and side.numel() == 0 and int(ev.item()) == 0
