@@ -206,6 +206,55 @@ def bench_pipeline(rsr, torch, reps=5, quick=False):
     }
 
 
+def bench_levels(rsr, torch, N=1_000_000, reps=5):
+    """System-state pmf over all levels of the C4 flow network (three levels,
+    boundaries m' = 0 and 1; Sec. 4.5) in one rsr_level_pmf call, against the
+    per-boundary path (classification + Stage 2 for each boundary).  CUDA
+    events; a 256 MB L2 flush between repetitions."""
+    import workloads.large as L
+    p0, p1 = L.c4_flow(0), L.c4_flow(1)
+    m = p0.meta
+    sessions, paths = [], []
+    for p in (p0, p1):                               # the autotuner picks each boundary's classifier
+        P = rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_AUTO)
+        probe = rsr.Session(P)
+        P.path = rsr.rsr_autotune(P, probe.ws)
+        del probe
+        sessions.append(rsr.Session(P))
+        paths.append("tcgen05" if P.path == rsr.RSR_PATH_TC else "popc")
+    system = rsr.System(rsr.RSR_PHI_ST_MAXFLOW_LEVELS, m["n_nodes"], m["arcs"], m["s"], m["t"],
+                        (m["l1"], m["l2"]), 0)
+    per_b = [rsr.System(rsr.RSR_PHI_ST_MAXFLOW_LEVELS, m["n_nodes"], m["arcs"], m["s"], m["t"],
+                        (m["l1"], m["l2"]), b) for b in range(2)]
+    dev = torch.device("cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    labels = torch.empty(N, dtype=torch.uint8, device=dev)
+    counts = torch.zeros(3, dtype=torch.int64, device=dev)
+    st = torch.cuda.current_stream()
+    t_one, t_sep, out = [], [], None
+    for k in range(reps + 2):
+        flush.fill_(k)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(st)
+        out = rsr.rsr_level_pmf(sessions, system, 3, k * N, N, levels=False, stream=st)
+        e[1].record(st)
+        flush.fill_(k + 1)
+        e[2].record(st)
+        for b in range(2):
+            counts.zero_()
+            rsr.rsr_classify(sessions[b].problem, 3, k * N, N, sessions[b].ws, counts, None, labels, None, None, st)
+            rsr.rsr_resolve(sessions[b].problem, per_b[b], 3, k * N, N, labels, sessions[b].ws, stream=st)
+        e[3].record(st)
+        torch.cuda.synchronize()
+        if k >= 2:
+            t_one.append(e[0].elapsed_time(e[1]))
+            t_sep.append(e[2].elapsed_time(e[3]))
+    lc = out["level_counts"].cpu().numpy()
+    return {"workload": "c4_flow40n100a_K4_levels3_N1e6", "paths": paths, "level_pmf_ms": sum(t_one) / len(t_one),
+            "per_boundary_classify_resolve_ms": sum(t_sep) / len(t_sep),
+            "P_S_eq": (lc / N).tolist(), "samples_needing_phi": int(out["n_phi"].item())}
+
+
 def bench_batch(rsr, torch, N=200_000, reps=5):
     """256 hazard scenarios (n = 50..300 edges, 1e2..1e5 references, N samples
     each): one persistent launch replayed from a CUDA graph vs the per-scenario
@@ -556,6 +605,7 @@ def main():
                                 "note": "Phi evaluated on the device for every unclassified sample; the step "
                                         "estimate is the Stage-2 P(S<=m')"}
         extras["pipeline_119_295"] = bench_pipeline(rsr, torch)
+        extras["level_pmf_c4"] = bench_levels(rsr, torch)
         if args.workload == "c3" and not args.no_batch:
             extras["batch_c5"] = bench_batch(rsr, torch, N=200_000)
             extras["batch_c5_N2e4"] = bench_batch(rsr, torch, N=20_000)

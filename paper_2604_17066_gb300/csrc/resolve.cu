@@ -703,6 +703,32 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
     }
 }
 
+// Phi(x) given that it lies in [lo, hi] (lo < hi).  Max flow: one computation up
+// to the top open threshold, then S = the first m' in [lo, hi) whose threshold
+// the flow does not reach.  Connectivity grade: connectivity once, bridges once.
+// Otherwise decisions Phi <= m' from lo upwards.
+__device__ int phi_in_bracket(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
+                              int lo, int hi, int32_t *err) {
+    if (g.kind == RSR_PHI_ST_MAXFLOW_LEVELS && hi <= g.n_levels) {
+        const int f = maxflow_to(g, n, w, s_src, s_dst, g.thr[hi - 1], err);
+        int S = lo;
+        while (S < hi && f >= g.thr[S]) ++S;
+        return S;
+    }
+    if (g.kind == RSR_PHI_GLOBAL_CONN_LEVEL) {
+        int S;
+        if (bfs_tree(g, n, w, s_src, s_dst) < g.n_nodes) S = 0;
+        else S = bridgeless(g, n, w, s_src, s_dst, err) ? 2 : 1;
+        return S < lo ? lo : (S > hi ? hi : S);
+    }
+    for (int m = lo; m < hi; ++m) {
+        Sys gm = g;
+        gm.m_prime = m;
+        if (phi_le(gm, n, w, s_src, s_dst, err)) return m;
+    }
+    return hi;
+}
+
 // System-state level of every sample from the labels of nb boundaries
 // (labels[b*N + h], boundary m' = b): a lower match at b bounds S <= b, an
 // upper match S >= b+1.  Where the bounds meet the level is known; otherwise
@@ -747,15 +773,7 @@ __global__ void __launch_bounds__(kWarps * 32) levels_kernel(const ClassifyParam
             const int64_t hs = base + src_lane;
             const int slo = __shfl_sync(0xffffffffu, lo, src_lane), shi = __shfl_sync(0xffffffffu, hi, src_lane);
             regen_sample(p, hs, w, s_thr);
-            int S = shi;
-            for (int m = slo; m < shi; ++m) {
-                Sys gm = g;
-                gm.m_prime = m;
-                if (phi_le(gm, p.n, w, s_src, s_dst, err)) {
-                    S = m;
-                    break;
-                }
-            }
+            const int S = phi_in_bracket(g, p.n, w, s_src, s_dst, slo, shi, err);
             if (lane == 0) {
                 if (levels_out) levels_out[hs] = (uint8_t)S;
                 atomicAdd(&s_hist[S], 1ull);
