@@ -399,6 +399,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-scenario batched comparison")
     ap.add_argument("--samples", type=int, default=0, help="override samples per GPU (profiling runs)")
+    ap.add_argument("--early-exit", action="store_true",
+                    help="time the C3 line in production mode (early exit) instead of dense mode")
     ap.add_argument("--quick", action="store_true",
                     help="--workload pipeline: only the permuted-order Stage 1 and Stage 2 (profiling runs)")
     args = ap.parse_args()
@@ -430,8 +432,11 @@ def main():
     if args.samples > 0:
         N = args.samples
         wname += "_N%d" % N
+    if args.early_exit and args.workload == "c3":
+        wname += "_early_exit"
     path = rsr.RSR_PATH_TC if args.workload == "c3" else rsr.RSR_PATH_POPC
-    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=(args.workload == "c3"))
+    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path,
+                    dense=(args.workload == "c3" and not args.early_exit))
     if args.workload == "c4":
         # multi-state: let the autotuner pick the classifier path for this problem
         P.path = rsr.RSR_PATH_AUTO
