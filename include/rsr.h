@@ -67,6 +67,13 @@ typedef enum rsr_path {
 
 /* rsr_problem.flags */
 #define RSR_FLAG_DENSE 1u  /* test every sample against every reference (no early exit) */
+/* Bit-packed path, early-exit mode: scan the upper set reference by reference
+ * instead of through its component-major index.  The index (built by
+ * rsr_prepare) tests a chunk of 256 upper references with one 256-bit OR per
+ * component of the sample below its top state, after a direct test of the 16
+ * most probable upper references; labels, counts and gradient counts are the
+ * same either way. */
+#define RSR_FLAG_NO_INDEX 2u
 /* Failure-detection test hook (tensor-core path only): the reference producer
  * never starts, so the kernel's bounded waits run out after about 10 ms; the
  * kernel records RSR_ERR_TIMEOUT in the workspace header (rsr_workspace_status),

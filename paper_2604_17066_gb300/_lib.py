@@ -21,6 +21,7 @@ RSR_PATH_POPC = 1
 RSR_PATH_TC = 2
 
 RSR_FLAG_DENSE = 1
+RSR_FLAG_NO_INDEX = 2
 RSR_FLAG_TEST_STALL = 0x100
 
 

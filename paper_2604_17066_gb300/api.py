@@ -14,7 +14,7 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (RSR_FLAG_DENSE, RSR_PATH_AUTO, RSR_PATH_POPC, RSR_PATH_TC,  # noqa: F401
+from ._lib import (RSR_FLAG_DENSE, RSR_FLAG_NO_INDEX, RSR_PATH_AUTO, RSR_PATH_POPC, RSR_PATH_TC,  # noqa: F401
                    RSR_PHI_GLOBAL_CONN_LEVEL, RSR_PHI_GLOBAL_CONNECTIVITY, RSR_PHI_ST_CONNECTIVITY,
                    RSR_PHI_ST_MAXFLOW_LEVELS, RSR_SEARCH_INDEX_ORDER, RSR_SEARCH_PERMUTED, RSRError, check,
                    rsr_estimate_out,
@@ -43,7 +43,7 @@ class Problem:
     at them."""
 
     def __init__(self, pmf, ref_L, ref_U, path: int = RSR_PATH_AUTO, dense: bool = False,
-                 device: Optional[torch.device] = None):
+                 device: Optional[torch.device] = None, index: bool = True):
         self.pmf = np.ascontiguousarray(pmf, dtype=np.float64)
         if self.pmf.ndim != 2:
             raise ValueError("pmf must be n x K")
@@ -53,6 +53,7 @@ class Problem:
         self.ref_U = torch.as_tensor(np.asarray(ref_U, dtype=np.uint8).reshape(-1, n)).to(dev).contiguous()
         self.path = int(path)
         self.dense = bool(dense)
+        self.index = bool(index)   # bit-packed path: upper set through its component-major index
         self.extra_flags = 0   # further RSR_FLAG_* bits (e.g. the failure-detection test hook)
 
     @property
@@ -79,7 +80,8 @@ class Problem:
         s.ref_L = self.ref_L.data_ptr() if self.R_L else None
         s.ref_U = self.ref_U.data_ptr() if self.R_U else None
         s.path = self.path
-        s.flags = (RSR_FLAG_DENSE if self.dense else 0) | int(self.extra_flags)
+        s.flags = ((RSR_FLAG_DENSE if self.dense else 0) | (0 if self.index else RSR_FLAG_NO_INDEX) |
+                   int(self.extra_flags))
         return s
 
 

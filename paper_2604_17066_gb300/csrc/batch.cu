@@ -12,9 +12,12 @@
 // the last block to finish converts them into the per-state gradient counts,
 // zeroes the scratch, resets the work counter and advances the round, so the
 // same launch can be replayed (e.g. from a CUDA graph) on the next N_s samples
-// of every scenario without any host work.
+// of every scenario without any host work.  Scenarios whose upper set has a
+// component-major index (popc_index.cuh) test their upper chunks through it,
+// after a direct test of their kHot most probable upper references.
 #include <cuda_runtime.h>
 
+#include "popc_index.cuh"
 #include "rsr_batch.h"
 #include "rsr_internal.cuh"
 #include "rsr_launch.h"
@@ -27,6 +30,8 @@ constexpr int kThreads = 256;
 constexpr int kChunk = 256;
 constexpr int kMaxWB = 16;  // batch path: n*(K-1) <= 512
 constexpr int kCoopLanes = 16; // at most this many unresolved lanes: cooperative warp scan
+constexpr int kHot = 16;        // upper references tried one by one before the index
+constexpr int kCoopIdx = 4;     // at most this many unresolved lanes: cooperative index test
 
 struct Shared {
     BatchDesc d;
@@ -38,7 +43,8 @@ struct Shared {
 
 template <int WB>
 __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, const unsigned long long *s_thr,
-                              uint32_t *s_tw, uint32_t *s_ref, uint32_t *s_cum, Shared &sh) {
+                              uint32_t *s_tw, uint32_t *s_ref, uint32_t *s_cum, const uint32_t *s_hot,
+                              const uint32_t *s_first, const uint32_t *s_zero, Shared &sh) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t hl = tile * kThreads + tid;
     const bool valid = hl < d.N;
@@ -86,6 +92,23 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
 
     const bool overlap = *((volatile const int32_t *)d.overlap) != 0;
     bool mL = false, mU = false, done = !valid;
+    const bool use_idx = d.popc_UT != nullptr;
+    const int kenc = d.n * d.km1;
+    // index mode: the most probable upper references first, one by one (not with an
+    // overlapping pair, where every lower chunk has to come first)
+    if (use_idx && !overlap && !done) {
+        const int hotc = (int)(d.R_U < kHot ? d.R_U : kHot);
+        for (int r = 0; r < hotc; ++r) {
+            uint32_t acc = 0;
+#pragma unroll
+            for (int w = 0; w < WB; ++w) acc |= s_hot[r * WB + w] & ~t[w];
+            if (acc == 0u) {
+                mU = true;
+                done = true;
+                break;
+            }
+        }
+    }
     const int64_t nU = (d.R_U + kChunk - 1) / kChunk, nL = (d.R_L + kChunk - 1) / kChunk;
     for (int64_t step = 0; step < nU + nL; ++step) {
         if (__syncthreads_and(done)) break;
@@ -96,11 +119,39 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         const int64_t R = upper ? d.R_U : d.R_L;
         const int64_t base = ci * kChunk;
         const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
-        for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+        const bool idx_chunk = use_idx && upper;
+        if (idx_chunk) {
+            // rows j < n(K-1) of index chunk ci: 8 words each
+            const uint4 *isrc = reinterpret_cast<const uint4 *>(d.popc_UT + (size_t)ci * kIdxChunk * WB);
+            uint4 *dst = reinterpret_cast<uint4 *>(s_ref);
+            for (int idx = tid; idx < kenc * 2; idx += kThreads) dst[idx] = isrc[idx];
+        } else {
+            for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+        }
         __syncthreads();
         // per-lane scan while many lanes are unresolved, cooperative warp scan otherwise
         const unsigned active = __ballot_sync(0xffffffffu, !done);
-        if (__popc(active) > kCoopLanes) {
+        if (idx_chunk) {
+            if (__popc(active) > kCoopIdx) {
+                if (!done && idx_match_lane<WB>(t, s_ref, s_first, s_zero, kenc, cnt)) {
+                    mU = true;
+                    done = true;
+                }
+            } else {
+                unsigned rem = active;
+                while (rem) {
+                    const int src = __ffs(rem) - 1;
+                    rem &= rem - 1;
+                    const bool found =
+                        idx_match_warp<WB, kThreads>(s_tw + (tid - lane + src), s_ref, s_first, kenc, cnt, lane);
+                    if (lane == src && found) {
+                        mU = true;
+                        done = true;
+                    }
+                }
+                __syncwarp();  // the columns read above are rewritten by their lanes for the next item
+            }
+        } else if (__popc(active) > kCoopLanes) {
             if (!done) {
                 bool m = false;
                 if (upper) {
@@ -188,13 +239,17 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
                                                              int64_t total_items, BatchHeader *hdr) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
+    __shared__ __align__(16) uint32_t s_zero[kIdxWords];
     const int tid = threadIdx.x;
     unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);        // [512]
     uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + 512 * 8);                     // [kMaxWB][256]
     uint32_t *s_ref = s_tw + kMaxWB * kThreads;                                         // [kChunk * kMaxWB]
     uint32_t *s_cum = s_ref + kChunk * kMaxWB;                                          // [kMaxWB * 32]
+    uint32_t *s_hot = s_cum + kMaxWB * 32;                                              // [kHot * kMaxWB]
+    uint32_t *s_first = s_hot + kHot * kMaxWB;                                          // [kMaxWB]
     const uint64_t round = *((volatile unsigned long long *)&hdr->round);
     if (tid == 0) sh.scenario = -1;
+    if (tid < kIdxWords) s_zero[tid] = 0u;
     __syncthreads();
     while (true) {
         if (tid == 0) sh.item = (long long)atomicAdd(&hdr->next_item, 1ull);
@@ -219,17 +274,22 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
         const int nthr = d.n * d.km1;
         for (int i = tid; i < nthr; i += kThreads) s_thr[i] = d.thr[i];
         for (int j = tid; j < d.words_b * 32; j += kThreads) s_cum[j] = 0u;
+        if (d.popc_UT) {
+            const int hotw = (int)(d.R_U < kHot ? d.R_U : kHot) * d.words_b;
+            for (int i = tid; i < hotw; i += kThreads) s_hot[i] = d.popc_U[i];
+            for (int w = tid; w < d.words_b; w += kThreads) s_first[w] = component_first_bits(d.km1, nthr, w);
+        }
         __syncthreads();
         const int64_t tile = item - item_begin[sh.scenario];
         switch (d.words_b) {
-            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
-            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
-            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
-            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
-            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
-            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
-            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
-            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_ref, s_cum, sh); break;
+            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
         }
         __syncthreads();
         if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);
@@ -277,7 +337,8 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
 }  // namespace
 
 size_t batch_kernel_smem() {
-    return 512 * 8 + sizeof(uint32_t) * ((size_t)kMaxWB * kThreads + (size_t)kChunk * kMaxWB + (size_t)kMaxWB * 32);
+    return 512 * 8 + sizeof(uint32_t) * ((size_t)kMaxWB * kThreads + (size_t)kChunk * kMaxWB + (size_t)kMaxWB * 32 +
+                                         (size_t)kHot * kMaxWB + (size_t)kMaxWB);
 }
 
 int batch_max_words() { return kMaxWB; }

@@ -18,10 +18,18 @@
 // Fused in the same pass: Philox sampling (or a read of given states), the
 // label write, the three counts, and the per-bit counts of I^L samples that the
 // score-function gradient needs.  A persistent grid walks 256-sample tiles.
+//
+// Early-exit mode with the component-major index of the upper set
+// (popc_index.cuh, the default): each sample first tries the kHot most
+// probable upper references one by one, then the upper chunks are tested
+// through the index (one 256-bit OR per decisive zero bit of the sample)
+// instead of reference by reference.  Lower chunks are always scanned
+// reference by reference.
 #include <algorithm>
 
 #include <cuda_runtime.h>
 
+#include "popc_index.cuh"
 #include "rsr_internal.cuh"
 #include "rsr_launch.h"
 
@@ -32,6 +40,8 @@ namespace {
 constexpr int kThreads = 256;   // one sample per thread
 constexpr int kChunk = 256;     // references per shared-memory chunk
 constexpr int kCoopLanes = 16;  // at most this many unresolved lanes: cooperative warp scan
+constexpr int kHot = 16;        // upper references tried one by one before the index
+constexpr int kCoopIdx = 4;     // at most this many unresolved lanes: cooperative index test
 
 // Resident blocks per SM the register budget is sized for: four (64 registers a
 // thread) while a sample's words fit beside the Philox state, fewer for wide
@@ -78,10 +88,20 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + (size_t)kMaxKenc * 8);
     uint32_t *s_ref = s_tw + WB * kThreads;
     uint32_t *s_cum = s_ref + kChunk * WB;  // per thermometer bit: # I^L samples with the bit set
+    uint32_t *s_hot = s_cum + WB * 32;      // the first kHot upper references (index mode)
+    uint32_t *s_first = s_hot + kHot * WB;  // component start bits per encoding word (index mode)
+    __shared__ __align__(16) uint32_t s_zero[kIdxWords];
     __shared__ unsigned long long s_cnt[3];
     __shared__ unsigned long long s_exec;
 
+    const bool use_idx = p.popc_UT != nullptr && !p.dense && p.R_U > 0;
+    const int hotc = use_idx ? (int)(p.R_U < kHot ? p.R_U : kHot) : 0;
     for (int i = tid; i < nthr; i += kThreads) s_thr[i] = p.thr[i];
+    if (use_idx) {
+        for (int i = tid; i < hotc * WB; i += kThreads) s_hot[i] = p.popc_U[i];
+        for (int w = tid; w < WB; w += kThreads) s_first[w] = component_first_bits(p.km1, p.kenc, w);
+        if (tid < kIdxWords) s_zero[tid] = 0u;
+    }
     if (p.grad_counts)
         for (int j = tid; j < WB * 32; j += kThreads) s_cum[j] = 0u;
     if (tid < 3) s_cnt[tid] = 0ull;
@@ -129,6 +149,23 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
         // ---- classify ---------------------------------------------------------
         bool mL = false, mU = false;
         bool done = !valid;
+        // index mode: the most probable upper references first, one by one (with an
+        // overlapping pair every lower chunk has to come first: no shortcut then)
+        if (hotc > 0 && !overlap && !done) {
+            int r = 0;
+            for (; r < hotc; ++r) {
+                uint32_t acc = 0;
+#pragma unroll
+                for (int w = 0; w < WB; ++w) acc |= s_hot[r * WB + w] & ~t[w];
+                if (acc == 0u) {
+                    mU = true;
+                    done = true;
+                    ++r;
+                    break;
+                }
+            }
+            my_exec += (unsigned long long)r;
+        }
         const int64_t nU = (p.R_U + kChunk - 1) / kChunk, nL = (p.R_L + kChunk - 1) / kChunk;
         for (int64_t step = 0; step < nU + nL; ++step) {
             const bool all_done = __syncthreads_and(done);  // also: previous chunk consumed
@@ -142,7 +179,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
             const uint4 *src = reinterpret_cast<const uint4 *>(refs + base * WB);
             uint4 *dst = reinterpret_cast<uint4 *>(s_ref);
-            if ((WB & 3) == 0) {
+            const bool idx_chunk = use_idx && upper;
+            if (idx_chunk) {
+                // rows j < n(K-1) of index chunk ci: 8 words each
+                const uint4 *isrc = reinterpret_cast<const uint4 *>(p.popc_UT + (size_t)ci * kIdxChunk * WB);
+                for (int idx = tid; idx < p.kenc * 2; idx += kThreads) dst[idx] = isrc[idx];
+            } else if ((WB & 3) == 0) {
                 for (int idx = tid; idx < cnt * WB / 4; idx += kThreads) dst[idx] = src[idx];
             } else {
                 for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
@@ -169,6 +211,35 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                     my_exec += (unsigned long long)cnt;
                 }
                 if (upper) mU |= m; else mL |= m;
+            } else if (idx_chunk) {
+                // Early exit through the index: per lane while several lanes are
+                // unresolved, one sample per warp otherwise.
+                const unsigned active = __ballot_sync(0xffffffffu, !done);
+                if (__popc(active) > kCoopIdx) {
+                    if (!done) {
+                        my_exec += (unsigned long long)cnt;
+                        if (idx_match_lane<WB>(t, s_ref, s_first, s_zero, p.kenc, cnt)) {
+                            mU = true;
+                            done = true;
+                        }
+                    }
+                } else {
+                    unsigned rem = active;
+                    while (rem) {
+                        const int src_lane = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        const bool found = idx_match_warp<WB, kThreads>(s_tw + (tid - lane + src_lane), s_ref,
+                                                                        s_first, p.kenc, cnt, lane);
+                        if (lane == src_lane) {
+                            my_exec += (unsigned long long)cnt;
+                            if (found) {
+                                mU = true;
+                                done = true;
+                            }
+                        }
+                    }
+                    __syncwarp();  // the columns read above are rewritten by their lanes for the next tile
+                }
             } else {
                 // Early-exit mode.  While many lanes of the warp are unresolved each lane
                 // scans for its own sample; once few remain, the warp scans cooperatively,
@@ -302,7 +373,8 @@ cudaError_t launch_wb(const ClassifyParams &p, cudaStream_t s) {
     // the occupancy are queried once per device so that launches made during
     // stream capture issue nothing but the kernel
     const size_t smem = (size_t)kMaxKenc * 8 +
-                        sizeof(uint32_t) * ((size_t)WB * kThreads + (size_t)kChunk * WB + (size_t)WB * 32);
+                        sizeof(uint32_t) * ((size_t)WB * kThreads + (size_t)kChunk * WB + (size_t)WB * 32 +
+                                            (size_t)kHot * WB + (size_t)WB);
     static int occ_cache[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

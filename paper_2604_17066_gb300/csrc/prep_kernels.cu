@@ -35,6 +35,31 @@ __global__ void encode_popc_kernel(const uint8_t *__restrict__ refs, const int32
     out[gid] = word;
 }
 
+// Component-major index of the upper set (layout in popc_index.cuh): word q of
+// row j of chunk c has bit b = t_j of the reference in slot 256c + 32q + b, 0
+// past R_U and for rows j >= kenc.  One thread per output word, reading the
+// already ordered bit-packed rows.
+__global__ void encode_index_kernel(const uint32_t *__restrict__ popc_U, int64_t R_U, int words_b, int kenc,
+                                    int64_t total, uint32_t *__restrict__ out) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const int rows = 32 * words_b;
+    const int q = (int)(gid % 8);
+    const int64_t cj = gid / 8;
+    const int j = (int)(cj % rows);
+    const int64_t c = cj / rows;
+    uint32_t word = 0;
+    if (j < kenc) {
+        const int jw = j >> 5, jb = j & 31;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t r = c * 256 + 32 * q + b;
+            if (r >= R_U) break;
+            word |= ((popc_U[r * words_b + jw] >> jb) & 1u) << b;
+        }
+    }
+    out[gid] = word;
+}
+
 // Overlap pre-check: some upper reference r^U <= some lower reference r^L iff
 // OR_w (t_w(r^U) AND NOT t_w(r^L)) == 0 for that pair.  One upper reference
 // per thread against lower references streamed through shared memory.
@@ -145,6 +170,15 @@ cudaError_t launch_score_refs(const uint8_t *refs, int64_t R, int n, int K, cons
                               cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
     score_refs_kernel<<<(unsigned)((R + 255) / 256), 256, 0, s>>>(refs, R, n, K, table, score);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_encode_index(const uint32_t *popc_U, int64_t R_U, int words_b, int kenc, uint32_t *out,
+                                cudaStream_t s) {
+    if (R_U <= 0) return cudaSuccess;
+    const int64_t total = ((R_U + 255) / 256) * (int64_t)(32 * words_b) * 8;
+    const int64_t grid = (total + 255) / 256;
+    encode_index_kernel<<<(unsigned)grid, 256, 0, s>>>(popc_U, R_U, words_b, kenc, total, out);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@ struct BatchDesc {
     int64_t N;
     const unsigned long long *thr;       // [n*(K-1)]
     const uint32_t *popc_L, *popc_U;     // [R][words_b]
+    const uint32_t *popc_UT;             // component-major index of the upper set, or NULL
     const int32_t *overlap;              // precedence pre-check result
     uint8_t *labels;                     // [N] or NULL
     unsigned long long *counts3;         // [3]

@@ -58,7 +58,8 @@ uint64_t tune_key(const rsr_problem *p) {
     int64_t R = p->R_L + p->R_U;
     int bucket = 0;
     while ((int64_t(1) << bucket) < R) ++bucket;
-    return ((uint64_t)p->n << 32) ^ ((uint64_t)p->K << 24) ^ ((uint64_t)bucket << 8) ^ (uint64_t)(p->flags & 1u);
+    return ((uint64_t)p->n << 32) ^ ((uint64_t)p->K << 24) ^ ((uint64_t)bucket << 8) ^
+           (uint64_t)(p->flags & (RSR_FLAG_DENSE | RSR_FLAG_NO_INDEX));
 }
 
 int current_device() {
@@ -124,6 +125,9 @@ ClassifyParams make_params(const rsr_problem *p, const WsLayout &L, void *ws) {
     c.thr = reinterpret_cast<const unsigned long long *>(base + L.off_thr);
     c.popc_L = reinterpret_cast<const uint32_t *>(base + L.off_popc_L);
     c.popc_U = reinterpret_cast<const uint32_t *>(base + L.off_popc_U);
+    c.popc_UT = (p->R_U > 0 && !(p->flags & RSR_FLAG_NO_INDEX))
+                    ? reinterpret_cast<const uint32_t *>(base + L.off_popc_UT)
+                    : nullptr;
     c.tc_L = reinterpret_cast<const uint8_t *>(base + L.off_tc_L);
     c.tc_U = reinterpret_cast<const uint8_t *>(base + L.off_tc_U);
     c.R_L = p->R_L;
@@ -307,6 +311,8 @@ int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_strea
                                d_table + (size_t)problem->n * problem->K, d_score, d_perm, s)) != RSR_OK)
         return st;
     RSR_CUDA(launch_encode_popc(problem->ref_U, problem->R_U, problem->n, km1, L.words, false, pU, s, d_perm));
+    RSR_CUDA(launch_encode_index(pU, problem->R_U, L.words, L.kenc, reinterpret_cast<uint32_t *>(base + L.off_popc_UT),
+                                 s));
     if (tc_enc)
         RSR_CUDA(launch_encode_tc(problem->ref_U, problem->R_U, L.tc_rows_U, problem->n, km1, L.tc_kpad, true,
                                   reinterpret_cast<uint8_t *>(base + L.off_tc_U), s, d_perm));
@@ -538,7 +544,7 @@ namespace {
 
 struct BatchLayout {
     size_t off_descs = 0, off_begin = 0, off_tune = 0, off_table = 0, off_score = 0, off_perm = 0, total = 0;
-    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_bit, off_lc, off_tgrad;
+    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_bit, off_lc, off_tgrad;
     std::vector<int> words_b;
 };
 
@@ -575,6 +581,8 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
         off = align256(off + 4 * (size_t)p.R_L * wb);
         B.off_pU.push_back(off);
         off = align256(off + 4 * (size_t)p.R_U * wb);
+        B.off_pUT.push_back(off);  // component-major index of the upper set
+        off = align256(off + 4 * (size_t)((p.R_U + 255) / 256) * 256 * wb);
         B.off_bit.push_back(off);
         off = align256(off + 4 * (size_t)p.n * km1);
         B.off_lc.push_back(off);
@@ -609,6 +617,7 @@ uint64_t batch_fingerprint(const rsr_problem *probs, int32_t S, const uint64_t *
         h = fnv1a(&p.R_U, sizeof(p.R_U), h);
         h = fnv1a(&p.ref_L, sizeof(p.ref_L), h);
         h = fnv1a(&p.ref_U, sizeof(p.ref_U), h);
+        h = fnv1a(&p.flags, sizeof(p.flags), h);
         h = fnv1a(p.pmf, sizeof(double) * (size_t)p.n * p.K, h);
         h = fnv1a(&seeds[s], 8, h);
         h = fnv1a(&offsets[s], 8, h);
@@ -710,6 +719,8 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
             RSR_OK)
             return st;
         RSR_CUDA(launch_encode_popc(p.ref_U, p.R_U, p.n, km1, B.words_b[k], false, pU, s, d_perm));
+        uint32_t *pUT = reinterpret_cast<uint32_t *>(base + B.off_pUT[k]);
+        RSR_CUDA(launch_encode_index(pU, p.R_U, B.words_b[k], p.n * km1, pUT, s));
         WsHeader *hs = reinterpret_cast<WsHeader *>(base + B.off_hdr[k]);
         RSR_CUDA(launch_overlap(pL, p.R_L, pU, p.R_U, B.words_b[k], hs, s));
         BatchDesc &d = descs[k];
@@ -725,6 +736,7 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.thr = reinterpret_cast<const unsigned long long *>(base + B.off_thr[k]);
         d.popc_L = pL;
         d.popc_U = pU;
+        d.popc_UT = (p.R_U > 0 && !(p.flags & RSR_FLAG_NO_INDEX)) ? pUT : nullptr;
         d.overlap = &hs->overlap;
         d.labels = labels_or_null ? labels_or_null[k] : nullptr;
         d.counts3 = reinterpret_cast<unsigned long long *>(counts3xS + 3 * (size_t)k);

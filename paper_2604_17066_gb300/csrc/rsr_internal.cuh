@@ -106,6 +106,7 @@ struct WsLayout {
     size_t off_table = 0;       // float [2][n*K]: per-state log-probability tables (reference ordering)
     size_t off_score = 0;       // float [max(R_L, R_U)]: reference scores (ordering)
     size_t off_perm = 0;        // int32 [max(R_L, R_U)]: reference order (ordering)
+    size_t off_popc_UT = 0;     // uint32 [ceil(R_U/256)][32*words][8]: component-major index of the upper set
     size_t total = 0;
 };
 
@@ -146,6 +147,9 @@ inline WsLayout make_layout(int32_t n, int32_t K, int64_t R_L, int64_t R_U, int3
     off = align256(off + sizeof(float) * rmax);
     L.off_perm = off;
     off = align256(off + sizeof(int32_t) * rmax);
+    // placed last so that the offsets of the regions above do not depend on it
+    L.off_popc_UT = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)((R_U + 255) / 256) * 256 * L.words);
     L.total = off;
     return L;
 }
@@ -158,6 +162,7 @@ struct ClassifyParams {
     const uint8_t *samples;            // NULL = Philox
     const unsigned long long *thr;     // [n*(K-1)]
     const uint32_t *popc_L, *popc_U;   // bit-packed references
+    const uint32_t *popc_UT;           // component-major index of the upper set, or NULL (no index)
     const uint8_t *tc_L, *tc_U;        // FP8 reference tiles
     int64_t R_L, R_U;
     int32_t tc_kpad;

@@ -14,6 +14,9 @@ int popc_word_bucket(int words);
 // Preparation (prep_kernels.cu).
 cudaError_t launch_encode_popc(const uint8_t *refs, int64_t R, int n, int km1, int words_b,
                                bool complement, uint32_t *out, cudaStream_t s, const int32_t *perm = nullptr);
+// Component-major index of the upper set (popc_index.cuh) from its bit-packed rows.
+cudaError_t launch_encode_index(const uint32_t *popc_U, int64_t R_U, int words_b, int kenc, uint32_t *out,
+                                cudaStream_t s);
 cudaError_t launch_score_refs(const uint8_t *refs, int64_t R, int n, int K, const float *table, float *score,
                               cudaStream_t s);
 cudaError_t launch_overlap(const uint32_t *popc_L, int64_t R_L, const uint32_t *popc_U, int64_t R_U,

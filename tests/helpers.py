@@ -49,3 +49,23 @@ def tc_executed_tests(n, K, R_L, R_U, N):
     bn = 256 if tc_kpad(n, K) <= 320 else 128
     tiles = -(-R_L // bn) + -(-R_U // bn)
     return (-(-N // 128)) * 128 * tiles * bn
+
+
+def deep_refs_problem(n, K, R_L, R_U, seed, lo=8, hi=30):
+    """Upper references that few samples reach: each asks for a random subset of
+    lo..hi components to be at or above a random state >= 1, so a sample's first
+    match (if any) lies deep in the upper set and many samples stay
+    unclassified.  Lower references as in random_refs_problem."""
+    rng = np.random.default_rng(seed)
+    pmf = rng.dirichlet(np.ones(K), size=n)
+    pmf[:, -1] += 1.0
+    pmf /= pmf.sum(1, keepdims=True)
+    ref_L = np.full((R_L, n), K - 1, dtype=np.uint8)
+    for r in range(R_L):
+        idx = rng.choice(n, size=min(n, int(rng.integers(1, 4))), replace=False)
+        ref_L[r, idx] = rng.integers(0, K - 1, size=idx.size)
+    ref_U = np.zeros((R_U, n), dtype=np.uint8)
+    for r in range(R_U):
+        idx = rng.choice(n, size=min(n, int(rng.integers(lo, hi + 1))), replace=False)
+        ref_U[r, idx] = rng.integers(1, K, size=idx.size)
+    return W.Problem("deep_refs", pmf, ref_L, ref_U)

@@ -43,6 +43,15 @@ def test_every_declared_symbol_is_exported(lib):
         assert name in _lib.SIGNATURES, "binding lacks " + name
 
 
+def test_flags_match_the_header():
+    from paper_2604_17066_gb300 import _lib
+    text = open(os.path.join(ROOT, "include", "rsr.h")).read()
+    for name in ("RSR_FLAG_DENSE", "RSR_FLAG_NO_INDEX", "RSR_FLAG_TEST_STALL"):
+        m = re.search(r"#define\s+%s\s+(0x[0-9a-fA-F]+|\d+)u" % name, text)
+        assert m, name
+        assert int(m.group(1), 0) == getattr(_lib, name), name
+
+
 def _problem_struct(n=4, K=2, R_L=1, R_U=1, pmf=None, path=0):
     from paper_2604_17066_gb300._lib import rsr_problem
     pmf = np.full((n, K), 1.0 / K) if pmf is None else pmf
@@ -58,7 +67,8 @@ def test_workspace_size_and_validation(lib):
     s, pmf = _problem_struct(n=300, K=2, R_L=50000, R_U=200000)
     size = lib.rsr_workspace_size(ctypes.byref(s), 0)
     # thresholds + 10 bit-words per reference + FP8 rows of 320 bytes per reference (padded to 128)
-    assert size >= 300 * 8 + 250000 * 10 * 4 + 250000 * 320
+    # + the component-major index of the upper set (10 words per upper reference, chunks of 256)
+    assert size >= 300 * 8 + 250000 * 10 * 4 + 250000 * 320 + 782 * 256 * 10 * 4
     assert size % 256 == 0
     bad = [
         _problem_struct(n=0),
