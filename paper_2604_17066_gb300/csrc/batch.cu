@@ -110,11 +110,12 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         }
     }
     const int64_t nU = (d.R_U + kChunk - 1) / kChunk, nL = (d.R_L + kChunk - 1) / kChunk;
+    ChunkWalk walk(nU, nL, overlap, use_idx);
     for (int64_t step = 0; step < nU + nL; ++step) {
         if (__syncthreads_and(done)) break;
         bool upper;
         int64_t ci;
-        chunk_at(step, nU, nL, overlap, &upper, &ci);
+        walk.next(&upper, &ci);
         const uint32_t *refs = upper ? d.popc_U : d.popc_L;
         const int64_t R = upper ? d.R_U : d.R_L;
         const int64_t base = ci * kChunk;

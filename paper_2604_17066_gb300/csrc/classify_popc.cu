@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     if (tid == 0) s_exec = 0ull;
     __syncthreads();
 
-    // Set order: see chunk_at() (alternating without overlapping pairs, lower
-    // first with them, as Algorithm 1's precedence requires).
+    // Set order: see ChunkWalk (upper bursts between lower chunks without
+    // overlapping pairs, lower first with them, as Algorithm 1's precedence requires).
     const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     unsigned long long my_cnt0 = 0, my_cnt1 = 0, my_cnt2 = 0, my_exec = 0;
@@ -167,12 +167,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             my_exec += (unsigned long long)r;
         }
         const int64_t nU = (p.R_U + kChunk - 1) / kChunk, nL = (p.R_L + kChunk - 1) / kChunk;
+        ChunkWalk walk(nU, nL, overlap, use_idx);
         for (int64_t step = 0; step < nU + nL; ++step) {
             const bool all_done = __syncthreads_and(done);  // also: previous chunk consumed
             if (all_done && !p.dense) break;
             bool upper;
             int64_t ci;
-            chunk_at(step, nU, nL, overlap, &upper, &ci);
+            walk.next(&upper, &ci);
             const uint32_t *refs = upper ? p.popc_U : p.popc_L;
             const int64_t R = upper ? p.R_U : p.R_L;
             const int64_t base = ci * kChunk;

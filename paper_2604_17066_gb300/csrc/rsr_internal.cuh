@@ -81,6 +81,42 @@ __host__ __device__ __forceinline__ void chunk_at(int64_t step, int64_t nU, int6
     *idx = m + (step - 2 * m);
 }
 
+// The bit-packed classifiers' order, visited step by step (the same on every
+// thread of a block).  Without an overlapping pair: upper chunk 0, lower chunk
+// 0, then bursts of upper chunks that double in length between lower chunks
+// (U0 L0 U1 L1 U2 U3 L2 U4..U7 L3 U8..U15 L4 ...), each set continuing alone
+// once the other runs out.  With the upper index an upper chunk costs a small
+// fraction of a lower chunk scanned reference by reference, and lower matches
+// sit in the first chunks (the references are ordered by probability), so a
+// sample whose first upper match lies k chunks deep meets about log2(k) lower
+// chunks instead of k.  Without the index (grow = false) the bursts stay at one
+// chunk: strict alternation, as chunk_at().  With an overlapping pair: every
+// lower chunk first.
+struct ChunkWalk {
+    int64_t nU, nL;
+    int32_t u = 0, l = 0, burst = 1;   // chunk counts stay far below 2^31
+    bool overlap, grow;
+    __host__ __device__ ChunkWalk(int64_t nU_, int64_t nL_, bool ov, bool grow_)
+        : nU(nU_), nL(nL_), overlap(ov), grow(grow_) {}
+    // next chunk: *upper and *idx; call at most nU + nL times
+    __host__ __device__ __forceinline__ void next(bool *upper, int64_t *idx) {
+        bool up;
+        if (overlap) up = l >= nL;
+        else if (u >= nU) up = false;
+        else if (l >= nL) up = true;
+        else up = burst > 0;
+        if (up) {
+            *upper = true;
+            *idx = u++;
+            --burst;
+        } else {
+            *upper = false;
+            *idx = l++;
+            burst = !grow ? 1 : (l >= 31 ? 0x7fffffff : (1 << (l - 1)));
+        }
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Workspace layout.  The caller passes one 256-byte aligned buffer; offsets
 // below are derived from the problem sizes only (rsr_workspace_size()).
