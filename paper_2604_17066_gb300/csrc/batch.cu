@@ -50,7 +50,15 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
     const bool valid = hl < d.N;
     const uint32_t key0 = (uint32_t)d.seed, key1 = (uint32_t)(d.seed >> 32);
     // ---- sample and encode (thermometer words, one column per thread) ----
-    {
+    if (d.km1 == 1) {
+        // binary: 32-bit thresholds and never-bits (binary_tables_to_smem) in the s_thr region
+        const uint32_t *s_t32 = reinterpret_cast<const uint32_t *>(s_thr);
+        if (valid)
+            sample_binary_words<WB, kThreads>(d.offset + round * (uint64_t)d.N + (uint64_t)hl, key0, key1, d.n,
+                                              s_t32, s_t32 + 512, s_tw + tid);
+        else
+            for (int w = 0; w < WB; ++w) s_tw[w * kThreads + tid] = 0u;
+    } else {
         uint32_t *col = s_tw + tid;
         int w = 0, pos = 0;
         uint32_t cur = 0;
@@ -273,7 +281,12 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
         __syncthreads();
         const BatchDesc &d = sh.d;
         const int nthr = d.n * d.km1;
-        for (int i = tid; i < nthr; i += kThreads) s_thr[i] = d.thr[i];
+        if (d.km1 == 1) {
+            uint32_t *s_t32 = reinterpret_cast<uint32_t *>(s_thr);   // [512] + never-words [16]
+            binary_tables_to_smem(d.thr, d.n, s_t32, s_t32 + 512, tid, kThreads);
+        } else {
+            for (int i = tid; i < nthr; i += kThreads) s_thr[i] = d.thr[i];
+        }
         for (int j = tid; j < d.words_b * 32; j += kThreads) s_cum[j] = 0u;
         if (d.popc_UT) {
             const int hotw = (int)(d.R_U < kHot ? d.R_U : kHot) * d.words_b;

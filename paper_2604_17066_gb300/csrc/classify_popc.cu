@@ -96,7 +96,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
 
     const bool use_idx = p.popc_UT != nullptr && !p.dense && p.R_U > 0;
     const int hotc = use_idx ? (int)(p.R_U < kHot ? p.R_U : kHot) : 0;
-    for (int i = tid; i < nthr; i += kThreads) s_thr[i] = p.thr[i];
+    // binary states: 32-bit thresholds and never-bits in the same region
+    uint32_t *s_t32 = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *s_never = s_t32 + kMaxKenc;
+    const bool binary = p.km1 == 1;
+    if (binary) binary_tables_to_smem(p.thr, p.n, s_t32, s_never, tid, kThreads);
+    else
+        for (int i = tid; i < nthr; i += kThreads) s_thr[i] = p.thr[i];
     if (use_idx) {
         for (int i = tid; i < hotc * WB; i += kThreads) s_hot[i] = p.popc_U[i];
         for (int w = tid; w < WB; w += kThreads) s_first[w] = component_first_bits(p.km1, p.kenc, w);
@@ -121,7 +127,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
 
         // ---- sample (or read) and encode this thread's state ----------------
         WordWriter ww{s_tw + tid, 0, 0, 0u, p.km1};
-        if (valid) {
+        if (valid && binary && !p.samples) {
+            sample_binary_words<WB, kThreads>(p.offset + (uint64_t)hl, key0, key1, p.n, s_t32, s_never, s_tw + tid);
+            ww.w = WB;  // every word written
+        } else if (valid) {
             if (p.samples) {
                 const uint8_t *row = p.samples + hl * (int64_t)p.n;
                 for (int i = 0; i < p.n; ++i) ww.put(row[i]);

@@ -55,6 +55,60 @@ __device__ __forceinline__ uint32_t state_from_uniform(uint32_t u, const unsigne
     return x;
 }
 
+// Binary components (K = 2): x = [u >= T] with T <= 2^32.  The bit-packed
+// classifiers keep T as 32 bits, T32 = min(T, 2^32 - 1), plus a "never" bit
+// for T = 2^32 (the state 1 has probability 0): x = [u >= T32] AND NOT never,
+// which equals [u >= T] for every u < 2^32.  Entries i >= n are "never", so
+// padding bits stay 0.  Tables hold roundup(n, 8) thresholds and
+// ceil(roundup(n, 8) / 32) never-words.
+__device__ __forceinline__ void binary_tables_to_smem(const unsigned long long *__restrict__ thr, int n,
+                                                      uint32_t *s_t32, uint32_t *s_never, int tid, int nthreads) {
+    const int npad = (n + 7) & ~7;
+    for (int i = tid; i < npad; i += nthreads) {
+        const unsigned long long T = i < n ? thr[i] : (1ull << 32);
+        s_t32[i] = T >= (1ull << 32) ? 0xffffffffu : (uint32_t)T;
+    }
+    for (int w = tid; 32 * w < npad; w += nthreads) {
+        uint32_t m = 0u;
+        for (int b = 0; b < 32; ++b) {
+            const int i = 32 * w + b;
+            if (i >= n || thr[i] >= (1ull << 32)) m |= 1u << b;
+        }
+        s_never[w] = m;
+    }
+}
+
+// Philox-sample a binary state straight into its thermometer words (bit i =
+// x_i), eight components per step, and write the words to col[w * stride];
+// words up to WB - 1 beyond the state are zeroed.  Same draws as
+// state_from_uniform(): u_i = word (i mod 4) of Philox(h, i / 4).
+template <int WB, int stride>
+__device__ __forceinline__ void sample_binary_words(uint64_t h, uint32_t key0, uint32_t key1, int n,
+                                                    const uint32_t *s_t32, const uint32_t *s_never,
+                                                    uint32_t *col) {
+    const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
+    const uint4 *t4 = reinterpret_cast<const uint4 *>(s_t32);
+    uint32_t word = 0u;
+    int w = 0;
+    for (int q = 0; 4 * q < n; q += 2) {
+        const U32x4 ra = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
+        const U32x4 rb = philox4x32_10(h0, h1, (uint32_t)(q + 1), 0u, key0, key1);
+        const uint4 ta = t4[q], tb = t4[q + 1];
+        const uint32_t byte = (ra.x >= ta.x ? 1u : 0u) | (ra.y >= ta.y ? 2u : 0u) | (ra.z >= ta.z ? 4u : 0u) |
+                              (ra.w >= ta.w ? 8u : 0u) | (rb.x >= tb.x ? 16u : 0u) | (rb.y >= tb.y ? 32u : 0u) |
+                              (rb.z >= tb.z ? 64u : 0u) | (rb.w >= tb.w ? 128u : 0u);
+        const int i0 = 4 * q;  // a multiple of 8: the byte never straddles two words
+        word |= byte << (i0 & 31);
+        if (((i0 + 8) & 31) == 0 || i0 + 8 >= n) {
+            w = i0 >> 5;
+            col[w * stride] = word & ~s_never[w];
+            ++w;
+            word = 0u;
+        }
+    }
+    for (; w < WB; ++w) col[w * stride] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // Visiting order of the two reference sets, in chunks (tiles) of references.
 // Without an overlapping pair (no upper reference below a lower one) a sample

@@ -152,3 +152,31 @@ def test_autograd_function_matches_oracle(rsr):
     assert P.item() == O.estimate(cnt, N)["P_lower"]
     g_o, _ = O.grad(O.grad_counts(X, lab, p.K), N, p.pmf)
     np.testing.assert_allclose(q.grad.numpy(), g_o, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("n", [1, 7, 8, 37, 64, 300])
+def test_binary_sampler_edge_thresholds(rsr, n):
+    """Binary states are drawn with 32-bit thresholds plus a 'never' bit (T = 2^32);
+    a lower reference at the top state labels every sample I^L, so the gradient
+    counts are the per-component state counts of all N samples: they must equal
+    the oracle's exactly, for the single-problem and the batched kernels."""
+    rng = np.random.default_rng(n)
+    p1 = rng.uniform(0, 1, size=n)
+    edge = [0.0, 1.0, 2.0 ** -32, 1 - 2.0 ** -32, 0.5, 1 - 2.0 ** -33, 2.0 ** -33]
+    p1[:min(n, len(edge))] = edge[:min(n, len(edge))]
+    pmf = np.stack([1 - p1, p1], axis=1)
+    ref_L = np.ones((1, n), np.uint8)
+    ref_U = rng.integers(0, 2, size=(3, n)).astype(np.uint8)
+    prob = W.Problem("edges", pmf, ref_L, ref_U)
+    N = 3001
+    X = O.sample(pmf, 12, 99, N)
+    lab, cnt = O.classify(X, ref_L, ref_U)
+    C = O.grad_counts(X, lab, 2)
+    assert cnt[0] == N
+    got = run(make_session(rsr, prob), 12, 99, N)
+    assert np.array_equal(got["grad_counts"].reshape(n, 2), C)
+    b = rsr.Batch([rsr.Problem(pmf, ref_L, ref_U, path=POPC)], [12], [99], [N])
+    rsr.rsr_batch(b)
+    torch.cuda.synchronize()
+    assert np.array_equal(b.grad_counts[0].cpu().numpy().reshape(n, 2), C)
+    assert np.array_equal(b.counts3[0].cpu().numpy(), cnt)
