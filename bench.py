@@ -394,13 +394,52 @@ def run_pipeline(args):
     return 0
 
 
+def run_batch_line(args):
+    """--workload c5: the 256-scenario batch on its own line (value = samples/s of
+    the batched launch, beside the per-scenario path).  With --quick: prepare,
+    two warm-up launches and one timed launch, no autotuning and no graph (the
+    launch list and captures of the batched kernel)."""
+    import torch
+    from paper_2604_17066_gb300 import api as rsr
+    from paper_2604_17066_gb300 import build as rsr_build
+    rsr_build.build()
+    torch.cuda.set_device(0)
+    N = args.samples or 200_000
+    with Clocks(None) as clk:
+        if args.quick:
+            import workloads.large as L
+            probs = L.c5_batch()
+            S = len(probs)
+            b = rsr.Batch([rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_POPC) for p in probs],
+                          [1000 + s for s in range(S)], [0] * S, [N] * S)
+            for _ in range(2):
+                rsr.rsr_batch(b)
+            torch.cuda.synchronize()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record()
+            rsr.rsr_batch(b)
+            e[1].record()
+            torch.cuda.synchronize()
+            ms = e[0].elapsed_time(e[1])
+            res = {"workload": "c5_256_scenarios_N%d" % N, "batched_ms": ms, "samples_per_s": S * N / (ms / 1e3)}
+        else:
+            res = bench_batch(rsr, torch, N=N)
+    line = {"metric": "batched classification of 256 hazard scenarios: samples/s of one persistent launch",
+            "value": res["samples_per_s"], "unit": "samples/s", "n_gpus": 1, "steps": 1 if args.quick else 5,
+            "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 bit-packed", "data": "synthetic", "config": {"workload": res["workload"]},
+            "clocks": clk.summary(), "batch": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "pipeline"])
+    ap.add_argument("--workload", default="c3", choices=["c3", "c2", "c4", "c5", "pipeline"])
     ap.add_argument("--ref-samples", type=int, default=8000)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-scenario batched comparison")
@@ -408,8 +447,15 @@ def main():
     ap.add_argument("--early-exit", action="store_true",
                     help="time the C3 line in production mode (early exit) instead of dense mode")
     ap.add_argument("--quick", action="store_true",
-                    help="--workload pipeline: only the permuted-order Stage 1 and Stage 2 (profiling runs)")
+                    help="--workload pipeline: only the permuted-order Stage 1 and Stage 2; --workload c5: "
+                         "one batched launch after two warm-ups (profiling runs)")
     args = ap.parse_args()
+    if args.workload == "c5":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched line has no oracle arm; the "
+                              "oracle is timed on the C3 line"}), flush=True)
+            return 0
+        return run_batch_line(args)
     if args.workload == "pipeline":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the workflow line has no oracle arm; "

@@ -43,12 +43,37 @@ struct Shared {
 
 template <int WB>
 __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, const unsigned long long *s_thr,
-                              uint32_t *s_tw, uint32_t *s_ref, uint32_t *s_cum, const uint32_t *s_hot,
+                              uint32_t *s_tw, uint32_t *s_buf, uint32_t *s_cum, const uint32_t *s_hot,
                               const uint32_t *s_first, const uint32_t *s_zero, Shared &sh) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t hl = tile * kThreads + tid;
     const bool valid = hl < d.N;
     const uint32_t key0 = (uint32_t)d.seed, key1 = (uint32_t)(d.seed >> 32);
+    // chunk walk; chunk 0 is copied (cp.async) while the item is sampled.  Every
+    // thread is past the item's set-up barrier, so both buffers are free.
+    const bool overlap = *((volatile const int32_t *)d.overlap) != 0;
+    const bool use_idx = d.popc_UT != nullptr;
+    const int kenc = d.n * d.km1;
+    const int64_t nU = (d.R_U + kChunk - 1) / kChunk, nL = (d.R_L + kChunk - 1) / kChunk;
+    const int64_t nsteps = nU + nL;
+    ChunkWalk walk(nU, nL, overlap, use_idx);
+    bool upper = false;
+    int64_t ci = 0;
+    walk.next(&upper, &ci);   // nsteps >= 1: some reference exists
+    auto chunk_refs = [&](bool up, int64_t c, int *cnt_out) {
+        const int64_t R = up ? d.R_U : d.R_L;
+        const int64_t base = c * kChunk;
+        *cnt_out = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
+        return (up ? d.popc_U : d.popc_L) + base * WB;
+    };
+    auto issue = [&](uint32_t *dst, bool up, int64_t c) {
+        int cnt_c;
+        const uint32_t *rows = chunk_refs(up, c, &cnt_c);
+        const bool ix = use_idx && up;
+        load_chunk_async<WB, kThreads>(dst, ix, ix ? d.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, kenc, rows,
+                                       cnt_c, tid);
+    };
+    issue(s_buf, upper, ci);
     // ---- sample and encode (thermometer words, one column per thread) ----
     if (d.km1 == 1) {
         // binary: 32-bit thresholds and never-bits (binary_tables_to_smem) in the s_thr region
@@ -98,10 +123,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
 #pragma unroll
     for (int w = 0; w < WB; ++w) t[w] = s_tw[w * kThreads + tid];
 
-    const bool overlap = *((volatile const int32_t *)d.overlap) != 0;
     bool mL = false, mU = false, done = !valid;
-    const bool use_idx = d.popc_UT != nullptr;
-    const int kenc = d.n * d.km1;
     // index mode: the most probable upper references first, one by one (not with an
     // overlapping pair, where every lower chunk has to come first)
     if (use_idx && !overlap && !done) {
@@ -117,27 +139,19 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
             }
         }
     }
-    const int64_t nU = (d.R_U + kChunk - 1) / kChunk, nL = (d.R_L + kChunk - 1) / kChunk;
-    ChunkWalk walk(nU, nL, overlap, use_idx);
-    for (int64_t step = 0; step < nU + nL; ++step) {
-        if (__syncthreads_and(done)) break;
-        bool upper;
-        int64_t ci;
-        walk.next(&upper, &ci);
-        const uint32_t *refs = upper ? d.popc_U : d.popc_L;
-        const int64_t R = upper ? d.R_U : d.R_L;
-        const int64_t base = ci * kChunk;
-        const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
+    for (int64_t step = 0; step < nsteps; ++step) {
+        cp_async_wait_all();                       // this thread's copies of chunk `step`
+        if (__syncthreads_and(done)) break;        // chunk `step` visible; chunk step-1 consumed
+        uint32_t *s_ref = s_buf + (int)(step & 1) * (kChunk * kMaxWB);
+        int cnt;
+        (void)chunk_refs(upper, ci, &cnt);
         const bool idx_chunk = use_idx && upper;
-        if (idx_chunk) {
-            // rows j < n(K-1) of index chunk ci: 8 words each
-            const uint4 *isrc = reinterpret_cast<const uint4 *>(d.popc_UT + (size_t)ci * kIdxChunk * WB);
-            uint4 *dst = reinterpret_cast<uint4 *>(s_ref);
-            for (int idx = tid; idx < kenc * 2; idx += kThreads) dst[idx] = isrc[idx];
-        } else {
-            for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+        bool up_next = false;
+        int64_t ci_next = 0;
+        if (step + 1 < nsteps) {
+            walk.next(&up_next, &ci_next);
+            issue(s_buf + (int)((step + 1) & 1) * (kChunk * kMaxWB), up_next, ci_next);
         }
-        __syncthreads();
         // per-lane scan while many lanes are unresolved, cooperative warp scan otherwise
         const unsigned active = __ballot_sync(0xffffffffu, !done);
         if (idx_chunk) {
@@ -214,6 +228,8 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
                 }
             }
         }
+        upper = up_next;
+        ci = ci_next;
     }
     const int label = mL ? 0 : (mU ? 1 : 2);
     if (valid && d.labels) d.labels[hl] = (uint8_t)label;
@@ -252,8 +268,8 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
     const int tid = threadIdx.x;
     unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);        // [512]
     uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + 512 * 8);                     // [kMaxWB][256]
-    uint32_t *s_ref = s_tw + kMaxWB * kThreads;                                         // [kChunk * kMaxWB]
-    uint32_t *s_cum = s_ref + kChunk * kMaxWB;                                          // [kMaxWB * 32]
+    uint32_t *s_buf = s_tw + kMaxWB * kThreads;                                         // [2][kChunk * kMaxWB]
+    uint32_t *s_cum = s_buf + 2 * kChunk * kMaxWB;                                      // [kMaxWB * 32]
     uint32_t *s_hot = s_cum + kMaxWB * 32;                                              // [kHot * kMaxWB]
     uint32_t *s_first = s_hot + kHot * kMaxWB;                                          // [kMaxWB]
     const uint64_t round = *((volatile unsigned long long *)&hdr->round);
@@ -296,14 +312,14 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
         __syncthreads();
         const int64_t tile = item - item_begin[sh.scenario];
         switch (d.words_b) {
-            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
-            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_ref, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
         }
         __syncthreads();
         if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);
@@ -351,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
 }  // namespace
 
 size_t batch_kernel_smem() {
-    return 512 * 8 + sizeof(uint32_t) * ((size_t)kMaxWB * kThreads + (size_t)kChunk * kMaxWB + (size_t)kMaxWB * 32 +
+    return 512 * 8 + sizeof(uint32_t) * ((size_t)kMaxWB * kThreads + 2 * (size_t)kChunk * kMaxWB + (size_t)kMaxWB * 32 +
                                          (size_t)kHot * kMaxWB + (size_t)kMaxWB);
 }
 

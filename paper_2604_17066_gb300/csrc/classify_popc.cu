@@ -48,6 +48,10 @@ constexpr int kCoopIdx = 4;     // at most this many unresolved lanes: cooperati
 // encodings, where a tighter budget would spill (C2 at n = 295: 1.30 -> 1.05 ms
 // with four instead of two).
 constexpr int min_blocks(int wb) { return wb <= 12 ? 4 : (wb <= 16 ? 3 : 2); }
+// Chunk buffers: two (the next chunk is copied while the current one is
+// tested) unless that would cost a resident block (32 words: one buffer).
+template <int WB>
+__host__ __device__ constexpr int kBufs() { return WB <= 24 ? 2 : 1; }
 
 struct WordWriter {
     // Appends per-component thermometer runs to a column of 32-bit words in
@@ -86,8 +90,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     const int nthr = p.n * p.km1;
     unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + (size_t)kMaxKenc * 8);
-    uint32_t *s_ref = s_tw + WB * kThreads;
-    uint32_t *s_cum = s_ref + kChunk * WB;  // per thermometer bit: # I^L samples with the bit set
+    uint32_t *s_buf = s_tw + WB * kThreads;           // kBufs chunk buffers of kChunk * WB words
+    uint32_t *s_cum = s_buf + kBufs<WB>() * kChunk * WB;  // per thermometer bit: # I^L samples with the bit set
     uint32_t *s_hot = s_cum + WB * 32;      // the first kHot upper references (index mode)
     uint32_t *s_first = s_hot + kHot * WB;  // component start bits per encoding word (index mode)
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
@@ -124,6 +128,29 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t hl = tile * kThreads + tid;
         const bool valid = hl < p.N;
+        const int64_t nU = (p.R_U + kChunk - 1) / kChunk, nL = (p.R_L + kChunk - 1) / kChunk;
+        const int64_t nsteps = nU + nL;
+        ChunkWalk walk(nU, nL, overlap, use_idx);
+        bool upper = false;
+        int64_t ci = 0;
+        walk.next(&upper, &ci);   // nsteps >= 1: some reference exists
+        auto chunk_refs = [&](bool up, int64_t c, int *cnt_out) {
+            const int64_t R = up ? p.R_U : p.R_L;
+            const int64_t base = c * kChunk;
+            *cnt_out = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
+            return (up ? p.popc_U : p.popc_L) + base * WB;
+        };
+        auto issue = [&](uint32_t *dst, bool up, int64_t c) {
+            int cnt_c;
+            const uint32_t *rows = chunk_refs(up, c, &cnt_c);
+            const bool ix = use_idx && up;
+            load_chunk_async<WB, kThreads>(dst, ix, ix ? p.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, p.kenc,
+                                           rows, cnt_c, tid);
+        };
+        if (kBufs<WB>() == 2) {
+            __syncthreads();            // every thread is done with the previous tile's buffers
+            issue(s_buf, upper, ci);    // chunk 0, copied while the tile is sampled
+        }
 
         // ---- sample (or read) and encode this thread's state ----------------
         WordWriter ww{s_tw + tid, 0, 0, 0u, p.km1};
@@ -175,31 +202,24 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             }
             my_exec += (unsigned long long)r;
         }
-        const int64_t nU = (p.R_U + kChunk - 1) / kChunk, nL = (p.R_L + kChunk - 1) / kChunk;
-        ChunkWalk walk(nU, nL, overlap, use_idx);
-        for (int64_t step = 0; step < nU + nL; ++step) {
-            const bool all_done = __syncthreads_and(done);  // also: previous chunk consumed
+        for (int64_t step = 0; step < nsteps; ++step) {
+            if (kBufs<WB>() == 2) cp_async_wait_all();      // this thread's copies of chunk `step`
+            const bool all_done = __syncthreads_and(done);  // chunk `step` visible; chunk step-1 consumed
             if (all_done && !p.dense) break;
-            bool upper;
-            int64_t ci;
-            walk.next(&upper, &ci);
-            const uint32_t *refs = upper ? p.popc_U : p.popc_L;
-            const int64_t R = upper ? p.R_U : p.R_L;
-            const int64_t base = ci * kChunk;
-            const int cnt = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
-            const uint4 *src = reinterpret_cast<const uint4 *>(refs + base * WB);
-            uint4 *dst = reinterpret_cast<uint4 *>(s_ref);
+            uint32_t *s_ref = s_buf + (kBufs<WB>() == 2 ? (int)(step & 1) : 0) * (kChunk * WB);
+            int cnt;
+            (void)chunk_refs(upper, ci, &cnt);
             const bool idx_chunk = use_idx && upper;
-            if (idx_chunk) {
-                // rows j < n(K-1) of index chunk ci: 8 words each
-                const uint4 *isrc = reinterpret_cast<const uint4 *>(p.popc_UT + (size_t)ci * kIdxChunk * WB);
-                for (int idx = tid; idx < p.kenc * 2; idx += kThreads) dst[idx] = isrc[idx];
-            } else if ((WB & 3) == 0) {
-                for (int idx = tid; idx < cnt * WB / 4; idx += kThreads) dst[idx] = src[idx];
+            bool up_next = false;
+            int64_t ci_next = 0;
+            if (step + 1 < nsteps) walk.next(&up_next, &ci_next);
+            if (kBufs<WB>() == 2) {
+                if (step + 1 < nsteps) issue(s_buf + (int)((step + 1) & 1) * (kChunk * WB), up_next, ci_next);
             } else {
-                for (int idx = tid; idx < cnt * WB; idx += kThreads) s_ref[idx] = refs[base * WB + idx];
+                issue(s_ref, upper, ci);
+                cp_async_wait_all();
+                __syncthreads();
             }
-            __syncthreads();
             if (p.dense) {
                 bool m = false;
                 if (valid) {
@@ -317,6 +337,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                     }
                 }
             }
+            upper = up_next;
+            ci = ci_next;
         }
         const int label = mL ? 0 : (mU ? 1 : 2);
         if (valid) {
@@ -383,7 +405,7 @@ cudaError_t launch_wb(const ClassifyParams &p, cudaStream_t s) {
     // the occupancy are queried once per device so that launches made during
     // stream capture issue nothing but the kernel
     const size_t smem = (size_t)kMaxKenc * 8 +
-                        sizeof(uint32_t) * ((size_t)WB * kThreads + (size_t)kChunk * WB + (size_t)WB * 32 +
+                        sizeof(uint32_t) * ((size_t)WB * kThreads + (size_t)kBufs<WB>() * kChunk * WB + (size_t)WB * 32 +
                                             (size_t)kHot * WB + (size_t)WB);
     static int occ_cache[64] = {0};
     int dev = 0;

@@ -130,6 +130,37 @@ __device__ __forceinline__ bool idx_match_warp(const uint32_t *col, const uint32
     return __any_sync(0xffffffffu, bl != 0xffffffffu);
 }
 
+// ---- asynchronous chunk copies (cp.async, global -> shared) ------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage one chunk into shared memory, without waiting: an index chunk (kenc
+// rows of 8 words, from idx_src) or cnt bit-packed references of WB words
+// (from rows_src).  Every address is 16-byte aligned: chunks start at
+// multiples of 256 references in 256-byte aligned regions.  The caller waits
+// with cp_async_wait_all() and a block barrier before reading.
+template <int WB, int nthreads>
+__device__ __forceinline__ void load_chunk_async(uint32_t *dst, bool idx_chunk, const uint32_t *idx_src, int kenc,
+                                                 const uint32_t *rows_src, int cnt, int tid) {
+    if (idx_chunk) {
+        for (int i = tid; i < kenc * 2; i += nthreads) cp_async16(dst + 4 * i, idx_src + 4 * i);
+    } else {
+        const int nw = cnt * WB, n16 = nw >> 2;
+        for (int i = tid; i < n16; i += nthreads) cp_async16(dst + 4 * i, rows_src + 4 * i);
+        for (int i = 4 * n16 + tid; i < nw; i += nthreads) cp_async4(dst + i, rows_src + i);
+    }
+    cp_async_commit();
+}
+
 // Component start bits of encoding word w for K-1 bits per component.
 __device__ __forceinline__ uint32_t component_first_bits(int km1, int kenc, int w) {
     uint32_t m = 0u;
