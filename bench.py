@@ -322,8 +322,23 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
         plain(10 + r, True)
     torch.cuda.synchronize()
     plain_round_ms = 1000 * (time.perf_counter() - t0) / reps
+    # the same batched launch with the upper sets scanned reference by reference
+    Pn = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_POPC, index=False) for p in probs]
+    bn = rsr.Batch(Pn, seeds, offsets, Ns, labels=True, grad=True)
+    rsr.rsr_batch_autotune(bn)
+    for _ in range(2):
+        rsr.rsr_batch(bn)
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(reps):
+        rsr.rsr_batch(bn)
+    ev[1].record()
+    torch.cuda.synchronize()
+    no_index_ms = ev[0].elapsed_time(ev[1]) / reps
+    del bn
     R = [p.R_L + p.R_U for p in P]
     return {"workload": "c5_256_scenarios_N%d" % N, "scenarios": S, "refs_total": int(sum(R)),
+            "batched_no_index_ms": no_index_ms,
             "batched_ms": batched_ms, "per_scenario_ms": plain_ms, "speedup_kernels": plain_ms / batched_ms,
             "batched_fwd_grad_round_ms": batched_round_ms, "per_scenario_fwd_grad_round_ms": plain_round_ms,
             "speedup_fwd_grad_round": plain_round_ms / batched_round_ms,
@@ -634,8 +649,9 @@ def main():
         # early exit (production mode) on the same references, both classifier paths
         if args.workload == "c3":
             ee_all = {}
-            for pname, pth in (("tc", rsr.RSR_PATH_TC), ("popc", rsr.RSR_PATH_POPC)):
-                P2 = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=pth, dense=False)
+            for pname, pth, idx in (("tc", rsr.RSR_PATH_TC, True), ("popc", rsr.RSR_PATH_POPC, True),
+                                    ("popc_no_index", rsr.RSR_PATH_POPC, False)):
+                P2 = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=pth, dense=False, index=idx)
                 s2 = rsr.Session(P2)
                 ee = []
                 ex = torch.zeros(1, dtype=torch.int64, device=dev)
@@ -655,6 +671,23 @@ def main():
                                  "executed_tests_per_sample": int(ex.item()) / N}
                 del s2
             extras["early_exit"] = ee_all
+        if path == rsr.RSR_PATH_POPC:
+            # the classifier kernel alone, with and without the upper index
+            for key, idx in (("classifier_ms", True), ("classifier_no_index_ms", False)):
+                P3 = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=path, dense=P.dense, index=idx)
+                s3 = rsr.Session(P3)
+                tk = []
+                for k in range(5):
+                    flush.fill_(k)
+                    counts.zero_()
+                    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                    e[0].record(stream)
+                    rsr.rsr_classify(P3, 1, 13 * N + k * N, n_rank, s3.ws, counts, None, labels, None, None, stream)
+                    e[1].record(stream)
+                    torch.cuda.synchronize()
+                    tk.append(e[0].elapsed_time(e[1]))
+                extras[key] = statistics.median(tk[1:])
+                del s3
         extras["prepare_ms"] = prep_ms
         extras["overlap_pairs"] = bool(overlap)
         if stage2_ms:
