@@ -32,12 +32,14 @@ constexpr int kMaxWB = 16;  // batch path: n*(K-1) <= 512
 constexpr int kCoopLanes = 16; // at most this many unresolved lanes: cooperative warp scan
 constexpr int kHot = 16;        // upper references tried one by one before the index
 constexpr int kCoopIdx = 4;     // at most this many unresolved lanes: cooperative index test
+constexpr int kZeroLanes = 8;   // at most this many I^L lanes in a warp: count their zero bits
 
 struct Shared {
     BatchDesc d;
     int scenario;
     long long item;
     unsigned long long cnt[3];
+    unsigned int fz;   // I^L samples of the item counted by their zero bits
     int last;
 };
 
@@ -242,8 +244,23 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         if (b1) atomicAdd(&sh.cnt[1], (unsigned long long)__popc(b1));
         if (b2) atomicAdd(&sh.cnt[2], (unsigned long long)__popc(b2));
     }
-    // per-bit counts of I^L samples
-    if (d.bitcnt && b0) {
+    // per-bit counts of I^L samples: zero bits with shared atomics for a warp with
+    // few I^L samples, 32 ballots per word (one bits) otherwise
+    if (d.bitcnt && b0 && __popc(b0) <= kZeroLanes) {
+        if (valid && label == 0) {
+            const int kenc = d.n * d.km1;
+#pragma unroll
+            for (int w = 0; w < WB; ++w) {
+                uint32_t z = ~t[w] & enc_valid_bits(kenc, w);
+                while (z) {
+                    const int b = __ffs(z) - 1;
+                    z &= z - 1u;
+                    atomicSub(&s_cum[w * 32 + b], 1u);   // ones = (zero-route samples) - zeros
+                }
+            }
+        }
+        if (lane == 0) atomicAdd(&sh.fz, (unsigned)__popc(b0));
+    } else if (d.bitcnt && b0) {
         const bool isL = valid && label == 0;
 #pragma unroll
         for (int w = 0; w < WB; ++w) {
@@ -293,6 +310,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
                 sh.d = descs[lo];
             }
             sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0ull;
+            sh.fz = 0u;
         }
         __syncthreads();
         const BatchDesc &d = sh.d;
@@ -325,8 +343,10 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
         if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);
         if (d.bitcnt && sh.cnt[0]) {
             if (tid == 0) atomicAdd(d.lcount, sh.cnt[0]);
-            for (int j = tid; j < nthr; j += kThreads)
-                if (s_cum[j]) atomicAdd(&d.bitcnt[j], s_cum[j]);
+            for (int j = tid; j < nthr; j += kThreads) {
+                const uint32_t ones = s_cum[j] + sh.fz;   // one bits of the item's I^L samples (mod 2^32)
+                if (ones) atomicAdd(&d.bitcnt[j], ones);
+            }
         }
         __syncthreads();
     }

@@ -42,6 +42,7 @@ constexpr int kChunk = 256;     // references per shared-memory chunk
 constexpr int kCoopLanes = 16;  // at most this many unresolved lanes: cooperative warp scan
 constexpr int kHot = 16;        // upper references tried one by one before the index
 constexpr int kCoopIdx = 4;     // at most this many unresolved lanes: cooperative index test
+constexpr int kZeroLanes = 8;   // at most this many I^L lanes in a warp: count their zero bits
 
 // Resident blocks per SM the register budget is sized for: four (64 registers a
 // thread) while a sample's words fit beside the Philox state, fewer for wide
@@ -91,12 +92,15 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);
     uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + (size_t)kMaxKenc * 8);
     uint32_t *s_buf = s_tw + WB * kThreads;           // kBufs chunk buffers of kChunk * WB words
-    uint32_t *s_cum = s_buf + kBufs<WB>() * kChunk * WB;  // per thermometer bit: # I^L samples with the bit set
+    // per thermometer bit: one bits of I^L samples counted by ballots, minus zero bits
+    // of those counted by their zero bits (modulo 2^32; s_fz of them are added at the end)
+    uint32_t *s_cum = s_buf + kBufs<WB>() * kChunk * WB;
     uint32_t *s_hot = s_cum + WB * 32;      // the first kHot upper references (index mode)
     uint32_t *s_first = s_hot + kHot * WB;  // component start bits per encoding word (index mode)
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
     __shared__ unsigned long long s_cnt[3];
     __shared__ unsigned long long s_exec;
+    __shared__ unsigned int s_fz;           // I^L samples counted by their zero bits
 
     const bool use_idx = p.popc_UT != nullptr && !p.dense && p.R_U > 0;
     const int hotc = use_idx ? (int)(p.R_U < kHot ? p.R_U : kHot) : 0;
@@ -114,6 +118,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     }
     if (p.grad_counts)
         for (int j = tid; j < WB * 32; j += kThreads) s_cum[j] = 0u;
+    if (tid == 0) s_fz = 0u;
     if (tid < 3) s_cnt[tid] = 0ull;
     if (tid == 0) s_exec = 0ull;
     __syncthreads();
@@ -349,9 +354,25 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
         }
 
         // ---- per-bit counts of I^L samples (gradient) ------------------------
+        // A warp with few I^L samples counts their zero bits (sparse) with shared
+        // atomics; otherwise 32 ballots per word count the one bits of all lanes.
         if (p.grad_counts) {
             const bool isL = valid && label == 0;
-            if (__ballot_sync(0xffffffffu, isL)) {
+            const unsigned lmask = __ballot_sync(0xffffffffu, isL);
+            if (lmask && __popc(lmask) <= kZeroLanes) {
+                if (isL) {
+#pragma unroll
+                    for (int w = 0; w < WB; ++w) {
+                        uint32_t z = ~t[w] & enc_valid_bits(p.kenc, w);
+                        while (z) {
+                            const int b = __ffs(z) - 1;
+                            z &= z - 1u;
+                            atomicSub(&s_cum[w * 32 + b], 1u);   // ones = (zero-route samples) - zeros
+                        }
+                    }
+                }
+                if (lane == 0) atomicAdd(&s_fz, (unsigned)__popc(lmask));
+            } else if (lmask) {
 #pragma unroll
                 for (int w = 0; w < WB; ++w) {
                     uint32_t mine = 0;
@@ -385,11 +406,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     if (tid < 3 && s_cnt[tid]) atomicAdd(&p.counts3[tid], s_cnt[tid]);
     if (tid == 0 && p.exec_tests && s_exec) atomicAdd(p.exec_tests, s_exec);
     if (p.grad_counts && s_cnt[0]) {
-        // C[i,0] += F - cum_1 ; C[i,k] += cum_k - cum_{k+1} (cum_K = 0)
+        // C[i,0] += F - cum_1 ; C[i,k] += cum_k - cum_{k+1} (cum_K = 0); cum_j = one bits
+        // counted by ballots + (samples counted by zero bits - their zero bits)
         for (int i = tid; i < p.n; i += kThreads) {
             long long prev = (long long)s_cnt[0];
             for (int k = 1; k <= p.km1; ++k) {
-                const long long cum = (long long)s_cum[i * p.km1 + (k - 1)];
+                const int j = i * p.km1 + (k - 1);
+                const long long cum = (long long)(uint32_t)(s_cum[j] + s_fz);
                 const long long d = prev - cum;
                 if (d) atomicAdd(&p.grad_counts[(size_t)i * p.K + (k - 1)], (unsigned long long)d);
                 prev = cum;

@@ -919,9 +919,13 @@ int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stre
     if ((st = check_ws(L, ws, ws_bytes)) != RSR_OK) return st;
     if ((st = check_prepared(problem, ws)) != RSR_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // time both classifiers on the same slice; counts go to the header's spare words
+    // time both classifiers on the same slice; counts go to the header's spare words.
+    // The slice fills the machine several times over for both kernels (a slice
+    // smaller than one wave of the bit-packed kernel's grid favours the tensor-core
+    // kernel, whose one-CTA-per-SM grid fills sooner): 2^20 samples in early-exit
+    // mode, 2^18 in dense mode (every sample meets every reference there).
     ClassifyParams c = make_params(problem, L, ws);
-    c.N = 1 << 16;
+    c.N = c.dense ? (1 << 18) : (1 << 20);
     c.seed = 0x5EEDull;
     c.offset = 0;
     c.counts3 = reinterpret_cast<unsigned long long *>(&reinterpret_cast<WsHeader *>(ws)->reserved[2]);
