@@ -46,7 +46,7 @@ struct Shared {
 template <int WB>
 __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, const unsigned long long *s_thr,
                               uint32_t *s_tw, uint32_t *s_buf, uint32_t *s_cum, const uint32_t *s_hot,
-                              const uint32_t *s_first, const uint32_t *s_zero, Shared &sh) {
+                              const uint32_t *s_first, const uint32_t *s_zero, uint32_t *s_and, Shared &sh) {
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t hl = tile * kThreads + tid;
     const bool valid = hl < d.N;
@@ -68,14 +68,16 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         *cnt_out = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
         return (up ? d.popc_U : d.popc_L) + base * WB;
     };
-    auto issue = [&](uint32_t *dst, bool up, int64_t c) {
+    auto issue = [&](int buf, bool up, int64_t c) {
         int cnt_c;
         const uint32_t *rows = chunk_refs(up, c, &cnt_c);
         const bool ix = use_idx && up;
-        load_chunk_async<WB, kThreads>(dst, ix, ix ? d.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, kenc, rows,
-                                       cnt_c, tid);
+        load_chunk_async<WB, kThreads>(s_buf + buf * (kChunk * kMaxWB), ix,
+                                       ix ? d.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, kenc,
+                                       ix ? d.popc_UA + (size_t)c * WB : nullptr, s_and + buf * kMaxWB, rows, cnt_c,
+                                       tid);
     };
-    issue(s_buf, upper, ci);
+    issue(0, upper, ci);
     // ---- sample and encode (thermometer words, one column per thread) ----
     if (d.km1 == 1) {
         // binary: 32-bit thresholds and never-bits (binary_tables_to_smem) in the s_thr region
@@ -144,7 +146,8 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
     for (int64_t step = 0; step < nsteps; ++step) {
         cp_async_wait_all();                       // this thread's copies of chunk `step`
         if (__syncthreads_and(done)) break;        // chunk `step` visible; chunk step-1 consumed
-        uint32_t *s_ref = s_buf + (int)(step & 1) * (kChunk * kMaxWB);
+        const int cur_buf = (int)(step & 1);
+        uint32_t *s_ref = s_buf + cur_buf * (kChunk * kMaxWB);
         int cnt;
         (void)chunk_refs(upper, ci, &cnt);
         const bool idx_chunk = use_idx && upper;
@@ -152,18 +155,21 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         int64_t ci_next = 0;
         if (step + 1 < nsteps) {
             walk.next(&up_next, &ci_next);
-            issue(s_buf + (int)((step + 1) & 1) * (kChunk * kMaxWB), up_next, ci_next);
+            issue((int)((step + 1) & 1), up_next, ci_next);
         }
         // per-lane scan while many lanes are unresolved, cooperative warp scan otherwise
         const unsigned active = __ballot_sync(0xffffffffu, !done);
         if (idx_chunk) {
-            if (__popc(active) > kCoopIdx) {
-                if (!done && idx_match_lane<WB>(t, s_ref, s_first, s_zero, kenc, cnt)) {
+            // a sample lacking a bit of the chunk's AND row dominates none of its references
+            const bool ruled = !done && chunk_ruled_out<WB>(t, s_and + cur_buf * kMaxWB);
+            const unsigned need = __ballot_sync(0xffffffffu, !done && !ruled);
+            if (__popc(need) > kCoopIdx) {
+                if (!done && !ruled && idx_match_lane<WB>(t, s_ref, s_first, s_zero, kenc, cnt)) {
                     mU = true;
                     done = true;
                 }
             } else {
-                unsigned rem = active;
+                unsigned rem = need;
                 while (rem) {
                     const int src = __ffs(rem) - 1;
                     rem &= rem - 1;
@@ -282,6 +288,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
+    __shared__ uint32_t s_and[2 * kMaxWB];   // AND rows of the staged index chunks
     const int tid = threadIdx.x;
     unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);        // [512]
     uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + 512 * 8);                     // [kMaxWB][256]
@@ -330,14 +337,14 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
         __syncthreads();
         const int64_t tile = item - item_begin[sh.scenario];
         switch (d.words_b) {
-            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
-            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
-            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, sh); break;
+            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
         }
         __syncthreads();
         if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);

@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     uint32_t *s_hot = s_cum + WB * 32;      // the first kHot upper references (index mode)
     uint32_t *s_first = s_hot + kHot * WB;  // component start bits per encoding word (index mode)
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
+    __shared__ uint32_t s_and[2][kMaxWords];   // AND rows of the staged index chunks
     __shared__ unsigned long long s_cnt[3];
     __shared__ unsigned long long s_exec;
     __shared__ unsigned int s_fz;           // I^L samples counted by their zero bits
@@ -145,16 +146,17 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             *cnt_out = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
             return (up ? p.popc_U : p.popc_L) + base * WB;
         };
-        auto issue = [&](uint32_t *dst, bool up, int64_t c) {
+        auto issue = [&](int buf, bool up, int64_t c) {
             int cnt_c;
             const uint32_t *rows = chunk_refs(up, c, &cnt_c);
             const bool ix = use_idx && up;
-            load_chunk_async<WB, kThreads>(dst, ix, ix ? p.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, p.kenc,
-                                           rows, cnt_c, tid);
+            load_chunk_async<WB, kThreads>(s_buf + buf * (kChunk * WB), ix,
+                                           ix ? p.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, p.kenc,
+                                           ix ? p.popc_UA + (size_t)c * WB : nullptr, s_and[buf], rows, cnt_c, tid);
         };
         if (kBufs<WB>() == 2) {
             __syncthreads();            // every thread is done with the previous tile's buffers
-            issue(s_buf, upper, ci);    // chunk 0, copied while the tile is sampled
+            issue(0, upper, ci);        // chunk 0, copied while the tile is sampled
         }
 
         // ---- sample (or read) and encode this thread's state ----------------
@@ -211,7 +213,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             if (kBufs<WB>() == 2) cp_async_wait_all();      // this thread's copies of chunk `step`
             const bool all_done = __syncthreads_and(done);  // chunk `step` visible; chunk step-1 consumed
             if (all_done && !p.dense) break;
-            uint32_t *s_ref = s_buf + (kBufs<WB>() == 2 ? (int)(step & 1) : 0) * (kChunk * WB);
+            const int cur_buf = kBufs<WB>() == 2 ? (int)(step & 1) : 0;
+            uint32_t *s_ref = s_buf + cur_buf * (kChunk * WB);
             int cnt;
             (void)chunk_refs(upper, ci, &cnt);
             const bool idx_chunk = use_idx && upper;
@@ -219,9 +222,9 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             int64_t ci_next = 0;
             if (step + 1 < nsteps) walk.next(&up_next, &ci_next);
             if (kBufs<WB>() == 2) {
-                if (step + 1 < nsteps) issue(s_buf + (int)((step + 1) & 1) * (kChunk * WB), up_next, ci_next);
+                if (step + 1 < nsteps) issue((int)((step + 1) & 1), up_next, ci_next);
             } else {
-                issue(s_ref, upper, ci);
+                issue(0, upper, ci);
                 cp_async_wait_all();
                 __syncthreads();
             }
@@ -247,30 +250,27 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                 }
                 if (upper) mU |= m; else mL |= m;
             } else if (idx_chunk) {
-                // Early exit through the index: per lane while several lanes are
-                // unresolved, one sample per warp otherwise.
-                const unsigned active = __ballot_sync(0xffffffffu, !done);
-                if (__popc(active) > kCoopIdx) {
-                    if (!done) {
-                        my_exec += (unsigned long long)cnt;
-                        if (idx_match_lane<WB>(t, s_ref, s_first, s_zero, p.kenc, cnt)) {
-                            mU = true;
-                            done = true;
-                        }
+                // Early exit through the index.  A sample lacking a bit of the chunk's
+                // AND row dominates none of its references; the others are tested
+                // per lane while several need it, one sample per warp otherwise.
+                const bool ruled = !done && chunk_ruled_out<WB>(t, s_and[cur_buf]);
+                if (!done) my_exec += (unsigned long long)cnt;
+                const unsigned need = __ballot_sync(0xffffffffu, !done && !ruled);
+                if (__popc(need) > kCoopIdx) {
+                    if (!done && !ruled && idx_match_lane<WB>(t, s_ref, s_first, s_zero, p.kenc, cnt)) {
+                        mU = true;
+                        done = true;
                     }
                 } else {
-                    unsigned rem = active;
+                    unsigned rem = need;
                     while (rem) {
                         const int src_lane = __ffs(rem) - 1;
                         rem &= rem - 1;
                         const bool found = idx_match_warp<WB, kThreads>(s_tw + (tid - lane + src_lane), s_ref,
                                                                         s_first, p.kenc, cnt, lane);
-                        if (lane == src_lane) {
-                            my_exec += (unsigned long long)cnt;
-                            if (found) {
-                                mU = true;
-                                done = true;
-                            }
+                        if (lane == src_lane && found) {
+                            mU = true;
+                            done = true;
                         }
                     }
                     __syncwarp();  // the columns read above are rewritten by their lanes for the next tile

@@ -144,21 +144,33 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Stage one chunk into shared memory, without waiting: an index chunk (kenc
-// rows of 8 words, from idx_src) or cnt bit-packed references of WB words
-// (from rows_src).  Every address is 16-byte aligned: chunks start at
+// rows of 8 words, from idx_src, and its AND row of WB words, from and_src) or
+// cnt bit-packed references of WB words (from rows_src).  Every address is 16-byte aligned: chunks start at
 // multiples of 256 references in 256-byte aligned regions.  The caller waits
 // with cp_async_wait_all() and a block barrier before reading.
 template <int WB, int nthreads>
 __device__ __forceinline__ void load_chunk_async(uint32_t *dst, bool idx_chunk, const uint32_t *idx_src, int kenc,
+                                                 const uint32_t *and_src, uint32_t *and_dst,
                                                  const uint32_t *rows_src, int cnt, int tid) {
     if (idx_chunk) {
         for (int i = tid; i < kenc * 2; i += nthreads) cp_async16(dst + 4 * i, idx_src + 4 * i);
+        if (tid < WB) cp_async4(and_dst + tid, and_src + tid);   // the chunk's AND row
     } else {
         const int nw = cnt * WB, n16 = nw >> 2;
         for (int i = tid; i < n16; i += nthreads) cp_async16(dst + 4 * i, rows_src + 4 * i);
         for (int i = 4 * n16 + tid; i < nw; i += nthreads) cp_async4(dst + i, rows_src + i);
     }
     cp_async_commit();
+}
+
+// Does the sample (words t) lack a bit that every reference of the chunk has
+// (chunk AND row a)?  Then it dominates none of them.
+template <int WB>
+__device__ __forceinline__ bool chunk_ruled_out(const uint32_t (&t)[WB], const uint32_t *a) {
+    uint32_t acc = 0u;
+#pragma unroll
+    for (int w = 0; w < WB; ++w) acc |= a[w] & ~t[w];
+    return acc != 0u;
 }
 
 // Component start bits of encoding word w for K-1 bits per component.

@@ -37,10 +37,10 @@ __global__ void encode_popc_kernel(const uint8_t *__restrict__ refs, const int32
 
 // Component-major index of the upper set (layout in popc_index.cuh): word q of
 // row j of chunk c has bit b = t_j of the reference in slot 256c + 32q + b, 0
-// past R_U and for rows j >= kenc.  One thread per output word, reading the
-// already ordered bit-packed rows.
-__global__ void encode_index_kernel(const uint32_t *__restrict__ popc_U, int64_t R_U, int words_b, int kenc,
-                                    int64_t total, uint32_t *__restrict__ out) {
+// past R_U and for rows j >= kenc.  Slot r holds bit-packed row perm[r] (the
+// clustered order; identity without perm).  One thread per output word.
+__global__ void encode_index_kernel(const uint32_t *__restrict__ popc_U, const int32_t *__restrict__ perm,
+                                    int64_t R_U, int words_b, int kenc, int64_t total, uint32_t *__restrict__ out) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= total) return;
     const int rows = 32 * words_b;
@@ -52,12 +52,44 @@ __global__ void encode_index_kernel(const uint32_t *__restrict__ popc_U, int64_t
     if (j < kenc) {
         const int jw = j >> 5, jb = j & 31;
         for (int b = 0; b < 32; ++b) {
-            const int64_t r = c * 256 + 32 * q + b;
-            if (r >= R_U) break;
+            const int64_t slot = c * 256 + 32 * q + b;
+            if (slot >= R_U) break;
+            const int64_t r = perm ? (int64_t)perm[slot] : slot;
             word |= ((popc_U[r * words_b + jw] >> jb) & 1u) << b;
         }
     }
     out[gid] = word;
+}
+
+// Per index chunk, the AND of its references' bit-packed rows: the bits every
+// reference of the chunk has.  A sample lacking one of them dominates no
+// reference of the chunk.  One thread per (chunk, word).
+__global__ void chunk_and_kernel(const uint32_t *__restrict__ popc_U, const int32_t *__restrict__ perm, int64_t R_U,
+                                 int words_b, int64_t nchunks, uint32_t *__restrict__ out) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= nchunks * words_b) return;
+    const int w = (int)(gid % words_b);
+    const int64_t c = gid / words_b;
+    uint32_t a = 0xffffffffu;
+    for (int64_t slot = c * 256; slot < R_U && slot < (c + 1) * 256; ++slot) {
+        const int64_t r = perm ? (int64_t)perm[slot] : slot;
+        a &= popc_U[r * words_b + w];
+    }
+    out[gid] = a;
+}
+
+// Clustering key of each upper reference: its bits at up to 32 chosen
+// thermometer positions (most significant first).
+__global__ void cluster_keys_kernel(const uint32_t *__restrict__ popc_U, int64_t R_U, int words_b, KeyBits kb,
+                                    uint32_t *__restrict__ keys) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R_U) return;
+    uint32_t k = 0;
+    for (int b = 0; b < kb.nbits; ++b) {
+        const int j = kb.pos[b];
+        k |= ((popc_U[r * words_b + (j >> 5)] >> (j & 31)) & 1u) << (31 - b);
+    }
+    keys[r] = k;
 }
 
 // Overlap pre-check: some upper reference r^U <= some lower reference r^L iff
@@ -173,12 +205,24 @@ cudaError_t launch_score_refs(const uint8_t *refs, int64_t R, int n, int K, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_encode_index(const uint32_t *popc_U, int64_t R_U, int words_b, int kenc, uint32_t *out,
+cudaError_t launch_encode_index(const uint32_t *popc_U, const int32_t *perm, int64_t R_U, int words_b, int kenc,
+                                uint32_t *out_index, uint32_t *out_and, cudaStream_t s) {
+    if (R_U <= 0) return cudaSuccess;
+    const int64_t nchunks = (R_U + 255) / 256;
+    const int64_t total = nchunks * (int64_t)(32 * words_b) * 8;
+    encode_index_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(popc_U, perm, R_U, words_b, kenc, total,
+                                                                        out_index);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    chunk_and_kernel<<<(unsigned)((nchunks * words_b + 255) / 256), 256, 0, s>>>(popc_U, perm, R_U, words_b, nchunks,
+                                                                                 out_and);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cluster_keys(const uint32_t *popc_U, int64_t R_U, int words_b, const KeyBits &kb, uint32_t *keys,
                                 cudaStream_t s) {
     if (R_U <= 0) return cudaSuccess;
-    const int64_t total = ((R_U + 255) / 256) * (int64_t)(32 * words_b) * 8;
-    const int64_t grid = (total + 255) / 256;
-    encode_index_kernel<<<(unsigned)grid, 256, 0, s>>>(popc_U, R_U, words_b, kenc, total, out);
+    cluster_keys_kernel<<<(unsigned)((R_U + 255) / 256), 256, 0, s>>>(popc_U, R_U, words_b, kb, keys);
     return cudaGetLastError();
 }
 

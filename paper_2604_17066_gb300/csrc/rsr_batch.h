@@ -15,6 +15,7 @@ struct BatchDesc {
     const unsigned long long *thr;       // [n*(K-1)]
     const uint32_t *popc_L, *popc_U;     // [R][words_b]
     const uint32_t *popc_UT;             // component-major index of the upper set, or NULL
+    const uint32_t *popc_UA;             // per index chunk: AND of its references
     const int32_t *overlap;              // precedence pre-check result
     uint8_t *labels;                     // [N] or NULL
     unsigned long long *counts3;         // [3]

@@ -125,9 +125,9 @@ ClassifyParams make_params(const rsr_problem *p, const WsLayout &L, void *ws) {
     c.thr = reinterpret_cast<const unsigned long long *>(base + L.off_thr);
     c.popc_L = reinterpret_cast<const uint32_t *>(base + L.off_popc_L);
     c.popc_U = reinterpret_cast<const uint32_t *>(base + L.off_popc_U);
-    c.popc_UT = (p->R_U > 0 && !(p->flags & RSR_FLAG_NO_INDEX))
-                    ? reinterpret_cast<const uint32_t *>(base + L.off_popc_UT)
-                    : nullptr;
+    const bool idx = p->R_U > 0 && !(p->flags & RSR_FLAG_NO_INDEX);
+    c.popc_UT = idx ? reinterpret_cast<const uint32_t *>(base + L.off_popc_UT) : nullptr;
+    c.popc_UA = idx ? reinterpret_cast<const uint32_t *>(base + L.off_popc_UA) : nullptr;
     c.tc_L = reinterpret_cast<const uint8_t *>(base + L.off_tc_L);
     c.tc_U = reinterpret_cast<const uint8_t *>(base + L.off_tc_U);
     c.R_L = p->R_L;
@@ -194,6 +194,71 @@ int order_references(const uint8_t *refs, int64_t R, int n, int K, const float *
 }
 
 }  // namespace
+
+// Component-major index of the upper set in clustered order (popc_index.cuh).
+// The references (bit-packed rows in probability order at pU) after the first
+// chunk are reordered by a 32-bit key: their bits at the 32 thermometer
+// positions most likely to be 0 in a sample (P(x_i < k) largest first), in
+// decreasing key order, stably.
+// References that share their failure-prone components then share index
+// chunks, so the chunk AND (bits every reference of the chunk has) rules out
+// whole chunks for samples where such a component failed.  Labels do not
+// depend on the order.  keys / perm: workspace scratch of R_U entries; the
+// stream is synchronised (the keys are sorted on the host).
+int build_upper_index(const rsr_problem *p, const uint32_t *pU, int64_t R_U, int words_b, uint32_t *d_keys,
+                      int32_t *d_perm, uint32_t *out_index, uint32_t *out_and, cudaStream_t s) {
+    if (R_U <= 0) return RSR_OK;
+    const int kenc = p->n * (p->K - 1);
+    const int32_t *perm = nullptr;
+    // positions: thermometer bits (i, k) by decreasing P(x_i < k), ties by position
+    std::vector<std::pair<double, int>> pz;
+    pz.reserve((size_t)kenc);
+    for (int i = 0; i < p->n; ++i) {
+        double c = 0.0;
+        for (int k = 1; k < p->K; ++k) {
+            c += p->pmf[(size_t)i * p->K + (k - 1)];
+            pz.push_back({c, i * (p->K - 1) + (k - 1)});
+        }
+    }
+    std::stable_sort(pz.begin(), pz.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first > b.first;
+    });
+    // Clustering pays where a few components fail far more often than the rest
+    // (a hazard's footprint): binary components, more than two chunks, and the
+    // 32nd most failure-prone component at least twice as likely to fail as the
+    // median one.  Otherwise the key would order the references arbitrarily.
+    const bool cluster = p->K == 2 && R_U > 2 * 256 && kenc > 32 &&
+                         pz[31].first >= 2.0 * pz[(size_t)kenc / 2].first;
+    if (cluster) {
+        KeyBits kb{};
+        kb.nbits = (int)std::min<size_t>(32, pz.size());
+        for (int b = 0; b < kb.nbits; ++b) kb.pos[b] = (int16_t)pz[(size_t)b].second;
+        RSR_CUDA(launch_cluster_keys(pU, R_U, words_b, kb, d_keys, s));
+        std::vector<uint32_t> keys((size_t)R_U);
+        RSR_CUDA(cudaMemcpyAsync(keys.data(), d_keys, sizeof(uint32_t) * (size_t)R_U, cudaMemcpyDeviceToHost, s));
+        RSR_CUDA(cudaStreamSynchronize(s));
+        // The first chunk keeps the 256 most probable references (shallow matches
+        // are found there); the rest is ordered by decreasing key (stable LSD radix
+        // sort of ~key, 8 bits per pass).
+        const int64_t head = 256, m = R_U - head;
+        std::vector<int32_t> a((size_t)R_U), b((size_t)m);
+        for (int64_t r = 0; r < R_U; ++r) a[(size_t)r] = (int32_t)r;
+        int32_t *tail = a.data() + head;
+        for (int shift = 0; shift < 32; shift += 8) {
+            size_t cnt[257] = {0};
+            for (int64_t r = 0; r < m; ++r) ++cnt[((~keys[(size_t)tail[r]]) >> shift & 255u) + 1];
+            for (int v = 0; v < 256; ++v) cnt[v + 1] += cnt[v];
+            for (int64_t r = 0; r < m; ++r) b[cnt[(~keys[(size_t)tail[r]]) >> shift & 255u]++] = tail[r];
+            std::copy(b.begin(), b.end(), tail);
+        }
+        RSR_CUDA(cudaMemcpyAsync(d_perm, a.data(), sizeof(int32_t) * (size_t)R_U, cudaMemcpyHostToDevice, s));
+        // the host vector must outlive the copy
+        RSR_CUDA(cudaStreamSynchronize(s));
+        perm = d_perm;
+    }
+    RSR_CUDA(launch_encode_index(pU, perm, R_U, words_b, kenc, out_index, out_and, s));
+    return RSR_OK;
+}
 
 int cuda_fail(cudaError_t e, const char *where) {
     // consume the runtime's last-error state so that a later, unrelated
@@ -311,11 +376,14 @@ int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_strea
                                d_table + (size_t)problem->n * problem->K, d_score, d_perm, s)) != RSR_OK)
         return st;
     RSR_CUDA(launch_encode_popc(problem->ref_U, problem->R_U, problem->n, km1, L.words, false, pU, s, d_perm));
-    RSR_CUDA(launch_encode_index(pU, problem->R_U, L.words, L.kenc, reinterpret_cast<uint32_t *>(base + L.off_popc_UT),
-                                 s));
     if (tc_enc)
         RSR_CUDA(launch_encode_tc(problem->ref_U, problem->R_U, L.tc_rows_U, problem->n, km1, L.tc_kpad, true,
                                   reinterpret_cast<uint8_t *>(base + L.off_tc_U), s, d_perm));
+    // the index reuses the ordering scratch (keys in the score array, its own permutation)
+    if ((st = build_upper_index(problem, pU, problem->R_U, L.words, reinterpret_cast<uint32_t *>(d_score), d_perm,
+                                reinterpret_cast<uint32_t *>(base + L.off_popc_UT),
+                                reinterpret_cast<uint32_t *>(base + L.off_popc_UA), s)) != RSR_OK)
+        return st;
     RSR_CUDA(launch_overlap(pL, problem->R_L, pU, problem->R_U, L.words, reinterpret_cast<WsHeader *>(base), s));
     std::lock_guard<std::mutex> g(g_mu);
     g_prepared[ws] = Prepared{problem->n, problem->K, problem->R_L, problem->R_U, problem->ref_L, problem->ref_U,
@@ -544,7 +612,7 @@ namespace {
 
 struct BatchLayout {
     size_t off_descs = 0, off_begin = 0, off_tune = 0, off_table = 0, off_score = 0, off_perm = 0, total = 0;
-    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_bit, off_lc, off_tgrad;
+    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_pUA, off_bit, off_lc, off_tgrad;
     std::vector<int> words_b;
 };
 
@@ -583,6 +651,8 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
         off = align256(off + 4 * (size_t)p.R_U * wb);
         B.off_pUT.push_back(off);  // component-major index of the upper set
         off = align256(off + 4 * (size_t)((p.R_U + 255) / 256) * 256 * wb);
+        B.off_pUA.push_back(off);  // per index chunk: AND of its references
+        off = align256(off + 4 * (size_t)((p.R_U + 255) / 256) * wb);
         B.off_bit.push_back(off);
         off = align256(off + 4 * (size_t)p.n * km1);
         B.off_lc.push_back(off);
@@ -720,7 +790,10 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
             return st;
         RSR_CUDA(launch_encode_popc(p.ref_U, p.R_U, p.n, km1, B.words_b[k], false, pU, s, d_perm));
         uint32_t *pUT = reinterpret_cast<uint32_t *>(base + B.off_pUT[k]);
-        RSR_CUDA(launch_encode_index(pU, p.R_U, B.words_b[k], p.n * km1, pUT, s));
+        uint32_t *pUA = reinterpret_cast<uint32_t *>(base + B.off_pUA[k]);
+        if ((st = build_upper_index(&p, pU, p.R_U, B.words_b[k], reinterpret_cast<uint32_t *>(d_score), d_perm, pUT,
+                                    pUA, s)) != RSR_OK)
+            return st;
         WsHeader *hs = reinterpret_cast<WsHeader *>(base + B.off_hdr[k]);
         RSR_CUDA(launch_overlap(pL, p.R_L, pU, p.R_U, B.words_b[k], hs, s));
         BatchDesc &d = descs[k];
@@ -737,6 +810,7 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.popc_L = pL;
         d.popc_U = pU;
         d.popc_UT = (p.R_U > 0 && !(p.flags & RSR_FLAG_NO_INDEX)) ? pUT : nullptr;
+        d.popc_UA = d.popc_UT ? pUA : nullptr;
         d.overlap = &hs->overlap;
         d.labels = labels_or_null ? labels_or_null[k] : nullptr;
         d.counts3 = reinterpret_cast<unsigned long long *>(counts3xS + 3 * (size_t)k);

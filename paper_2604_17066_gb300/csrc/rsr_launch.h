@@ -14,8 +14,16 @@ int popc_word_bucket(int words);
 // Preparation (prep_kernels.cu).
 cudaError_t launch_encode_popc(const uint8_t *refs, int64_t R, int n, int km1, int words_b,
                                bool complement, uint32_t *out, cudaStream_t s, const int32_t *perm = nullptr);
-// Component-major index of the upper set (popc_index.cuh) from its bit-packed rows.
-cudaError_t launch_encode_index(const uint32_t *popc_U, int64_t R_U, int words_b, int kenc, uint32_t *out,
+// Component-major index of the upper set (popc_index.cuh) from its bit-packed rows,
+// slot r taking row perm[r] (identity if perm is NULL), and the per-chunk AND rows.
+cudaError_t launch_encode_index(const uint32_t *popc_U, const int32_t *perm, int64_t R_U, int words_b, int kenc,
+                                uint32_t *out_index, uint32_t *out_and, cudaStream_t s);
+// Clustering keys of the upper references (bits at the positions of kb, most significant first).
+struct KeyBits {
+    int32_t nbits;
+    int16_t pos[32];
+};
+cudaError_t launch_cluster_keys(const uint32_t *popc_U, int64_t R_U, int words_b, const KeyBits &kb, uint32_t *keys,
                                 cudaStream_t s);
 cudaError_t launch_score_refs(const uint8_t *refs, int64_t R, int n, int K, const float *table, float *score,
                               cudaStream_t s);

@@ -101,3 +101,50 @@ def test_batch_index_parity(rsr):
             assert np.array_equal(counts[s], cnt), (index, s)
             assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K),
                                   O.grad_counts(X, lab, p.K)), (index, s)
+
+
+def hazard_problem(n, R_L, R_U, seed):
+    """A hazard footprint: 40 components fail with probability 0.3-0.5, the rest
+    with 1e-3, so the index is built in clustered order (binary components, the
+    32nd most failure-prone component far above the median).  Upper references
+    are random subsets that mostly include footprint components, so first
+    matches lie deep and chunk AND rows rule out whole chunks."""
+    rng = np.random.default_rng(seed)
+    pf = np.full(n, 1e-3)
+    hot = rng.choice(n, size=40, replace=False)
+    pf[hot] = rng.uniform(0.3, 0.5, size=40)
+    pmf = np.stack([pf, 1 - pf], axis=1)
+    ref_U = np.zeros((R_U, n), np.uint8)
+    for r in range(R_U):
+        k_hot = int(rng.integers(8, 20))
+        ref_U[r, rng.choice(hot, size=k_hot, replace=False)] = 1
+        ref_U[r, rng.choice(n, size=int(rng.integers(3, 15)), replace=False)] = 1
+    ref_L = np.ones((R_L, n), np.uint8)
+    for r in range(R_L):
+        ref_L[r, rng.choice(hot, size=int(rng.integers(8, 16)), replace=False)] = 0
+    return W.Problem("hazard", pmf, ref_L, ref_U)
+
+
+@pytest.mark.parametrize("n,R_L,R_U,N", [(150, 30, 3000, 4000), (290, 200, 2049, 3000), (64, 0, 1100, 2000)])
+def test_index_parity_clustered_order(rsr, n, R_L, R_U, N):
+    prob = hazard_problem(n, R_L, R_U, seed=n + R_U)
+    cnt, _ = check(rsr, prob, 21, 1 << 20, N)
+    assert cnt[1] > 0 and cnt.sum() == N
+
+
+def test_batch_index_parity_clustered_order(rsr):
+    probs = [hazard_problem(n, RL, RU, seed=7 * n) for n, RL, RU in [(150, 30, 3000), (64, 0, 1100), (200, 50, 600)]]
+    Ns = [3000, 2000, 1000]
+    seeds = [3, 4, 5]
+    offsets = [0, 1 << 30, 17]
+    P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=POPC) for p in probs]
+    b = rsr.Batch(P, seeds, offsets, Ns)
+    rsr.rsr_batch(b)
+    torch.cuda.synchronize()
+    counts = b.counts3.cpu().numpy()
+    for s, p in enumerate(probs):
+        X = O.sample(p.pmf, seeds[s], offsets[s], Ns[s])
+        lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+        assert np.array_equal(b.labels[s].cpu().numpy(), lab), s
+        assert np.array_equal(counts[s], cnt), s
+        assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K), O.grad_counts(X, lab, p.K)), s
