@@ -11,6 +11,8 @@ namespace rsr {
 
 namespace {
 
+constexpr int kMaxCorrHist = 2048;  // n*K <= n + n(K-1) <= 2 * 1024 (K >= 2)
+
 // Thermometer word w of reference r: bit j = i*(K-1) + (k-1) is [r_i >= k];
 // lower references are stored complemented (within the n*(K-1) valid bits) so
 // that the classifier's failure test is t(x) AND stored == 0 (Sec. 3.3: the
@@ -38,44 +40,46 @@ __global__ void encode_popc_kernel(const uint8_t *__restrict__ refs, const int32
 // Component-major index of the upper set (layout in popc_index.cuh): word q of
 // row j of chunk c has bit b = t_j of the reference in slot 256c + 32q + b, 0
 // past R_U and for rows j >= kenc.  Slot r holds bit-packed row perm[r] (the
-// clustered order; identity without perm).  One thread per output word.
+// clustered order; identity without perm).  One warp per (chunk, word q,
+// encoding word jw): lane b loads word jw of slot 256c + 32q + b, and 32
+// ballots transpose the 32 x 32 bit block into rows 32jw .. 32jw + 31.
 __global__ void encode_index_kernel(const uint32_t *__restrict__ popc_U, const int32_t *__restrict__ perm,
-                                    int64_t R_U, int words_b, int kenc, int64_t total, uint32_t *__restrict__ out) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= total) return;
-    const int rows = 32 * words_b;
-    const int q = (int)(gid % 8);
-    const int64_t cj = gid / 8;
-    const int j = (int)(cj % rows);
-    const int64_t c = cj / rows;
-    uint32_t word = 0;
-    if (j < kenc) {
-        const int jw = j >> 5, jb = j & 31;
-        for (int b = 0; b < 32; ++b) {
-            const int64_t slot = c * 256 + 32 * q + b;
-            if (slot >= R_U) break;
-            const int64_t r = perm ? (int64_t)perm[slot] : slot;
-            word |= ((popc_U[r * words_b + jw] >> jb) & 1u) << b;
+                                    int64_t R_U, int words_b, int kenc, int64_t nwarps, uint32_t *__restrict__ out) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= nwarps) return;   // whole warps: nwarps * 32 threads, blocks of 256
+    const int jw = (int)(wid % words_b);
+    const int q = (int)((wid / words_b) % 8);
+    const int64_t c = wid / ((int64_t)words_b * 8);
+    const int64_t slot = c * 256 + 32 * q + lane;
+    uint32_t v = 0u;
+    if (slot < R_U) v = popc_U[(perm ? (int64_t)perm[slot] : slot) * words_b + jw];
+    for (int jb = 0; jb < 32; ++jb) {
+        const uint32_t m = __ballot_sync(0xffffffffu, (v >> jb) & 1u);
+        if (lane == jb) {
+            const int j = 32 * jw + jb;
+            out[((size_t)c * 32 * words_b + j) * 8 + q] = j < kenc ? m : 0u;
         }
     }
-    out[gid] = word;
 }
 
 // Per index chunk, the AND of its references' bit-packed rows: the bits every
 // reference of the chunk has.  A sample lacking one of them dominates no
-// reference of the chunk.  One thread per (chunk, word).
+// reference of the chunk.  One warp per (chunk, word), eight slots per lane.
 __global__ void chunk_and_kernel(const uint32_t *__restrict__ popc_U, const int32_t *__restrict__ perm, int64_t R_U,
-                                 int words_b, int64_t nchunks, uint32_t *__restrict__ out) {
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= nchunks * words_b) return;
-    const int w = (int)(gid % words_b);
-    const int64_t c = gid / words_b;
+                                 int words_b, int64_t nwarps, uint32_t *__restrict__ out) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= nwarps) return;
+    const int w = (int)(wid % words_b);
+    const int64_t c = wid / words_b;
     uint32_t a = 0xffffffffu;
-    for (int64_t slot = c * 256; slot < R_U && slot < (c + 1) * 256; ++slot) {
-        const int64_t r = perm ? (int64_t)perm[slot] : slot;
-        a &= popc_U[r * words_b + w];
+    for (int k = 0; k < 8; ++k) {
+        const int64_t slot = c * 256 + 32 * k + lane;
+        if (slot < R_U) a &= popc_U[(perm ? (int64_t)perm[slot] : slot) * words_b + w];
     }
-    out[gid] = a;
+    a = __reduce_and_sync(0xffffffffu, a);
+    if (lane == 0) out[wid] = a;
 }
 
 // Clustering key of each upper reference: its bits at up to 32 chosen
@@ -166,25 +170,36 @@ __global__ void sample_kernel(const ClassifyParams p, uint8_t *__restrict__ stat
 
 // Gradient correction: unclassified samples that Phi resolved to S <= m' join
 // the failure set; their states are regenerated from Philox and counted.
-__global__ void grad_correction_kernel(const ClassifyParams p, const int64_t *__restrict__ idx, int64_t m) {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    const int64_t hl = idx[j];
-    if (hl < 0 || hl >= p.N) {
-        atomicMax(&p.hdr->error, 1);  // index out of range: recorded, not counted
-        return;
-    }
-    const uint64_t h = p.offset + (uint64_t)hl;
+__global__ void __launch_bounds__(256) grad_correction_kernel(const ClassifyParams p, const int64_t *__restrict__ idx,
+                                                               int64_t m) {
+    // one warp per listed sample, lanes over its components (one Philox block each);
+    // per-(component, state) counts gathered in shared memory, flushed once per block
+    __shared__ unsigned int s_hist[kMaxCorrHist];
+    const int nk = p.n * p.K;
+    for (int i = threadIdx.x; i < nk; i += blockDim.x) s_hist[i] = 0u;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
-    for (int q = 0; 4 * q < p.n; ++q) {
-        const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
-        const uint32_t us[4] = {r.x, r.y, r.z, r.w};
-        for (int c = 0; c < 4 && 4 * q + c < p.n; ++c) {
-            const int i = 4 * q + c;
-            const uint32_t x = state_from_uniform(us[c], p.thr + (size_t)i * p.km1, p.km1);
-            atomicAdd(&p.grad_counts[(size_t)i * p.K + x], 1ull);
+    for (int64_t j = (int64_t)blockIdx.x * nwarps + warp; j < m; j += (int64_t)gridDim.x * nwarps) {
+        const int64_t hl = idx[j];
+        if (hl < 0 || hl >= p.N) {
+            if (lane == 0) atomicMax(&p.hdr->error, 1);  // index out of range: recorded, not counted
+            continue;
+        }
+        const uint64_t h = p.offset + (uint64_t)hl;
+        for (int q = lane; 4 * q < p.n; q += 32) {
+            const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
+            const uint32_t us[4] = {r.x, r.y, r.z, r.w};
+            for (int c = 0; c < 4 && 4 * q + c < p.n; ++c) {
+                const int i = 4 * q + c;
+                const uint32_t x = state_from_uniform(us[c], p.thr + (size_t)i * p.km1, p.km1);
+                atomicAdd(&s_hist[i * p.K + (int)x], 1u);
+            }
         }
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nk; i += blockDim.x)
+        if (s_hist[i]) atomicAdd(&p.grad_counts[i], (unsigned long long)s_hist[i]);
 }
 
 }  // namespace
@@ -209,13 +224,12 @@ cudaError_t launch_encode_index(const uint32_t *popc_U, const int32_t *perm, int
                                 uint32_t *out_index, uint32_t *out_and, cudaStream_t s) {
     if (R_U <= 0) return cudaSuccess;
     const int64_t nchunks = (R_U + 255) / 256;
-    const int64_t total = nchunks * (int64_t)(32 * words_b) * 8;
-    encode_index_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(popc_U, perm, R_U, words_b, kenc, total,
-                                                                        out_index);
+    const int64_t nw_idx = nchunks * 8 * words_b, nw_and = nchunks * words_b;   // warps
+    encode_index_kernel<<<(unsigned)((nw_idx + 7) / 8), 256, 0, s>>>(popc_U, perm, R_U, words_b, kenc, nw_idx,
+                                                                     out_index);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    chunk_and_kernel<<<(unsigned)((nchunks * words_b + 255) / 256), 256, 0, s>>>(popc_U, perm, R_U, words_b, nchunks,
-                                                                                 out_and);
+    chunk_and_kernel<<<(unsigned)((nw_and + 7) / 8), 256, 0, s>>>(popc_U, perm, R_U, words_b, nw_and, out_and);
     return cudaGetLastError();
 }
 
@@ -252,7 +266,8 @@ cudaError_t launch_sample(const ClassifyParams &p, uint8_t *states, cudaStream_t
 
 cudaError_t launch_grad_correction(const ClassifyParams &p, const int64_t *idx, int64_t m, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
-    grad_correction_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(p, idx, m);
+    const int64_t grid = std::min<int64_t>((m + 7) / 8, (int64_t)device_sm_count() * 4);
+    grad_correction_kernel<<<(unsigned)grid, 256, 0, s>>>(p, idx, m);
     return cudaGetLastError();
 }
 
