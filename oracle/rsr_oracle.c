@@ -22,7 +22,7 @@
  *   - system functions of the experiments: s-t connectivity (Sec. 4.1-4.2),
  *     global connectivity (Sec. 4.3), s-t maximum-flow levels (d-MC / d-MP
  *     systems, Sec. 2.2) and the three-state global connectivity level (Sec. 4.6)
- * Not in the paper (defined by this build, see the function comments):
+ * Not in the paper (defined by this library, see the function comments):
  *   - the sampler (Philox4x32-10 counter layout and integer inverse-CDF
  *     thresholds); the paper only states that P(X) is available (Sec. 3.1)
  *   - the score-function gradient of P(S <= m') with respect to the
