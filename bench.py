@@ -679,14 +679,25 @@ def main():
                 "note": "FP8 dense peak = 2 x bf16 sustained (%s); flops = 2*n(K-1)*%s tests"
                         % (peak_src, "N*(R_L+R_U)" if P.dense else "executed")}
     else:
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        ops = n_rank * (((P.n + 3) // 4) * 80 + kenc) + exec_per_launch * ((kenc + 31) // 32 + 1)
+        # integer-op model: per Philox4x32-10 block 20 wide products (IMAD.WIDE) and 60
+        # logic / add ops; n(K-1) compares per sample; ceil(n(K-1)/32) + 1 per executed
+        # test (an index chunk counts all its references, as the scan it replaces).
+        # Peak: the measured LOP3 and IMAD.WIDE rates of this GPU, combined for this mix
+        # (time bound = max(ALU ops / LOP3 rate, IMAD ops / IMAD rate)).
+        meas = rsr.rsr_measure_int_peak()
+        blocks = n_rank * ((P.n + 3) // 4)
+        imad_ops = 20.0 * blocks
+        alu_ops = 60.0 * blocks + n_rank * kenc + exec_per_launch * ((kenc + 31) // 32 + 1)
+        ops = imad_ops + alu_ops
+        t_bound = max(alu_ops / meas["lop3_ops_per_s"], imad_ops / meas["imad_ops_per_s"])
         achieved = ops / (kern_avg / 1000.0) / 1e12
-        peak = sms * 128 * mhz * 1e6 / 1e12
+        peak = ops / t_bound / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "note": "integer-op model (80 per Philox block, n(K-1) compares per sample, "
-                                         "ceil(n(K-1)/32)+1 per executed test); peak = SMs x 128 x max SM clock"}
+                "traffic": None, "measured_lop3_tops": meas["lop3_ops_per_s"] / 1e12,
+                "measured_imad_wide_tops": meas["imad_ops_per_s"] / 1e12,
+                "note": "integer-op model (per Philox block 20 IMAD.WIDE + 60 ALU ops, n(K-1) compares per "
+                        "sample, ceil(n(K-1)/32)+1 per executed test); peak = this mix at the LOP3 and "
+                        "IMAD.WIDE rates measured on this GPU (rsr_measure_int_peak)"}
 
     extras = {}
     if rank == 0 and not args.no_extras:

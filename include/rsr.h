@@ -446,6 +446,17 @@ RSR_API int rsr_stage1(const rsr_problem *problem, const rsr_system *system, con
                        uint8_t *ref_L_buf, uint8_t *ref_U_buf, int64_t *history_or_null,
                        rsr_stage1_result *result, void *ws, size_t ws_bytes, rsr_stream_t stream);
 
+/*
+ * Measured integer throughput of the current GPU, for the roofline of the
+ * bit-packed classifiers (not a step of the method; the paper has no
+ * counterpart).  Runs two short kernels on a full grid, each with eight
+ * independent chains per thread: three-input logic ops (LOP3, the classifiers'
+ * and-or test) and 32x32->64 multiply-adds (the products of Philox4x32-10).
+ *   lop3_ops_per_s, imad_ops_per_s : host double[1] each, set to thread-ops per second.
+ * Synchronous (waits for its own kernels on `stream`); allocates nothing.
+ */
+RSR_API int rsr_measure_int_peak(double *lop3_ops_per_s, double *imad_ops_per_s, rsr_stream_t stream);
+
 /* Message for a status code (static storage). */
 RSR_API const char *rsr_status_string(int status);
 

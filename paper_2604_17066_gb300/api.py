@@ -469,3 +469,13 @@ def rsr_level_pmf(sessions, system: System, seed: int, offset: int, N: int, leve
                                     _stream(stream)), "rsr_level_pmf")
     return dict(level_counts=level_counts, levels=None if lv is None else lv[:int(N)], counts3=counts3,
                 n_phi=n_phi)
+
+
+def rsr_measure_int_peak(stream=None) -> dict:
+    """rsr_measure_int_peak: measured LOP3 and IMAD.WIDE thread-ops per second
+    of the current GPU (the bit-packed classifiers' roofline denominator)."""
+    lop3 = ctypes.c_double(0.0)
+    imad = ctypes.c_double(0.0)
+    check(_lib.load().rsr_measure_int_peak(ctypes.addressof(lop3), ctypes.addressof(imad), _stream(stream)),
+          "rsr_measure_int_peak")
+    return {"lop3_ops_per_s": lop3.value, "imad_ops_per_s": imad.value}

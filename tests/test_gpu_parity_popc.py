@@ -180,3 +180,12 @@ def test_binary_sampler_edge_thresholds(rsr, n):
     torch.cuda.synchronize()
     assert np.array_equal(b.grad_counts[0].cpu().numpy().reshape(n, 2), C)
     assert np.array_equal(b.counts3[0].cpu().numpy(), cnt)
+
+
+def test_measured_integer_peaks_are_plausible(rsr):
+    """rsr_measure_int_peak (the bit-packed roofline's denominator) returns rates
+    between 16 and 256 thread-ops per SM per cycle at 0.5-3 GHz."""
+    m = rsr.rsr_measure_int_peak()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for k in ("lop3_ops_per_s", "imad_ops_per_s"):
+        assert sms * 16 * 0.5e9 < m[k] < sms * 256 * 3e9, (k, m[k])
