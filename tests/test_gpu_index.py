@@ -148,3 +148,58 @@ def test_batch_index_parity_clustered_order(rsr):
         assert np.array_equal(b.labels[s].cpu().numpy(), lab), s
         assert np.array_equal(counts[s], cnt), s
         assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K), O.grad_counts(X, lab, p.K)), s
+
+
+def _random_problem(rng):
+    """A random mix of the shapes the kernels branch on: binary or multi-state,
+    concentrated or spread failure probabilities (clustered index order or not),
+    shallow or deep first matches, empty sets, ragged chunks."""
+    K = int(rng.choice([2, 2, 3, 4, 5]))
+    n = int(rng.integers(1, min(300, 512 // (K - 1)) + 1))
+    if K == 2 and rng.random() < 0.5:
+        pf = np.full(n, 1e-3)
+        hot = rng.choice(n, size=min(n, 40), replace=False)
+        pf[hot] = rng.uniform(0.2, 0.5, size=hot.size)
+        pmf = np.stack([pf, 1 - pf], axis=1)
+    else:
+        pmf = rng.dirichlet(np.ones(K), size=n)
+        pmf[:, -1] += rng.uniform(0.5, 3.0)
+        pmf /= pmf.sum(1, keepdims=True)
+    R_U = int(rng.choice([0, 1, 15, 17, 255, 256, 257, int(rng.integers(300, 2500))]))
+    R_L = int(rng.choice([0, 1, int(rng.integers(2, 400))]))
+    if R_L + R_U == 0:
+        R_U = 1
+    lo, hi = (1, 6) if rng.random() < 0.5 else (8, 30)
+    ref_U = np.zeros((R_U, n), np.uint8)
+    for r in range(R_U):
+        idx = rng.choice(n, size=min(n, int(rng.integers(lo, hi + 1))), replace=False)
+        ref_U[r, idx] = rng.integers(1, K, size=idx.size)
+    ref_L = np.full((R_L, n), K - 1, np.uint8)
+    for r in range(R_L):
+        idx = rng.choice(n, size=min(n, int(rng.integers(1, 6))), replace=False)
+        ref_L[r, idx] = rng.integers(0, K - 1, size=idx.size)
+    return W.Problem("random", pmf, ref_L, ref_U)
+
+
+def test_index_parity_randomized(rsr):
+    rng = np.random.default_rng(2026)
+    probs = [_random_problem(rng) for _ in range(24)]
+    Ns = [int(rng.integers(1, 3000)) for _ in probs]
+    for s, (p, N) in enumerate(zip(probs, Ns)):
+        check(rsr, p, 100 + s, int(rng.integers(0, 1 << 40)), N)
+    # the same problems in one batched launch, with and without the index
+    seeds = [300 + s for s in range(len(probs))]
+    offsets = [int(x) for x in rng.integers(0, 1 << 40, size=len(probs))]
+    for index in (True, False):
+        P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=POPC, index=index) for p in probs]
+        b = rsr.Batch(P, seeds, offsets, Ns)
+        rsr.rsr_batch(b)
+        torch.cuda.synchronize()
+        counts = b.counts3.cpu().numpy()
+        for s, p in enumerate(probs):
+            X = O.sample(p.pmf, seeds[s], offsets[s], Ns[s])
+            lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+            assert np.array_equal(b.labels[s].cpu().numpy(), lab), (index, s)
+            assert np.array_equal(counts[s], cnt), (index, s)
+            assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K),
+                                  O.grad_counts(X, lab, p.K)), (index, s)
