@@ -41,7 +41,7 @@ constexpr int kThreads = 256;   // one sample per thread
 constexpr int kChunk = 256;     // references per shared-memory chunk
 constexpr int kCoopLanes = 16;  // at most this many unresolved lanes: cooperative warp scan
 constexpr int kHot = 16;        // upper references tried one by one before the index
-constexpr int kCoopIdx = 4;     // at most this many unresolved lanes: cooperative index test
+constexpr int kCoopIdx = 1;     // at most this many lanes needing the index test: cooperative test
 constexpr int kZeroLanes = 8;   // at most this many I^L lanes in a warp: count their zero bits
 
 // Resident blocks per SM the register budget is sized for: four (64 registers a
