@@ -84,3 +84,30 @@ def test_c4_multistate_full_size(rsr, m_prime, path):
     check_subset(p, got["labels"], 4, 0, 3000, 6 + m_prime)
     dense = run(make_session(rsr, p, path=path, dense=True), 4, 0, N)
     assert np.array_equal(dense["labels"], got["labels"])
+
+
+def test_c5_batched_full_size(rsr):
+    """The 256 hazard scenarios at N = 2e5 each, in the batched launch the bench
+    times: per scenario the label histogram equals the counts, a seeded subset of
+    rows equals the oracle's, and the labels equal those of the launch without the
+    upper index; every fourth scenario also equals the single-problem path."""
+    import workloads.large as L
+    probs = L.c5_batch()
+    S, N = len(probs), 200_000
+    seeds, offsets = [1000 + s for s in range(S)], [0] * S
+    out = {}
+    for index in (True, False):
+        P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=POPC, index=index) for p in probs]
+        b = rsr.Batch(P, seeds, offsets, [N] * S)
+        rsr.rsr_batch(b)
+        torch.cuda.synchronize()
+        out[index] = ([t.cpu().numpy() for t in b.labels], b.counts3.cpu().numpy())
+        del b
+    labels, counts = out[True]
+    for s, p in enumerate(probs):
+        assert np.array_equal(np.bincount(labels[s], minlength=3), counts[s]), s
+        assert np.array_equal(labels[s], out[False][0][s]), s
+        check_subset(p, labels[s], seeds[s], offsets[s], 40, 100 + s)
+    for s in range(0, S, 4):
+        got = run(make_session(rsr, probs[s]), seeds[s], offsets[s], N, grad=False)
+        assert np.array_equal(got["labels"], labels[s]), s
