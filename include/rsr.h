@@ -120,14 +120,17 @@ RSR_API size_t rsr_workspace_size(const rsr_problem *problem, int64_t N);
 
 /*
  * Prepare `ws` for `problem` (Sec. 3.2 encoding, plus the sampler thresholds):
- * computes the thresholds on the host, encodes both reference sets for the
- * chosen path (bit-packed thermometer words; FP8 0/1 tiles in the tensor-core
- * shared-memory layout) and runs the precedence pre-check (does any upper
- * reference lie below a lower reference?  Algorithm 1 lets lower win; if no
- * pair overlaps, the kernels may stop at the first match in either set).
- * Asynchronous on `stream` except for a host->device copy of the thresholds
- * from pageable memory.  `ref_L` / `ref_U` must stay valid until the stream
- * reaches this point.  Not capturable in a CUDA graph.
+ * computes the thresholds on the host, orders each reference set by the
+ * probability of the region its references dominate, encodes both sets
+ * (bit-packed thermometer words; FP8 0/1 tiles in the tensor-core
+ * shared-memory layout), builds the component-major index of the upper set
+ * with one AND row per chunk of 256 references (in a clustered order when a
+ * few binary components fail far more often than the rest), and runs the
+ * precedence pre-check (does any upper reference lie below a lower
+ * reference?  Algorithm 1 lets lower win; if no pair overlaps, the kernels may
+ * stop at the first match in either set).  None of these orders changes a
+ * label.  Synchronises `stream`: reference scores and clustering keys are
+ * sorted on the host.  Not capturable in a CUDA graph.
  */
 RSR_API int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream);
 
