@@ -55,12 +55,81 @@ struct Sys {
     const int32_t *src, *dst;
 };
 
+// One warp's scratch, as pointers into dynamic shared memory sized by the
+// system (SysSmem, SearchSmem), so that small graphs leave room for more
+// resident warps.
 struct WarpScratch {
-    uint8_t x[kMaxKenc];           // component states of the sample
-    uint32_t vis[kMaxNodes / 32];  // reached nodes (connectivity)
-    int32_t parent[kMaxNodes];     // claimed residual arc (max flow), -1 = unreached
-    int16_t flow[kMaxKenc];        // arc flows (max flow)
+    uint8_t *x;        // [n] component states of the sample
+    uint32_t *vis;     // [ceil(max(n, n_nodes) / 32)] reached nodes, or a witness edge mask (search)
+    int32_t *parent;   // [n_nodes] claimed residual arc (max flow) / tree parent, -1 = unreached
+    int16_t *flow;     // [max(n, n_nodes)] arc flows (max flow), covered marks (bridges), a node queue (search)
 };
+
+// Dynamic shared memory of resolve_kernel / levels_kernel: the block's graph
+// (src, dst: int32 [n]) and thresholds (uint64 [n (K-1)]), then per warp x
+// (uint8 [n]), vis (uint32 [ceil(m / 32)]), parent (int32 [n_nodes]) and flow
+// (int16 [m]), m = max(n, n_nodes), every region 16-byte aligned.
+struct SysSmem {
+    size_t off_src, off_dst, off_thr, off_warps, warp_bytes, off_x, off_vis, off_parent, off_flow, total;
+};
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+__host__ __device__ inline SysSmem sys_smem(int n, int km1, int n_nodes, int warps) {
+    SysSmem L{};
+    size_t o = 0;
+    L.off_src = o;
+    o = align16(o + sizeof(int32_t) * (size_t)n);
+    L.off_dst = o;
+    o = align16(o + sizeof(int32_t) * (size_t)n);
+    L.off_thr = o;
+    o = align16(o + sizeof(unsigned long long) * (size_t)n * km1);
+    L.off_warps = o;
+    size_t w = 0;
+    L.off_x = w;
+    w = align16(w + (size_t)n);
+    const int m = n > n_nodes ? n : n_nodes;   // vis and flow also serve as edge arrays / node queues
+    L.off_vis = w;
+    w = align16(w + sizeof(uint32_t) * (size_t)((m + 31) / 32));
+    L.off_parent = w;
+    w = align16(w + sizeof(int32_t) * (size_t)n_nodes);
+    L.off_flow = w;
+    w = align16(w + sizeof(int16_t) * (size_t)m);
+    L.warp_bytes = w;
+    L.total = o + w * (size_t)warps;
+    return L;
+}
+// The search kernel's dynamic shared memory: SysSmem's regions, then the
+// block's adjacency (off, cur: int32 [n_nodes + 1]; adj: int16 [2n]; one
+// frontier counter per warp) and per warp a visiting order (int16 [n]) and a
+// saved flow / second frontier buffer (int16 [max(n, n_nodes)]).
+struct SearchSmem {
+    SysSmem sys;
+    size_t off_off, off_cur, off_adj, off_cnt, off_ord, off_bak, warp_bytes, total;
+};
+__host__ __device__ inline SearchSmem search_smem(int n, int km1, int n_nodes, int warps) {
+    SearchSmem L{};
+    L.sys = sys_smem(n, km1, n_nodes, warps);
+    const int m = n > n_nodes ? n : n_nodes;
+    size_t o = L.sys.total;
+    L.off_off = o;
+    o = align16(o + sizeof(int32_t) * (size_t)(n_nodes + 1));
+    L.off_cur = o;
+    o = align16(o + sizeof(int32_t) * (size_t)(n_nodes + 1));
+    L.off_adj = o;
+    o = align16(o + sizeof(int16_t) * 2 * (size_t)n);
+    L.off_cnt = o;
+    o = align16(o + sizeof(int32_t) * (size_t)warps);
+    L.off_ord = o;
+    L.warp_bytes = align16(sizeof(int16_t) * (size_t)n) + align16(sizeof(int16_t) * (size_t)m);
+    L.off_bak = align16(sizeof(int16_t) * (size_t)n);   // within a warp's slice
+    L.total = o + L.warp_bytes * (size_t)warps;
+    return L;
+}
+
+__device__ inline WarpScratch warp_view(unsigned char *dyn, const SysSmem &L, int warp) {
+    unsigned char *b = dyn + L.off_warps + L.warp_bytes * (size_t)warp;
+    return WarpScratch{b + L.off_x, reinterpret_cast<uint32_t *>(b + L.off_vis),
+                       reinterpret_cast<int32_t *>(b + L.off_parent), reinterpret_cast<int16_t *>(b + L.off_flow)};
+}
 
 __device__ __forceinline__ bool bit(const uint32_t *v, int i) { return (v[i >> 5] >> (i & 31)) & 1u; }
 
@@ -300,13 +369,15 @@ __device__ void regen_sample(const ClassifyParams &p, int64_t hl, WarpScratch &w
 __global__ void __launch_bounds__(kWarps * 32) resolve_kernel(const ClassifyParams p, const Sys g, uint8_t *labels,
                                                               int64_t *u_lower_idx, int64_t cap,
                                                               unsigned long long *counts2) {
-    __shared__ WarpScratch ws[kWarps];
-    __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
-    __shared__ unsigned long long s_thr[kMaxKenc];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    const SysSmem L = sys_smem(p.n, p.km1, g.n_nodes, kWarps);
+    int32_t *s_src = reinterpret_cast<int32_t *>(s_dyn + L.off_src);
+    int32_t *s_dst = reinterpret_cast<int32_t *>(s_dyn + L.off_dst);
+    unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(s_dyn + L.off_thr);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *err = &p.hdr->error;
     stage_system(p, g, s_src, s_dst, s_thr, err);
-    WarpScratch &w = ws[warp];
+    WarpScratch w = warp_view(s_dyn, L, warp);
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
     for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < p.N; base += warps_total * 32) {
         const int64_t mine = base + lane;
@@ -645,25 +716,22 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
                                                              const int64_t *starts, int64_t n_starts,
                                                              uint8_t *refs_out, uint8_t *side_out,
                                                              unsigned long long *evals, int order_mode) {
-    __shared__ WarpScratch ws[kWarps];
-    __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
-    __shared__ unsigned long long s_thr[kMaxKenc];
-    // dynamic: per warp a visiting order and a saved flow (int16 [kMaxKenc] each), then
-    // the block's adjacency (off, cur: int32 [kMaxNodes + 1]; adj: int16 [2 kMaxKenc]) and
-    // one frontier counter per warp
-    extern __shared__ __align__(16) unsigned char s_dyn[];
+    extern __shared__ __align__(16) unsigned char s_dyn[];   // SearchSmem
+    const SearchSmem L = search_smem(p.n, p.km1, g.n_nodes, kWarps);
+    int32_t *s_src = reinterpret_cast<int32_t *>(s_dyn + L.sys.off_src);
+    int32_t *s_dst = reinterpret_cast<int32_t *>(s_dyn + L.sys.off_dst);
+    unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(s_dyn + L.sys.off_thr);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t *err = &p.hdr->error;
     stage_system(p, g, s_src, s_dst, s_thr, err);
-    WarpScratch &w = ws[warp];
-    int16_t *ord = reinterpret_cast<int16_t *>(s_dyn) + (size_t)warp * 2 * kMaxKenc;
-    int16_t *bak = ord + kMaxKenc;
-    int32_t *csr_base = reinterpret_cast<int32_t *>(s_dyn + (size_t)kWarps * 2 * kMaxKenc * sizeof(int16_t));
+    WarpScratch w = warp_view(s_dyn, L.sys, warp);
+    int16_t *ord = reinterpret_cast<int16_t *>(s_dyn + L.off_ord + L.warp_bytes * (size_t)warp);
+    int16_t *bak = reinterpret_cast<int16_t *>(s_dyn + L.off_ord + L.warp_bytes * (size_t)warp + L.off_bak);
     SearchBufs sb;
-    sb.csr.off = csr_base;
-    sb.csr.cur = csr_base + (kMaxNodes + 1);
-    sb.csr.adj = reinterpret_cast<int16_t *>(csr_base + 2 * (kMaxNodes + 1));
-    sb.cnt = reinterpret_cast<int *>(sb.csr.adj + 2 * kMaxKenc) + warp;
+    sb.csr.off = reinterpret_cast<int32_t *>(s_dyn + L.off_off);
+    sb.csr.cur = reinterpret_cast<int32_t *>(s_dyn + L.off_cur);
+    sb.csr.adj = reinterpret_cast<int16_t *>(s_dyn + L.off_adj);
+    sb.cnt = reinterpret_cast<int *>(s_dyn + L.off_cnt) + warp;
     sb.qa = w.flow;
     sb.qb = bak;
     const bool csr = g.kind == RSR_PHI_ST_CONNECTIVITY || g.kind == RSR_PHI_GLOBAL_CONNECTIVITY;
@@ -737,9 +805,11 @@ __global__ void __launch_bounds__(kWarps * 32) levels_kernel(const ClassifyParam
                                                              const uint8_t *labels, uint8_t *levels_out,
                                                              unsigned long long *level_counts,
                                                              unsigned long long *n_phi) {
-    __shared__ WarpScratch ws[kWarps];
-    __shared__ int32_t s_src[kMaxKenc], s_dst[kMaxKenc];
-    __shared__ unsigned long long s_thr[kMaxKenc];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    const SysSmem L = sys_smem(p.n, p.km1, g.n_nodes, kWarps);
+    int32_t *s_src = reinterpret_cast<int32_t *>(s_dyn + L.off_src);
+    int32_t *s_dst = reinterpret_cast<int32_t *>(s_dyn + L.off_dst);
+    unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(s_dyn + L.off_thr);
     __shared__ unsigned long long s_hist[kMaxLevels];
     __shared__ unsigned long long s_phi;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -747,7 +817,7 @@ __global__ void __launch_bounds__(kWarps * 32) levels_kernel(const ClassifyParam
     if (threadIdx.x < kMaxLevels) s_hist[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) s_phi = 0ull;
     stage_system(p, g, s_src, s_dst, s_thr, err);
-    WarpScratch &w = ws[warp];
+    WarpScratch w = warp_view(s_dyn, L, warp);
     const int64_t warps_total = (int64_t)gridDim.x * kWarps;
     for (int64_t base = ((int64_t)blockIdx.x * kWarps + warp) * 32; base < p.N; base += warps_total * 32) {
         const int64_t h = base + lane;
@@ -805,13 +875,32 @@ Sys make_sys(const rsr_system &sys) {
 }
 }  // namespace
 
+// The largest dynamic shared memory the two Stage-2 kernels can ask for (n and
+// n_nodes at their limits), allowed once per device.
+cudaError_t allow_dynamic_smem() {
+    static int done[64] = {0};
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) return e;
+    if (d >= 0 && d < 64 && done[d]) return cudaSuccess;
+    const int mx = (int)sys_smem(kMaxKenc, 1, kMaxNodes, kWarps).total;   // n (K-1) <= kMaxKenc, n <= kMaxKenc
+    if ((e = cudaFuncSetAttribute(resolve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(levels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx)) != cudaSuccess)
+        return e;
+    if (d >= 0 && d < 64) done[d] = 1;
+    return cudaSuccess;
+}
+
 cudaError_t launch_resolve(const ClassifyParams &p, const rsr_system &sys, uint8_t *labels, int64_t *u_lower_idx,
                            int64_t cap, unsigned long long *counts2, cudaStream_t s) {
     if (p.N <= 0) return cudaSuccess;
     const Sys g = make_sys(sys);
+    const size_t smem = sys_smem(p.n, p.km1, g.n_nodes, kWarps).total;
+    cudaError_t e = allow_dynamic_smem();
+    if (e != cudaSuccess) return e;
     const int64_t warps = (p.N + 31) / 32;
-    const int64_t grid = std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
-    resolve_kernel<<<(unsigned)grid, kWarps * 32, 0, s>>>(p, g, labels, u_lower_idx, cap, counts2);
+    const int64_t grid = std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 16);
+    resolve_kernel<<<(unsigned)grid, kWarps * 32, smem, s>>>(p, g, labels, u_lower_idx, cap, counts2);
     return cudaGetLastError();
 }
 
@@ -819,18 +908,19 @@ cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const 
                           uint8_t *refs_out, uint8_t *side_out, unsigned long long *evals, int order_mode,
                           cudaStream_t s) {
     if (n_starts <= 0) return cudaSuccess;
-    constexpr int kDyn = kWarps * 2 * kMaxKenc * (int)sizeof(int16_t) + 2 * (kMaxNodes + 1) * (int)sizeof(int32_t) +
-                         2 * kMaxKenc * (int)sizeof(int16_t) + kWarps * (int)sizeof(int);
+    // the largest layout (n and n_nodes at their limits) is allowed once per device
     static int attr_set[64] = {0};
     const int d = [] { int v = 0; cudaGetDevice(&v); return v; }();
     if (d >= 0 && d < 64 && !attr_set[d]) {
-        const cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kDyn);
+        const int mx = (int)search_smem(kMaxKenc, 1, kMaxNodes, kWarps).total;
+        const cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         if (e != cudaSuccess) return e;
         attr_set[d] = 1;
     }
     const Sys g = make_sys(sys);
-    const int64_t grid = std::min<int64_t>((n_starts + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
-    search_kernel<<<(unsigned)grid, kWarps * 32, kDyn, s>>>(p, g, starts, n_starts, refs_out, side_out, evals,
+    const size_t smem = search_smem(p.n, p.km1, g.n_nodes, kWarps).total;
+    const int64_t grid = std::min<int64_t>((n_starts + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 16);
+    search_kernel<<<(unsigned)grid, kWarps * 32, smem, s>>>(p, g, starts, n_starts, refs_out, side_out, evals,
                                                              order_mode);
     return cudaGetLastError();
 }
@@ -841,9 +931,12 @@ cudaError_t launch_levels(const ClassifyParams &p, const rsr_system &sys, int nb
     if (p.N <= 0) return cudaSuccess;
     if (nb < 1 || nb >= kMaxLevels) return cudaErrorInvalidValue;
     const Sys g = make_sys(sys);
+    const size_t smem = sys_smem(p.n, p.km1, g.n_nodes, kWarps).total;
+    cudaError_t e = allow_dynamic_smem();
+    if (e != cudaSuccess) return e;
     const int64_t warps = (p.N + 31) / 32;
-    const int64_t grid = std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 8);
-    levels_kernel<<<(unsigned)grid, kWarps * 32, 0, s>>>(p, g, nb, labels, levels_out, level_counts, n_phi);
+    const int64_t grid = std::min<int64_t>((warps + kWarps - 1) / kWarps, (int64_t)device_sm_count() * 16);
+    levels_kernel<<<(unsigned)grid, kWarps * 32, smem, s>>>(p, g, nb, labels, levels_out, level_counts, n_phi);
     return cudaGetLastError();
 }
 
