@@ -539,6 +539,36 @@ __device__ void build_witness(const Sys &g, int n, WarpScratch &w, const int32_t
     __syncwarp();
 }
 
+// With w.parent a spanning tree of the working graph (depth << 16 | edge,
+// 0xFFFF at the root) and its tree edge e just removed (w.x[e] = 0): is there a
+// working non-tree edge with one end below e and the other above?  The nodes
+// below e are marked in w.flow (int16 per node) by walking each node up to the
+// depth of e's lower end.  Warp-uniform.
+__device__ bool tree_edge_has_cover(const Sys &g, int n, WarpScratch &w, const int32_t *s_src, const int32_t *s_dst,
+                                    int e) {
+    const int lane = threadIdx.x & 31;
+    const int a = s_src[e], b = s_dst[e];
+    const int c = (w.parent[a] & 0xFFFF) == e ? a : b;   // the lower end
+    const int dc = w.parent[c] >> 16;
+    for (int v = lane; v < g.n_nodes; v += 32) {
+        int y = v;
+        for (int guard = 0; (w.parent[y] >> 16) > dc && guard < g.n_nodes; ++guard) {
+            const int pe = w.parent[y] & 0xFFFF;
+            y = s_src[pe] == y ? s_dst[pe] : s_src[pe];
+        }
+        w.flow[v] = (int16_t)(y == c ? 1 : 0);
+    }
+    __syncwarp();
+    bool found = false;
+    for (int f = lane; f < n && !found; f += 32) {
+        if (f == e || !w.x[f] || ((w.vis[f >> 5] >> (f & 31)) & 1u)) continue;
+        found = w.flow[s_src[f]] != w.flow[s_dst[f]];
+    }
+    found = __any_sync(0xffffffffu, found);
+    __syncwarp();
+    return found;
+}
+
 struct SearchBufs {
     Csr csr;
     int16_t *qa, *qb;   // frontier buffers (the flow arrays; connectivity does not use them)
@@ -633,6 +663,15 @@ __device__ bool try_step(const Sys &g, int n, int mode, bool lower, int i, WarpS
                 bfs_csr(g, w, s_src, s_dst, sb.csr, g.s, g.t, sb.qa, sb.qb, sb.cnt);
                 ok = vload(&w.parent[g.t]) != -1;
             } else {
+                // w.parent is the witness spanning tree (depth << 16 | edge).  Removing
+                // its edge i splits it into the subtree below i and the rest; the
+                // working graph stays connected iff another working edge joins the two.
+                // Only then is the tree rebuilt; a bridge costs no search.
+                if (!tree_edge_has_cover(g, n, w, s_src, s_dst, i)) {
+                    if (lane == 0) w.x[i] = 1;
+                    __syncwarp();
+                    return false;
+                }
                 ok = bfs_csr(g, w, s_src, s_dst, sb.csr, 0, -1, sb.qa, sb.qb, sb.cnt) == g.n_nodes;
             }
             if (ok) {
