@@ -32,7 +32,7 @@ constexpr int kMaxWB = 16;  // batch path: n*(K-1) <= 512
 constexpr int kCoopLanes = 16; // at most this many unresolved lanes: cooperative warp scan
 constexpr int kHot = 16;        // upper references tried one by one before the index
 constexpr int kCoopIdx = 1;     // at most this many lanes needing the index test: cooperative test
-constexpr int kZeroLanes = 8;   // at most this many I^L lanes in a warp: count their zero bits
+constexpr int kZeroLanes = 32;  // at most this many I^L lanes in a warp: count their zero bits (all: measured fastest)
 
 struct Shared {
     BatchDesc d;
