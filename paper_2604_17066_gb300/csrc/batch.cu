@@ -251,7 +251,8 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         if (b2) atomicAdd(&sh.cnt[2], (unsigned long long)__popc(b2));
     }
     // per-bit counts of I^L samples: zero bits with shared atomics for a warp with
-    // few I^L samples, 32 ballots per word (one bits) otherwise
+    // at most kZeroLanes I^L samples (every warp at 32), 32 ballots per word (one
+    // bits) otherwise
     if (d.bitcnt && b0 && __popc(b0) <= kZeroLanes) {
         if (valid && label == 0) {
             const int kenc = d.n * d.km1;
