@@ -394,6 +394,7 @@ class OraclePool:
         O.grad(C, n_total, prob.pmf)
         O.estimate(cnt, n_total)
         dt = time.perf_counter() - t0
+        self.last_counts, self.last_grad_counts = cnt, C
         return n_total / dt, dt
 
     def close(self):
