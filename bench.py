@@ -380,7 +380,9 @@ class OraclePool:
         import multiprocessing as mp
         self.workers = workers or os.cpu_count() or 1
         self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_oracle_init, initargs=(name,))
-        self.pool.map(_oracle_slice, [(1, 0, 16)] * self.workers)   # every worker loaded and warm
+        # the initializer loads the workload in every worker; a first small map starts
+        # them all and loads the oracle library outside the timed runs
+        self.pool.map(_oracle_slice, [(1, 0, 16)] * self.workers, chunksize=1)
 
     def run(self, prob, seed, offset, n_total):
         from oracle import oracle as O
