@@ -122,6 +122,54 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
 
+    def power_max(self):
+        pw = []
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            try:
+                pw.append(float(f[3]))
+            except (IndexError, ValueError):
+                continue
+        return max(pw) if pw else None
+
+
+def measure_fp8_peak(rsr, torch, uuid, seconds=3.0):
+    """The tensor roofline's denominator, measured on this GPU: librsr's own
+    back-to-back tcgen05 FP8 MMA loop (rsr_measure_fp8_peak), burst and
+    sustained, each with the SM clock sampled while it ran; plus cuBLASLt's FP8
+    GEMM (torch._scaled_mm, 8192^3) as a cross-check."""
+    out = {}
+    with Clocks(uuid) as ck:
+        torch.cuda.synchronize()
+        r = rsr.rsr_measure_fp8_peak(0.0)
+    out["burst_tflops"] = r["burst_flops_per_s"] / 1e12
+    out["burst_clocks"] = ck.summary()
+    with Clocks(uuid) as ck:
+        torch.cuda.synchronize()
+        r = rsr.rsr_measure_fp8_peak(seconds)
+    out["sustained_tflops"] = r["sustained_flops_per_s"] / 1e12
+    out["sustained_clocks"] = ck.summary()
+    out["sustained_power_w_max"] = ck.power_max()
+    try:
+        n = 8192
+        a = (torch.rand(n, n, device="cuda") - 0.5).to(torch.float8_e4m3fn)
+        b = (torch.rand(n, n, device="cuda") - 0.5).to(torch.float8_e4m3fn)
+        one = torch.ones((), device="cuda")
+        best = 1e30
+        for _ in range(6):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            e[0].record()
+            torch._scaled_mm(a, b.t(), scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+            e[1].record()
+            torch.cuda.synchronize()
+            best = min(best, e[0].elapsed_time(e[1]))
+        out["cublaslt_fp8_8192_tflops"] = 2.0 * n ** 3 / (best / 1000.0) / 1e12
+        del a, b
+    except Exception as exc:  # the cross-check is optional; the measured peak above stands alone
+        out["cublaslt_fp8_8192_tflops"] = None
+        out["cublaslt_error"] = str(exc)[:200]
+    return out
+
 
 def _stage1_timed(rsr, torch, pmf, system, B, R_max, rounds, order):
     rsr.rsr_stage1(pmf, system, 99, 10000, 16, 1e-5, 64, 2, order=order)      # warm-up
@@ -552,7 +600,7 @@ def main():
 
     from paper_2604_17066_gb300 import api as rsr
     from paper_2604_17066_gb300 import build as rsr_build
-    from paper_2604_17066_gb300.shard import shard_range
+    from paper_2604_17066_gb300.shard import combine_counts, shard_range
     rsr_build.build()
 
     prob, N, wname = _workload(args.workload)
@@ -654,6 +702,12 @@ def main():
     exec_tests = int(exec_t.item())
     total_ms = sum(step_ms)
     if world > 1:
+        # the estimate of the last timed step over every rank's samples: the integer counts
+        # (and the Stage-2 lower count) add up exactly across ranks
+        tot = torch.cat([counts, c2[:1] if system is not None else torch.zeros(1, dtype=torch.int64, device=dev)])
+        combine_counts(tot)
+        tot_h = tot.cpu().numpy()
+        est = rsr.rsr_estimate(tot_h[:3], world * n_rank, int(tot_h[3]))
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
@@ -676,11 +730,19 @@ def main():
         work_tests = tests_per_launch if P.dense else exec_per_launch
         flops = 2.0 * kenc * work_tests
         achieved = flops / (kern_avg / 1000.0) / 1e12
-        peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        kpad = ((kenc + (kenc + 15) // 16 + 31) // 32) * 32       # FP8 row incl. bias columns, padded to 32
+        achieved_exec = 2.0 * kpad * exec_per_launch / (kern_avg / 1000.0) / 1e12
+        fp8 = measure_fp8_peak(rsr, torch, uuid)
+        peak = fp8["burst_tflops"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": _captured_traffic(wname) if P.dense else None,
-                "note": "FP8 dense peak = 2 x bf16 sustained (%s); flops = 2*n(K-1)*%s tests"
-                        % (peak_src, "N*(R_L+R_U)" if P.dense else "executed")}
+                "frac": achieved / peak, "frac_executed": achieved_exec / peak,
+                "achieved_executed": achieved_exec,
+                "traffic": _captured_traffic(wname) if P.dense else None,
+                "peak_measured": fp8,
+                "note": "peak = measured FP8 tcgen05 burst of this GPU (rsr_measure_fp8_peak: back-to-back "
+                        "kind::f8f6f4 MMAs from shared memory, one CTA per SM); frac = algorithmic flops "
+                        "2*n(K-1)*%s tests / kernel time / peak; frac_executed counts the executed tests at "
+                        "the padded row of %d bytes" % ("N*(R_L+R_U)" if P.dense else "executed", kpad)}
     else:
         # integer-op model: per Philox4x32-10 block 20 wide products (IMAD.WIDE) and 60
         # logic / add ops; n(K-1) compares per sample; ceil(n(K-1)/32) + 1 per executed

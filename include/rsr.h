@@ -137,7 +137,8 @@ RSR_API int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, r
 /*
  * Recompute only the sampler thresholds after `problem->pmf` changed (the
  * references stay valid when component probabilities change, Sec. 5).  `ws`
- * must have been prepared for the same references.
+ * must have been prepared for the same references.  Clears the workspace's
+ * device error word (rsr_workspace_status).
  */
 RSR_API int rsr_update_pmf(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream);
 
@@ -175,6 +176,11 @@ RSR_API int rsr_estimate(const int64_t counts3[3], int64_t N, int64_t n_u_lower,
  *                 that Phi resolved to S <= m'; may be NULL if n_u_lower = 0.
  *   grad_out, se_out : host fp64[n*K]: g = (C/H)/q, se = sqrt(p(1-p)/H)/q with p = C/H.
  * Synchronises `stream` (reads the counts back).  Uses the thresholds in `ws`.
+ * Errors: RSR_ERR_INVALID_ARG if a listed index lies outside [0, N); the
+ * indices are checked on the device before any count changes, so grad_counts
+ * is then left as it was.  Each call checks only its own indices: a device
+ * error recorded in the workspace by an earlier call (rsr_workspace_status)
+ * does not make rsr_grad fail.
  */
 RSR_API int rsr_grad(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N,
              int64_t *grad_counts, const int64_t *u_lower_idx, int64_t n_u_lower,
@@ -190,7 +196,10 @@ RSR_API int rsr_sample(const rsr_problem *problem, uint64_t seed, uint64_t offse
 /*
  * Device-side results of the precedence pre-check and error flag, copied to
  * host int32[2] = {overlapping pairs > 0, device error code}.  Synchronises
- * `stream`.
+ * `stream`.  The error word records problems that kernels find while they run
+ * (RSR_ERR_TIMEOUT from a bounded wait; 2 = a node index out of range; 3 = a
+ * broken flow path; 4 = the Stage-2 index list was full) and keeps the first
+ * or largest code: it is sticky until rsr_prepare or rsr_update_pmf clears it.
  */
 RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t stream);
 
@@ -267,6 +276,8 @@ RSR_API int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, 
  * rejected with RSR_ERR_WORKSPACE before any GPU work.  The first call on a
  * device looks up the array's device address once (cudaGetSymbolAddress, with
  * that device current), so make that first call before any stream capture.
+ * Asynchronous on `stream`: the sampler thresholds reach the array as a kernel
+ * argument, not through a host-to-device copy, so no step waits for it.
  * Every call shares the array and re-initialises what it needs; calls whose
  * GPU work overlaps (other streams, other host threads) race on it, so
  * serialise them.  The library itself calls no allocation routine here.
@@ -459,6 +470,25 @@ RSR_API int rsr_stage1(const rsr_problem *problem, const rsr_system *system, con
  * Synchronous (waits for its own kernels on `stream`); allocates nothing.
  */
 RSR_API int rsr_measure_int_peak(double *lop3_ops_per_s, double *imad_ops_per_s, rsr_stream_t stream);
+
+/*
+ * Measured dense FP8 tensor-core rate of the current GPU, for the roofline of
+ * the tensor-core classifier (not a step of the method; the paper has no
+ * counterpart).  One CTA per SM issues tcgen05.mma.cta_group::1.kind::f8f6f4
+ * (M = 128, N = 256, K = 32, E4M3 operands resident in shared memory, FP32
+ * accumulators in tensor memory) back to back, with no copies and no
+ * epilogue: 2*128*256*32 flop per instruction.
+ *   seconds           : length of the sustained run, in [0, 60]; 0 skips it.
+ *   burst_flops_per_s : host double[1], the fastest of five single launches of
+ *                       about 16 ms each (after one warm-up launch).
+ *   sustained_flops_per_s : host double[1], launches back to back for about
+ *                       `seconds` (0.0 when skipped).
+ * Synchronous (waits for its own kernels on `stream`); allocates nothing.
+ * RSR_ERR_UNSUPPORTED on a GPU without tcgen05; RSR_ERR_TIMEOUT if the final
+ * bounded wait for the issued MMAs ran out.
+ */
+RSR_API int rsr_measure_fp8_peak(double seconds, double *burst_flops_per_s, double *sustained_flops_per_s,
+                                 rsr_stream_t stream);
 
 /* Message for a status code (static storage). */
 RSR_API const char *rsr_status_string(int status);

@@ -22,12 +22,15 @@
 // current, on the first call that runs on it; that first call should
 // therefore come before any stream capture.
 //
+// Ordering: the call is asynchronous on its stream.  The sampler thresholds
+// reach the array as a kernel argument (copied when the kernel is launched),
+// not through a copy from host memory, so no step waits for the stream.
+//
 // Sharing: all calls on a device share the one array, which keeps whatever
 // the previous call left; each call re-clears the header that must start at
 // zero (the precedence flag and the error word) and rewrites thresholds and
 // encodings.  Calls whose GPU work overlaps (different streams, or another
 // host thread) race on the array: serialise them.
-#include <cmath>
 #include <mutex>
 
 #include <cuda_runtime.h>
@@ -70,21 +73,23 @@ int fail() {
     return RSR_ERR_CUDA;
 }
 
+// Every check of the caller-workspace entry points (sizes, reference counts
+// below 2^31, pmf rows), with problem->path ignored as documented.
 int check_problem(const rsr_problem *p) {
-    if (!p || p->n < 1 || p->K < 2 || p->R_L < 0 || p->R_U < 0 || p->R_L + p->R_U < 1 || !p->pmf)
-        return RSR_ERR_INVALID_ARG;
-    if (p->K > kMaxK || (int64_t)p->n * (p->K - 1) > kMaxKenc) return RSR_ERR_UNSUPPORTED;
-    if ((p->R_L > 0 && !p->ref_L) || (p->R_U > 0 && !p->ref_U)) return RSR_ERR_INVALID_ARG;
-    for (int i = 0; i < p->n; ++i) {
-        double s = 0.0;
-        for (int k = 0; k < p->K; ++k) {
-            const double q = p->pmf[(size_t)i * p->K + k];
-            if (!(q >= 0.0 && q <= 1.0)) return RSR_ERR_INVALID_ARG;
-            s += q;
-        }
-        if (std::fabs(s - 1.0) > 1e-9) return RSR_ERR_INVALID_ARG;
-    }
-    return RSR_OK;
+    if (!p) return RSR_ERR_INVALID_ARG;
+    rsr_problem q = *p;
+    q.path = RSR_PATH_POPC;
+    return validate_problem(&q);
+}
+
+// The thresholds travel inside the kernel's argument block (8 KB; launches
+// accept up to 32 KB of arguments), so no host buffer has to outlive the call.
+struct ThresholdArg {
+    unsigned long long v[kMaxKenc];
+};
+
+__global__ void store_thresholds_kernel(const ThresholdArg a, int count, unsigned long long *dst) {
+    for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = a.v[i];
 }
 
 }  // namespace
@@ -109,21 +114,13 @@ extern "C" int rsr_classify_static(const rsr_problem *problem, uint64_t seed, ui
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(scratch);
 
-    // thresholds on the host, in a fixed-size stack array (no host allocation either)
-    unsigned long long T[kMaxKenc];
-    for (int i = 0; i < problem->n; ++i) {
-        double c = 0.0;
-        for (int k = 1; k <= km1; ++k) {
-            c += problem->pmf[(size_t)i * problem->K + (k - 1)];
-            const double v = std::floor(std::ldexp(c, 32));
-            T[(size_t)i * km1 + (k - 1)] = v <= 0.0 ? 0ull : (v >= 4294967296.0 ? 4294967296ull : (unsigned long long)v);
-        }
-    }
+    // thresholds on the host, in a fixed-size argument block (no host allocation either)
+    ThresholdArg T;
+    const int nthr = problem->n * km1;
+    host_thresholds(problem->n, problem->K, problem->pmf, T.v);
     if (cudaMemsetAsync(base, 0, sizeof(WsHeader), s) != cudaSuccess) return fail();
-    // pageable source: the copy is staged before the call returns, so T may go out of scope
-    if (cudaMemcpyAsync(base + L.off_thr, T, sizeof(unsigned long long) * (size_t)problem->n * km1,
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return fail();
+    store_thresholds_kernel<<<1, 256, 0, s>>>(T, nthr, reinterpret_cast<unsigned long long *>(base + L.off_thr));
+    if (cudaGetLastError() != cudaSuccess) return fail();
     uint32_t *pL = reinterpret_cast<uint32_t *>(base + L.off_popc_L);
     uint32_t *pU = reinterpret_cast<uint32_t *>(base + L.off_popc_U);
     if (launch_encode_popc(problem->ref_L, problem->R_L, problem->n, km1, words_b, true, pL, s) != cudaSuccess ||

@@ -170,8 +170,18 @@ __global__ void sample_kernel(const ClassifyParams p, uint8_t *__restrict__ stat
 
 // Gradient correction: unclassified samples that Phi resolved to S <= m' join
 // the failure set; their states are regenerated from Philox and counted.
+// First pass: every listed index is checked, and one outside [0, N) sets the
+// call's flag; the counting pass then changes nothing.
+__global__ void grad_index_check_kernel(const int64_t *__restrict__ idx, int64_t m, int64_t N, int32_t *bad) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t hl = idx[j];
+        if (hl < 0 || hl >= N) *bad = 1;
+    }
+}
+
 __global__ void __launch_bounds__(256) grad_correction_kernel(const ClassifyParams p, const int64_t *__restrict__ idx,
                                                                int64_t m) {
+    if (*((volatile const int32_t *)&p.hdr->grad_bad) != 0) return;   // rejected by the check pass
     // one warp per listed sample, lanes over its components (one Philox block each);
     // per-(component, state) counts gathered in shared memory, flushed once per block
     __shared__ unsigned int s_hist[kMaxCorrHist];
@@ -181,11 +191,7 @@ __global__ void __launch_bounds__(256) grad_correction_kernel(const ClassifyPara
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     for (int64_t j = (int64_t)blockIdx.x * nwarps + warp; j < m; j += (int64_t)gridDim.x * nwarps) {
-        const int64_t hl = idx[j];
-        if (hl < 0 || hl >= p.N) {
-            if (lane == 0) atomicMax(&p.hdr->error, 1);  // index out of range: recorded, not counted
-            continue;
-        }
+        const int64_t hl = idx[j];   // in [0, N): checked by the first pass
         const uint64_t h = p.offset + (uint64_t)hl;
         for (int q = lane; 4 * q < p.n; q += 32) {
             const U32x4 r = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
@@ -266,6 +272,8 @@ cudaError_t launch_sample(const ClassifyParams &p, uint8_t *states, cudaStream_t
 
 cudaError_t launch_grad_correction(const ClassifyParams &p, const int64_t *idx, int64_t m, cudaStream_t s) {
     if (m <= 0) return cudaSuccess;
+    const int64_t cgrid = std::min<int64_t>((m + 255) / 256, (int64_t)device_sm_count() * 4);
+    grad_index_check_kernel<<<(unsigned)cgrid, 256, 0, s>>>(idx, m, p.N, &p.hdr->grad_bad);
     const int64_t grid = std::min<int64_t>((m + 7) / 8, (int64_t)device_sm_count() * 4);
     grad_correction_kernel<<<(unsigned)grid, 256, 0, s>>>(p, idx, m);
     return cudaGetLastError();

@@ -270,6 +270,8 @@ int cuda_fail(cudaError_t e, const char *where) {
     return RSR_ERR_CUDA;
 }
 
+int validate_problem(const rsr_problem *p) { return validate(p); }
+
 int validate_system(const rsr_system *system, int K) {
     if (!system) return RSR_ERR_INVALID_ARG;
     const int kind = system->kind;
@@ -405,7 +407,10 @@ int rsr_update_pmf(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_st
             q.ref_L != problem->ref_L || q.ref_U != problem->ref_U || q.device != current_device())
             return RSR_ERR_NOT_PREPARED;
     }
-    if ((st = upload_thresholds(problem, L, ws, reinterpret_cast<cudaStream_t>(stream))) != RSR_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // a new pmf starts a new record of device errors
+    RSR_CUDA(cudaMemsetAsync(&reinterpret_cast<WsHeader *>(ws)->error, 0, sizeof(int32_t), s));
+    if ((st = upload_thresholds(problem, L, ws, s)) != RSR_OK) return st;
     std::lock_guard<std::mutex> g(g_mu);
     g_prepared[ws].pmf_hash = pmf_hash(problem);
     return RSR_OK;
@@ -477,15 +482,17 @@ int rsr_grad(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t
     c.seed = seed;
     c.offset = offset;
     c.grad_counts = reinterpret_cast<unsigned long long *>(grad_counts);
+    // this call's own flag: the listed indices are checked before any count changes
+    int32_t *bad = &reinterpret_cast<WsHeader *>(ws)->grad_bad;
+    RSR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), s));
     RSR_CUDA(launch_grad_correction(c, u_lower_idx, n_u_lower, s));
     const size_t nk = (size_t)problem->n * problem->K;
     std::vector<int64_t> C(nk);
-    int32_t err = 0;
+    int32_t bad_h = 0;
     RSR_CUDA(cudaMemcpyAsync(C.data(), grad_counts, nk * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    RSR_CUDA(cudaMemcpyAsync(&err, &reinterpret_cast<WsHeader *>(ws)->error, sizeof(int32_t),
-                             cudaMemcpyDeviceToHost, s));
+    RSR_CUDA(cudaMemcpyAsync(&bad_h, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     RSR_CUDA(cudaStreamSynchronize(s));
-    if (err != 0) return RSR_ERR_INVALID_ARG;
+    if (bad_h != 0) return RSR_ERR_INVALID_ARG;
     const double H = (double)N;
     for (size_t j = 0; j < nk; ++j) {
         const double p = (double)C[j] / H;
@@ -1002,7 +1009,7 @@ int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stre
     c.N = c.dense ? (1 << 18) : (1 << 20);
     c.seed = 0x5EEDull;
     c.offset = 0;
-    c.counts3 = reinterpret_cast<unsigned long long *>(&reinterpret_cast<WsHeader *>(ws)->reserved[2]);
+    c.counts3 = reinterpret_cast<WsHeader *>(ws)->tune_counts;
     cudaEvent_t e0, e1;
     RSR_CUDA(cudaEventCreate(&e0));
     RSR_CUDA(cudaEventCreate(&e1));

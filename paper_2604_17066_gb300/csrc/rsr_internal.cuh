@@ -177,8 +177,11 @@ struct ChunkWalk {
 // ---------------------------------------------------------------------------
 struct WsHeader {
     int32_t overlap;   // 1 if some upper reference lies below some lower reference
-    int32_t error;     // device error code (0 = none)
-    uint32_t reserved[62];
+    int32_t error;     // device error code (0 = none); kept until rsr_prepare / rsr_update_pmf
+    int32_t grad_bad;  // rsr_grad: a listed index lies outside [0, N) (cleared by each call)
+    int32_t pad;
+    unsigned long long tune_counts[3];  // rsr_autotune: counts of its timing runs
+    uint32_t reserved[54];
 };
 static_assert(sizeof(WsHeader) == 256, "header is one 256-byte line");
 

@@ -62,6 +62,7 @@ cudaError_t launch_gather_rows(const uint8_t *src, const int64_t *idx, int64_t c
                                cudaStream_t s);
 
 // Host helpers of the C ABI (rsr_capi.cu).
+int validate_problem(const rsr_problem *p);              // every rsr_problem check; RSR_OK or an error code
 int validate_states(int n, int K, const double *pmf);   // sizes and pmf rows; RSR_OK or an error code
 int validate_system(const rsr_system *system, int K);    // built-in Phi arguments
 void host_thresholds(int n, int K, const double *pmf, unsigned long long *T);   // n*(K-1) values

@@ -89,3 +89,26 @@ def test_lower_index_overflow_is_flagged_and_counts_stay_exact(rsr):
     assert c2.tolist() == [n_lower, int(cnt[2]) - n_lower]
     assert np.array_equal(labels, res)
     assert rsr.rsr_workspace_status(sess.ws)[1] == 4
+
+
+def test_grad_rejects_bad_index_without_touching_counts_then_recovers(rsr):
+    """rsr_grad checks its listed indices before any count changes: a call with
+    an index outside [0, N) fails with RSR_ERR_INVALID_ARG and leaves the counts
+    as they were, and the next valid call on the same workspace succeeds (the
+    check is per call, not a sticky workspace state)."""
+    p = W.c1_grid()
+    part = W.Problem("grid_partial", p.pmf, p.ref_L[::3], p.ref_U[::4])
+    args = (0, p.meta["n_nodes"], p.meta["edges"], p.meta["s"], p.meta["t"], [], 0)
+    sess, out, labels, u_idx, c2 = run_stage2(rsr, part, args, 3, 0, 50000)
+    n_lower = int(c2[0])
+    before = out["grad_counts"].clone()
+    bad = u_idx[:n_lower].clone()
+    bad[n_lower // 2] = 50000
+    with pytest.raises(rsr.RSRError) as e:
+        rsr.rsr_grad(sess.problem, 3, 0, 50000, out["grad_counts"], sess.ws, u_lower_idx=bad)
+    assert e.value.status == -1
+    assert torch.equal(out["grad_counts"], before)
+    g, _ = rsr.rsr_grad(sess.problem, 3, 0, 50000, out["grad_counts"], sess.ws, u_lower_idx=u_idx[:n_lower])
+    X, lab, cnt, res, n_lower_o = oracle_stage2(part, *args[:5], 3, 0, 50000)
+    g_o, _ = O.grad(O.grad_counts(X, lab, part.K, u_lower_idx=np.nonzero(res == 3)[0]), 50000, part.pmf)
+    np.testing.assert_allclose(g, g_o, rtol=1e-12, atol=0)

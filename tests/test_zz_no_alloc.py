@@ -3,7 +3,8 @@ device memory (its workspace is a 4 MiB device array owned by the library).
 
 Called twice in a row through the C ABI, it must return exactly what the
 caller-workspace entry point (rsr_prepare + rsr_classify, bit-packed path)
-returns: labels, counts and gradient counts are integers, compared exactly.
+returns, and what the oracle's own sampler, first-match loops and gradient
+counts give: labels, counts and gradient counts are integers, compared exactly.
 The first call uses references with an overlapping (upper below lower) pair,
 the second a consistent set, so the second call also shows that the shared
 array's header is re-initialised.  This file is collected last on purpose.
@@ -14,6 +15,7 @@ import torch
 
 import workloads as W
 from helpers import POPC, random_refs_problem
+from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +49,11 @@ def test_static_scratch_matches_workspace_path_twice_in_a_row(rsr):
         got = _via_static(rsr, prob, seed, offset, N)
         for key in ("labels", "counts3", "grad_counts"):
             assert np.array_equal(got[key], want[key]), key
+        X = O.sample(prob.pmf, seed, offset, N)
+        lab, cnt = O.classify(X, prob.ref_L, prob.ref_U)
+        assert np.array_equal(got["labels"], lab)
+        assert np.array_equal(got["counts3"], cnt)
+        assert np.array_equal(got["grad_counts"].reshape(prob.n, prob.K), O.grad_counts(X, lab, prob.K))
 
 
 def test_static_scratch_rejects_problems_beyond_its_size(rsr):
