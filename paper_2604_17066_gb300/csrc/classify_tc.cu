@@ -17,7 +17,8 @@
 //                     -> V = -#{(i,k): r_i >= k > x_i} <= 0, zero iff x >= r
 // All values are integers of magnitude <= 16 in FP8 e4m3 and every partial sum
 // is an integer far below 2^24, so FP32 accumulation is exact.  Padding
-// references carry a +1 in the first bias column and never give 0.
+// references carry +1 (lower tiles) or -1 (upper tiles) in the first bias
+// column and never give 0.
 //
 // Kernel structure (one CTA per SM, persistent over 128-sample blocks):
 //   all 8 warps : Philox-sample the block's 128 states (two threads per row,
@@ -42,6 +43,7 @@
 
 #include "rsr_internal.cuh"
 #include "rsr_launch.h"
+#include "tc_common.cuh"
 #include "tc_ptx.cuh"
 
 namespace rsr {
@@ -55,37 +57,6 @@ constexpr int kMaxStages = 4;
 constexpr int kSmemLimit = 232448;   // 227 KB opt-in per CTA
 // tensor memory: two FP32 accumulator buffers of BN columns each (BN = MMA N)
 using namespace tc;
-
-// 4 bits -> 4 bytes of e4m3 {0, 1.0 = 0x38}.
-__device__ __forceinline__ uint32_t nibble_to_fp8(uint32_t x) {
-    return ((x * 0x00204081u) & 0x01010101u) * 0x38u;
-}
-
-struct Bits {
-    // appends runs of bits to a word column in shared memory
-    uint32_t *col;
-    int w, pos;
-    uint32_t cur;
-    __device__ __forceinline__ void put(uint32_t bits, int len) {  // len <= 16
-        cur |= bits << pos;
-        const int np = pos + len;
-        if (np >= 32) {
-            col[w * kThreads] = cur;
-            ++w;
-            cur = (np > 32) ? (bits >> (32 - pos)) : 0u;
-            pos = np - 32;
-        } else {
-            pos = np;
-        }
-    }
-    __device__ __forceinline__ void finish(int words) {
-        if (pos > 0) {
-            col[w * kThreads] = cur;
-            ++w;
-        }
-        for (; w < words; ++w) col[w * kThreads] = 0u;
-    }
-};
 
 struct TcSmem {
     // offsets (bytes) from the dynamic shared memory base
@@ -119,6 +90,7 @@ struct TcCtl {
     uint64_t empty[kMaxStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
+    uint64_t drain;      // after an abort: completion of every MMA issued so far
     int stage_tile[kMaxStages];
     int acc_tile[2];
     uint32_t tmem_base;
@@ -143,7 +115,6 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int kp = p.tc_kpad;
-    const int kwords = kp / 32;
     const int nthr = p.n * p.km1;
     const TcSmem plan = tc_smem_plan(kp, nthr, BN, kMaxStages);
     const int S = plan.nstages;
@@ -167,6 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
             mbar_init(&ctl.tfull[b], 2);    // MMA completion + the issuer's release arrive
             mbar_init(&ctl.tempty[b], 4);   // one arrive per epilogue warp
         }
+        mbar_init(&ctl.drain, 1);
         ctl.done = 0;
         ctl.abort_flag = 0;
         ctl.exec = 0ull;
@@ -188,14 +160,12 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
     const int64_t tiles_L = (p.R_L + BN - 1) / BN;
     const int64_t T = tiles_U + tiles_L;
     const uint32_t tile_bytes = (uint32_t)BN * kp;   // BN/128 consecutive encoded tiles
-    const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
-    const int bias_cols = (p.kenc + 15) / 16;
-    // component split between the two threads that sample one row (a multiple of 4: whole Philox blocks)
-    const int n_half = ((p.n + 7) / 8) * 4;
 
     // ring state (continuous across blocks)
     int st_stage = 0;
     uint32_t st_phase = 0;
+    // producer: full-barrier phase of the last copy into each stage (bit s set = a copy was issued)
+    uint32_t copy_phase = 0u, copy_made = 0u;
     int acc_buf = 0;
     uint32_t acc_phase = 0;
 
@@ -205,64 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
     const int64_t nblocks = (p.N + kRows - 1) / kRows;
     for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
         // ---- 1. sample the block into the thermometer scratch and the A tile -----
-        {
-            const int row = tid & (kRows - 1), half = tid >> 7;
-            const int64_t hl = blk * kRows + row;
-            const int i_lo = half ? (n_half < p.n ? n_half : p.n) : 0;
-            const int i_hi = half ? p.n : (n_half < p.n ? n_half : p.n);
-            // this thread's bits start at bit i_lo*(K-1) of the row; earlier words stay zero
-            const int start = i_lo * p.km1;
-            Bits bw{sTw + tid, start >> 5, start & 31, 0u};
-            for (int w = 0; w < (start >> 5); ++w) sTw[w * kThreads + tid] = 0u;
-            if (hl < p.N) {
-                if (p.samples) {
-                    const uint8_t *srow = p.samples + hl * (int64_t)p.n;
-                    for (int i = i_lo; i < i_hi; ++i) bw.put((1u << srow[i]) - 1u, p.km1);
-                } else {
-                    const uint64_t h = p.offset + (uint64_t)hl;
-                    // two independent Philox blocks per iteration (instruction-level parallelism)
-                    for (int q = i_lo / 4; 4 * q < i_hi; q += 2) {
-                        const U32x4 ra = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
-                        const U32x4 rb =
-                            philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)(q + 1), 0u, key0, key1);
-                        const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const int i = 4 * q + c;
-                            if (i < i_hi) {
-                                const uint32_t x = state_from_uniform(us[c], sThr + (size_t)i * p.km1, p.km1);
-                                bw.put((1u << x) - 1u, p.km1);
-                            }
-                        }
-                    }
-                }
-                if (half) {  // the constant-one bias columns follow the last component
-                    for (int b = bias_cols; b > 0; b -= 16) {
-                        const int len = b < 16 ? b : 16;
-                        bw.put((1u << len) - 1u, len);
-                    }
-                }
-            }
-            bw.finish(kwords);
-        }
-        __syncthreads();
-        {
-            // expand the row's bits (the OR of its two halves) to FP8 bytes in the MMA layout;
-            // thread t does chunks [0, kp/32) of row t, thread t + 128 the rest
-            const int row = tid & (kRows - 1), half = tid >> 7;
-            const int c_lo = half ? kp / 32 : 0, c_hi = half ? kp / 16 : kp / 32;
-            for (int c = c_lo; c < c_hi; ++c) {
-                const int w = c >> 1;
-                const uint32_t word = sTw[w * kThreads + row] | sTw[w * kThreads + row + kRows];
-                const uint32_t b16 = (word >> ((c & 1) * 16)) & 0xFFFFu;
-                uint4 v;
-                v.x = nibble_to_fp8(b16 & 0xF);
-                v.y = nibble_to_fp8((b16 >> 4) & 0xF);
-                v.z = nibble_to_fp8((b16 >> 8) & 0xF);
-                v.w = nibble_to_fp8((b16 >> 12) & 0xF);
-                *reinterpret_cast<uint4 *>(sA + tile_off(row, c, kp)) = v;
-            }
-        }
+        sample_a_tile(p, blk * kRows, sThr, sTw, sA, kp);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         if (tid == 0) {
             ctl.done = 0;
@@ -278,6 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                     if (!mbar_wait(&ctl.empty[st_stage], st_phase ^ 1u, abort_flag, err, budget)) break;
                     if (stop) {
                         ctl.stage_tile[st_stage] = -1;
+                        copy_made &= ~(1u << st_stage);   // the stage's last copy was consumed (empty wait)
                         mbar_arrive(&ctl.full[st_stage]);
                     } else {
                         ctl.stage_tile[st_stage] = (int)j;
@@ -287,6 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                         const uint8_t *src = (up ? p.tc_U : p.tc_L) + (size_t)ti * tile_bytes;
                         mbar_arrive_expect_tx(&ctl.full[st_stage], tile_bytes);
                         bulk_g2s(sStage + (size_t)st_stage * tile_bytes, src, tile_bytes, &ctl.full[st_stage]);
+                        copy_made |= 1u << st_stage;
+                        copy_phase = (copy_phase & ~(1u << st_stage)) | (st_phase << st_stage);
                     }
                     if (++st_stage == S) {
                         st_stage = 0;
@@ -393,31 +309,20 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
                 if (p.labels) p.labels[h] = (uint8_t)lab;
                 c0 += lab == 0; c1 += lab == 1; c2 += lab == 2;
             }
-            if (p.grad_counts) {
-                // per-bit counts of I^L rows, from the thermometer scratch (OR of the two halves)
-                const bool isL = v && lab == 0;
-                if (__ballot_sync(0xffffffffu, isL)) {
-                    const int kw = (p.kenc + 31) / 32;
-                    for (int w = 0; w < kw; ++w) {
-                        const uint32_t tw =
-                            isL ? (sTw[w * kThreads + row] | sTw[w * kThreads + row + kRows]) : 0u;
-                        uint32_t mine = 0;
-#pragma unroll 4
-                        for (int b = 0; b < 32; ++b) {
-                            const uint32_t mm = __ballot_sync(0xffffffffu, (tw >> b) & 1u);
-                            if (lane == b) mine = __popc(mm);
-                        }
-                        if (mine) atomicAdd(&sCum[w * 32 + lane], mine);
-                    }
-                }
-            }
+            if (p.grad_counts) count_lower_bits(v && lab == 0, row, lane, sTw, sCum, p.kenc);
         }
         // Each role advanced its private copy of the ring positions by the same
         // number of entries (issued tiles + the sentinel), so the copies agree.
-        if (warp == 0 && lane == 0 && *abort_flag) {
-            // let bulk copies that may still be in flight land before the CTA exits
-            const long long t0 = clock64();
-            while (clock64() - t0 < 2000000ll) {
+        if (*abort_flag && lane == 0) {
+            if (warp == 0) {
+                // every copy issued into a stage completes its full barrier's phase:
+                // wait for the last one of each stage before shared memory is released
+                for (int s = 0; s < S; ++s)
+                    if (copy_made & (1u << s)) (void)mbar_wait_drain(&ctl.full[s], (copy_phase >> s) & 1u);
+            } else if (warp == 1) {
+                // a commit tracks every MMA this thread issued before it
+                mma_commit(&ctl.drain);
+                (void)mbar_wait_drain(&ctl.drain, 0u);
             }
         }
         __syncthreads();
@@ -442,29 +347,9 @@ __global__ void __launch_bounds__(kThreads, 1) classify_tc_kernel(const Classify
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        if (*abort_flag && lane == 0) {
-            // after a timeout, give MMAs that may still be running time to finish
-            const long long t0 = clock64();
-            while (clock64() - t0 < 2000000ll) {
-            }
-        }
-        __syncwarp();
-        tmem_dealloc(tmem, kTmemCols);
+        tmem_dealloc(tmem, kTmemCols);   // after an abort, the drain above waited for the MMAs
     }
-    if (tid < 3 && ctl.cnt[tid]) atomicAdd(&p.counts3[tid], ctl.cnt[tid]);
-    if (tid == 0 && p.exec_tests && ctl.exec) atomicAdd(p.exec_tests, ctl.exec);
-    if (p.grad_counts && ctl.cnt[0]) {
-        for (int i = tid; i < p.n; i += kThreads) {
-            long long prev = (long long)ctl.cnt[0];
-            for (int k = 1; k <= p.km1; ++k) {
-                const long long cum = (long long)sCum[i * p.km1 + (k - 1)];
-                const long long dd = prev - cum;
-                if (dd) atomicAdd(&p.grad_counts[(size_t)i * p.K + (k - 1)], (unsigned long long)dd);
-                prev = cum;
-            }
-            if (prev) atomicAdd(&p.grad_counts[(size_t)i * p.K + p.km1], (unsigned long long)prev);
-        }
-    }
+    flush_counts(p, ctl.cnt, ctl.exec, sCum);
 }
 
 // Reference rows in the MMA layout: tile t = r / 128 holds rows r in
@@ -488,7 +373,9 @@ __global__ void encode_tc_kernel(const uint8_t *__restrict__ refs, const int32_t
         const int j = c * 16 + e;
         float v = 0.0f;
         if (r >= R) {
-            v = (j == kenc) ? 1.0f : 0.0f;  // padding: never zero
+            // padding: never zero, and of the sign of the set's real values (lower
+            // V >= 0, upper V <= 0) so that a min / max reduction ignores it
+            v = (j == kenc) ? (upper ? -1.0f : 1.0f) : 0.0f;
         } else if (j < kenc) {
             const int i = j / km1, k = j % km1 + 1;
             const bool a = refs[src * n + i] >= k;
@@ -588,6 +475,9 @@ cudaError_t launch_tc_bn(const ClassifyParams &p, cudaStream_t s) {
 // B stages fit next to the A tile; narrower 128-row tiles for wider rows.
 cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s) {
     if (p.tc_kpad > tc_max_kpad() || p.tc_kpad % 32 != 0) return cudaErrorNotSupported;
+    // dense mode: the CTA-pair kernel (classify_tc2.cu) halves the shared-memory
+    // traffic per MMA; early exit stays here (its blocks stop at different tiles)
+    if (p.dense && tc2_available(p.tc_kpad)) return launch_classify_tc2(p, s);
     if (tc_smem_plan(p.tc_kpad, p.n * p.km1, 256, kMaxStages).nstages >= 2) return launch_tc_bn<256>(p, s);
     return launch_tc_bn<128>(p, s);
 }

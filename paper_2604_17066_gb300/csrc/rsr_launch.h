@@ -37,7 +37,9 @@ cudaError_t launch_grad_correction(const ClassifyParams &p, const int64_t *idx, 
 cudaError_t launch_classify_popc(const ClassifyParams &p, cudaStream_t s);
 cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded, int n, int km1,
                              int kpad, bool upper, uint8_t *out, cudaStream_t s, const int32_t *perm = nullptr);
-cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s);
+cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s);   // dense: the pair kernel below
+cudaError_t launch_classify_tc2(const ClassifyParams &p, cudaStream_t s);  // dense, CTA pairs (cta_group::2)
+bool tc2_available(int kpad);   // the pair kernel runs on this device for rows of kpad bytes
 bool tc_supported();
 int tc_max_kpad();
 

@@ -42,10 +42,14 @@ def run(sess, seed, offset, N, samples=None, grad=True):
     return {k: (v.cpu().numpy() if v is not None else None) for k, v in out.items()}
 
 
-def tc_executed_tests(n, K, R_L, R_U, N):
-    """Reference tests the tensor-core path executes in dense mode: 128-sample
-    blocks times BN-reference tiles (BN = 256 when a row fits in 320 bytes,
-    else 128), padding included."""
+def tc_executed_tests(n, K, R_L, R_U, N, dense=True):
+    """Reference tests the tensor-core path executes.  Dense mode runs on CTA
+    pairs: 256-sample pair blocks times 256-reference tiles.  Early exit runs one
+    CTA per MMA: at most 128-sample blocks times BN-reference tiles (BN = 256 when
+    a row fits in 320 bytes, else 128), padding included."""
+    if dense:
+        tiles = -(-R_L // 256) + -(-R_U // 256)
+        return (-(-N // 256)) * 256 * tiles * 256
     bn = 256 if tc_kpad(n, K) <= 320 else 128
     tiles = -(-R_L // bn) + -(-R_U // bn)
     return (-(-N // 128)) * 128 * tiles * bn

@@ -42,7 +42,7 @@ def test_c3_dense_tc_full_size(rsr, c3):
     got = run(make_session(rsr, c3, path=TC, dense=True), 1, 0, N)
     assert np.array_equal(np.bincount(got["labels"], minlength=3), got["counts3"])
     check_subset(c3, got["labels"], 1, 0, 1500, 3)
-    assert got["exec_tests"][0] == tc_executed_tests(c3.n, c3.K, c3.R_L, c3.R_U, N)
+    assert got["exec_tests"][0] == tc_executed_tests(c3.n, c3.K, c3.R_L, c3.R_U, N, dense=True)
     # early exit gives the same labels
     got_ee = run(make_session(rsr, c3, path=TC, dense=False), 1, 0, N)
     assert np.array_equal(got_ee["labels"], got["labels"])

@@ -1,8 +1,9 @@
 """GPU parity of the tensor-core (tcgen05 FP8 contraction) path against the
 oracle: labels, counts and gradient counts bit-exact on the same seeded
-samples, in dense (every reference) and early-exit modes, across several
-128-reference tiles, several 256-sample blocks and ragged tails, for binary
-and multi-state encodings, with and without overlapping reference pairs."""
+samples, in dense mode (every reference; the CTA-pair kernel) and early-exit
+mode (one CTA per MMA), across several reference tiles, several sample blocks
+and ragged tails, for binary and multi-state encodings, with and without
+overlapping reference pairs."""
 import numpy as np
 import pytest
 import torch
@@ -22,7 +23,7 @@ def check(rsr, prob, seed, offset, N, dense, samples=None):
     assert np.array_equal(got["counts3"], cnt), (got["counts3"], cnt)
     assert np.array_equal(got["labels"], lab)
     assert np.array_equal(got["grad_counts"].reshape(prob.n, prob.K), O.grad_counts(X, lab, prob.K))
-    full = tc_executed_tests(prob.n, prob.K, prob.R_L, prob.R_U, N)
+    full = tc_executed_tests(prob.n, prob.K, prob.R_L, prob.R_U, N, dense=dense)
     if dense:
         assert got["exec_tests"][0] == full
     else:
@@ -85,6 +86,23 @@ def test_tc_bounded_waits_time_out_and_leave_the_context_usable(rsr):
     # the context still works: a normal run on a fresh workspace matches the oracle
     P.extra_flags = 0
     check(rsr, prob, 1, 0, 4096, dense=False)
+
+
+def test_tc_pair_kernel_bounded_waits_time_out_and_leave_the_context_usable(rsr):
+    """The same failure detection on the dense CTA-pair kernel: neither CTA's
+    producer starts, the leader's and the peer's waits run out, both CTAs agree
+    to stop at their cluster barrier, free the pair's tensor memory and return."""
+    from paper_2604_17066_gb300._lib import RSR_FLAG_TEST_STALL
+    prob = random_refs_problem(120, 3, 130, 129, seed=3)
+    P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=TC, dense=True)
+    sess = rsr.Session(P)
+    P.extra_flags = RSR_FLAG_TEST_STALL
+    sess.classify(1, 0, 4096)
+    torch.cuda.synchronize()
+    overlap, err = rsr.rsr_workspace_status(sess.ws)
+    assert err == -4
+    P.extra_flags = 0
+    check(rsr, prob, 1, 0, 4096, dense=True)
 
 
 def test_measured_fp8_peak_is_plausible(rsr):
