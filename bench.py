@@ -39,14 +39,16 @@ def _peaks():
 
 
 def _captured_traffic(workload_tag):
-    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
-    record, if the kernel source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch of the dense tensor-core kernel from the committed
+    ncu record, if its sources are unchanged since the capture (else None)."""
     import hashlib
-    rec = os.path.join(ROOT, "profiles", "classify_tc_c3_dense_traffic.json")
-    src = os.path.join(ROOT, "paper_2604_17066_gb300", "csrc", "classify_tc.cu")
+    rec = os.path.join(ROOT, "profiles", "classify_tc2_c3_dense_traffic.json")
     try:
         d = json.load(open(rec))
-        if hashlib.sha1(open(src, "rb").read()).hexdigest() != d["source_sha1"]:
+        h = hashlib.sha1()
+        for src in d["sources"]:
+            h.update(open(os.path.join(ROOT, src), "rb").read())
+        if h.hexdigest() != d["source_sha1"]:
             return None
         if not workload_tag.startswith(d["workload"].split()[0]) or "_N" in workload_tag.split("p0.9")[-1]:
             return None
@@ -135,18 +137,22 @@ class Clocks:
 
 def measure_fp8_peak(rsr, torch, uuid, seconds=3.0):
     """The tensor roofline's denominator, measured on this GPU: librsr's own
-    back-to-back tcgen05 FP8 MMA loop (rsr_measure_fp8_peak), burst and
-    sustained, each with the SM clock sampled while it ran; plus cuBLASLt's FP8
-    GEMM (torch._scaled_mm, 8192^3) as a cross-check."""
+    back-to-back tcgen05 FP8 MMA loops (rsr_measure_fp8_peak), on single CTAs
+    (M = 128) and on CTA pairs (cta_group::2, M = 256), each a burst with the SM
+    clock sampled while it ran, plus a sustained run of the pair variant; the
+    peak is the larger burst.  cuBLASLt's FP8 GEMM (torch._scaled_mm, 8192^3)
+    is a cross-check."""
     out = {}
+    for key, pair in (("cta1", False), ("cta_pair", True)):
+        with Clocks(uuid) as ck:
+            torch.cuda.synchronize()
+            r = rsr.rsr_measure_fp8_peak(0.0, cta_pair=pair)
+        out["burst_tflops_" + key] = r["burst_flops_per_s"] / 1e12
+        out["burst_clocks_" + key] = ck.summary()
+    out["burst_tflops"] = max(out["burst_tflops_cta1"], out["burst_tflops_cta_pair"])
     with Clocks(uuid) as ck:
         torch.cuda.synchronize()
-        r = rsr.rsr_measure_fp8_peak(0.0)
-    out["burst_tflops"] = r["burst_flops_per_s"] / 1e12
-    out["burst_clocks"] = ck.summary()
-    with Clocks(uuid) as ck:
-        torch.cuda.synchronize()
-        r = rsr.rsr_measure_fp8_peak(seconds)
+        r = rsr.rsr_measure_fp8_peak(seconds, cta_pair=True)
     out["sustained_tflops"] = r["sustained_flops_per_s"] / 1e12
     out["sustained_clocks"] = ck.summary()
     out["sustained_power_w_max"] = ck.power_max()
@@ -739,8 +745,9 @@ def main():
                 "achieved_executed": achieved_exec,
                 "traffic": _captured_traffic(wname) if P.dense else None,
                 "peak_measured": fp8,
-                "note": "peak = measured FP8 tcgen05 burst of this GPU (rsr_measure_fp8_peak: back-to-back "
-                        "kind::f8f6f4 MMAs from shared memory, one CTA per SM); frac = algorithmic flops "
+                "note": "peak = measured FP8 tcgen05 burst of this GPU, the larger of single-CTA and CTA-pair "
+                        "MMA loops (rsr_measure_fp8_peak: back-to-back kind::f8f6f4 MMAs from shared memory, "
+                        "one CTA per SM); frac = algorithmic flops "
                         "2*n(K-1)*%s tests / kernel time / peak; frac_executed counts the executed tests at "
                         "the padded row of %d bytes" % ("N*(R_L+R_U)" if P.dense else "executed", kpad)}
     else:

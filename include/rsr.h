@@ -473,22 +473,26 @@ RSR_API int rsr_measure_int_peak(double *lop3_ops_per_s, double *imad_ops_per_s,
 
 /*
  * Measured dense FP8 tensor-core rate of the current GPU, for the roofline of
- * the tensor-core classifier (not a step of the method; the paper has no
- * counterpart).  One CTA per SM issues tcgen05.mma.cta_group::1.kind::f8f6f4
- * (M = 128, N = 256, K = 32, E4M3 operands resident in shared memory, FP32
- * accumulators in tensor memory) back to back, with no copies and no
- * epilogue: 2*128*256*32 flop per instruction.
+ * the tensor-core classifiers (not a step of the method; the paper has no
+ * counterpart).  One CTA per SM issues tcgen05.mma.kind::f8f6f4 (K = 32, E4M3
+ * operands resident in shared memory, FP32 accumulators in tensor memory)
+ * back to back, with no copies and no epilogue.
+ *   cta_pair          : 0 = cta_group::1, M = 128 x N = 256 per CTA (as the
+ *                       early-exit classifier); 1 = cta_group::2 on clusters
+ *                       of two CTAs, M = 256 x N = 256 per pair (as the dense
+ *                       classifier).  Either way 2*128*256*32 flop per CTA per
+ *                       instruction.
  *   seconds           : length of the sustained run, in [0, 60]; 0 skips it.
  *   burst_flops_per_s : host double[1], the fastest of five single launches of
  *                       about 16 ms each (after one warm-up launch).
  *   sustained_flops_per_s : host double[1], launches back to back for about
  *                       `seconds` (0.0 when skipped).
  * Synchronous (waits for its own kernels on `stream`); allocates nothing.
- * RSR_ERR_UNSUPPORTED on a GPU without tcgen05; RSR_ERR_TIMEOUT if the final
+ * RSR_ERR_UNSUPPORTED on a GPU without tcgen05; RSR_ERR_TIMEOUT if a final
  * bounded wait for the issued MMAs ran out.
  */
-RSR_API int rsr_measure_fp8_peak(double seconds, double *burst_flops_per_s, double *sustained_flops_per_s,
-                                 rsr_stream_t stream);
+RSR_API int rsr_measure_fp8_peak(int32_t cta_pair, double seconds, double *burst_flops_per_s,
+                                 double *sustained_flops_per_s, rsr_stream_t stream);
 
 /* Message for a status code (static storage). */
 RSR_API const char *rsr_status_string(int status);

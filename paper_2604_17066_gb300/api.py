@@ -481,13 +481,14 @@ def rsr_measure_int_peak(stream=None) -> dict:
     return {"lop3_ops_per_s": lop3.value, "imad_ops_per_s": imad.value}
 
 
-def rsr_measure_fp8_peak(seconds: float = 0.0, stream=None) -> dict:
+def rsr_measure_fp8_peak(seconds: float = 0.0, cta_pair: bool = False, stream=None) -> dict:
     """rsr_measure_fp8_peak: measured dense FP8 tensor-core rate of the current
     GPU (tcgen05.mma kind::f8f6f4, E4M3 operands, FP32 accumulation), in
-    flop/s: the fastest single ~16 ms launch (burst) and, for seconds > 0,
-    back-to-back launches for that long (sustained; 0.0 when skipped)."""
+    flop/s, for single CTAs (M = 128) or CTA pairs (cta_group::2, M = 256): the
+    fastest single ~16 ms launch (burst) and, for seconds > 0, back-to-back
+    launches for that long (sustained; 0.0 when skipped)."""
     burst = ctypes.c_double(0.0)
     sustained = ctypes.c_double(0.0)
-    check(_lib.load().rsr_measure_fp8_peak(float(seconds), ctypes.addressof(burst), ctypes.addressof(sustained),
-                                           _stream(stream)), "rsr_measure_fp8_peak")
+    check(_lib.load().rsr_measure_fp8_peak(1 if cta_pair else 0, float(seconds), ctypes.addressof(burst),
+                                           ctypes.addressof(sustained), _stream(stream)), "rsr_measure_fp8_peak")
     return {"burst_flops_per_s": burst.value, "sustained_flops_per_s": sustained.value}

@@ -20,10 +20,12 @@
 //                 FP8 A tile (tc_common.cuh), then a cluster barrier
 //   warp 0      : producer in each CTA: one cp.async.bulk per stage, its half
 //                 (one encoded 128-row tile) of B tile j, into its own ring
-//   warp 1      : both CTAs allocate the pair's tensor memory (cta_group::2);
-//                 the leader issues the MMAs, which write each CTA's 128 rows
-//                 of D into that CTA's tensor memory; the peer forwards the
-//                 completion of its stages to the leader (remote arrive)
+//   warps 1, 2  : both CTAs' warp 1 allocates the pair's tensor memory
+//                 (cta_group::2); in the leader, warps 1 and 2 issue the MMAs
+//                 of the even and odd tiles (one accumulator each), which write
+//                 each CTA's 128 rows of D into that CTA's tensor memory; in the
+//                 peer, warp 1 forwards the completion of its stages to the
+//                 leader (remote arrive)
 //   warps 4-7   : epilogue in each CTA, the thread of TMEM lane r owns sample
 //                 row r; it reduces "some V = 0" over the 256 columns (a min
 //                 on lower tiles, where V >= 0; a max on upper tiles, where
@@ -54,7 +56,8 @@ using namespace tc;
 
 constexpr int kThreads = kTcThreads;   // 8 warps
 constexpr int kProducerWarp = 0;
-constexpr int kMmaWarp = 1;
+constexpr int kMmaWarp = 1;            // leader: issues the even tiles; peer: forwards stage completions
+constexpr int kMmaWarp2 = 2;           // leader: issues the odd tiles
 constexpr int kEpiWarp0 = 4;           // warps 4-7: one per TMEM lane quarter
 constexpr int kRows = kTcRows;       // samples per CTA per pair block (the pair: 256)
 constexpr int kHalfRefs = 128;       // references per CTA per B tile: one encoded 128-row tile
@@ -97,7 +100,7 @@ struct PairCtl {
     uint64_t pfull[kMaxStages];   // leader: the peer's copy of stage s landed (peer's remote arrive)
     uint64_t tfull[2];            // accumulator b holds a finished tile (leader's commit, both CTAs)
     uint64_t tempty[2];           // leader: the 8 epilogue warps of the pair have read accumulator b
-    uint64_t drain;               // leader, after an abort: every MMA issued so far completed
+    uint64_t drain;               // leader, after an abort: every MMA issued so far completed (2 issuers)
     uint32_t tmem_base;
     int abort_flag;
     unsigned long long exec;
@@ -139,7 +142,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             mbar_init(&ctl.tfull[b], 1);
             mbar_init(&ctl.tempty[b], 8);   // four epilogue warps per CTA
         }
-        mbar_init(&ctl.drain, 1);
+        mbar_init(&ctl.drain, 2);   // one commit from each issuing thread
         ctl.abort_flag = 0;
         ctl.exec = 0ull;
         ctl.cnt[0] = ctl.cnt[1] = ctl.cnt[2] = 0ull;
@@ -171,6 +174,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     int acc_buf = 0;
     uint32_t acc_phase = 0;
     uint32_t copy_phase = 0u, copy_made = 0u;   // producer: phase of the last copy into each stage
+    int64_t g_base = 0;                         // tiles of the earlier blocks (tile g uses stage g mod S, accumulator g mod 2)
     unsigned long long c0 = 0, c1 = 0, c2 = 0;  // epilogue per-thread totals
 
     const int64_t npb = (p.N + 2 * kRows - 1) / (2 * kRows);
@@ -199,25 +203,31 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     }
                 }
             }
-        } else if (warp == kMmaWarp) {
+        } else if (warp == kMmaWarp || warp == kMmaWarp2) {
             if (lane == 0 && leader) {
+                // Two issuing threads, one per accumulator (tile parity): while one is
+                // blocked in the MMA queue the other commits and waits for its next tile,
+                // so the tensor pipe is not left idle between tiles.
+                const int64_t parity = warp == kMmaWarp ? 0 : 1;
                 const uint32_t a_base = smem_u32(sA);
                 const uint32_t sbo = (uint32_t)kp * 8u;
                 unsigned long long issued = 0;
                 for (int64_t j = 0; j < T; ++j) {
-                    if (!mbar_wait(&ctl.full[st_stage], st_phase, abort_flag, err, budget)) break;
-                    if (!mbar_wait(&ctl.pfull[st_stage], st_phase, abort_flag, err, budget)) break;
-                    if (!mbar_wait(&ctl.tempty[acc_buf], acc_phase ^ 1u, abort_flag, err, budget)) break;
-                    tc_fence_after();
-                    const uint32_t b_base = smem_u32(sStage + (size_t)st_stage * half_bytes);
-                    const uint32_t d = tmem + (uint32_t)(acc_buf * kPairRefs);
+                    if (((g_base + j) & 1) == parity) {
+                        if (!mbar_wait(&ctl.full[st_stage], st_phase, abort_flag, err, budget)) break;
+                        if (!mbar_wait(&ctl.pfull[st_stage], st_phase, abort_flag, err, budget)) break;
+                        if (!mbar_wait(&ctl.tempty[acc_buf], acc_phase ^ 1u, abort_flag, err, budget)) break;
+                        tc_fence_after();
+                        const uint32_t b_base = smem_u32(sStage + (size_t)st_stage * half_bytes);
+                        const uint32_t d = tmem + (uint32_t)(acc_buf * kPairRefs);
 #pragma unroll 1
-                    for (int kk = 0; kk < kp / 32; ++kk)
-                        mma_f8_pair(d, smem_desc(a_base + kk * 256, 128, sbo), smem_desc(b_base + kk * 256, 128, sbo),
-                                    kIdesc, kk > 0 ? 1u : 0u);
-                    mma_commit_pair(&ctl.empty[st_stage], kBoth);
-                    mma_commit_pair(&ctl.tfull[acc_buf], kBoth);
-                    ++issued;
+                        for (int kk = 0; kk < kp / 32; ++kk)
+                            mma_f8_pair(d, smem_desc(a_base + kk * 256, 128, sbo),
+                                        smem_desc(b_base + kk * 256, 128, sbo), kIdesc, kk > 0 ? 1u : 0u);
+                        mma_commit_pair(&ctl.empty[st_stage], kBoth);
+                        mma_commit_pair(&ctl.tfull[acc_buf], kBoth);
+                        ++issued;
+                    }
                     if (++st_stage == S) {
                         st_stage = 0;
                         st_phase ^= 1u;
@@ -227,8 +237,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         acc_phase ^= 1u;
                     }
                 }
-                ctl.exec += issued * (unsigned long long)(kPairRefs * 2 * kRows);
-            } else if (lane == 0) {
+                if (issued) atomicAdd(&ctl.exec, issued * (unsigned long long)(kPairRefs * 2 * kRows));
+            } else if (lane == 0 && warp == kMmaWarp) {
                 // peer: tell the leader when each stage of this CTA has landed
                 for (int64_t j = 0; j < T; ++j) {
                     if (!mbar_wait(&ctl.full[st_stage], st_phase, abort_flag, err, budget)) break;
@@ -256,18 +266,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 // max V > -0.5 on an upper tile
                 float m = is_upper ? -1.0f : 1.0f;
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc_buf * kPairRefs);
+                // 128 columns per load round trip (the latency of a tensor-memory load,
+                // not the arithmetic, sets the epilogue's time)
 #pragma unroll 1
-                for (int c = 0; c < kPairRefs / 64; ++c) {
-                    uint32_t va[32], vb[32];
-                    tmem_ld32(tbase + c * 64, va);
-                    tmem_ld32(tbase + c * 64 + 32, vb);
+                for (int c = 0; c < kPairRefs / 128; ++c) {
+                    uint32_t va[64], vb[64];
+                    tmem_ld64(tbase + c * 128, va);
+                    tmem_ld64(tbase + c * 128 + 64, vb);
                     tmem_ld_wait();
                     if (is_upper) {
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) m = fmax3(m, __uint_as_float(va[e]), __uint_as_float(vb[e]));
+                        for (int e = 0; e < 64; ++e) m = fmax3(m, __uint_as_float(va[e]), __uint_as_float(vb[e]));
                     } else {
 #pragma unroll
-                        for (int e = 0; e < 32; ++e) m = fmin3(m, __uint_as_float(va[e]), __uint_as_float(vb[e]));
+                        for (int e = 0; e < 64; ++e) m = fmin3(m, __uint_as_float(va[e]), __uint_as_float(vb[e]));
                     }
                 }
                 tc_fence_before();
@@ -293,11 +305,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 for (int s = 0; s < S; ++s)
                     if (copy_made & (1u << s)) (void)mbar_wait_drain(&ctl.full[s], (copy_phase >> s) & 1u);
                 copy_made = 0u;
-            } else if (warp == kMmaWarp && leader) {
-                mma_commit_pair(&ctl.drain, 0x1);   // tracks every MMA issued before it
+            } else if ((warp == kMmaWarp || warp == kMmaWarp2) && leader) {
+                mma_commit_pair(&ctl.drain, 0x1);   // tracks every MMA this thread issued before it
                 (void)mbar_wait_drain(&ctl.drain, 0u);
             }
         }
+        g_base += T;
         __syncthreads();
         cluster_sync();
         // Every role of both CTAs has finished this block, so both abort flags

@@ -12,12 +12,14 @@
 // The results feed a never-taken store into a file-scope device word, so
 // nothing is allocated and nothing is eliminated.
 //
-// Tensor (FP8): the dense classifier issues tcgen05.mma kind::f8f6f4 with E4M3
-// operands from shared memory and FP32 accumulators in tensor memory.  Its
-// roofline denominator is the same instruction run back to back: one CTA per
-// SM, operands resident in shared memory (pseudo-random E4M3 bytes, never NaN
-// or infinite), no copies and no epilogue, alternating between two
-// accumulators so that consecutive MMAs are independent.
+// Tensor (FP8): the classifiers issue tcgen05.mma kind::f8f6f4 with E4M3
+// operands from shared memory and FP32 accumulators in tensor memory.  The
+// roofline denominator is the same instruction run back to back, one CTA per
+// SM, either alone (cta_group::1, M = 128) or on CTA pairs (cta_group::2,
+// M = 256, as the dense classifier): operands resident in shared memory
+// (pseudo-random E4M3 bytes, never NaN or infinite), no copies and no
+// epilogue, alternating between two accumulators so that consecutive MMAs are
+// independent.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -135,23 +137,91 @@ __global__ void __launch_bounds__(kFp8Threads, 1) fp8_mma_peak_kernel(long long 
     }
 }
 
+// The same on CTA pairs (cta_group::2): the even CTA of each cluster issues
+// M = 256 x N = 256 x K = 32 MMAs whose A rows and B rows are split between
+// the two CTAs' shared memory; its commit reaches both CTAs, which then meet at
+// a cluster barrier before the pair's tensor memory is freed.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kFp8Threads, 1) fp8_mma_pair_peak_kernel(long long iters) {
+    using namespace tc;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const bool leader = cluster_ctarank() == 0;
+    unsigned char *sA = smem;                        // this CTA's 128 rows of A
+    unsigned char *sB = smem + kMmaM * kMmaKBytes;   // this CTA's 128 rows of B
+    for (int i = tid; i < 2 * kMmaM * kMmaKBytes / 4; i += blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B1u ^ ((uint32_t)blockIdx.x * 0x85EBCA77u);
+        h ^= h >> 15;
+        h *= 0x2C1B3C6Du;
+        h ^= h >> 12;
+        reinterpret_cast<uint32_t *>(smem)[i] = h & 0xBFBFBFBFu;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tmem_alloc_pair(&tmem_base, 2 * kMmaN);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();   // both CTAs' operands and barriers are ready
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0 && leader) {
+        constexpr uint32_t idesc = idesc_f8<2 * kMmaM, kMmaN>();
+        const uint32_t sbo = kMmaKBytes * 8, a0 = smem_u32(sA), b0 = smem_u32(sB);
+        for (long long it = 0; it < iters; ++it) {
+            const uint32_t d = tmem + (uint32_t)((it & 1) * kMmaN);
+#pragma unroll
+            for (int kk = 0; kk < kMmaKBytes / 32; ++kk)
+                mma_f8_pair(d, smem_desc(a0 + kk * 256, 128, sbo), smem_desc(b0 + kk * 256, 128, sbo), idesc,
+                            kk > 0 ? 1u : 0u);
+        }
+        mma_commit_pair(&bar, 0x3);
+    }
+    if (tid == 0) {
+        // every CTA waits for the leader's MMAs, which read its shared memory and write its tensor memory
+        if (!mbar_wait(&bar, 0, &abort_flag, &g_fp8_peak_err)) {
+            abort_flag = 0;
+            (void)mbar_wait(&bar, 0, &abort_flag, &g_fp8_peak_err);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 2 * kMmaN);
+    }
+}
+
 }  // namespace
 
 }  // namespace rsr
 
 using namespace rsr;
 
-extern "C" int rsr_measure_fp8_peak(double seconds, double *burst_flops_per_s, double *sustained_flops_per_s,
-                                    rsr_stream_t stream) {
-    if (!burst_flops_per_s || !sustained_flops_per_s || !(seconds >= 0.0) || seconds > 60.0)
+extern "C" int rsr_measure_fp8_peak(int32_t cta_pair, double seconds, double *burst_flops_per_s,
+                                    double *sustained_flops_per_s, rsr_stream_t stream) {
+    if ((cta_pair != 0 && cta_pair != 1) || !burst_flops_per_s || !sustained_flops_per_s || !(seconds >= 0.0) ||
+        seconds > 60.0)
         return RSR_ERR_INVALID_ARG;
     if (!tc_supported()) return RSR_ERR_UNSUPPORTED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int grid = device_sm_count();
+    const int grid = cta_pair ? 2 * (device_sm_count() / 2) : device_sm_count();
+    // per CTA: the MMAs of its own 128 rows of D (a pair MMA covers 256 rows over two CTAs)
     const double flops_per_launch =
         (double)grid * (double)kFp8Iters * (kMmaKBytes / 32) * 2.0 * kMmaM * kMmaN * 32.0;
-    cudaError_t e = cudaFuncSetAttribute(fp8_mma_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kFp8Smem);
+    cudaError_t e = cta_pair ? cudaFuncSetAttribute(fp8_mma_pair_peak_kernel,
+                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFp8Smem)
+                             : cudaFuncSetAttribute(fp8_mma_peak_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)kFp8Smem);
     if (e != cudaSuccess) return cuda_fail(e, "rsr_measure_fp8_peak");
     const int32_t zero = 0;
     e = cudaMemcpyToSymbolAsync(g_fp8_peak_err, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
@@ -165,7 +235,12 @@ extern "C" int rsr_measure_fp8_peak(double seconds, double *burst_flops_per_s, d
     int st = RSR_OK;
     auto timed = [&](int launches, float *ms) -> cudaError_t {
         cudaEventRecord(e0, s);
-        for (int l = 0; l < launches; ++l) fp8_mma_peak_kernel<<<grid, kFp8Threads, kFp8Smem, s>>>(kFp8Iters);
+        for (int l = 0; l < launches; ++l) {
+            if (cta_pair)
+                fp8_mma_pair_peak_kernel<<<grid, kFp8Threads, kFp8Smem, s>>>(kFp8Iters);
+            else
+                fp8_mma_peak_kernel<<<grid, kFp8Threads, kFp8Smem, s>>>(kFp8Iters);
+        }
         cudaEventRecord(e1, s);
         cudaError_t r = cudaEventSynchronize(e1);
         if (r == cudaSuccess) r = cudaGetLastError();

@@ -105,10 +105,11 @@ def test_tc_pair_kernel_bounded_waits_time_out_and_leave_the_context_usable(rsr)
     check(rsr, prob, 1, 0, 4096, dense=True)
 
 
-def test_measured_fp8_peak_is_plausible(rsr):
+@pytest.mark.parametrize("pair", [False, True])
+def test_measured_fp8_peak_is_plausible(rsr, pair):
     """rsr_measure_fp8_peak (the tensor roofline's denominator) returns rates
-    within the range a GB300 can reach: above half of the nominal 4.5 PFLOP/s
-    dense FP8 figure and below twice it."""
-    m = rsr.rsr_measure_fp8_peak(0.2)
+    within the range a GB300 can reach, on single CTAs and on CTA pairs: above
+    half of the nominal 4.5 PFLOP/s dense FP8 figure and below twice it."""
+    m = rsr.rsr_measure_fp8_peak(0.2, cta_pair=pair)
     for key in ("burst_flops_per_s", "sustained_flops_per_s"):
         assert 2.25e15 < m[key] < 9e15, m
