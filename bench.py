@@ -317,9 +317,10 @@ def bench_levels(rsr, torch, N=1_000_000, reps=5):
 
 def bench_batch(rsr, torch, N=200_000, reps=5):
     """256 hazard scenarios (n = 50..300 edges, 1e2..1e5 references, N samples
-    each): one persistent launch replayed from a CUDA graph vs the per-scenario
-    path on prepared workspaces.  Two comparisons: kernels only (one batched
-    launch vs one rsr_classify per scenario), and a forward+gradient round
+    each): the batched launches (tile pass + deep pass) replayed from a CUDA
+    graph vs the per-scenario path on prepared workspaces.  Two comparisons:
+    kernels only (the batched launches vs one rsr_classify per scenario), and a
+    forward+gradient round
     (batched launch + rsr_batch_grad vs rsr_classify + rsr_grad per scenario,
     each rsr_grad reading its counts back)."""
     import workloads.large as L
@@ -329,7 +330,7 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
     seeds, offsets, Ns = [1000 + s for s in range(S)], [0] * S, [N] * S
     t0 = time.perf_counter()
     b = rsr.Batch(P, seeds, offsets, Ns, labels=True, grad=True)
-    grid, order = rsr.rsr_batch_autotune(b)
+    grid, order, k0 = rsr.rsr_batch_autotune(b)
     prep_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
@@ -397,7 +398,8 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
             "batched_fwd_grad_round_ms": batched_round_ms, "per_scenario_fwd_grad_round_ms": plain_round_ms,
             "speedup_fwd_grad_round": plain_round_ms / batched_round_ms,
             "samples_per_s": S * N / (batched_ms / 1000.0), "autotune_grid": grid,
-            "autotune_order": "longest-first" if order == 0 else "as-given", "prepare_s": prep_s}
+            "autotune_order": "longest-first" if order == 0 else "as-given", "autotune_k0": k0,
+            "prepare_s": prep_s}
 
 
 _ORACLE_PROB = None

@@ -219,15 +219,20 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  * rsr_batch_workspace_size : bytes of the batch workspace (0 on invalid input).
  * rsr_batch_prepare        : thresholds, reference encodings, precedence pre-checks and the work
  *                            list (longest scenarios first) into `ws`; not capturable.
- * rsr_batch                : ONE persistent kernel launch over every (scenario, 256-sample tile);
- *                            the arguments must equal those given to rsr_batch_prepare (else
- *                            RSR_ERR_NOT_PREPARED).  The launch re-arms its own counters, so it
- *                            can be captured once in a CUDA graph and replayed.
- * rsr_batch_autotune       : times grid sizes and work orders on the prepared batch (writing only
- *                            into the workspace's scratch, never the caller's outputs), keeps the
- *                            fastest for later rsr_batch calls and resets the round to 0;
- *                            chosen[0] = grid, chosen[1] = order (0 = longest first, 1 = as given).
- *                            Synchronises `stream`.
+ * rsr_batch                : two persistent kernel launches for the whole batch: every
+ *                            (scenario, 256-sample tile) walks at most k0 reference chunks, and
+ *                            the samples still unresolved then are queued and finished 256 at a
+ *                            time by the second launch (same labels and counts as one walk; a
+ *                            full queue leaves its tile to finish the walk itself).  The arguments
+ *                            must equal those given to rsr_batch_prepare (else
+ *                            RSR_ERR_NOT_PREPARED).  The launches re-arm their own counters, so
+ *                            they can be captured once in a CUDA graph and replayed.
+ * rsr_batch_autotune       : times the first pass's chunk budget k0 (0 = no second pass, 2, 4, 8,
+ *                            16, 32), then work orders and grid sizes, on the prepared batch
+ *                            (writing only into the workspace's scratch, never the caller's
+ *                            outputs), keeps the fastest for later rsr_batch calls and resets the
+ *                            round to 0; chosen[0] = grid, chosen[1] = order (0 = longest first,
+ *                            1 = as given), chosen[2] = k0 (8 until tuned).  Synchronises `stream`.
  */
 RSR_API size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S);
 RSR_API int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
@@ -240,7 +245,7 @@ RSR_API int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *se
 RSR_API int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
                                const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
                                int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws,
-                               size_t ws_bytes, rsr_stream_t stream, int32_t chosen[2]);
+                               size_t ws_bytes, rsr_stream_t stream, int32_t chosen[3]);
 
 /*
  * Gradients of every scenario of a batch from its per-state I^L counts (the

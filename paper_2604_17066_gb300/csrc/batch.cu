@@ -1,5 +1,5 @@
 // batch.cu -- many classification problems (hazard scenarios) in one
-// persistent launch.
+// persistent launch per pass.
 //
 // Each scenario s has its own n, K, pmf thresholds, reference sets, sample
 // count N_s, seed and offset.  Work items are (scenario, 256-sample tile),
@@ -7,14 +7,28 @@
 // scenarios first); a persistent grid pulls items from an atomic counter, so
 // short and long scenarios share the machine without per-scenario launch
 // tails.  Per item the block runs the same bit-packed test as classify_popc.cu
-// (Sec. 3.3, Algorithm 1) for the scenario's word count.  Counts go to the
-// scenario's counts3; I^L per-bit counts go to a scenario scratch counter, and
-// the last block to finish converts them into the per-state gradient counts,
-// zeroes the scratch, resets the work counter and advances the round, so the
-// same launch can be replayed (e.g. from a CUDA graph) on the next N_s samples
-// of every scenario without any host work.  Scenarios whose upper set has a
-// component-major index (popc_index.cuh) test their upper chunks through it,
-// after a direct test of their kHot most probable upper references.
+// (Sec. 3.3, Algorithm 1) for the scenario's word count.  Scenarios whose upper
+// set has a component-major index (popc_index.cuh) test their upper chunks
+// through it, after a direct test of their kHot most probable upper references.
+//
+// Two passes.  The 256 samples of a tile walk the reference chunks together
+// (one shared copy of each chunk), so a tile costs as many chunk steps as its
+// deepest sample needs, and in scenarios with partial reference sets every
+// tile holds a few samples that match nothing and visit every chunk while the
+// other lanes idle.  The first pass (batch_kernel) therefore walks at most k0
+// chunks per tile; samples still unresolved then are appended to their
+// scenario's deep queue (a block-wide reservation; a tile whose reservation
+// would overflow the queue keeps walking itself).  The second pass
+// (batch_deep_kernel) takes the queued samples 256 at a time, regenerates
+// their states from Philox, and resumes the walk at chunk k0 with every lane
+// busy.  Labels, counts and gradient counts are the same as one pass would
+// give: the visiting order of the chunks is the same, and a sample is counted
+// once, in the pass that resolves it.  k0 = 0 runs everything in the first
+// pass.  I^L per-bit counts go to a scenario scratch counter; the last block of
+// the second pass converts them into the per-state gradient counts, zeroes the
+// scratch and the queues, resets the work counters and advances the round, so
+// the same two launches can be replayed (e.g. from a CUDA graph) on the next
+// N_s samples of every scenario without any host work.
 #include <cuda_runtime.h>
 
 #include "popc_index.cuh"
@@ -41,15 +55,25 @@ struct Shared {
     unsigned long long cnt[3];
     unsigned int fz;   // I^L samples of the item counted by their zero bits
     int last;
+    long long deep_pos;          // the item's reservation in its scenario's deep queue
+    unsigned int warp_pend[kThreads / 32];
 };
 
+// One item.  First pass (deep == nullptr): samples tile*256 + tid, chunk steps
+// 0 .. k0-1 (all steps if k0 = 0), then the unresolved samples go to the deep
+// queue.  Second pass: the sample whose local index is deep[tid] (none if
+// tid >= n_deep or the entry is negative), chunk steps from k0 on.
 template <int WB>
-__device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, const unsigned long long *s_thr,
-                              uint32_t *s_tw, uint32_t *s_buf, uint32_t *s_cum, const uint32_t *s_hot,
-                              const uint32_t *s_first, const uint32_t *s_zero, uint32_t *s_and, Shared &sh) {
+__device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *deep, int n_deep, uint64_t round,
+                              const unsigned long long *s_thr, uint32_t *s_tw, uint32_t *s_buf, uint32_t *s_cum,
+                              const uint32_t *s_hot, const uint32_t *s_first, const uint32_t *s_zero,
+                              uint32_t *s_and, Shared &sh) {
     const int tid = threadIdx.x, lane = tid & 31;
-    const int64_t hl = tile * kThreads + tid;
-    const bool valid = hl < d.N;
+    const bool second = deep != nullptr;
+    int64_t hl;
+    if (second) hl = tid < n_deep ? deep[tid] : -1;
+    else hl = tile * kThreads + tid;
+    const bool valid = hl >= 0 && hl < d.N;
     const uint32_t key0 = (uint32_t)d.seed, key1 = (uint32_t)(d.seed >> 32);
     // chunk walk; chunk 0 is copied (cp.async) while the item is sampled.  Every
     // thread is past the item's set-up barrier, so both buffers are free.
@@ -61,7 +85,12 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
     ChunkWalk walk(nU, nL, overlap, use_idx);
     bool upper = false;
     int64_t ci = 0;
-    walk.next(&upper, &ci);   // nsteps >= 1: some reference exists
+    // first pass: steps [0, lim); second pass: steps [k0, nsteps) (the walk is replayed up to k0)
+    const int64_t k0 = d.k0 > 0 && (int64_t)d.k0 < nsteps ? (int64_t)d.k0 : nsteps;
+    const int64_t step0 = second ? k0 : 0;
+    int64_t lim = second ? nsteps : k0;
+    for (int64_t i = 0; i < step0; ++i) walk.next(&upper, &ci);
+    walk.next(&upper, &ci);   // step0 < nsteps: some reference exists, and the second pass only runs below nsteps
     auto chunk_refs = [&](bool up, int64_t c, int *cnt_out) {
         const int64_t R = up ? d.R_U : d.R_L;
         const int64_t base = c * kChunk;
@@ -77,7 +106,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
                                        ix ? d.popc_UA + (size_t)c * WB : nullptr, s_and + buf * kMaxWB, rows, cnt_c,
                                        tid);
     };
-    issue(0, upper, ci);
+    issue((int)(step0 & 1), upper, ci);
     // ---- sample and encode (thermometer words, one column per thread) ----
     if (d.km1 == 1) {
         // binary: 32-bit thresholds and never-bits (binary_tables_to_smem) in the s_thr region
@@ -127,10 +156,10 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
 #pragma unroll
     for (int w = 0; w < WB; ++w) t[w] = s_tw[w * kThreads + tid];
 
-    bool mL = false, mU = false, done = !valid;
+    bool mL = false, mU = false, done = !valid, deferred = false;
     // index mode: the most probable upper references first, one by one (not with an
-    // overlapping pair, where every lower chunk has to come first)
-    if (use_idx && !overlap && !done) {
+    // overlapping pair, where every lower chunk has to come first); first pass only
+    if (!second && use_idx && !overlap && !done) {
         const int hotc = (int)(d.R_U < kHot ? d.R_U : kHot);
         for (int r = 0; r < hotc; ++r) {
             uint32_t acc = 0;
@@ -143,9 +172,38 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
             }
         }
     }
-    for (int64_t step = 0; step < nsteps; ++step) {
+    for (int64_t step = step0; step < nsteps; ++step) {
         cp_async_wait_all();                       // this thread's copies of chunk `step`
         if (__syncthreads_and(done)) break;        // chunk `step` visible; chunk step-1 consumed
+        if (step == lim) {
+            // First pass, budget spent: queue the unresolved samples for the second pass.
+            // (An unresolved sample has no match so far: with an overlapping pair a lower
+            // match is final and upper chunks only follow the lower ones.)
+            const bool pend = !done;
+            const unsigned wb = __ballot_sync(0xffffffffu, pend);
+            if (lane == 0) sh.warp_pend[tid >> 5] = (unsigned)__popc(wb);
+            __syncthreads();
+            int before = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const int c = (int)sh.warp_pend[w];
+                before += (w < (tid >> 5)) ? c : 0;
+                total += c;
+            }
+            if (tid == 0) sh.deep_pos = (long long)atomicAdd(d.deep_count, (unsigned long long)total);
+            __syncthreads();
+            const long long pos = sh.deep_pos;
+            if (pos + total <= (long long)d.deep_cap) {
+                if (pend) {
+                    d.deep[pos + before + __popc(wb & ((1u << lane) - 1u))] = hl;
+                    deferred = true;
+                }
+                break;
+            }
+            // the queue is full: void this reservation's slots below the capacity and walk on here
+            for (long long k = tid; k < total && pos + k < (long long)d.deep_cap; k += kThreads) d.deep[pos + k] = -1;
+            lim = nsteps;
+        }
         const int cur_buf = (int)(step & 1);
         uint32_t *s_ref = s_buf + cur_buf * (kChunk * kMaxWB);
         int cnt;
@@ -239,12 +297,14 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         upper = up_next;
         ci = ci_next;
     }
+    cp_async_wait_all();   // the copy of a chunk that a finished walk did not reach
+    const bool final_ = valid && !deferred;   // resolved here (a deferred sample is counted by the second pass)
     const int label = mL ? 0 : (mU ? 1 : 2);
-    if (valid && d.labels) d.labels[hl] = (uint8_t)label;
+    if (final_ && d.labels) d.labels[hl] = (uint8_t)label;
     // counts
-    const unsigned b0 = __ballot_sync(0xffffffffu, valid && label == 0);
-    const unsigned b1 = __ballot_sync(0xffffffffu, valid && label == 1);
-    const unsigned b2 = __ballot_sync(0xffffffffu, valid && label == 2);
+    const unsigned b0 = __ballot_sync(0xffffffffu, final_ && label == 0);
+    const unsigned b1 = __ballot_sync(0xffffffffu, final_ && label == 1);
+    const unsigned b2 = __ballot_sync(0xffffffffu, final_ && label == 2);
     if (lane == 0) {
         if (b0) atomicAdd(&sh.cnt[0], (unsigned long long)__popc(b0));
         if (b1) atomicAdd(&sh.cnt[1], (unsigned long long)__popc(b1));
@@ -254,7 +314,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
     // at most kZeroLanes I^L samples (every warp at 32), 32 ballots per word (one
     // bits) otherwise
     if (d.bitcnt && b0 && __popc(b0) <= kZeroLanes) {
-        if (valid && label == 0) {
+        if (final_ && label == 0) {
             const int kenc = d.n * d.km1;
 #pragma unroll
             for (int w = 0; w < WB; ++w) {
@@ -268,7 +328,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
         }
         if (lane == 0) atomicAdd(&sh.fz, (unsigned)__popc(b0));
     } else if (d.bitcnt && b0) {
-        const bool isL = valid && label == 0;
+        const bool isL = final_ && label == 0;
 #pragma unroll
         for (int w = 0; w < WB; ++w) {
             const uint32_t tw = isL ? t[w] : 0u;
@@ -283,35 +343,42 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, uint64_t round, 
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__restrict__ descs,
-                                                             const int64_t *__restrict__ item_begin, int S,
-                                                             int64_t total_items, BatchHeader *hdr) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Shared sh;
-    __shared__ __align__(16) uint32_t s_zero[kIdxWords];
-    __shared__ uint32_t s_and[2 * kMaxWB];   // AND rows of the staged index chunks
+// Shared-memory carve-up of both passes.
+struct BatchSmem {
+    unsigned long long *thr;   // [512] thresholds (or 32-bit binary tables and never-words)
+    uint32_t *tw, *buf, *cum, *hot, *first;
+};
+
+__device__ __forceinline__ BatchSmem batch_smem(unsigned char *smem) {
+    BatchSmem m;
+    m.thr = reinterpret_cast<unsigned long long *>(smem);          // [512]
+    m.tw = reinterpret_cast<uint32_t *>(smem + 512 * 8);            // [kMaxWB][256]
+    m.buf = m.tw + kMaxWB * kThreads;                               // [2][kChunk * kMaxWB]
+    m.cum = m.buf + 2 * kChunk * kMaxWB;                            // [kMaxWB * 32]
+    m.hot = m.cum + kMaxWB * 32;                                    // [kHot * kMaxWB]
+    m.first = m.hot + kHot * kMaxWB;                                // [kMaxWB]
+    return m;
+}
+
+// The persistent item loop of one pass: items [begin[s], begin[s+1]) belong to
+// scenario s; first pass: item = tile, second pass: item = group of 256 queued
+// samples.  Counts are flushed per item.
+template <bool kSecond>
+__device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__restrict__ begin, int S,
+                          int64_t total_items, unsigned long long *counter, uint64_t round, const BatchSmem &m,
+                          const uint32_t *s_zero, uint32_t *s_and, Shared &sh) {
     const int tid = threadIdx.x;
-    unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);        // [512]
-    uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + 512 * 8);                     // [kMaxWB][256]
-    uint32_t *s_buf = s_tw + kMaxWB * kThreads;                                         // [2][kChunk * kMaxWB]
-    uint32_t *s_cum = s_buf + 2 * kChunk * kMaxWB;                                      // [kMaxWB * 32]
-    uint32_t *s_hot = s_cum + kMaxWB * 32;                                              // [kHot * kMaxWB]
-    uint32_t *s_first = s_hot + kHot * kMaxWB;                                          // [kMaxWB]
-    const uint64_t round = *((volatile unsigned long long *)&hdr->round);
-    if (tid == 0) sh.scenario = -1;
-    if (tid < kIdxWords) s_zero[tid] = 0u;
-    __syncthreads();
     while (true) {
-        if (tid == 0) sh.item = (long long)atomicAdd(&hdr->next_item, 1ull);
+        if (tid == 0) sh.item = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
         const long long item = sh.item;
         if (item >= total_items) break;
-        // scenario of this item: last s with item_begin[s] <= item
+        // scenario of this item: last s with begin[s] <= item
         if (tid == 0) {
             int lo = 0, hi = S - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (item_begin[mid] <= item) lo = mid; else hi = mid - 1;
+                if (begin[mid] <= item) lo = mid; else hi = mid - 1;
             }
             if (lo != sh.scenario) {
                 sh.scenario = lo;
@@ -324,70 +391,142 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
         const BatchDesc &d = sh.d;
         const int nthr = d.n * d.km1;
         if (d.km1 == 1) {
-            uint32_t *s_t32 = reinterpret_cast<uint32_t *>(s_thr);   // [512] + never-words [16]
+            uint32_t *s_t32 = reinterpret_cast<uint32_t *>(m.thr);   // [512] + never-words [16]
             binary_tables_to_smem(d.thr, d.n, s_t32, s_t32 + 512, tid, kThreads);
         } else {
-            for (int i = tid; i < nthr; i += kThreads) s_thr[i] = d.thr[i];
+            for (int i = tid; i < nthr; i += kThreads) m.thr[i] = d.thr[i];
         }
-        for (int j = tid; j < d.words_b * 32; j += kThreads) s_cum[j] = 0u;
+        for (int j = tid; j < d.words_b * 32; j += kThreads) m.cum[j] = 0u;
         if (d.popc_UT) {
             const int hotw = (int)(d.R_U < kHot ? d.R_U : kHot) * d.words_b;
-            for (int i = tid; i < hotw; i += kThreads) s_hot[i] = d.popc_U[i];
-            for (int w = tid; w < d.words_b; w += kThreads) s_first[w] = component_first_bits(d.km1, nthr, w);
+            for (int i = tid; i < hotw; i += kThreads) m.hot[i] = d.popc_U[i];
+            for (int w = tid; w < d.words_b; w += kThreads) m.first[w] = component_first_bits(d.km1, nthr, w);
         }
         __syncthreads();
-        const int64_t tile = item - item_begin[sh.scenario];
-        switch (d.words_b) {
-            case 1: classify_item<1>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
-            case 2: classify_item<2>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
-            case 4: classify_item<4>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
-            case 6: classify_item<6>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
-            case 8: classify_item<8>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
-            case 10: classify_item<10>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
-            case 12: classify_item<12>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
-            default: classify_item<16>(d, tile, round, s_thr, s_tw, s_buf, s_cum, s_hot, s_first, s_zero, s_and, sh); break;
+        const int64_t k = item - begin[sh.scenario];   // tile, or group of queued samples
+        const int64_t *deep = nullptr;
+        int n_deep = 0;
+        if (kSecond) {
+            const int64_t queued = (int64_t)min(*((volatile unsigned long long *)d.deep_count),
+                                                (unsigned long long)d.deep_cap);
+            deep = d.deep + k * kThreads;
+            n_deep = (int)min((int64_t)kThreads, queued - k * kThreads);
         }
+#define RSR_ITEM(WBV) classify_item<WBV>(d, k, deep, n_deep, round, m.thr, m.tw, m.buf, m.cum, m.hot, m.first, s_zero, s_and, sh)
+        switch (d.words_b) {
+            case 1: RSR_ITEM(1); break;
+            case 2: RSR_ITEM(2); break;
+            case 4: RSR_ITEM(4); break;
+            case 6: RSR_ITEM(6); break;
+            case 8: RSR_ITEM(8); break;
+            case 10: RSR_ITEM(10); break;
+            case 12: RSR_ITEM(12); break;
+            default: RSR_ITEM(16); break;
+        }
+#undef RSR_ITEM
         __syncthreads();
         if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);
         if (d.bitcnt && sh.cnt[0]) {
             if (tid == 0) atomicAdd(d.lcount, sh.cnt[0]);
             for (int j = tid; j < nthr; j += kThreads) {
-                const uint32_t ones = s_cum[j] + sh.fz;   // one bits of the item's I^L samples (mod 2^32)
+                const uint32_t ones = m.cum[j] + sh.fz;   // one bits of the item's I^L samples (mod 2^32)
                 if (ones) atomicAdd(&d.bitcnt[j], ones);
             }
         }
         __syncthreads();
     }
-    // ---- the last block converts bit counts to per-state counts and re-arms ----
+}
+
+// True in exactly one thread block, the last of the grid to get here (its
+// threads see every other block's writes).
+__device__ __forceinline__ bool last_block(unsigned int *done_counter, Shared &sh) {
     __threadfence();
     __syncthreads();
-    if (tid == 0) sh.last = (atomicAdd(&hdr->blocks_done, 1u) == gridDim.x - 1) ? 1 : 0;
+    if (threadIdx.x == 0) sh.last = (atomicAdd(done_counter, 1u) == gridDim.x - 1) ? 1 : 0;
     __syncthreads();
-    if (!sh.last) return;
+    if (!sh.last) return false;
     __threadfence();
-    for (int s = 0; s < S; ++s) {
-        const BatchDesc &d = descs[s];
-        if (!d.bitcnt) continue;
-        const unsigned long long F = *((volatile unsigned long long *)d.lcount);
-        if (F) {
-            for (int i = tid; i < d.n; i += kThreads) {
-                long long prev = (long long)F;
-                for (int k = 1; k <= d.km1; ++k) {
-                    const long long cum = (long long)((volatile uint32_t *)d.bitcnt)[i * d.km1 + (k - 1)];
-                    const long long delta = prev - cum;
-                    if (delta) atomicAdd(&d.grad_counts[(size_t)i * d.K + (k - 1)], (unsigned long long)delta);
-                    prev = cum;
-                }
-                if (prev) atomicAdd(&d.grad_counts[(size_t)i * d.K + d.km1], (unsigned long long)prev);
-            }
-        }
-        __syncthreads();
-        for (int j = tid; j < d.n * d.km1; j += kThreads) d.bitcnt[j] = 0u;
-        if (tid == 0) *d.lcount = 0ull;
-    }
+    return true;
+}
+
+// First pass.  Its last block lays out the second pass's items (groups of 256
+// queued samples per scenario) and re-arms the first pass's counters.
+__global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__restrict__ descs,
+                                                             const int64_t *__restrict__ item_begin, int S,
+                                                             int64_t total_items, BatchHeader *hdr,
+                                                             int64_t *deep_begin) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared sh;
+    __shared__ __align__(16) uint32_t s_zero[kIdxWords];
+    __shared__ uint32_t s_and[2 * kMaxWB];   // AND rows of the staged index chunks
+    const int tid = threadIdx.x;
+    const BatchSmem m = batch_smem(smem);
+    const uint64_t round = *((volatile unsigned long long *)&hdr->round);
+    if (tid == 0) sh.scenario = -1;
+    if (tid < kIdxWords) s_zero[tid] = 0u;
+    __syncthreads();
+    item_loop<false>(descs, item_begin, S, total_items, &hdr->next_item, round, m, s_zero, s_and, sh);
+    if (!last_block(&hdr->blocks_done, sh)) return;
     if (tid == 0) {
+        int64_t acc = 0;
+        for (int s = 0; s < S; ++s) {
+            deep_begin[s] = acc;
+            const unsigned long long q = *((volatile unsigned long long *)descs[s].deep_count);
+            const int64_t queued = (int64_t)(q < (unsigned long long)descs[s].deep_cap ? q : descs[s].deep_cap);
+            acc += (queued + kThreads - 1) / kThreads;
+        }
+        deep_begin[S] = acc;
+        hdr->deep_total = acc;
         hdr->next_item = 0ull;
         hdr->blocks_done = 0u;
+        __threadfence();
+    }
+}
+
+// Second pass.  Its last block converts the I^L bit counts to per-state
+// gradient counts, zeroes the scratch and the queues, re-arms its counters and
+// advances the round.
+__global__ void __launch_bounds__(kThreads, 4) batch_deep_kernel(const BatchDesc *__restrict__ descs,
+                                                                  const int64_t *__restrict__ deep_begin, int S,
+                                                                  BatchHeader *hdr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Shared sh;
+    __shared__ __align__(16) uint32_t s_zero[kIdxWords];
+    __shared__ uint32_t s_and[2 * kMaxWB];
+    const int tid = threadIdx.x;
+    const BatchSmem m = batch_smem(smem);
+    const uint64_t round = *((volatile unsigned long long *)&hdr->round);
+    const int64_t total = *((volatile long long *)&hdr->deep_total);
+    if (tid == 0) sh.scenario = -1;
+    if (tid < kIdxWords) s_zero[tid] = 0u;
+    __syncthreads();
+    item_loop<true>(descs, deep_begin, S, total, &hdr->next_deep, round, m, s_zero, s_and, sh);
+    if (!last_block(&hdr->blocks_done2, sh)) return;
+    for (int s = 0; s < S; ++s) {
+        const BatchDesc &d = descs[s];
+        if (d.bitcnt) {
+            const unsigned long long F = *((volatile unsigned long long *)d.lcount);
+            if (F) {
+                for (int i = tid; i < d.n; i += kThreads) {
+                    long long prev = (long long)F;
+                    for (int k = 1; k <= d.km1; ++k) {
+                        const long long cum = (long long)((volatile uint32_t *)d.bitcnt)[i * d.km1 + (k - 1)];
+                        const long long delta = prev - cum;
+                        if (delta) atomicAdd(&d.grad_counts[(size_t)i * d.K + (k - 1)], (unsigned long long)delta);
+                        prev = cum;
+                    }
+                    if (prev) atomicAdd(&d.grad_counts[(size_t)i * d.K + d.km1], (unsigned long long)prev);
+                }
+            }
+            __syncthreads();
+            for (int j = tid; j < d.n * d.km1; j += kThreads) d.bitcnt[j] = 0u;
+            if (tid == 0) *d.lcount = 0ull;
+        }
+        if (tid == 0) *d.deep_count = 0ull;
+    }
+    if (tid == 0) {
+        hdr->next_deep = 0ull;
+        hdr->blocks_done2 = 0u;
         hdr->round = round + 1ull;
     }
 }
@@ -405,16 +544,28 @@ cudaError_t batch_max_grid(int *blocks_per_sm) {
     const size_t smem = batch_kernel_smem();
     cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batch_kernel, kThreads, smem);
+    e = cudaFuncSetAttribute(batch_deep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int a = 0, b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_deep_kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    *blocks_per_sm = a < b ? a : b;
+    return cudaSuccess;
 }
 
-// The shared-memory attribute is set by batch_max_grid() (called when a batch
-// is prepared), so a launch issues nothing but the kernel and can be captured.
+// The shared-memory attributes are set by batch_max_grid() (called when a
+// batch is prepared), so a launch issues nothing but the two kernels and can
+// be captured.  The second pass always runs: it also closes the round.
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
-                         BatchHeader *hdr, int grid, cudaStream_t s) {
+                         BatchHeader *hdr, int64_t *deep_begin, int grid, cudaStream_t s) {
     const size_t smem = batch_kernel_smem();
     if (grid <= 0 || total_items <= 0) return cudaSuccess;
-    batch_kernel<<<grid, kThreads, smem, s>>>(descs, item_begin, S, total_items, hdr);
+    batch_kernel<<<grid, kThreads, smem, s>>>(descs, item_begin, S, total_items, hdr, deep_begin);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_deep_kernel<<<grid, kThreads, smem, s>>>(descs, deep_begin, S, hdr);
     return cudaGetLastError();
 }
 

@@ -22,22 +22,33 @@ struct BatchDesc {
     unsigned long long *grad_counts;     // [n*K] or NULL
     uint32_t *bitcnt;                    // [n*(K-1)] I^L per-bit scratch, or NULL
     unsigned long long *lcount;          // I^L count scratch
+    int64_t *deep;                       // [deep_cap] deep queue: local indices of deferred samples
+    unsigned long long *deep_count;      // samples appended to the queue (may exceed deep_cap)
+    int64_t deep_cap;
+    int32_t k0;                          // chunk steps of the first pass (0 = all)
+    int32_t pad;
 };
 
 // Work counter and round of a batch workspace (256 bytes at its start).
 struct BatchHeader {
-    unsigned long long next_item;
-    unsigned int blocks_done;
-    unsigned int pad;
-    unsigned long long round;       // launches since prepare: sample window index
-    unsigned long long reserved[29];
+    unsigned long long next_item;   // first pass: work counter
+    unsigned int blocks_done;       // first pass: finished blocks
+    unsigned int blocks_done2;      // second pass: finished blocks
+    unsigned long long round;       // launch pairs since prepare: sample window index
+    unsigned long long next_deep;   // second pass: work counter
+    long long deep_total;           // second pass: items (groups of 256 queued samples)
+    unsigned long long reserved[27];
 };
 static_assert(sizeof(BatchHeader) == 256, "batch header is one 256-byte line");
 
 size_t batch_kernel_smem();
 int batch_max_words();
 cudaError_t batch_max_grid(int *blocks_per_sm);
+// Both passes: the tile pass, then the pass over the queued deep samples
+// (deep_begin: workspace int64[S+1], written by the first pass).
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
-                         BatchHeader *hdr, int grid, cudaStream_t s);
+                         BatchHeader *hdr, int64_t *deep_begin, int grid, cudaStream_t s);
+constexpr int64_t kBatchDeepCap = 32768;   // deep-queue entries per scenario
+constexpr int kBatchDefaultK0 = 8;         // first-pass chunk steps before rsr_batch_autotune picks them
 
 }  // namespace rsr

@@ -618,8 +618,9 @@ namespace rsr {
 namespace {
 
 struct BatchLayout {
-    size_t off_descs = 0, off_begin = 0, off_tune = 0, off_table = 0, off_score = 0, off_perm = 0, total = 0;
-    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_pUA, off_bit, off_lc, off_tgrad;
+    size_t off_descs = 0, off_begin = 0, off_deep_begin = 0, off_tune = 0, off_table = 0, off_score = 0,
+           off_perm = 0, total = 0;
+    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_pUA, off_bit, off_lc, off_tgrad, off_deep;
     std::vector<int> words_b;
 };
 
@@ -629,6 +630,8 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
     B.off_descs = off;
     off = align256(off + sizeof(BatchDesc) * (size_t)S);
     B.off_begin = off;
+    off = align256(off + sizeof(int64_t) * (size_t)(S + 1));
+    B.off_deep_begin = off;  // second-pass items per scenario (written by the first pass)
     off = align256(off + sizeof(int64_t) * (size_t)(S + 1));
     B.off_tune = off;  // tuning scratch: counts3 per scenario
     off = align256(off + sizeof(int64_t) * 3 * (size_t)S);
@@ -666,6 +669,8 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
         off = align256(off + 8);
         B.off_tgrad.push_back(off);  // tuning scratch: gradient counts
         off = align256(off + 8 * (size_t)p.n * p.K);
+        B.off_deep.push_back(off);   // deep-queue count (8 bytes) and queue of kBatchDeepCap entries
+        off = align256(off + 8 + 8 * (size_t)kBatchDeepCap);
     }
     B.total = off;
     return B;
@@ -676,6 +681,7 @@ struct BatchPrepared {
     int S;
     int64_t total_items;
     int grid;
+    int k0;                           // first-pass chunk steps (0 = all)
     int device;
     std::vector<BatchDesc> descs;     // the caller's outputs
     std::vector<int64_t> begin;
@@ -824,6 +830,10 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.grad_counts = grad_counts_or_null ? reinterpret_cast<unsigned long long *>(grad_counts_or_null[k]) : nullptr;
         d.bitcnt = d.grad_counts ? reinterpret_cast<uint32_t *>(base + B.off_bit[k]) : nullptr;
         d.lcount = reinterpret_cast<unsigned long long *>(base + B.off_lc[k]);
+        d.deep_count = reinterpret_cast<unsigned long long *>(base + B.off_deep[k]);
+        d.deep = reinterpret_cast<int64_t *>(base + B.off_deep[k] + 8);
+        d.deep_cap = kBatchDeepCap;
+        d.k0 = kBatchDefaultK0;
     }
     std::vector<int64_t> begin;
     int64_t total = 0;
@@ -836,6 +846,7 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
     bp.S = S;
     bp.total_items = total;
     bp.grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)device_sm_count() * occ);
+    bp.k0 = kBatchDefaultK0;
     bp.device = current_device();
     bp.descs = descs;
     bp.begin = begin;
@@ -865,7 +876,8 @@ int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, con
     char *base = static_cast<char *>(ws);
     RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
                           reinterpret_cast<const int64_t *>(base + B.off_begin), S, bp.total_items,
-                          reinterpret_cast<BatchHeader *>(base), bp.grid, reinterpret_cast<cudaStream_t>(stream)));
+                          reinterpret_cast<BatchHeader *>(base), reinterpret_cast<int64_t *>(base + B.off_deep_begin),
+                          bp.grid, reinterpret_cast<cudaStream_t>(stream)));
     return RSR_OK;
 }
 
@@ -907,29 +919,56 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     cudaEvent_t e0, e1;
     RSR_CUDA(cudaEventCreate(&e0));
     RSR_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_grid = bp.grid, best_order = 0;
-    for (int ord = 0; ord < 2; ++ord) {
+    // time one configuration (order, blocks per SM, first-pass chunk steps): the sum of two
+    // timed launch pairs after a warm-up pair
+    auto time_config = [&](int ord, int bps, int k0, float *ms_out, int64_t *grid_out) -> int {
+        for (int k = 0; k < S; ++k) scratch[k].k0 = k0;
         std::vector<int64_t> begin;
         int64_t total = 0;
-        if ((st = upload_schedule(ws, B, scratch, ord ? natural : lpt, begin, total, s)) != RSR_OK) return st;
+        int st2 = upload_schedule(ws, B, scratch, ord ? natural : lpt, begin, total, s);
+        if (st2 != RSR_OK) return st2;
+        const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)sms * bps);
+        float ms_sum = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {
+            RSR_CUDA(cudaEventRecord(e0, s));
+            RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
+                                  reinterpret_cast<const int64_t *>(base + B.off_begin), S, total,
+                                  reinterpret_cast<BatchHeader *>(base),
+                                  reinterpret_cast<int64_t *>(base + B.off_deep_begin), grid, s));
+            RSR_CUDA(cudaEventRecord(e1, s));
+            RSR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            RSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) ms_sum += ms;
+        }
+        *ms_out = ms_sum;
+        *grid_out = grid;
+        return RSR_OK;
+    };
+    float best = 1e30f;
+    int best_grid = bp.grid, best_order = 0, best_k0 = bp.k0;
+    // first the chunk budget of the first pass (longest scenarios first, the full grid) ...
+    static const int kK0[] = {0, 2, 4, 8, 16, 32};
+    for (int k0 : kK0) {
+        float ms = 0.0f;
+        int64_t grid = 0;
+        if ((st = time_config(0, occ, k0, &ms, &grid)) != RSR_OK) return st;
+        if (ms < best) {
+            best = ms;
+            best_k0 = k0;
+            best_grid = (int)grid;
+        }
+    }
+    // ... then the work order and the grid size with that budget
+    for (int ord = 0; ord < 2; ++ord) {
         for (int bps = 1; bps <= occ; bps *= 2) {
-            const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)sms * bps);
-            float ms_sum = 0.0f;
-            for (int rep = 0; rep < 3; ++rep) {
-                RSR_CUDA(cudaEventRecord(e0, s));
-                RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
-                                      reinterpret_cast<const int64_t *>(base + B.off_begin), S, total,
-                                      reinterpret_cast<BatchHeader *>(base), grid, s));
-                RSR_CUDA(cudaEventRecord(e1, s));
-                RSR_CUDA(cudaEventSynchronize(e1));
-                float ms = 0.0f;
-                RSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                if (rep > 0) ms_sum += ms;
-            }
-            if (ms_sum < best) {
-                best = ms_sum;
-                best_grid = grid;
+            if (ord == 0 && bps == occ) continue;   // timed above
+            float ms = 0.0f;
+            int64_t grid = 0;
+            if ((st = time_config(ord, bps, best_k0, &ms, &grid)) != RSR_OK) return st;
+            if (ms < best) {
+                best = ms;
+                best_grid = (int)grid;
                 best_order = ord;
             }
         }
@@ -937,9 +976,11 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // restore the caller's descriptors in the chosen order, reset the round counter
+    std::vector<BatchDesc> tuned = bp.descs;
+    for (int k = 0; k < S; ++k) tuned[k].k0 = best_k0;
     std::vector<int64_t> begin;
     int64_t total = 0;
-    if ((st = upload_schedule(ws, B, bp.descs, best_order ? natural : lpt, begin, total, s)) != RSR_OK) return st;
+    if ((st = upload_schedule(ws, B, tuned, best_order ? natural : lpt, begin, total, s)) != RSR_OK) return st;
     RSR_CUDA(cudaMemsetAsync(base, 0, sizeof(BatchHeader), s));
     for (int k = 0; k < S; ++k) {
         RSR_CUDA(cudaMemsetAsync(base + B.off_lc[k], 0, 8, s));
@@ -949,10 +990,13 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     if (chosen) {
         chosen[0] = best_grid;
         chosen[1] = best_order;
+        chosen[2] = best_k0;
     }
     std::lock_guard<std::mutex> g(g_mu);
     BatchPrepared &ref = g_batches[ws];
     ref.grid = best_grid;
+    ref.k0 = best_k0;
+    ref.descs = tuned;
     ref.total_items = total;
     ref.begin = begin;
     return RSR_OK;

@@ -73,3 +73,19 @@ def deep_refs_problem(n, K, R_L, R_U, seed, lo=8, hi=30):
         idx = rng.choice(n, size=min(n, int(rng.integers(lo, hi + 1))), replace=False)
         ref_U[r, idx] = rng.integers(1, K, size=idx.size)
     return W.Problem("deep_refs", pmf, ref_L, ref_U)
+
+
+def sparse_match_problem(n, R_L, R_U, lo, hi, seed, down=20):
+    """Binary components with P(up) = 1/2; each lower reference needs `down`
+    given components failed (almost never met) and each upper reference a
+    random set of lo..hi given components working, so the samples that match
+    only a large set, or nothing, walk deep into the upper set."""
+    rng = np.random.default_rng(seed)
+    pmf = np.tile([0.5, 0.5], (n, 1))
+    ref_L = np.ones((R_L, n), dtype=np.uint8)
+    for r in range(R_L):
+        ref_L[r, rng.choice(n, size=down, replace=False)] = 0
+    ref_U = np.zeros((R_U, n), dtype=np.uint8)
+    for r in range(R_U):
+        ref_U[r, rng.choice(n, size=int(rng.integers(lo, hi + 1)), replace=False)] = 1
+    return W.Problem("sparse_match", pmf, ref_L, ref_U)

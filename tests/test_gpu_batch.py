@@ -1,13 +1,15 @@
-"""GPU parity of the batched persistent launch (many scenarios, one kernel):
-every scenario's labels, counts and gradient counts equal the single-problem
-path's and the oracle's; replays (direct and from a CUDA graph) advance to the
-next window of samples; autotuning never touches the caller's outputs."""
+"""GPU parity of the batched persistent launches (many scenarios; a tile pass
+and a pass over the queued deep samples): every scenario's labels, counts and
+gradient counts equal the single-problem path's and the oracle's, including a
+scenario whose samples mostly reach the second pass and one that overflows its
+deep queue; replays (direct and from a CUDA graph) advance to the next window
+of samples; autotuning never touches the caller's outputs."""
 import numpy as np
 import pytest
 import torch
 
 import workloads as W
-from helpers import POPC, make_session, random_refs_problem, run
+from helpers import POPC, make_session, random_refs_problem, run, sparse_match_problem
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -18,7 +20,10 @@ def scenarios():
              for n, K, RL, RU in [(50, 2, 20, 40), (300, 2, 300, 700), (120, 3, 40, 1), (17, 2, 1, 1),
                                   (200, 2, 600, 5), (64, 4, 30, 30), (33, 2, 0, 9), (96, 5, 7, 0)]]
     probs.append(W.c1_grid())
-    Ns = [1000, 5000, 257, 1, 3001, 2048, 700, 999, 20000]
+    # 2 + 12 reference chunks; samples that match only large upper references, or
+    # nothing (about 10%), are still unresolved after the first pass's 8 chunks
+    probs.append(sparse_match_problem(80, 300, 3000, 6, 24, seed=5))
+    Ns = [1000, 5000, 257, 1, 3001, 2048, 700, 999, 20000, 40000]
     seeds = [100 + s for s in range(len(probs))]
     offsets = [7 * s for s in range(len(probs))]
     return probs, seeds, offsets, Ns
@@ -92,8 +97,8 @@ def test_batch_replay_and_graph_capture(rsr):
 def test_batch_autotune_leaves_outputs_alone(rsr):
     probs, seeds, offsets, Ns = scenarios()
     b = make_batch(rsr, probs, seeds, offsets, Ns)
-    grid, order = rsr.rsr_batch_autotune(b)
-    assert grid >= 1 and order in (0, 1)
+    grid, order, k0 = rsr.rsr_batch_autotune(b)
+    assert grid >= 1 and order in (0, 1) and k0 in (0, 2, 4, 8, 16, 32)
     torch.cuda.synchronize()
     assert int(b.counts3.abs().sum()) == 0
     assert all(int(t.abs().sum()) == 0 for t in b.grad_counts)
@@ -123,3 +128,26 @@ def test_single_problem_autotune_picks_a_path(rsr):
     X = O.sample(p.pmf, 2, 0, 4096)
     lab, _ = O.classify(X, p.ref_L, p.ref_U)
     assert np.array_equal(got["labels"], lab)
+
+
+def test_batch_deep_queue_overflow_falls_back_to_the_tile(rsr):
+    """A scenario with more unresolved samples after the first pass's chunk
+    budget than its deep queue holds (32768): the tiles that find the queue full
+    finish their walk themselves, and every label and count still equals the
+    oracle's."""
+    probs = [sparse_match_problem(64, 200, 4000, 10, 30, seed=8), random_refs_problem(50, 2, 20, 40, seed=9)]
+    seeds, offsets, Ns = [41, 42], [0, 5], [100000, 3000]
+    b = make_batch(rsr, probs, seeds, offsets, Ns)
+    rsr.rsr_batch(b)
+    torch.cuda.synchronize()
+    counts = b.counts3.cpu().numpy()
+    X = O.sample(probs[0].pmf, seeds[0], offsets[0], Ns[0])
+    lab, cnt = O.classify(X, probs[0].ref_L, probs[0].ref_U)
+    assert cnt[2] > 40000          # far more unresolved samples than one queue holds
+    for s, p in enumerate(probs):
+        if s:
+            X = O.sample(p.pmf, seeds[s], offsets[s], Ns[s])
+            lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+        assert np.array_equal(b.labels[s].cpu().numpy(), lab), s
+        assert np.array_equal(counts[s], cnt), s
+        assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K), O.grad_counts(X, lab, p.K)), s
