@@ -330,7 +330,7 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
     seeds, offsets, Ns = [1000 + s for s in range(S)], [0] * S, [N] * S
     t0 = time.perf_counter()
     b = rsr.Batch(P, seeds, offsets, Ns, labels=True, grad=True)
-    grid, order, k0 = rsr.rsr_batch_autotune(b)
+    grid, order, k0, n_tc = rsr.rsr_batch_autotune(b)
     prep_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
@@ -372,6 +372,16 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
     ev[1].record()
     torch.cuda.synchronize()
     plain_ms = ev[0].elapsed_time(ev[1]) / reps
+    # the same per-scenario launches, each timed by its own events: the sum of kernel
+    # durations, and what is left of plain_ms between them (launch gaps)
+    pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in P]
+    for s_, (p, se) in enumerate(zip(P, sessions)):
+        pev[s_][0].record(cur)
+        rsr.rsr_classify(p, seeds[s_], offsets[s_] + 20 * N, N, se.ws, cnt, None, lab, grads[s_], None, cur)
+        pev[s_][1].record(cur)
+    torch.cuda.synchronize()
+    per_launch = [a.elapsed_time(b_) for a, b_ in pev]
+    kernel_sum_ms = float(sum(per_launch))
     t0 = time.perf_counter()
     for r in range(reps):
         plain(10 + r, True)
@@ -395,10 +405,12 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
     return {"workload": "c5_256_scenarios_N%d" % N, "scenarios": S, "refs_total": int(sum(R)),
             "batched_no_index_ms": no_index_ms,
             "batched_ms": batched_ms, "per_scenario_ms": plain_ms, "speedup_kernels": plain_ms / batched_ms,
+            "per_scenario_kernel_sum_ms": kernel_sum_ms, "per_scenario_gaps_ms": plain_ms - kernel_sum_ms,
+            "per_scenario_launch_ms_max": max(per_launch), "per_scenario_launch_ms_median": statistics.median(per_launch),
             "batched_fwd_grad_round_ms": batched_round_ms, "per_scenario_fwd_grad_round_ms": plain_round_ms,
             "speedup_fwd_grad_round": plain_round_ms / batched_round_ms,
             "samples_per_s": S * N / (batched_ms / 1000.0), "autotune_grid": grid,
-            "autotune_order": "longest-first" if order == 0 else "as-given", "autotune_k0": k0,
+            "autotune_order": "longest-first" if order == 0 else "as-given", "autotune_k0": k0, "autotune_tc_scenarios": n_tc,
             "prepare_s": prep_s}
 
 

@@ -204,11 +204,17 @@ RSR_API int rsr_sample(const rsr_problem *problem, uint64_t seed, uint64_t offse
 RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t stream);
 
 /*
- * Batched launch (many problems, e.g. hazard scenarios, in one persistent
- * kernel).  Arrays of length S describe the scenarios; scenario s classifies
+ * Batched launch (many problems, e.g. hazard scenarios, in persistent
+ * kernels).  Arrays of length S describe the scenarios; scenario s classifies
  * samples offsets[s] + r*Ns[s] .. offsets[s] + (r+1)*Ns[s] - 1 of its own
- * Philox stream (key seeds[s]) on the r-th launch after rsr_batch_prepare
- * (r = 0 first), with the bit-packed test of Algorithm 1 (Sec. 3.3).
+ * Philox stream (key seeds[s]) on the r-th rsr_batch call after
+ * rsr_batch_prepare (r = 0 first), with the test of Algorithm 1 (Sec. 3.3):
+ * on the tensor cores (the CTA-pair FP8 contraction, one persistent launch
+ * over every dense tensor-core scenario's 256-sample blocks) for scenarios in
+ * dense mode whose path is RSR_PATH_TC, or RSR_PATH_AUTO when timing (or,
+ * before rsr_batch_autotune, the reference-count rule of RSR_PATH_AUTO)
+ * picks the tensor cores; on the bit-packed path otherwise (early-exit
+ * scenarios always).
  *   labels_or_null       : host array of S device pointers (N_s uint8 each, NULL entries
  *                          allowed), or NULL.
  *   counts3xS            : device int64[S*3]; counts are ADDED.
@@ -219,20 +225,26 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  * rsr_batch_workspace_size : bytes of the batch workspace (0 on invalid input).
  * rsr_batch_prepare        : thresholds, reference encodings, precedence pre-checks and the work
  *                            list (longest scenarios first) into `ws`; not capturable.
- * rsr_batch                : two persistent kernel launches for the whole batch: every
- *                            (scenario, 256-sample tile) walks at most k0 reference chunks, and
- *                            the samples still unresolved then are queued and finished 256 at a
- *                            time by the second launch (same labels and counts as one walk; a
- *                            full queue leaves its tile to finish the walk itself).  The arguments
- *                            must equal those given to rsr_batch_prepare (else
- *                            RSR_ERR_NOT_PREPARED).  The launches re-arm their own counters, so
- *                            they can be captured once in a CUDA graph and replayed.
- * rsr_batch_autotune       : times the first pass's chunk budget k0 (0 = no second pass, 2, 4, 8,
- *                            16, 32), then work orders and grid sizes, on the prepared batch
- *                            (writing only into the workspace's scratch, never the caller's
- *                            outputs), keeps the fastest for later rsr_batch calls and resets the
- *                            round to 0; chosen[0] = grid, chosen[1] = order (0 = longest first,
- *                            1 = as given), chosen[2] = k0 (8 until tuned).  Synchronises `stream`.
+ * rsr_batch                : the pair-kernel launch (if any scenario runs on the tensor cores),
+ *                            then two bit-packed persistent launches: every (scenario, 256-sample
+ *                            tile) walks at most k0 reference chunks, and the samples still
+ *                            unresolved then are queued and finished 256 at a time by the second
+ *                            launch (same labels and counts as one walk; a full queue leaves its
+ *                            tile to finish the walk itself).  The arguments must equal those given
+ *                            to rsr_batch_prepare (else RSR_ERR_NOT_PREPARED).  The launches re-arm
+ *                            their own counters, so they can be captured once in a CUDA graph and
+ *                            replayed.
+ * rsr_batch_autotune       : first picks the path of every dense RSR_PATH_AUTO scenario by timing
+ *                            the pair kernel and the bit-packed kernel on a slice of its samples
+ *                            (scenarios of one shape share the timing), then times the first
+ *                            pass's chunk budget k0 (0 = no second pass, 2, 4, 8, 16, 32), work
+ *                            orders and grid sizes, on the prepared batch (writing only into the
+ *                            workspace's scratch, never the caller's outputs), keeps the fastest
+ *                            for later rsr_batch calls and resets the round to 0; chosen[0] =
+ *                            grid, chosen[1] = order (0 = longest first, 1 = as given), chosen[2]
+ *                            = k0 (8 until tuned), chosen[3] = scenarios on the tensor cores.
+ *                            Synchronises `stream`.  With RSR_TUNE_CACHE set (see rsr_autotune)
+ *                            the choices are read from and written to the tuning cache.
  */
 RSR_API size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S);
 RSR_API int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
@@ -245,7 +257,7 @@ RSR_API int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *se
 RSR_API int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
                                const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
                                int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws,
-                               size_t ws_bytes, rsr_stream_t stream, int32_t chosen[3]);
+                               size_t ws_bytes, rsr_stream_t stream, int32_t chosen[4]);
 
 /*
  * Gradients of every scenario of a batch from its per-state I^L counts (the
@@ -258,10 +270,16 @@ RSR_API int rsr_batch_grad(const rsr_problem *problems, int32_t S, const int64_t
                            double *const *grad_out, double *const *se_out, rsr_stream_t stream);
 
 /*
- * Time both classifier paths on a 65536-sample slice of `problem` (prepared in
- * `ws`) and remember the faster one for RSR_PATH_AUTO on problems with the
- * same n, K, density flag and reference-count bucket (power of two).
- * *chosen_path receives it.  Synchronises `stream`.
+ * Time both classifier paths on a slice of `problem` (prepared in `ws`; 2^18
+ * samples in dense mode, 2^20 in early-exit mode) and remember the faster one
+ * for RSR_PATH_AUTO on problems with the same n, K, density flag and
+ * reference-count bucket (power of two).  *chosen_path receives it.
+ * Synchronises `stream`.
+ * Tuning cache: when the environment variable RSR_TUNE_CACHE names a file,
+ * decisions (this one, and those of rsr_batch_autotune) are also kept there as
+ * a JSON object {"key": [integers]}, keyed by the device (name and SM count)
+ * and the problem shape, read at the first lookup and rewritten on every new
+ * decision; RSR_PATH_AUTO then uses a cached decision without timing.
  */
 RSR_API int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream,
                          int32_t *chosen_path);

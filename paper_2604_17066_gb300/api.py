@@ -269,13 +269,14 @@ def rsr_batch(batch: Batch, stream=None) -> None:
 
 
 def rsr_batch_autotune(batch: Batch, stream=None):
-    """Tunes the batch's launches; returns (grid, order, k0): blocks of the
-    persistent grid, work order (0 = longest scenarios first, 1 = as given) and
-    the first pass's reference-chunk budget (0 = one pass)."""
-    chosen = np.zeros(3, dtype=np.int32)
+    """Tunes the batch's launches; returns (grid, order, k0, n_tc): blocks of
+    the bit-packed persistent grid, work order (0 = longest scenarios first,
+    1 = as given), the first pass's reference-chunk budget (0 = one pass) and
+    the number of scenarios on the tensor-core pair kernel."""
+    chosen = np.zeros(4, dtype=np.int32)
     check(_lib.load().rsr_batch_autotune(*batch.args(), _stream(stream if stream is not None else batch.stream),
                                          chosen.ctypes.data), "rsr_batch_autotune")
-    return int(chosen[0]), int(chosen[1]), int(chosen[2])
+    return int(chosen[0]), int(chosen[1]), int(chosen[2]), int(chosen[3])
 
 
 def rsr_batch_grad(batch: Batch, stream=None):

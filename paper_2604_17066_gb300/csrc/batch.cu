@@ -561,7 +561,7 @@ cudaError_t batch_max_grid(int *blocks_per_sm) {
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
                          BatchHeader *hdr, int64_t *deep_begin, int grid, cudaStream_t s) {
     const size_t smem = batch_kernel_smem();
-    if (grid <= 0 || total_items <= 0) return cudaSuccess;
+    if (grid <= 0) grid = 1;   // both passes run even without bit-packed items: the second closes the round
     batch_kernel<<<grid, kThreads, smem, s>>>(descs, item_begin, S, total_items, hdr, deep_begin);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -107,31 +107,48 @@ struct PairCtl {
     unsigned long long cnt[3];
 };
 
+// What one launch classifies.  One problem: p0, in pair blocks of 256
+// samples.  A batch (the tensor-core scenarios of rsr_batch): descs[s] per
+// scenario, items [begin[s], begin[s+1]) are its pair blocks, and scenario s
+// classifies samples offset + round*N .. of its stream.
+struct PairWork {
+    const ClassifyParams *descs;           // device, or NULL for one problem
+    const int64_t *begin;                  // device [S+1]
+    const unsigned long long *round;       // device, the batch's round counter
+    int S;
+    int kp_max, nthr_max;                  // widest row and largest threshold table of the launch
+    int64_t total_items;
+};
+
+template <bool kBatch>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-    classify_tc2_kernel(const ClassifyParams p) {
+    classify_tc2_kernel(const ClassifyParams p0, const PairWork wk) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ PairCtl ctl;
+    __shared__ ClassifyParams sp;   // batch: the current scenario (offset moved to its round)
+    __shared__ int s_scen;
+    __shared__ int s_changed;
+    __shared__ long long s_item0;   // batch: first item of the current scenario
     constexpr uint32_t kIdesc = idesc_f8<2 * kRows, kPairRefs>();
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const uint32_t rank = cluster_ctarank();
     const bool leader = rank == 0;
-    const int kp = p.tc_kpad;
-    const int nthr = p.n * p.km1;
-    const PairSmem plan = pair_smem_plan(kp, nthr);
+    const PairSmem plan = pair_smem_plan(wk.kp_max, wk.nthr_max);
     const int S = plan.nstages;
+    const uint32_t stage_stride = (uint32_t)kHalfRefs * wk.kp_max;
     uint8_t *sA = smem + plan.a;
     uint8_t *sStage = smem + plan.stages;
     uint32_t *sTw = reinterpret_cast<uint32_t *>(smem + plan.tw);
     unsigned long long *sThr = reinterpret_cast<unsigned long long *>(smem + plan.thr);
     uint32_t *sCum = reinterpret_cast<uint32_t *>(smem + plan.cum);
     volatile int *abort_flag = &ctl.abort_flag;
-    int32_t *err = &p.hdr->error;
-    const long long budget = p.test_stall ? kTestWaitCycles : kWaitCycles;
+    const ClassifyParams &p = kBatch ? sp : p0;
 
-    for (int i = tid; i < nthr; i += kThreads) sThr[i] = p.thr[i];
-    for (int j = tid; j < kp; j += kThreads) sCum[j] = 0u;
+    if (!kBatch)
+        for (int i = tid; i < p0.n * p0.km1; i += kThreads) sThr[i] = p0.thr[i];
+    for (int j = tid; j < wk.kp_max; j += kThreads) sCum[j] = 0u;
     if (tid == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&ctl.full[s], 1);
@@ -146,6 +163,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         ctl.abort_flag = 0;
         ctl.exec = 0ull;
         ctl.cnt[0] = ctl.cnt[1] = ctl.cnt[2] = 0ull;
+        s_scen = -1;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMmaWarp) {
@@ -157,12 +175,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     cluster_sync();   // both CTAs' barriers are initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem = ctl.tmem_base;
+    const unsigned long long round = kBatch ? *((volatile const unsigned long long *)wk.round) : 0ull;
 
-    const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
-    const int64_t tiles_U = (p.R_U + kPairRefs - 1) / kPairRefs;
-    const int64_t tiles_L = (p.R_L + kPairRefs - 1) / kPairRefs;
-    const int64_t T = tiles_U + tiles_L;
-    const uint32_t half_bytes = (uint32_t)kHalfRefs * kp;
     // the leader's barriers as the peer reaches them
     const uint32_t pfull_at_leader = cluster_map(&ctl.pfull[0], 0);
     const uint32_t tempty_at_leader = cluster_map(&ctl.tempty[0], 0);
@@ -175,10 +189,41 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
     uint32_t acc_phase = 0;
     uint32_t copy_phase = 0u, copy_made = 0u;   // producer: phase of the last copy into each stage
     int64_t g_base = 0;                         // tiles of the earlier blocks (tile g uses stage g mod S, accumulator g mod 2)
-    unsigned long long c0 = 0, c1 = 0, c2 = 0;  // epilogue per-thread totals
 
-    const int64_t npb = (p.N + 2 * kRows - 1) / (2 * kRows);
-    for (int64_t pb = cluster_id_x(); pb < npb; pb += cluster_count_x()) {
+    const int64_t n_items = kBatch ? wk.total_items : (p0.N + 2 * kRows - 1) / (2 * kRows);
+    for (int64_t item = cluster_id_x(); item < n_items; item += cluster_count_x()) {
+        int64_t pb = item;
+        if (kBatch) {
+            // the scenario of this item (the same in both CTAs: both walk the same items)
+            if (tid == 0) {
+                int lo = 0, hi = wk.S - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (wk.begin[mid] <= item) lo = mid; else hi = mid - 1;
+                }
+                s_changed = lo != s_scen;
+                if (s_changed) {
+                    s_scen = lo;
+                    sp = wk.descs[lo];
+                    sp.offset += round * (unsigned long long)sp.N;
+                    s_item0 = wk.begin[lo];
+                }
+            }
+            __syncthreads();
+            if (s_changed) {
+                for (int i = tid; i < sp.n * sp.km1; i += kThreads) sThr[i] = sp.thr[i];
+                __syncthreads();   // the sampler reads the table before its own barrier
+            }
+            pb = item - s_item0;
+        }
+        const int kp = p.tc_kpad;
+        const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
+        const int64_t tiles_U = (p.R_U + kPairRefs - 1) / kPairRefs;
+        const int64_t tiles_L = (p.R_L + kPairRefs - 1) / kPairRefs;
+        const int64_t T = tiles_U + tiles_L;
+        const uint32_t half_bytes = (uint32_t)kHalfRefs * kp;
+        int32_t *err = &p.hdr->error;
+        const long long budget = p.test_stall ? kTestWaitCycles : kWaitCycles;
         const int64_t row0 = pb * (2 * kRows) + (int64_t)rank * kRows;
         sample_a_tile(p, row0, sThr, sTw, sA, kp);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -194,7 +239,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     chunk_at(j, tiles_U, tiles_L, overlap, &up, &ti);
                     const uint8_t *src = (up ? p.tc_U : p.tc_L) + (size_t)(2 * ti + rank) * half_bytes;
                     mbar_arrive_expect_tx(&ctl.full[st_stage], half_bytes);
-                    bulk_g2s(sStage + (size_t)st_stage * half_bytes, src, half_bytes, &ctl.full[st_stage]);
+                    bulk_g2s(sStage + (size_t)st_stage * stage_stride, src, half_bytes, &ctl.full[st_stage]);
                     copy_made |= 1u << st_stage;
                     copy_phase = (copy_phase & ~(1u << st_stage)) | (st_phase << st_stage);
                     if (++st_stage == S) {
@@ -218,7 +263,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                         if (!mbar_wait(&ctl.pfull[st_stage], st_phase, abort_flag, err, budget)) break;
                         if (!mbar_wait(&ctl.tempty[acc_buf], acc_phase ^ 1u, abort_flag, err, budget)) break;
                         tc_fence_after();
-                        const uint32_t b_base = smem_u32(sStage + (size_t)st_stage * half_bytes);
+                        const uint32_t b_base = smem_u32(sStage + (size_t)st_stage * stage_stride);
                         const uint32_t d = tmem + (uint32_t)(acc_buf * kPairRefs);
 #pragma unroll 1
                         for (int kk = 0; kk < kp / 32; ++kk)
@@ -293,11 +338,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 }
             }
             const int lab = mL ? 0 : (mU ? 1 : 2);
-            if (v) {
-                if (p.labels) p.labels[h] = (uint8_t)lab;
-                c0 += lab == 0; c1 += lab == 1; c2 += lab == 2;
-            }
+            if (v && p.labels) p.labels[h] = (uint8_t)lab;
             if (p.grad_counts) count_lower_bits(v && lab == 0, row, lane, sTw, sCum, p.kenc);
+            // the item's label counts
+            unsigned long long c0 = __popc(__ballot_sync(0xffffffffu, v && lab == 0));
+            unsigned long long c1 = __popc(__ballot_sync(0xffffffffu, v && lab == 1));
+            unsigned long long c2 = __popc(__ballot_sync(0xffffffffu, v && lab == 2));
+            if (lane == 0) {
+                if (c0) atomicAdd(&ctl.cnt[0], c0);
+                if (c1) atomicAdd(&ctl.cnt[1], c1);
+                if (c2) atomicAdd(&ctl.cnt[2], c2);
+            }
         }
         if (*abort_flag && lane == 0) {
             if (warp == kProducerWarp) {
@@ -312,26 +363,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         }
         g_base += T;
         __syncthreads();
+        // the item's counts (label counts, executed tests, per-state I^L counts from the
+        // bit counts) go to its problem, and the shared totals start again at zero
+        flush_counts(p, ctl.cnt, ctl.exec, sCum);
+        __syncthreads();
+        if (tid < 3) ctl.cnt[tid] = 0ull;
+        if (tid == 0) ctl.exec = 0ull;
+        for (int j = tid; j < kp; j += kThreads) sCum[j] = 0u;
         cluster_sync();
         // Every role of both CTAs has finished this block, so both abort flags
         // are final here; both CTAs take the same decision.
         if (*abort_flag || ld_cluster_s32(partner_abort)) break;
     }
 
-    // ---- totals -------------------------------------------------------------
-    if (warp >= kEpiWarp0) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            c0 += __shfl_xor_sync(0xffffffffu, c0, o);
-            c1 += __shfl_xor_sync(0xffffffffu, c1, o);
-            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&ctl.cnt[0], c0);
-            atomicAdd(&ctl.cnt[1], c1);
-            atomicAdd(&ctl.cnt[2], c2);
-        }
-    }
     if (warp == kProducerWarp && lane == 0) {
         // the leader's last commits to this CTA's empty barriers have arrived
         for (int s = 0; s < S; ++s)
@@ -344,15 +388,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         tc_fence_after();
         tmem_dealloc_pair(tmem, kTmemCols);
     }
-    flush_counts(p, ctl.cnt, ctl.exec, sCum);
 }
 
 }  // namespace
 
 // Pairs that can be resident at once (one CTA per SM, both CTAs of a pair in
-// one GPC), cached per device together with the shared-memory attribute so
+// one GPC), cached per device together with the shared-memory attributes so
 // that a launch issues nothing but the kernel.
-static cudaError_t pair_limits(int *max_pairs) {
+template <bool kBatch>
+static cudaError_t pair_limits_of(int *max_pairs) {
     static int cached[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -360,20 +404,20 @@ static cudaError_t pair_limits(int *max_pairs) {
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (cached[dev] == 0) {
         cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, classify_tc2_kernel);
+        e = cudaFuncGetAttributes(&fa, classify_tc2_kernel<kBatch>);
         if (e != cudaSuccess) return e;
         int optin = 0;
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         if (e != cudaSuccess) return e;
         const size_t lim = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-        e = cudaFuncSetAttribute(classify_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        e = cudaFuncSetAttribute(classify_tc2_kernel<kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(2 * (unsigned)device_sm_count(), 1, 1);
         cfg.blockDim = dim3(kThreads, 1, 1);
         cfg.dynamicSmemBytes = lim;
         int n = 0;
-        e = cudaOccupancyMaxActiveClusters(&n, classify_tc2_kernel, &cfg);
+        e = cudaOccupancyMaxActiveClusters(&n, classify_tc2_kernel<kBatch>, &cfg);
         if (e != cudaSuccess) return e;
         cached[dev] = n > 0 ? n : -1;
     }
@@ -383,28 +427,49 @@ static cudaError_t pair_limits(int *max_pairs) {
 
 bool tc2_available(int kpad) {
     if (!tc_supported() || kpad > 512 || kpad % 32 != 0) return false;
-    int pairs = 0;
-    if (pair_limits(&pairs) != cudaSuccess) {
+    int pairs = 0, pairs_b = 0;
+    if (pair_limits_of<false>(&pairs) != cudaSuccess || pair_limits_of<true>(&pairs_b) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return pairs > 0 && pair_smem_plan(kpad, 1024).nstages >= 2;
+    return pairs > 0 && pairs_b > 0 && pair_smem_plan(kpad, 1024).nstages >= 2;
 }
+
+// more than half of an SM's shared memory: one CTA per SM
+static size_t pair_smem_bytes(const PairSmem &plan) { return plan.total > 122880u ? plan.total : 122880u; }
 
 cudaError_t launch_classify_tc2(const ClassifyParams &p, cudaStream_t s) {
     if (p.tc_kpad > 512 || p.tc_kpad % 32 != 0) return cudaErrorNotSupported;
     int pairs = 0;
-    cudaError_t e = pair_limits(&pairs);
+    cudaError_t e = pair_limits_of<false>(&pairs);
     if (e != cudaSuccess) return e;
     if (pairs <= 0) return cudaErrorNotSupported;
     const PairSmem plan = pair_smem_plan(p.tc_kpad, p.n * p.km1);
     if (plan.nstages < 2) return cudaErrorNotSupported;
-    // more than half of an SM's shared memory: one CTA per SM
-    const size_t smem = plan.total > 122880u ? plan.total : 122880u;
     const int64_t npb = (p.N + 2 * kRows - 1) / (2 * kRows);
     const int64_t grid_pairs = std::min<int64_t>(npb, (int64_t)pairs);
     if (grid_pairs <= 0) return cudaSuccess;
-    classify_tc2_kernel<<<(unsigned)(2 * grid_pairs), kThreads, smem, s>>>(p);
+    PairWork wk{};
+    wk.kp_max = p.tc_kpad;
+    wk.nthr_max = p.n * p.km1;
+    classify_tc2_kernel<false><<<(unsigned)(2 * grid_pairs), kThreads, pair_smem_bytes(plan), s>>>(p, wk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_tc2_batch(const ClassifyParams *descs, const int64_t *begin, int S, int64_t total_items,
+                                      const unsigned long long *round, int kp_max, int nthr_max, cudaStream_t s) {
+    if (kp_max > 512 || kp_max % 32 != 0) return cudaErrorNotSupported;
+    int pairs = 0;
+    cudaError_t e = pair_limits_of<true>(&pairs);
+    if (e != cudaSuccess) return e;
+    if (pairs <= 0) return cudaErrorNotSupported;
+    const PairSmem plan = pair_smem_plan(kp_max, nthr_max);
+    if (plan.nstages < 2) return cudaErrorNotSupported;
+    const int64_t grid_pairs = std::min<int64_t>(total_items, (int64_t)pairs);
+    if (grid_pairs <= 0) return cudaSuccess;
+    PairWork wk{descs, begin, round, S, kp_max, nthr_max, total_items};
+    ClassifyParams none{};
+    classify_tc2_kernel<true><<<(unsigned)(2 * grid_pairs), kThreads, pair_smem_bytes(plan), s>>>(none, wk);
     return cudaGetLastError();
 }
 

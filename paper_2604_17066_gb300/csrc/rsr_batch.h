@@ -26,7 +26,7 @@ struct BatchDesc {
     unsigned long long *deep_count;      // samples appended to the queue (may exceed deep_cap)
     int64_t deep_cap;
     int32_t k0;                          // chunk steps of the first pass (0 = all)
-    int32_t pad;
+    int32_t path;                        // RSR_PATH_POPC, or RSR_PATH_TC: the scenario runs on the pair kernel
 };
 
 // Work counter and round of a batch workspace (256 bytes at its start).

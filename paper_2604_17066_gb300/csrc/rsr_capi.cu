@@ -5,13 +5,20 @@
 // workspaces, kernel dispatch, and the fp64 estimators (Sec. 3.3 count
 // estimators and c.o.v.; Sec. 3.5 Stage 2) and gradient arithmetic.
 #include <algorithm>
+#include <cctype>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <mutex>
+#include <sstream>
 #include <string>
 #include <unordered_map>
 #include <vector>
+
+#include <unistd.h>
 
 #include <cuda_runtime.h>
 
@@ -66,6 +73,144 @@ int current_device() {
     int d = 0;
     cudaGetDevice(&d);
     return d;
+}
+
+// ---- persistent tuning cache --------------------------------------------------
+// Optional: the environment variable RSR_TUNE_CACHE names a JSON file holding
+// one object {"key": [integers], ...}.  A key names the device (its name and
+// SM count) and a problem shape; the integers are the tuned choices.  The file
+// is read once and rewritten (through a temporary file) on every new decision;
+// a file that does not parse is ignored.
+std::mutex g_cache_mu;
+bool g_cache_loaded = false;
+std::map<std::string, std::vector<long long>> g_cache;
+
+std::string cache_path() {
+    const char *e = std::getenv("RSR_TUNE_CACHE");
+    return e ? std::string(e) : std::string();
+}
+
+bool parse_cache(const std::string &t, std::map<std::string, std::vector<long long>> &out) {
+    size_t i = 0;
+    auto ws = [&]() { while (i < t.size() && std::isspace((unsigned char)t[i])) ++i; };
+    ws();
+    if (i >= t.size() || t[i] != '{') return false;
+    ++i;
+    ws();
+    if (i < t.size() && t[i] == '}') return true;
+    while (i < t.size()) {
+        ws();
+        if (t[i] != '"') return false;
+        const size_t k0 = ++i;
+        while (i < t.size() && t[i] != '"') ++i;
+        if (i >= t.size()) return false;
+        const std::string key = t.substr(k0, i - k0);
+        ++i;
+        ws();
+        if (i >= t.size() || t[i] != ':') return false;
+        ++i;
+        ws();
+        if (i >= t.size() || t[i] != '[') return false;
+        ++i;
+        std::vector<long long> v;
+        while (true) {
+            ws();
+            if (i < t.size() && t[i] == ']') { ++i; break; }
+            char *end = nullptr;
+            const long long x = std::strtoll(t.c_str() + i, &end, 10);
+            if (end == t.c_str() + i) return false;
+            v.push_back(x);
+            i = (size_t)(end - t.c_str());
+            ws();
+            if (i < t.size() && t[i] == ',') ++i;
+        }
+        out[key] = v;
+        ws();
+        if (i < t.size() && t[i] == ',') { ++i; continue; }
+        if (i < t.size() && t[i] == '}') return true;
+        return false;
+    }
+    return false;
+}
+
+bool cache_get(const std::string &key, std::vector<long long> *v) {
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    if (!g_cache_loaded) {
+        g_cache_loaded = true;
+        const std::string path = cache_path();
+        if (!path.empty()) {
+            std::ifstream f(path);
+            if (f) {
+                std::stringstream ss;
+                ss << f.rdbuf();
+                std::map<std::string, std::vector<long long>> m;
+                if (parse_cache(ss.str(), m)) g_cache = m;
+            }
+        }
+    }
+    auto it = g_cache.find(key);
+    if (it == g_cache.end()) return false;
+    *v = it->second;
+    return true;
+}
+
+void cache_put(const std::string &key, const std::vector<long long> &v) {
+    std::vector<long long> dummy;
+    (void)cache_get(key, &dummy);   // load first, so that earlier entries are kept
+    std::lock_guard<std::mutex> g(g_cache_mu);
+    g_cache[key] = v;
+    const std::string path = cache_path();
+    if (path.empty()) return;
+    const std::string tmp = path + ".tmp" + std::to_string((long long)getpid());
+    {
+        std::ofstream f(tmp);
+        if (!f) return;
+        f << "{";
+        bool first = true;
+        for (const auto &kv : g_cache) {
+            f << (first ? "\n  \"" : ",\n  \"") << kv.first << "\": [";
+            for (size_t j = 0; j < kv.second.size(); ++j) f << (j ? ", " : "") << kv.second[j];
+            f << "]";
+            first = false;
+        }
+        f << "\n}\n";
+    }
+    std::rename(tmp.c_str(), path.c_str());
+}
+
+// "<device name>/<SM count>" of the current device.
+std::string device_tag() {
+    static std::string tags[64];
+    const int d = current_device();
+    if (d >= 0 && d < 64 && !tags[d].empty()) return tags[d];
+    cudaDeviceProp prop;
+    std::string t = "unknown";
+    if (cudaGetDeviceProperties(&prop, d) == cudaSuccess) {
+        t = prop.name;
+        for (char &c : t)
+            if (c == '"' || c == '\\') c = '_';
+        t += "/" + std::to_string(prop.multiProcessorCount);
+    } else {
+        (void)cudaGetLastError();
+    }
+    if (d >= 0 && d < 64) tags[d] = t;
+    return t;
+}
+
+std::string path_cache_key(const rsr_problem *p) {
+    int64_t R = p->R_L + p->R_U;
+    int bucket = 0;
+    while ((int64_t(1) << bucket) < R) ++bucket;
+    return "path/" + device_tag() + "/n" + std::to_string(p->n) + "/K" + std::to_string(p->K) + "/f" +
+           std::to_string(p->flags & (RSR_FLAG_DENSE | RSR_FLAG_NO_INDEX)) + "/r" + std::to_string(bucket);
+}
+
+void remember_path(const rsr_problem *p, int path) {
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_tuned[tune_key(p)] = path;
+    }
+    cache_put(path_cache_key(p), {path});
 }
 
 int validate(const rsr_problem *p) {
@@ -147,6 +292,13 @@ int choose_path(const rsr_problem *p) {
         std::lock_guard<std::mutex> g(g_mu);
         auto it = g_tuned.find(tune_key(p));
         if (it != g_tuned.end()) return it->second;
+    }
+    std::vector<long long> cached;
+    if (cache_get(path_cache_key(p), &cached) && cached.size() == 1 &&
+        (cached[0] == RSR_PATH_POPC || cached[0] == RSR_PATH_TC)) {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_tuned[tune_key(p)] = (int)cached[0];
+        return (int)cached[0];
     }
     const WsLayout L = layout_of(p);
     if (tc_supported() && L.tc_kpad <= tc_max_kpad() && (p->R_L + p->R_U) >= 8192 && (p->flags & RSR_FLAG_DENSE))
@@ -618,11 +770,20 @@ namespace rsr {
 namespace {
 
 struct BatchLayout {
-    size_t off_descs = 0, off_begin = 0, off_deep_begin = 0, off_tune = 0, off_table = 0, off_score = 0,
-           off_perm = 0, total = 0;
+    size_t off_descs = 0, off_begin = 0, off_deep_begin = 0, off_tc_descs = 0, off_tc_begin = 0, off_tune = 0,
+           off_table = 0, off_score = 0, off_perm = 0, total = 0;
     std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_pUA, off_bit, off_lc, off_tgrad, off_deep;
-    std::vector<int> words_b;
+    std::vector<size_t> off_tcL, off_tcU;   // FP8 tiles of the scenarios that may run on the pair kernel (else 0)
+    std::vector<int> words_b, tc_kpad;
 };
+
+// Scenarios that may run on the tensor-core pair kernel inside a batch: dense
+// mode, path RSR_PATH_TC or RSR_PATH_AUTO, rows of at most 512 bytes.  (An
+// early-exit scenario always takes the bit-packed batch path.)
+bool batch_tc_eligible(const rsr_problem &p) {
+    return (p.flags & RSR_FLAG_DENSE) && (p.path == RSR_PATH_TC || p.path == RSR_PATH_AUTO) &&
+           layout_of(&p).tc_kpad <= 512;
+}
 
 BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
     BatchLayout B;
@@ -632,6 +793,10 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
     B.off_begin = off;
     off = align256(off + sizeof(int64_t) * (size_t)(S + 1));
     B.off_deep_begin = off;  // second-pass items per scenario (written by the first pass)
+    off = align256(off + sizeof(int64_t) * (size_t)(S + 1));
+    B.off_tc_descs = off;    // launch parameters of the tensor-core scenarios
+    off = align256(off + sizeof(ClassifyParams) * (size_t)S);
+    B.off_tc_begin = off;    // their first pair block in the pair kernel's item list
     off = align256(off + sizeof(int64_t) * (size_t)(S + 1));
     B.off_tune = off;  // tuning scratch: counts3 per scenario
     off = align256(off + sizeof(int64_t) * 3 * (size_t)S);
@@ -671,6 +836,17 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
         off = align256(off + 8 * (size_t)p.n * p.K);
         B.off_deep.push_back(off);   // deep-queue count (8 bytes) and queue of kBatchDeepCap entries
         off = align256(off + 8 + 8 * (size_t)kBatchDeepCap);
+        const WsLayout L = layout_of(&p);
+        B.tc_kpad.push_back(L.tc_kpad);
+        if (batch_tc_eligible(p)) {
+            B.off_tcL.push_back(off);
+            off = align256(off + (size_t)L.tc_rows_L * L.tc_kpad);
+            B.off_tcU.push_back(off);
+            off = align256(off + (size_t)L.tc_rows_U * L.tc_kpad);
+        } else {
+            B.off_tcL.push_back(0);
+            B.off_tcU.push_back(0);
+        }
     }
     B.total = off;
     return B;
@@ -685,6 +861,9 @@ struct BatchPrepared {
     int device;
     std::vector<BatchDesc> descs;     // the caller's outputs
     std::vector<int64_t> begin;
+    std::vector<ClassifyParams> tcp;  // per scenario: pair-kernel parameters (used where descs[s].path == TC)
+    int n_tc = 0, tc_kp_max = 0, tc_nthr_max = 0;
+    int64_t tc_total = 0;             // pair blocks of the tensor-core scenarios
 };
 std::unordered_map<const void *, BatchPrepared> g_batches;
 
@@ -736,12 +915,48 @@ int upload_schedule(void *ws, const BatchLayout &B, const std::vector<BatchDesc>
     for (int k = 0; k < S; ++k) {
         ordered[k] = descs[order[k]];
         begin[k] = total;
-        total += (ordered[k].N + 255) / 256;
+        if (ordered[k].path != RSR_PATH_TC) total += (ordered[k].N + 255) / 256;   // pair-kernel scenarios: none
     }
     begin[S] = total;
     char *base = static_cast<char *>(ws);
     RSR_CUDA(cudaMemcpyAsync(base + B.off_descs, ordered.data(), sizeof(BatchDesc) * S, cudaMemcpyHostToDevice, s));
     RSR_CUDA(cudaMemcpyAsync(base + B.off_begin, begin.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    return RSR_OK;
+}
+
+// The pair kernel's item list: the tensor-core scenarios, most work first
+// (pair blocks x reference tiles), each with ceil(N/256) pair blocks.
+int upload_tc_schedule(void *ws, const BatchLayout &B, BatchPrepared &bp, cudaStream_t s) {
+    std::vector<int> tc;
+    for (int k = 0; k < bp.S; ++k)
+        if (bp.descs[k].path == RSR_PATH_TC) tc.push_back(k);
+    auto work = [&](int k) {
+        const ClassifyParams &c = bp.tcp[k];
+        return (double)((c.N + 255) / 256) * (double)((c.R_L + 255) / 256 + (c.R_U + 255) / 256);
+    };
+    std::stable_sort(tc.begin(), tc.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<ClassifyParams> ordered;
+    std::vector<int64_t> begin;
+    int64_t total = 0;
+    bp.tc_kp_max = 0;
+    bp.tc_nthr_max = 0;
+    for (int k : tc) {
+        ordered.push_back(bp.tcp[k]);
+        begin.push_back(total);
+        total += (bp.tcp[k].N + 255) / 256;
+        bp.tc_kp_max = std::max(bp.tc_kp_max, bp.tcp[k].tc_kpad);
+        bp.tc_nthr_max = std::max(bp.tc_nthr_max, bp.tcp[k].n * bp.tcp[k].km1);
+    }
+    begin.push_back(total);
+    bp.n_tc = (int)tc.size();
+    bp.tc_total = total;
+    char *base = static_cast<char *>(ws);
+    if (!tc.empty()) {
+        RSR_CUDA(cudaMemcpyAsync(base + B.off_tc_descs, ordered.data(), sizeof(ClassifyParams) * ordered.size(),
+                                 cudaMemcpyHostToDevice, s));
+        RSR_CUDA(cudaMemcpyAsync(base + B.off_tc_begin, begin.data(), sizeof(int64_t) * begin.size(),
+                                 cudaMemcpyHostToDevice, s));
+    }
     return RSR_OK;
 }
 
@@ -780,6 +995,7 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
     char *base = static_cast<char *>(ws);
     RSR_CUDA(cudaMemsetAsync(base, 0, B.total, s));
     std::vector<BatchDesc> descs(S);
+    std::vector<ClassifyParams> tcp(S);
     for (int k = 0; k < S; ++k) {
         const rsr_problem &p = problems[k];
         const int km1 = p.K - 1;
@@ -796,12 +1012,20 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         // the previous scenario's encodes read the shared scratch: the ordering below syncs first
         RSR_CUDA(cudaStreamSynchronize(s));
         RSR_CUDA(cudaMemcpyAsync(d_table, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s));
+        const WsLayout Lk = layout_of(&p);
+        const bool tc_enc = B.off_tcL[k] != 0 && tc2_available(Lk.tc_kpad);
         if ((st = order_references(p.ref_L, p.R_L, p.n, p.K, d_table, d_score, d_perm, s)) != RSR_OK) return st;
         RSR_CUDA(launch_encode_popc(p.ref_L, p.R_L, p.n, km1, B.words_b[k], true, pL, s, d_perm));
+        if (tc_enc)
+            RSR_CUDA(launch_encode_tc(p.ref_L, p.R_L, Lk.tc_rows_L, p.n, km1, Lk.tc_kpad, false,
+                                      reinterpret_cast<uint8_t *>(base + B.off_tcL[k]), s, d_perm));
         if ((st = order_references(p.ref_U, p.R_U, p.n, p.K, d_table + (size_t)p.n * p.K, d_score, d_perm, s)) !=
             RSR_OK)
             return st;
         RSR_CUDA(launch_encode_popc(p.ref_U, p.R_U, p.n, km1, B.words_b[k], false, pU, s, d_perm));
+        if (tc_enc)
+            RSR_CUDA(launch_encode_tc(p.ref_U, p.R_U, Lk.tc_rows_U, p.n, km1, Lk.tc_kpad, true,
+                                      reinterpret_cast<uint8_t *>(base + B.off_tcU[k]), s, d_perm));
         uint32_t *pUT = reinterpret_cast<uint32_t *>(base + B.off_pUT[k]);
         uint32_t *pUA = reinterpret_cast<uint32_t *>(base + B.off_pUA[k]);
         if ((st = build_upper_index(&p, pU, p.R_U, B.words_b[k], reinterpret_cast<uint32_t *>(d_score), d_perm, pUT,
@@ -834,6 +1058,32 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.deep = reinterpret_cast<int64_t *>(base + B.off_deep[k] + 8);
         d.deep_cap = kBatchDeepCap;
         d.k0 = kBatchDefaultK0;
+        // pair-kernel parameters (dense); the path: RSR_PATH_TC where asked for, a tuned
+        // decision for RSR_PATH_AUTO (else the reference-count rule of choose_path)
+        ClassifyParams c{};
+        if (tc_enc) {
+            c.n = p.n;
+            c.K = p.K;
+            c.km1 = km1;
+            c.kenc = p.n * km1;
+            c.words = B.words_b[k];
+            c.N = Ns[k];
+            c.seed = seeds[k];
+            c.offset = offsets[k];
+            c.thr = d.thr;
+            c.tc_L = reinterpret_cast<const uint8_t *>(base + B.off_tcL[k]);
+            c.tc_U = reinterpret_cast<const uint8_t *>(base + B.off_tcU[k]);
+            c.R_L = p.R_L;
+            c.R_U = p.R_U;
+            c.tc_kpad = Lk.tc_kpad;
+            c.labels = d.labels;
+            c.counts3 = d.counts3;
+            c.grad_counts = d.grad_counts;
+            c.hdr = hs;
+            c.dense = 1;
+        }
+        tcp[k] = c;
+        d.path = (tc_enc && choose_path(&p) == RSR_PATH_TC) ? RSR_PATH_TC : RSR_PATH_POPC;
     }
     std::vector<int64_t> begin;
     int64_t total = 0;
@@ -850,6 +1100,8 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
     bp.device = current_device();
     bp.descs = descs;
     bp.begin = begin;
+    bp.tcp = tcp;
+    if ((st = upload_tc_schedule(ws, B, bp, s)) != RSR_OK) return st;
     std::lock_guard<std::mutex> g(g_mu);
     g_batches[ws] = bp;
     return RSR_OK;
@@ -874,10 +1126,18 @@ int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, con
         bp.device != current_device())
         return RSR_ERR_NOT_PREPARED;
     char *base = static_cast<char *>(ws);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // the dense scenarios assigned to the tensor cores first (they read the round before
+    // the bit-packed passes close it), then the two bit-packed passes
+    if (bp.n_tc > 0)
+        RSR_CUDA(launch_classify_tc2_batch(reinterpret_cast<const ClassifyParams *>(base + B.off_tc_descs),
+                                           reinterpret_cast<const int64_t *>(base + B.off_tc_begin), bp.n_tc,
+                                           bp.tc_total, &reinterpret_cast<BatchHeader *>(base)->round, bp.tc_kp_max,
+                                           bp.tc_nthr_max, s));
     RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
                           reinterpret_cast<const int64_t *>(base + B.off_begin), S, bp.total_items,
                           reinterpret_cast<BatchHeader *>(base), reinterpret_cast<int64_t *>(base + B.off_deep_begin),
-                          bp.grid, reinterpret_cast<cudaStream_t>(stream)));
+                          bp.grid, s));
     return RSR_OK;
 }
 
@@ -901,7 +1161,77 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
         return RSR_ERR_NOT_PREPARED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
-    // tuning runs write into the workspace's own scratch, never the caller's outputs
+    cudaEvent_t e0, e1;
+    RSR_CUDA(cudaEventCreate(&e0));
+    RSR_CUDA(cudaEventCreate(&e1));
+    auto timed = [&](auto &&launch, float *ms_out) -> int {
+        float sum = 0.0f;
+        for (int rep = 0; rep < 3; ++rep) {   // the first launch warms up
+            RSR_CUDA(cudaEventRecord(e0, s));
+            RSR_CUDA(launch());
+            RSR_CUDA(cudaEventRecord(e1, s));
+            RSR_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            RSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) sum += ms;
+        }
+        *ms_out = sum;
+        return RSR_OK;
+    };
+    // 1. The path of every dense scenario that leaves it open (RSR_PATH_AUTO): the pair kernel
+    //    or the bit-packed kernel, timed on a slice of up to 2^17 of its samples; problems of
+    //    one shape (n, K, flags, reference-count bucket) share the decision, which the
+    //    persistent cache keeps.  Tuning runs count into the workspace's scratch only.
+    unsigned long long *tune_counts = reinterpret_cast<unsigned long long *>(base + B.off_tune);
+    for (int k = 0; k < S; ++k) {
+        const rsr_problem &p = problems[k];
+        if (p.path != RSR_PATH_AUTO || bp.tcp[k].tc_L == nullptr) continue;
+        int path = -1;
+        {
+            std::lock_guard<std::mutex> g(g_mu);
+            auto it = g_tuned.find(tune_key(&p));
+            if (it != g_tuned.end()) path = it->second;
+        }
+        std::vector<long long> cached;
+        if (path < 0 && cache_get(path_cache_key(&p), &cached) && cached.size() == 1) path = (int)cached[0];
+        if (path != RSR_PATH_POPC && path != RSR_PATH_TC) {
+            const int64_t slice = std::max<int64_t>(1, std::min<int64_t>(Ns[k], int64_t(1) << 17));
+            ClassifyParams pc{};
+            pc.n = p.n;
+            pc.K = p.K;
+            pc.km1 = p.K - 1;
+            pc.kenc = p.n * (p.K - 1);
+            pc.words = B.words_b[k];
+            pc.N = slice;
+            pc.seed = 0x5EEDull;
+            pc.thr = bp.descs[k].thr;
+            pc.popc_L = bp.descs[k].popc_L;
+            pc.popc_U = bp.descs[k].popc_U;
+            pc.popc_UT = bp.descs[k].popc_UT;
+            pc.popc_UA = bp.descs[k].popc_UA;
+            pc.R_L = p.R_L;
+            pc.R_U = p.R_U;
+            pc.tc_kpad = B.tc_kpad[k];
+            pc.counts3 = tune_counts;
+            pc.hdr = reinterpret_cast<WsHeader *>(base + B.off_hdr[k]);
+            pc.dense = 1;
+            ClassifyParams tcp = bp.tcp[k];
+            tcp.N = slice;
+            tcp.seed = 0x5EEDull;
+            tcp.offset = 0;
+            tcp.labels = nullptr;
+            tcp.grad_counts = nullptr;
+            tcp.counts3 = tune_counts;
+            float t_popc = 0.0f, t_tc = 0.0f;
+            if ((st = timed([&]() { return launch_classify_popc(pc, s); }, &t_popc)) != RSR_OK) return st;
+            if ((st = timed([&]() { return launch_classify_tc2(tcp, s); }, &t_tc)) != RSR_OK) return st;
+            path = t_tc < t_popc ? RSR_PATH_TC : RSR_PATH_POPC;
+            remember_path(&p, path);
+        }
+        bp.descs[k].path = path;
+    }
+    // tuning runs of the batched launches write into the workspace's own scratch, never the
+    // caller's outputs
     std::vector<BatchDesc> scratch = bp.descs;
     for (int k = 0; k < S; ++k) {
         scratch[k].labels = nullptr;
@@ -916,81 +1246,90 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     std::vector<int> natural(S);
     for (int k = 0; k < S; ++k) natural[k] = k;
     const std::vector<int> lpt = lpt_order(bp.descs);
-    cudaEvent_t e0, e1;
-    RSR_CUDA(cudaEventCreate(&e0));
-    RSR_CUDA(cudaEventCreate(&e1));
-    // time one configuration (order, blocks per SM, first-pass chunk steps): the sum of two
-    // timed launch pairs after a warm-up pair
-    auto time_config = [&](int ord, int bps, int k0, float *ms_out, int64_t *grid_out) -> int {
-        for (int k = 0; k < S; ++k) scratch[k].k0 = k0;
-        std::vector<int64_t> begin;
-        int64_t total = 0;
-        int st2 = upload_schedule(ws, B, scratch, ord ? natural : lpt, begin, total, s);
-        if (st2 != RSR_OK) return st2;
-        const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)sms * bps);
-        float ms_sum = 0.0f;
-        for (int rep = 0; rep < 3; ++rep) {
-            RSR_CUDA(cudaEventRecord(e0, s));
-            RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
-                                  reinterpret_cast<const int64_t *>(base + B.off_begin), S, total,
-                                  reinterpret_cast<BatchHeader *>(base),
-                                  reinterpret_cast<int64_t *>(base + B.off_deep_begin), grid, s));
-            RSR_CUDA(cudaEventRecord(e1, s));
-            RSR_CUDA(cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            RSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (rep > 0) ms_sum += ms;
-        }
-        *ms_out = ms_sum;
-        *grid_out = grid;
-        return RSR_OK;
-    };
-    float best = 1e30f;
-    int best_grid = bp.grid, best_order = 0, best_k0 = bp.k0;
-    // first the chunk budget of the first pass (longest scenarios first, the full grid) ...
-    static const int kK0[] = {0, 2, 4, 8, 16, 32};
-    for (int k0 : kK0) {
-        float ms = 0.0f;
-        int64_t grid = 0;
-        if ((st = time_config(0, occ, k0, &ms, &grid)) != RSR_OK) return st;
-        if (ms < best) {
-            best = ms;
-            best_k0 = k0;
-            best_grid = (int)grid;
-        }
+    // 2. The bit-packed passes: the first pass's chunk budget k0, then the work order and the
+    //    grid size.  A batch of the same shapes on this device reuses the cached choice.
+    uint64_t shape = 1469598103934665603ull;
+    for (int k = 0; k < S; ++k) {
+        const rsr_problem &p = problems[k];
+        const int64_t v[7] = {p.n, p.K, p.R_L, p.R_U, (int64_t)(p.flags & (RSR_FLAG_DENSE | RSR_FLAG_NO_INDEX)),
+                              Ns[k], bp.descs[k].path};
+        shape = fnv1a(v, sizeof(v), shape);
     }
-    // ... then the work order and the grid size with that budget
-    for (int ord = 0; ord < 2; ++ord) {
-        for (int bps = 1; bps <= occ; bps *= 2) {
-            if (ord == 0 && bps == occ) continue;   // timed above
+    char hex[32];
+    snprintf(hex, sizeof(hex), "%016llx", (unsigned long long)shape);
+    const std::string batch_key = "batch/" + device_tag() + "/S" + std::to_string(S) + "/" + hex;
+    int best_grid = bp.grid, best_order = 0, best_k0 = bp.k0;
+    std::vector<long long> cached;
+    if (cache_get(batch_key, &cached) && cached.size() == 3 && cached[0] >= 1 && (cached[1] == 0 || cached[1] == 1) &&
+        cached[2] >= 0) {
+        best_grid = (int)cached[0];
+        best_order = (int)cached[1];
+        best_k0 = (int)cached[2];
+    } else {
+        auto time_config = [&](int ord, int bps, int k0, float *ms_out, int64_t *grid_out) -> int {
+            for (int k = 0; k < S; ++k) scratch[k].k0 = k0;
+            std::vector<int64_t> begin;
+            int64_t total = 0;
+            int st2 = upload_schedule(ws, B, scratch, ord ? natural : lpt, begin, total, s);
+            if (st2 != RSR_OK) return st2;
+            const int grid = (int)std::min<int64_t>(std::max<int64_t>(total, 1), (int64_t)sms * bps);
+            *grid_out = grid;
+            return timed([&]() {
+                return launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
+                                    reinterpret_cast<const int64_t *>(base + B.off_begin), S, total,
+                                    reinterpret_cast<BatchHeader *>(base),
+                                    reinterpret_cast<int64_t *>(base + B.off_deep_begin), grid, s);
+            }, ms_out);
+        };
+        float best = 1e30f;
+        static const int kK0[] = {0, 2, 4, 8, 16, 32};
+        for (int k0 : kK0) {
             float ms = 0.0f;
             int64_t grid = 0;
-            if ((st = time_config(ord, bps, best_k0, &ms, &grid)) != RSR_OK) return st;
+            if ((st = time_config(0, occ, k0, &ms, &grid)) != RSR_OK) return st;
             if (ms < best) {
                 best = ms;
+                best_k0 = k0;
                 best_grid = (int)grid;
-                best_order = ord;
             }
         }
+        for (int ord = 0; ord < 2; ++ord) {
+            for (int bps = 1; bps <= occ; bps *= 2) {
+                if (ord == 0 && bps == occ) continue;   // timed above
+                float ms = 0.0f;
+                int64_t grid = 0;
+                if ((st = time_config(ord, bps, best_k0, &ms, &grid)) != RSR_OK) return st;
+                if (ms < best) {
+                    best = ms;
+                    best_grid = (int)grid;
+                    best_order = ord;
+                }
+            }
+        }
+        cache_put(batch_key, {best_grid, best_order, best_k0});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    // restore the caller's descriptors in the chosen order, reset the round counter
+    // the caller's descriptors with the chosen paths and k0, in the chosen order; round 0
     std::vector<BatchDesc> tuned = bp.descs;
     for (int k = 0; k < S; ++k) tuned[k].k0 = best_k0;
     std::vector<int64_t> begin;
     int64_t total = 0;
     if ((st = upload_schedule(ws, B, tuned, best_order ? natural : lpt, begin, total, s)) != RSR_OK) return st;
+    bp.descs = tuned;
+    if ((st = upload_tc_schedule(ws, B, bp, s)) != RSR_OK) return st;
     RSR_CUDA(cudaMemsetAsync(base, 0, sizeof(BatchHeader), s));
     for (int k = 0; k < S; ++k) {
         RSR_CUDA(cudaMemsetAsync(base + B.off_lc[k], 0, 8, s));
         RSR_CUDA(cudaMemsetAsync(base + B.off_bit[k], 0, 4 * (size_t)problems[k].n * (problems[k].K - 1), s));
+        RSR_CUDA(cudaMemsetAsync(base + B.off_deep[k], 0, 8, s));
     }
     RSR_CUDA(cudaStreamSynchronize(s));
     if (chosen) {
         chosen[0] = best_grid;
         chosen[1] = best_order;
         chosen[2] = best_k0;
+        chosen[3] = bp.n_tc;
     }
     std::lock_guard<std::mutex> g(g_mu);
     BatchPrepared &ref = g_batches[ws];
@@ -999,6 +1338,10 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     ref.descs = tuned;
     ref.total_items = total;
     ref.begin = begin;
+    ref.n_tc = bp.n_tc;
+    ref.tc_total = bp.tc_total;
+    ref.tc_kp_max = bp.tc_kp_max;
+    ref.tc_nthr_max = bp.tc_nthr_max;
     return RSR_OK;
 }
 
@@ -1079,10 +1422,7 @@ int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stre
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    {
-        std::lock_guard<std::mutex> g(g_mu);
-        g_tuned[tune_key(problem)] = best_path;
-    }
+    remember_path(problem, best_path);
     if (chosen_path) *chosen_path = best_path;
     return RSR_OK;
 }

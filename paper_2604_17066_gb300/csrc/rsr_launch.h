@@ -40,6 +40,10 @@ cudaError_t launch_encode_tc(const uint8_t *refs, int64_t R, int64_t rows_padded
 cudaError_t launch_classify_tc(const ClassifyParams &p, cudaStream_t s);   // dense: the pair kernel below
 cudaError_t launch_classify_tc2(const ClassifyParams &p, cudaStream_t s);  // dense, CTA pairs (cta_group::2)
 bool tc2_available(int kpad);   // the pair kernel runs on this device for rows of kpad bytes
+// The tensor-core scenarios of a batch on the pair kernel: items [begin[s], begin[s+1]) are
+// scenario s's pair blocks of 256 samples; descs[s].offset is moved by round*N.
+cudaError_t launch_classify_tc2_batch(const ClassifyParams *descs, const int64_t *begin, int S, int64_t total_items,
+                                      const unsigned long long *round, int kp_max, int nthr_max, cudaStream_t s);
 bool tc_supported();
 int tc_max_kpad();
 

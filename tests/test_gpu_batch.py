@@ -97,8 +97,8 @@ def test_batch_replay_and_graph_capture(rsr):
 def test_batch_autotune_leaves_outputs_alone(rsr):
     probs, seeds, offsets, Ns = scenarios()
     b = make_batch(rsr, probs, seeds, offsets, Ns)
-    grid, order, k0 = rsr.rsr_batch_autotune(b)
-    assert grid >= 1 and order in (0, 1) and k0 in (0, 2, 4, 8, 16, 32)
+    grid, order, k0, n_tc = rsr.rsr_batch_autotune(b)
+    assert grid >= 1 and order in (0, 1) and k0 in (0, 2, 4, 8, 16, 32) and n_tc == 0
     torch.cuda.synchronize()
     assert int(b.counts3.abs().sum()) == 0
     assert all(int(t.abs().sum()) == 0 for t in b.grad_counts)
@@ -151,3 +151,77 @@ def test_batch_deep_queue_overflow_falls_back_to_the_tile(rsr):
         assert np.array_equal(b.labels[s].cpu().numpy(), lab), s
         assert np.array_equal(counts[s], cnt), s
         assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K), O.grad_counts(X, lab, p.K)), s
+
+
+def mixed_scenarios():
+    """Dense scenarios on the tensor cores (path TC), dense scenarios left to the
+    autotuner (path AUTO), and bit-packed ones, with ragged sample counts and a
+    multi-state encoding."""
+    spec = [  # n, K, R_L, R_U, N, path, dense
+        (295, 2, 300, 700, 5000, 2, True), (100, 4, 600, 300, 3001, 2, True), (40, 5, 1, 513, 2049, 0, True),
+        (120, 3, 130, 129, 257, 0, True), (300, 2, 3000, 9000, 4096, 0, True), (50, 2, 20, 40, 1000, 1, False),
+        (64, 4, 30, 30, 2048, 0, False), (200, 2, 600, 5, 1, 2, True)]
+    probs = [random_refs_problem(n, K, RL, RU, seed=13 * n + K) for n, K, RL, RU, _, _, _ in spec]
+    Ns = [sp[4] for sp in spec]
+    paths = [sp[5] for sp in spec]
+    dense = [sp[6] for sp in spec]
+    seeds = [300 + s for s in range(len(probs))]
+    offsets = [11 * s for s in range(len(probs))]
+    return probs, seeds, offsets, Ns, paths, dense
+
+
+def make_mixed_batch(rsr, probs, seeds, offsets, Ns, paths, dense):
+    P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=pa, dense=de) for p, pa, de in zip(probs, paths, dense)]
+    return rsr.Batch(P, seeds, offsets, Ns)
+
+
+def check_batch_round(rsr, b, probs, seeds, offsets, Ns, rnd):
+    counts = b.counts3.cpu().numpy()
+    for s, p in enumerate(probs):
+        X = O.sample(p.pmf, seeds[s], offsets[s] + rnd * Ns[s], Ns[s])
+        lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+        assert np.array_equal(b.labels[s].cpu().numpy(), lab), (rnd, s)
+        assert np.array_equal(counts[s], cnt), (rnd, s)
+        assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K), O.grad_counts(X, lab, p.K)), (rnd, s)
+
+
+def test_mixed_path_batch_matches_oracle_before_and_after_autotune(rsr):
+    """Tensor-core and bit-packed scenarios in one batch: every scenario equals
+    the oracle, before tuning (the reference-count rule) and after (timed paths,
+    k0, order and grid), and on graph replays of the tuned batch."""
+    probs, seeds, offsets, Ns, paths, dense = mixed_scenarios()
+    b = make_mixed_batch(rsr, probs, seeds, offsets, Ns, paths, dense)
+    rsr.rsr_batch(b)
+    torch.cuda.synchronize()
+    check_batch_round(rsr, b, probs, seeds, offsets, Ns, 0)
+    b2 = make_mixed_batch(rsr, probs, seeds, offsets, Ns, paths, dense)
+    grid, order, k0, n_tc = rsr.rsr_batch_autotune(b2)
+    assert n_tc >= 3                      # the three scenarios that ask for the tensor cores
+    torch.cuda.synchronize()
+    assert int(b2.counts3.abs().sum()) == 0
+    stream = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        rsr.rsr_batch(b2, stream=torch.cuda.current_stream())
+    for rnd in (0, 1):
+        b2.counts3.zero_()
+        for t in b2.grad_counts:
+            t.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        check_batch_round(rsr, b2, probs, seeds, offsets, Ns, rnd)
+
+
+def test_tuning_cache_round_trip(rsr, tmp_path, monkeypatch):
+    """With RSR_TUNE_CACHE set, rsr_autotune writes its decision to the JSON
+    cache keyed by device and shape (read back here as text)."""
+    import json
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("RSR_TUNE_CACHE", str(path))
+    p = random_refs_problem(96, 2, 700, 2100, seed=17)
+    sess = make_session(rsr, p, path=0, dense=True)
+    chosen = rsr.rsr_autotune(sess.problem, sess.ws)
+    d = json.loads(path.read_text())
+    keys = [k for k in d if k.startswith("path/") and "/n96/K2/" in k]
+    assert keys and d[keys[0]] == [chosen]
