@@ -414,6 +414,63 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
             "prepare_s": prep_s}
 
 
+def popc_roofline(rsr, n, K, n_samples, kern_ms, word_ops, meas=None):
+    """Roofline of the bit-packed classifier on the operations it issues:
+    per Philox4x32-10 block 20 wide products (IMAD.WIDE) and 60 logic / add ops,
+    n(K-1) threshold compares per sample, and the 32-bit logic operations on
+    reference data that the kernel counted (exec_tests[1]: scan words, AND-row
+    words, index rows).  Peak: this mix at the LOP3 and IMAD.WIDE rates measured
+    on this GPU (time bound = max(ALU ops / LOP3 rate, IMAD ops / IMAD rate))."""
+    meas = meas or rsr.rsr_measure_int_peak()
+    blocks = n_samples * ((n + 3) // 4)
+    imad_ops = 20.0 * blocks
+    alu_ops = 60.0 * blocks + n_samples * n * (K - 1) + float(word_ops)
+    ops = imad_ops + alu_ops
+    t_bound = max(alu_ops / meas["lop3_ops_per_s"], imad_ops / meas["imad_ops_per_s"])
+    achieved = ops / (kern_ms / 1000.0) / 1e12
+    peak = ops / t_bound / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": None, "issued_word_ops": float(word_ops), "philox_blocks": float(blocks),
+            "measured_lop3_tops": meas["lop3_ops_per_s"] / 1e12,
+            "measured_imad_wide_tops": meas["imad_ops_per_s"] / 1e12,
+            "note": "integer-op model on issued operations (per Philox block 20 IMAD.WIDE + 60 ALU ops, n(K-1) "
+                    "compares per sample, the kernel's own count of logic operations on reference data); peak = "
+                    "this mix at the LOP3 and IMAD.WIDE rates measured on this GPU (rsr_measure_int_peak)"}
+
+
+def bench_c2_popc(rsr, torch, meas, reps=5):
+    """The 119-node / 295-edge workload (1840 references, N = 1e6, early exit)
+    on the bit-packed classifier alone: kernel time and its roofline on issued
+    operations (classifier only; the --workload c2 line adds Stage 2 and the
+    gradient)."""
+    import workloads.large as L
+    p = L.c2_rgg()
+    N = 1_000_000
+    P = rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_POPC)
+    sess = rsr.Session(P)
+    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+    ex = torch.zeros(2, dtype=torch.int64, device="cuda")
+    labels = torch.empty(N, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ts, ops = [], []
+    for k in range(reps + 2):
+        flush.fill_(k & 0xFF)
+        counts.zero_()
+        ex.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        e[0].record()
+        rsr.rsr_classify(P, 1, k * N, N, sess.ws, counts, None, labels, None, ex)
+        e[1].record()
+        torch.cuda.synchronize()
+        if k >= 2:
+            ts.append(e[0].elapsed_time(e[1]))
+            ops.append(int(ex[1].item()))
+    ms = statistics.median(ts)
+    roof = popc_roofline(rsr, P.n, P.K, N, ms, statistics.median(ops), meas)
+    return {"workload": "c2_rgg119n295e_N1e6 classifier (early exit, bit-packed)", "classifier_ms": ms,
+            "samples_per_s": N / (ms / 1000.0), "roofline": roof}
+
+
 _ORACLE_PROB = None
 
 
@@ -650,7 +707,7 @@ def main():
     counts = torch.zeros(3, dtype=torch.int64, device=dev)
     gcounts = torch.zeros(P.n * P.K, dtype=torch.int64, device=dev)
     labels = torch.empty(n_rank, dtype=torch.uint8, device=dev)
-    exec_t = torch.zeros(1, dtype=torch.int64, device=dev)
+    exec_t = torch.zeros(2, dtype=torch.int64, device=dev)   # executed tests, issued word operations
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     # Stage 2 (Sec. 3.5) for the graph workloads: Phi on the unclassified samples, on the device
@@ -719,7 +776,8 @@ def main():
             if system is not None:
                 stage2_ms.append(ev[1].elapsed_time(ev[4]))
     torch.cuda.synchronize()
-    exec_tests = int(exec_t.item())
+    exec_tests = int(exec_t[0].item())
+    exec_ops = int(exec_t[1].item())
     total_ms = sum(step_ms)
     if world > 1:
         # the estimate of the last timed step over every rank's samples: the integer counts
@@ -765,25 +823,7 @@ def main():
                         "2*n(K-1)*%s tests / kernel time / peak; frac_executed counts the executed tests at "
                         "the padded row of %d bytes" % ("N*(R_L+R_U)" if P.dense else "executed", kpad)}
     else:
-        # integer-op model: per Philox4x32-10 block 20 wide products (IMAD.WIDE) and 60
-        # logic / add ops; n(K-1) compares per sample; ceil(n(K-1)/32) + 1 per executed
-        # test (an index chunk counts all its references, as the scan it replaces).
-        # Peak: the measured LOP3 and IMAD.WIDE rates of this GPU, combined for this mix
-        # (time bound = max(ALU ops / LOP3 rate, IMAD ops / IMAD rate)).
-        meas = rsr.rsr_measure_int_peak()
-        blocks = n_rank * ((P.n + 3) // 4)
-        imad_ops = 20.0 * blocks
-        alu_ops = 60.0 * blocks + n_rank * kenc + exec_per_launch * ((kenc + 31) // 32 + 1)
-        ops = imad_ops + alu_ops
-        t_bound = max(alu_ops / meas["lop3_ops_per_s"], imad_ops / meas["imad_ops_per_s"])
-        achieved = ops / (kern_avg / 1000.0) / 1e12
-        peak = ops / t_bound / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": None, "measured_lop3_tops": meas["lop3_ops_per_s"] / 1e12,
-                "measured_imad_wide_tops": meas["imad_ops_per_s"] / 1e12,
-                "note": "integer-op model (per Philox block 20 IMAD.WIDE + 60 ALU ops, n(K-1) compares per "
-                        "sample, ceil(n(K-1)/32)+1 per executed test); peak = this mix at the LOP3 and "
-                        "IMAD.WIDE rates measured on this GPU (rsr_measure_int_peak)"}
+        roof = popc_roofline(rsr, P.n, P.K, n_rank, kern_avg, exec_ops / args.steps)
 
     extras = {}
     if rank == 0 and not args.no_extras:
@@ -808,7 +848,7 @@ def main():
                 P2 = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=pth, dense=False, index=idx)
                 s2 = rsr.Session(P2)
                 ee = []
-                ex = torch.zeros(1, dtype=torch.int64, device=dev)
+                ex = torch.zeros(2, dtype=torch.int64, device=dev)
                 for k in range(4):
                     flush.fill_(k)
                     counts.zero_()
@@ -822,7 +862,7 @@ def main():
                 ee_ms = statistics.median(ee[1:])
                 ee_all[pname] = {"ms": ee_ms, "samples_per_s": N / (ee_ms / 1000.0),
                                  "nominal_tests_per_s": N * R / (ee_ms / 1000.0),
-                                 "executed_tests_per_sample": int(ex.item()) / N}
+                                 "executed_tests_per_sample": int(ex[0].item()) / N}
                 del s2
             extras["early_exit"] = ee_all
         if path == rsr.RSR_PATH_POPC:
@@ -848,6 +888,8 @@ def main():
             extras["stage2"] = {"resolve_ms": sum(stage2_ms) / len(stage2_ms), "n_u": int(c2.sum().item()),
                                 "note": "Phi evaluated on the device for every unclassified sample; the step "
                                         "estimate is the Stage-2 P(S<=m')"}
+        if args.workload == "c3":
+            extras["c2_popc"] = bench_c2_popc(rsr, torch, rsr.rsr_measure_int_peak())
         extras["pipeline_119_295"] = bench_pipeline(rsr, torch)
         extras["level_pmf_c4"] = bench_levels(rsr, torch)
         if args.workload == "c3" and not args.no_batch:

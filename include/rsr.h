@@ -149,8 +149,16 @@ RSR_API int rsr_update_pmf(const rsr_problem *problem, void *ws, size_t ws_bytes
  *   labels_or_null   : device N uint8 labels (0/1/2); NULL = do not write labels.
  *   counts3          : device int64[3], |I^L|, |I^U|, |I^u| are ADDED (the caller zeroes it).
  *   grad_counts_or_null : device int64[n*K]; C[i*K+k] += #{h in I^L : x_{h,i} = k}.
- *   exec_tests_or_null  : device int64[1]; += reference tests actually executed
- *                         (tiles issued x tile size on the tensor path).
+ *   exec_tests_or_null  : device int64[2]; [0] += reference tests actually executed
+ *                         (tiles issued x tile size on the tensor path; on the
+ *                         bit-packed path every reference of an upper chunk that
+ *                         the index test visits counts); [1] += the 32-bit logic
+ *                         operations the bit-packed path issued on reference data:
+ *                         one per word of each scanned reference test, one per
+ *                         word of each chunk AND-row test, 4 per index row ORed
+ *                         by one lane (8 words, two rows per three-input OR) plus
+ *                         8 per encoding word it visits, 1 per index word ORed in
+ *                         the warp-cooperative test (0 on the tensor path).
  * `ws` must be prepared for this problem and pmf (else RSR_ERR_NOT_PREPARED).
  * Capturable in a CUDA graph.
  */

@@ -182,7 +182,7 @@ class Session:
         out["labels"] = torch.empty(N, dtype=torch.uint8, device=dev) if labels else None
         out["grad_counts"] = (torch.zeros(self.problem.n * self.problem.K, dtype=torch.int64, device=dev)
                               if grad else None)
-        out["exec_tests"] = torch.zeros(1, dtype=torch.int64, device=dev) if count_tests else None
+        out["exec_tests"] = torch.zeros(2, dtype=torch.int64, device=dev) if count_tests else None
         rsr_classify(self.problem, seed, offset, N, self.ws, out["counts3"], samples, out["labels"],
                      out["grad_counts"], out["exec_tests"], self.stream)
         return out

@@ -222,7 +222,8 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
             const bool ruled = !done && chunk_ruled_out<WB>(t, s_and + cur_buf * kMaxWB);
             const unsigned need = __ballot_sync(0xffffffffu, !done && !ruled);
             if (__popc(need) > kCoopIdx) {
-                if (!done && !ruled && idx_match_lane<WB>(t, s_ref, s_first, s_zero, kenc, cnt)) {
+                unsigned long long ops_unused = 0;
+                if (!done && !ruled && idx_match_lane<WB>(t, s_ref, s_first, s_zero, kenc, cnt, &ops_unused)) {
                     mU = true;
                     done = true;
                 }
@@ -231,8 +232,9 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
                 while (rem) {
                     const int src = __ffs(rem) - 1;
                     rem &= rem - 1;
-                    const bool found =
-                        idx_match_warp<WB, kThreads>(s_tw + (tid - lane + src), s_ref, s_first, kenc, cnt, lane);
+                    unsigned long long ops_unused = 0;
+                    const bool found = idx_match_warp<WB, kThreads>(s_tw + (tid - lane + src), s_ref, s_first, kenc,
+                                                                    cnt, lane, &ops_unused);
                     if (lane == src && found) {
                         mU = true;
                         done = true;

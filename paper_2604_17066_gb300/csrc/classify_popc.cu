@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
     __shared__ uint32_t s_and[2][kMaxWords];   // AND rows of the staged index chunks
     __shared__ unsigned long long s_cnt[3];
-    __shared__ unsigned long long s_exec;
+    __shared__ unsigned long long s_exec, s_ops;
     __shared__ unsigned int s_fz;           // I^L samples counted by their zero bits
 
     const bool use_idx = p.popc_UT != nullptr && !p.dense && p.R_U > 0;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
         for (int j = tid; j < WB * 32; j += kThreads) s_cum[j] = 0u;
     if (tid == 0) s_fz = 0u;
     if (tid < 3) s_cnt[tid] = 0ull;
-    if (tid == 0) s_exec = 0ull;
+    if (tid == 0) s_exec = s_ops = 0ull;
     __syncthreads();
 
     // Set order: see ChunkWalk (upper bursts between lower chunks without
@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     const bool overlap = *((volatile const int32_t *)&p.hdr->overlap) != 0;
     const uint32_t key0 = (uint32_t)p.seed, key1 = (uint32_t)(p.seed >> 32);
     unsigned long long my_cnt0 = 0, my_cnt1 = 0, my_cnt2 = 0, my_exec = 0;
+    unsigned long long my_ops = 0;   // 32-bit logic operations on reference data (scan words, AND rows, index rows)
 
     const int64_t ntiles = (p.N + kThreads - 1) / kThreads;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                 }
             }
             my_exec += (unsigned long long)r;
+            my_ops += (unsigned long long)r * WB;
         }
         for (int64_t step = 0; step < nsteps; ++step) {
             if (kBufs<WB>() == 2) cp_async_wait_all();      // this thread's copies of chunk `step`
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                         }
                     }
                     my_exec += (unsigned long long)cnt;
+                    my_ops += (unsigned long long)cnt * WB;
                 }
                 if (upper) mU |= m; else mL |= m;
             } else if (idx_chunk) {
@@ -254,10 +257,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                 // AND row dominates none of its references; the others are tested
                 // per lane while several need it, one sample per warp otherwise.
                 const bool ruled = !done && chunk_ruled_out<WB>(t, s_and[cur_buf]);
-                if (!done) my_exec += (unsigned long long)cnt;
+                if (!done) {
+                    my_exec += (unsigned long long)cnt;
+                    my_ops += WB;   // the AND-row test
+                }
                 const unsigned need = __ballot_sync(0xffffffffu, !done && !ruled);
                 if (__popc(need) > kCoopIdx) {
-                    if (!done && !ruled && idx_match_lane<WB>(t, s_ref, s_first, s_zero, p.kenc, cnt)) {
+                    if (!done && !ruled && idx_match_lane<WB>(t, s_ref, s_first, s_zero, p.kenc, cnt, &my_ops)) {
                         mU = true;
                         done = true;
                     }
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                         const int src_lane = __ffs(rem) - 1;
                         rem &= rem - 1;
                         const bool found = idx_match_warp<WB, kThreads>(s_tw + (tid - lane + src_lane), s_ref,
-                                                                        s_first, p.kenc, cnt, lane);
+                                                                        s_first, p.kenc, cnt, lane, &my_ops);
                         if (lane == src_lane && found) {
                             mU = true;
                             done = true;
@@ -300,6 +306,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                             }
                         }
                         my_exec += (unsigned long long)r;
+                        my_ops += (unsigned long long)r * WB;
                         if (m) {
                             if (upper) mU = true; else mL = true;
                             done = true;
@@ -334,6 +341,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                         }
                         if (lane == src) {
                             my_exec += (unsigned long long)tested;
+                            my_ops += (unsigned long long)tested * WB;
                             if (found) {
                                 if (upper) mU = true; else mL = true;
                                 done = true;
@@ -397,16 +405,19 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
         my_cnt1 += __shfl_xor_sync(0xffffffffu, my_cnt1, o);
         my_cnt2 += __shfl_xor_sync(0xffffffffu, my_cnt2, o);
         my_exec += __shfl_xor_sync(0xffffffffu, my_exec, o);
+        my_ops += __shfl_xor_sync(0xffffffffu, my_ops, o);
     }
     if (lane == 0) {
         atomicAdd(&s_cnt[0], my_cnt0);
         atomicAdd(&s_cnt[1], my_cnt1);
         atomicAdd(&s_cnt[2], my_cnt2);
         atomicAdd(&s_exec, my_exec);
+        atomicAdd(&s_ops, my_ops);
     }
     __syncthreads();
     if (tid < 3 && s_cnt[tid]) atomicAdd(&p.counts3[tid], s_cnt[tid]);
     if (tid == 0 && p.exec_tests && s_exec) atomicAdd(p.exec_tests, s_exec);
+    if (tid == 0 && p.exec_tests && s_ops) atomicAdd(p.exec_tests + 1, s_ops);
     if (p.grad_counts && s_cnt[0]) {
         // C[i,0] += F - cum_1 ; C[i,k] += cum_k - cum_{k+1} (cum_K = 0); cum_j = one bits
         // counted by ballots + (samples counted by zero bits - their zero bits)

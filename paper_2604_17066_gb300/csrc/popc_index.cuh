@@ -64,11 +64,14 @@ __device__ __forceinline__ uint32_t decisive_zeros(uint32_t t_w, uint32_t prev_w
 // references, rows in s_idx) lie below the sample?  s_first[w] = component
 // start bits of word w; s_zero = 8 zero words (16-byte aligned), read in place
 // of a second row when a word has an odd number of decisive zeros.  Two rows
-// per iteration, combined with three-input ORs.
+// per iteration, combined with three-input ORs.  *ops += the 32-bit logic
+// operations on index data: 4 per row (8 words, two rows per three-input OR)
+// and 8 per encoding word visited (the all-ruled-out test).
 template <int WB>
 __device__ __forceinline__ bool idx_match_lane(const uint32_t (&t)[WB], const uint32_t *__restrict__ s_idx,
                                                const uint32_t *__restrict__ s_first,
-                                               const uint32_t *__restrict__ s_zero, int kenc, int cnt) {
+                                               const uint32_t *__restrict__ s_zero, int kenc, int cnt,
+                                               unsigned long long *ops) {
     uint32_t bl[kIdxWords];
 #pragma unroll
     for (int q = 0; q < kIdxWords; ++q) bl[q] = idx_missing_refs(cnt, q);
@@ -78,6 +81,7 @@ __device__ __forceinline__ bool idx_match_lane(const uint32_t (&t)[WB], const ui
         if (32 * w >= kenc) break;
         uint32_t z = decisive_zeros(t[w], prev, s_first[w], kenc, w);
         prev = t[w];
+        *ops += 8u + 4u * (unsigned)__popc(z);
         while (z) {
             const int b0 = __ffs(z) - 1;
             z &= z - 1u;
@@ -105,10 +109,11 @@ __device__ __forceinline__ bool idx_match_lane(const uint32_t (&t)[WB], const ui
 // col[w * stride], the same for every lane): lane = 8g + q takes the zero bits
 // in byte g of every word and reference word q of the chunk; the four byte
 // groups are OR-combined with two shuffles.  All lanes return the same answer.
+// *ops += this lane's ORs of index words.
 template <int WB, int stride>
 __device__ __forceinline__ bool idx_match_warp(const uint32_t *col, const uint32_t *__restrict__ s_idx,
                                                const uint32_t *__restrict__ s_first, int kenc, int cnt,
-                                               int lane) {
+                                               int lane, unsigned long long *ops) {
     const int q = lane & (kIdxWords - 1);
     const uint32_t gmask = 0xffu << (8 * (lane >> 3));
     uint32_t bl = idx_missing_refs(cnt, q);
@@ -119,6 +124,7 @@ __device__ __forceinline__ bool idx_match_warp(const uint32_t *col, const uint32
         const uint32_t tw = col[w * stride];
         uint32_t z = decisive_zeros(tw, prev, s_first[w], kenc, w) & gmask;
         prev = tw;
+        *ops += (unsigned)__popc(z);
         while (z) {
             const int b = __ffs(z) - 1;
             z &= z - 1u;

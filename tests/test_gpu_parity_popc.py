@@ -61,8 +61,11 @@ def test_grid_philox_parity(rsr, dense):
     np.testing.assert_allclose(se, se_o, rtol=1e-12, atol=0)
     if dense:
         assert got["exec_tests"][0] == N * (p.R_L + p.R_U)
+        # dense mode issues one and-or per word of every reference test (the grid: one word)
+        assert got["exec_tests"][1] == N * (p.R_L + p.R_U) * 1
     else:
         assert got["exec_tests"][0] < N * (p.R_L + p.R_U)
+        assert 0 < got["exec_tests"][1] < N * (p.R_L + p.R_U)
 
 
 @pytest.mark.parametrize("n,K,R_L,R_U,N", [(295, 2, 300, 700, 5000), (100, 4, 600, 300, 3001),
