@@ -597,8 +597,9 @@ def run_pipeline(args):
 def run_batch_line(args):
     """--workload c5: the 256-scenario batch on its own line (value = samples/s of
     the batched launch, beside the per-scenario path).  With --quick: prepare,
-    two warm-up launches and one timed launch, no autotuning and no graph (the
-    launch list and captures of the batched kernel)."""
+    two warm-up launches and one timed launch, no autotuning and no graph, then
+    one pass of the per-scenario path (the launch lists and captures of the
+    batched kernels and of the per-scenario launches)."""
     import torch
     from paper_2604_17066_gb300 import api as rsr
     from paper_2604_17066_gb300 import build as rsr_build
@@ -621,7 +622,19 @@ def run_batch_line(args):
             e[1].record()
             torch.cuda.synchronize()
             ms = e[0].elapsed_time(e[1])
-            res = {"workload": "c5_256_scenarios_N%d" % N, "batched_ms": ms, "samples_per_s": S * N / (ms / 1e3)}
+            # one pass of the per-scenario path over the same scenarios (launch list comparison)
+            P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_POPC) for p in probs]
+            sessions = [rsr.Session(pp) for pp in P]
+            cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+            lab = torch.empty(N, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            e[0].record()
+            for s_, (pp, se) in enumerate(zip(P, sessions)):
+                rsr.rsr_classify(pp, 1000 + s_, 0, N, se.ws, cnt, None, lab)
+            e[1].record()
+            torch.cuda.synchronize()
+            res = {"workload": "c5_256_scenarios_N%d" % N, "batched_ms": ms, "samples_per_s": S * N / (ms / 1e3),
+                   "per_scenario_ms": e[0].elapsed_time(e[1])}
         else:
             res = bench_batch(rsr, torch, N=N)
     line = {"metric": "batched classification of 256 hazard scenarios: samples/s of one persistent launch",
