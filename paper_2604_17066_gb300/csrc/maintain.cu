@@ -25,19 +25,22 @@ constexpr int kSelTile = 4096;
 constexpr int kSelThreads = 256;
 constexpr int kScanThreads = 1024;
 
+// keep[j] for the candidates j in [c0, c1): no row i in [d0, d1), i != j, dominates
+// row j, and none equals it with i < j (indices are global rows of enc).
 template <int WB>
-__global__ void __launch_bounds__(kNdThreads) nondominated_kernel(const uint32_t *__restrict__ enc, int64_t R,
-                                                                  int upper, uint8_t *__restrict__ keep,
+__global__ void __launch_bounds__(kNdThreads) nondominated_kernel(const uint32_t *__restrict__ enc, int64_t c0,
+                                                                  int64_t c1, int64_t d0, int64_t d1, int upper,
+                                                                  uint8_t *__restrict__ keep,
                                                                   unsigned long long *n_keep) {
     __shared__ __align__(16) uint32_t s_ref[kNdThreads * WB];
-    const int64_t j = (int64_t)blockIdx.x * kNdThreads + threadIdx.x;
+    const int64_t j = c0 + (int64_t)blockIdx.x * kNdThreads + threadIdx.x;
     uint32_t a[WB];
 #pragma unroll
-    for (int w = 0; w < WB; ++w) a[w] = (j < R) ? enc[j * WB + w] : 0u;
-    bool done = !(j < R);      // dominated, or no reference in this slot
-    for (int64_t base = 0; base < R; base += kNdThreads) {
+    for (int w = 0; w < WB; ++w) a[w] = (j < c1) ? enc[j * WB + w] : 0u;
+    bool done = !(j < c1);      // dominated, or no reference in this slot
+    for (int64_t base = d0; base < d1; base += kNdThreads) {
         if (__syncthreads_and(done)) break;
-        const int cnt = (int)((R - base) < kNdThreads ? (R - base) : kNdThreads);
+        const int cnt = (int)((d1 - base) < kNdThreads ? (d1 - base) : kNdThreads);
         for (int idx = threadIdx.x; idx < cnt * WB; idx += kNdThreads) s_ref[idx] = enc[base * WB + idx];
         __syncthreads();
         if (!done) {
@@ -58,17 +61,19 @@ __global__ void __launch_bounds__(kNdThreads) nondominated_kernel(const uint32_t
             }
         }
     }
-    if (j < R) {
+    if (j < c1) {
         keep[j] = done ? 0 : 1;
         if (!done) atomicAdd(n_keep, 1ull);
     }
 }
 
 template <int WB>
-cudaError_t launch_nd_wb(const uint32_t *enc, int64_t R, bool upper, uint8_t *keep, unsigned long long *n_keep,
-                         cudaStream_t s) {
-    const int64_t blocks = (R + kNdThreads - 1) / kNdThreads;
-    nondominated_kernel<WB><<<(unsigned)blocks, kNdThreads, 0, s>>>(enc, R, upper ? 1 : 0, keep, n_keep);
+cudaError_t launch_nd_wb(const uint32_t *enc, int64_t c0, int64_t c1, int64_t d0, int64_t d1, bool upper,
+                         uint8_t *keep, unsigned long long *n_keep, cudaStream_t s) {
+    const int64_t blocks = (c1 - c0 + kNdThreads - 1) / kNdThreads;
+    if (blocks <= 0) return cudaSuccess;
+    nondominated_kernel<WB><<<(unsigned)blocks, kNdThreads, 0, s>>>(enc, c0, c1, d0, d1, upper ? 1 : 0, keep,
+                                                                     n_keep);
     return cudaGetLastError();
 }
 
@@ -154,22 +159,42 @@ __global__ void gather_rows_kernel(const uint8_t *__restrict__ src, const int64_
 
 }  // namespace
 
+namespace {
+cudaError_t launch_nd_range(const uint32_t *enc, int64_t c0, int64_t c1, int64_t d0, int64_t d1, int words_b,
+                            bool upper, uint8_t *keep, unsigned long long *n_keep, cudaStream_t s) {
+    switch (words_b) {
+        case 1: return launch_nd_wb<1>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 2: return launch_nd_wb<2>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 4: return launch_nd_wb<4>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 6: return launch_nd_wb<6>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 8: return launch_nd_wb<8>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 10: return launch_nd_wb<10>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 12: return launch_nd_wb<12>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 16: return launch_nd_wb<16>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 24: return launch_nd_wb<24>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 32: return launch_nd_wb<32>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+}  // namespace
+
 cudaError_t launch_nondominated(const uint32_t *enc, int64_t R, int words_b, bool upper, uint8_t *keep,
                                 unsigned long long *n_keep, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
-    switch (words_b) {
-        case 1: return launch_nd_wb<1>(enc, R, upper, keep, n_keep, s);
-        case 2: return launch_nd_wb<2>(enc, R, upper, keep, n_keep, s);
-        case 4: return launch_nd_wb<4>(enc, R, upper, keep, n_keep, s);
-        case 6: return launch_nd_wb<6>(enc, R, upper, keep, n_keep, s);
-        case 8: return launch_nd_wb<8>(enc, R, upper, keep, n_keep, s);
-        case 10: return launch_nd_wb<10>(enc, R, upper, keep, n_keep, s);
-        case 12: return launch_nd_wb<12>(enc, R, upper, keep, n_keep, s);
-        case 16: return launch_nd_wb<16>(enc, R, upper, keep, n_keep, s);
-        case 24: return launch_nd_wb<24>(enc, R, upper, keep, n_keep, s);
-        case 32: return launch_nd_wb<32>(enc, R, upper, keep, n_keep, s);
-        default: return cudaErrorInvalidValue;
-    }
+    return launch_nd_range(enc, 0, R, 0, R, words_b, upper, keep, n_keep, s);
+}
+
+// Rows [0, R_old) are already non-dominated among themselves (no row dominates
+// another and none repeats), rows [R_old, R) are new.  An old row can then only
+// be dominated by a new one (an equal new row comes later and does not count),
+// and a new row by any row: the same keep mask as the full test, with
+// 2 R_old (R - R_old) + (R - R_old)^2 row tests instead of R^2.
+cudaError_t launch_nondominated_appended(const uint32_t *enc, int64_t R_old, int64_t R, int words_b, bool upper,
+                                         uint8_t *keep, unsigned long long *n_keep, cudaStream_t s) {
+    if (R <= 0) return cudaSuccess;
+    cudaError_t e = launch_nd_range(enc, 0, R_old, R_old, R, words_b, upper, keep, n_keep, s);
+    if (e != cudaSuccess) return e;
+    return launch_nd_range(enc, R_old, R, 0, R, words_b, upper, keep, n_keep, s);
 }
 
 size_t select_scratch_bytes(int64_t N) {

@@ -786,9 +786,31 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
             __syncwarp();
         }
         const bool lower = phi_le(g, p.n, w, s_src, s_dst, err);
+        unsigned long long ev = 1;
+        if (!lower && g.kind == RSR_PHI_GLOBAL_CONNECTIVITY && g.m_prime == 0) {
+            // Lowering a connected state: each working edge, in the visiting order, is
+            // removed if the graph stays connected without it.  That is reverse deletion
+            // with the visit positions as distinct weights, and it keeps exactly the
+            // spanning tree that Kruskal's algorithm builds from the working edges taken
+            // in reverse visiting order (the unique minimum spanning tree for those
+            // weights).  One union-find pass gives the same state; the count of Phi
+            // evaluations is unchanged: one decision per working edge.
+            for (int v = lane; v < g.n_nodes; v += 32) w.parent[v] = v;
+            __syncwarp();
+            if (lane == 0) {
+                for (int step = p.n - 1; step >= 0; --step) {
+                    const int i = order_mode ? (int)ord[step] : step;
+                    if (!w.x[i]) continue;
+                    ++ev;
+                    const int ru = dsu_find(w.parent, s_src[i]), rv = dsu_find(w.parent, s_dst[i]);
+                    if (ru != rv) w.parent[ru] = rv;
+                    else w.x[i] = 0;
+                }
+            }
+            __syncwarp();
+        } else {
         int state = 0;
         const int mode = search_setup(g, p.n, lower, w, s_src, s_dst, &state, err, sb);
-        unsigned long long ev = 1;
         for (int step = 0; step < p.n; ++step) {
             const int i = order_mode ? (int)ord[step] : step;
             if (lower) {
@@ -802,6 +824,7 @@ __global__ void __launch_bounds__(kWarps * 32) search_kernel(const ClassifyParam
                     if (!try_step(g, p.n, mode, false, i, w, bak, s_src, s_dst, &state, err, sb)) break;
                 }
             }
+        }
         }
         __syncwarp();
         for (int i = lane; i < p.n; i += 32) refs_out[(size_t)j * p.n + i] = w.x[i];

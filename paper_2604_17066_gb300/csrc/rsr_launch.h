@@ -61,6 +61,9 @@ cudaError_t launch_search(const ClassifyParams &p, const rsr_system &sys, const 
 // Reference-set maintenance and order-preserving selection (maintain.cu).
 cudaError_t launch_nondominated(const uint32_t *enc, int64_t R, int words_b, bool upper, uint8_t *keep,
                                 unsigned long long *n_keep, cudaStream_t s);
+// The same keep mask when rows [0, R_old) are already non-dominated among themselves.
+cudaError_t launch_nondominated_appended(const uint32_t *enc, int64_t R_old, int64_t R, int words_b, bool upper,
+                                         uint8_t *keep, unsigned long long *n_keep, cudaStream_t s);
 size_t select_scratch_bytes(int64_t N);
 cudaError_t launch_select(const uint8_t *flags, uint8_t value, int64_t N, int64_t limit, int64_t *out_idx,
                           int64_t *n_out, int64_t *scratch, cudaStream_t s);

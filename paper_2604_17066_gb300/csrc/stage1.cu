@@ -206,6 +206,9 @@ int rsr_stage1(const rsr_problem *problem, const rsr_system *system, const rsr_s
 
     S1_CUDA(cudaMemsetAsync(scal, 0, 4 * sizeof(int64_t), s));
     int64_t RL = problem->R_L, RU = problem->R_U, n_u = 0;
+    // A side's rows are non-dominated among themselves once it has been reduced (an
+    // empty side trivially); from then on only the rows a round appends need testing.
+    bool reduced[2] = {RL == 0, RU == 0};
     int32_t stop = 2, rounds = 0;
     auto fetch = [&](const void *dev, void *host, size_t bytes) -> int {
         S1_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
@@ -272,8 +275,13 @@ int rsr_stage1(const rsr_problem *problem, const rsr_system *system, const rsr_s
             const int64_t total = Rs + c;
             S1_CUDA(launch_encode_popc(buf, total, n, K - 1, wb, false, enc, s));
             S1_CUDA(cudaMemsetAsync(&scal[1], 0, sizeof(int64_t), s));
-            S1_CUDA(launch_nondominated(enc, total, wb, v == 1, keep, reinterpret_cast<unsigned long long *>(&scal[1]),
-                                        s));
+            if (reduced[v])
+                S1_CUDA(launch_nondominated_appended(enc, Rs, total, wb, v == 1, keep,
+                                                     reinterpret_cast<unsigned long long *>(&scal[1]), s));
+            else
+                S1_CUDA(launch_nondominated(enc, total, wb, v == 1, keep,
+                                            reinterpret_cast<unsigned long long *>(&scal[1]), s));
+            reduced[v] = true;
             int64_t kept = 0;
             S1_CUDA(launch_select(keep, 1, total, total, sel, &scal[0], selscr, s));
             if ((st = fetch(&scal[0], &kept, sizeof(kept))) != RSR_OK) return st;

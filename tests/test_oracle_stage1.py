@@ -235,3 +235,46 @@ def test_stage1_permuted_order_converges_to_boundary_states():
     assert res["stop"] == 0
     assert all(bytes(r) in {bytes(q) for q in p.ref_L} for r in res["ref_L"])
     assert all(bytes(r) in {bytes(q) for q in p.ref_U} for r in res["ref_U"])
+
+
+def test_global_lowering_search_is_reverse_order_kruskal():
+    """The search that lowers a connected state under global connectivity (remove
+    each working edge, in the visiting order, if the graph stays connected)
+    keeps exactly the spanning tree that Kruskal's algorithm builds from the
+    working edges taken in reverse visiting order: reverse deletion with the
+    visit positions as distinct weights.  The CUDA search uses this one-pass
+    form; here the oracle's literal step-by-step search is compared with an
+    independent union-find Kruskal on random connected graphs and orders, and
+    its Phi-evaluation count is 1 + the number of working edges."""
+    rng = np.random.default_rng(12)
+    for trial in range(40):
+        nn = int(rng.integers(4, 14))
+        # a random spanning tree plus random extra edges
+        edges = [(int(rng.integers(0, v)), v) for v in range(1, nn)]
+        for _ in range(int(rng.integers(0, 3 * nn))):
+            a, b = (int(v) for v in rng.choice(nn, size=2, replace=False))
+            edges.append((a, b))
+        n = len(edges)
+        x = np.ones(n, dtype=np.uint8)
+        x[n - 1 - rng.choice(n - (nn - 1), size=int(rng.integers(0, n - nn + 2)), replace=False)] = 0
+        x[: nn - 1] = 1    # the spanning tree stays working: the start is connected
+        order = rng.permutation(n).astype(np.int32)
+        side, ref, ev = O.boundary_search(2, nn, edges, 0, 0, x, 2, order=order)
+        assert side == 1
+        parent = list(range(nn))
+
+        def find(v):
+            while parent[v] != v:
+                parent[v] = parent[parent[v]]
+                v = parent[v]
+            return v
+        want = np.zeros(n, dtype=np.uint8)
+        for i in order[::-1]:
+            if x[i]:
+                ru, rv = find(edges[i][0]), find(edges[i][1])
+                if ru != rv:
+                    parent[ru] = rv
+                    want[i] = 1
+        assert np.array_equal(ref, want), trial
+        assert int(ref.sum()) == nn - 1
+        assert ev == 1 + int(x.sum())
