@@ -79,6 +79,10 @@ typedef enum rsr_path {
  * kernel records RSR_ERR_TIMEOUT in the workspace header (rsr_workspace_status),
  * frees its tensor memory and returns, leaving the context usable. */
 #define RSR_FLAG_TEST_STALL 0x100u
+/* Test hook (batched bit-packed path): the scenario's deep queue holds 1024
+ * samples, so that tiles find it full and finish their walk themselves (the
+ * fallback a queue of one entry per sample never needs). */
+#define RSR_FLAG_TEST_DEEP_CAP 0x200u
 
 /*
  * One classification problem for a threshold m' (Sec. 3.2-3.3).
@@ -230,15 +234,17 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  *                          allowed), or NULL; per-state I^L counts are ADDED.
  * Limits: every scenario within the rsr_problem limits and n*(K-1) <= 512.
  *
- * rsr_batch_workspace_size : bytes of the batch workspace (0 on invalid input).
+ * rsr_batch_workspace_size : bytes of the batch workspace for these problems and sample counts
+ *                            Ns (host int64[S]; 0 on invalid input).  It includes a deep queue of
+ *                            min(Ns[s], 2^22) sample indices per scenario.
  * rsr_batch_prepare        : thresholds, reference encodings, precedence pre-checks and the work
  *                            list (longest scenarios first) into `ws`; not capturable.
  * rsr_batch                : the pair-kernel launch (if any scenario runs on the tensor cores),
  *                            then two bit-packed persistent launches: every (scenario, 256-sample
  *                            tile) walks at most k0 reference chunks, and the samples still
  *                            unresolved then are queued and finished 256 at a time by the second
- *                            launch (same labels and counts as one walk; a full queue leaves its
- *                            tile to finish the walk itself).  The arguments must equal those given
+ *                            launch (same labels and counts as one walk; a tile that would
+ *                            overflow a queue of more than 2^22 samples finishes its walk itself).  The arguments must equal those given
  *                            to rsr_batch_prepare (else RSR_ERR_NOT_PREPARED).  The launches re-arm
  *                            their own counters, so they can be captured once in a CUDA graph and
  *                            replayed.
@@ -254,7 +260,7 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  *                            Synchronises `stream`.  With RSR_TUNE_CACHE set (see rsr_autotune)
  *                            the choices are read from and written to the tuning cache.
  */
-RSR_API size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S);
+RSR_API size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S, const int64_t *Ns);
 RSR_API int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
                               const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
                               int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws,

@@ -23,6 +23,7 @@ RSR_PATH_TC = 2
 RSR_FLAG_DENSE = 1
 RSR_FLAG_NO_INDEX = 2
 RSR_FLAG_TEST_STALL = 0x100
+RSR_FLAG_TEST_DEEP_CAP = 0x200
 
 
 class rsr_problem(ctypes.Structure):
@@ -105,7 +106,7 @@ SIGNATURES = {
     "rsr_grad": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _I64, _P, _P, _P, _S, _P]),
     "rsr_sample": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _S, _P]),
     "rsr_workspace_status": (ctypes.c_int, [_P, _P, _P]),
-    "rsr_batch_workspace_size": (ctypes.c_size_t, [_PROB, _I32]),
+    "rsr_batch_workspace_size": (ctypes.c_size_t, [_PROB, _I32, _P]),
     "rsr_batch_prepare": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P]),
     "rsr_batch": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P]),
     "rsr_batch_autotune": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P, _P]),

@@ -241,7 +241,7 @@ class Batch:
                             if grad else None)
         self._lab_ptrs = (ctypes.c_void_p * S)(*[t.data_ptr() for t in self.labels]) if labels else None
         self._grad_ptrs = (ctypes.c_void_p * S)(*[t.data_ptr() for t in self.grad_counts]) if grad else None
-        size = _lib.load().rsr_batch_workspace_size(self._structs, S)
+        size = _lib.load().rsr_batch_workspace_size(self._structs, S, self.Ns.ctypes.data)
         if size == 0:
             raise RSRError(_lib.RSR_ERR_INVALID_ARG, "rsr_batch_workspace_size")
         raw = torch.empty(size + 256, dtype=torch.uint8, device=dev)

@@ -48,7 +48,8 @@ cudaError_t batch_max_grid(int *blocks_per_sm);
 // (deep_begin: workspace int64[S+1], written by the first pass).
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
                          BatchHeader *hdr, int64_t *deep_begin, int grid, cudaStream_t s);
-constexpr int64_t kBatchDeepCap = 32768;   // deep-queue entries per scenario
+constexpr int64_t kBatchDeepCap = int64_t(1) << 22;   // deep-queue entries per scenario at most (32 MB)
+constexpr int64_t kBatchTestDeepCap = 1024;           // with RSR_FLAG_TEST_DEEP_CAP (test hook)
 constexpr int kBatchDefaultK0 = 8;         // first-pass chunk steps before rsr_batch_autotune picks them
 
 }  // namespace rsr

@@ -775,6 +775,7 @@ struct BatchLayout {
     std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_pUA, off_bit, off_lc, off_tgrad, off_deep;
     std::vector<size_t> off_tcL, off_tcU;   // FP8 tiles of the scenarios that may run on the pair kernel (else 0)
     std::vector<int> words_b, tc_kpad;
+    std::vector<int64_t> deep_cap;          // deep-queue entries per scenario
 };
 
 // Scenarios that may run on the tensor-core pair kernel inside a batch: dense
@@ -785,7 +786,14 @@ bool batch_tc_eligible(const rsr_problem &p) {
            layout_of(&p).tc_kpad <= 512;
 }
 
-BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
+// Deep-queue entries of scenario s: one per sample it may defer (at most
+// kBatchDeepCap), or kBatchTestDeepCap with RSR_FLAG_TEST_DEEP_CAP.
+int64_t deep_cap_of(const rsr_problem &p, int64_t N) {
+    if (p.flags & RSR_FLAG_TEST_DEEP_CAP) return kBatchTestDeepCap;
+    return std::max<int64_t>(1, std::min<int64_t>(N, kBatchDeepCap));
+}
+
+BatchLayout batch_layout(const rsr_problem *probs, int32_t S, const int64_t *Ns) {
     BatchLayout B;
     size_t off = align256(sizeof(BatchHeader));
     B.off_descs = off;
@@ -834,8 +842,9 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S) {
         off = align256(off + 8);
         B.off_tgrad.push_back(off);  // tuning scratch: gradient counts
         off = align256(off + 8 * (size_t)p.n * p.K);
-        B.off_deep.push_back(off);   // deep-queue count (8 bytes) and queue of kBatchDeepCap entries
-        off = align256(off + 8 + 8 * (size_t)kBatchDeepCap);
+        B.off_deep.push_back(off);   // deep-queue count (8 bytes) and the queue
+        B.deep_cap.push_back(deep_cap_of(p, Ns[s]));
+        off = align256(off + 8 + 8 * (size_t)B.deep_cap.back());
         const WsLayout L = layout_of(&p);
         B.tc_kpad.push_back(L.tc_kpad);
         if (batch_tc_eligible(p)) {
@@ -977,11 +986,11 @@ std::vector<int> lpt_order(const std::vector<BatchDesc> &d) {
 
 extern "C" {
 
-size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S) {
-    if (!problems || S < 1) return 0;
+size_t rsr_batch_workspace_size(const rsr_problem *problems, int32_t S, const int64_t *Ns) {
+    if (!problems || S < 1 || !Ns) return 0;
     for (int s = 0; s < S; ++s)
-        if (validate(&problems[s]) != RSR_OK) return 0;
-    return batch_layout(problems, S).total;
+        if (validate(&problems[s]) != RSR_OK || Ns[s] < 0) return 0;
+    return batch_layout(problems, S, Ns).total;
 }
 
 int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
@@ -989,7 +998,7 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
                       int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream) {
     int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
     if (st != RSR_OK) return st;
-    const BatchLayout B = batch_layout(problems, S);
+    const BatchLayout B = batch_layout(problems, S, Ns);
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < B.total) return RSR_ERR_WORKSPACE;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     char *base = static_cast<char *>(ws);
@@ -1056,7 +1065,7 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.lcount = reinterpret_cast<unsigned long long *>(base + B.off_lc[k]);
         d.deep_count = reinterpret_cast<unsigned long long *>(base + B.off_deep[k]);
         d.deep = reinterpret_cast<int64_t *>(base + B.off_deep[k] + 8);
-        d.deep_cap = kBatchDeepCap;
+        d.deep_cap = B.deep_cap[k];
         d.k0 = kBatchDefaultK0;
         // pair-kernel parameters (dense); the path: RSR_PATH_TC where asked for, a tuned
         // decision for RSR_PATH_AUTO (else the reference-count rule of choose_path)
@@ -1112,7 +1121,7 @@ int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, con
               int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream) {
     int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
     if (st != RSR_OK) return st;
-    const BatchLayout B = batch_layout(problems, S);
+    const BatchLayout B = batch_layout(problems, S, Ns);
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < B.total) return RSR_ERR_WORKSPACE;
     BatchPrepared bp;
     {
@@ -1147,7 +1156,7 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
                        int32_t *chosen) {
     int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
     if (st != RSR_OK) return st;
-    const BatchLayout B = batch_layout(problems, S);
+    const BatchLayout B = batch_layout(problems, S, Ns);
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < B.total) return RSR_ERR_WORKSPACE;
     BatchPrepared bp;
     {

@@ -132,18 +132,22 @@ def test_single_problem_autotune_picks_a_path(rsr):
 
 def test_batch_deep_queue_overflow_falls_back_to_the_tile(rsr):
     """A scenario with more unresolved samples after the first pass's chunk
-    budget than its deep queue holds (32768): the tiles that find the queue full
-    finish their walk themselves, and every label and count still equals the
-    oracle's."""
+    budget than its deep queue holds (1024 entries under the test flag; a queue
+    otherwise holds one entry per sample): the first tiles queue their samples,
+    the tiles that find the queue full finish their walk themselves, and every
+    label and count still equals the oracle's."""
+    from paper_2604_17066_gb300._lib import RSR_FLAG_TEST_DEEP_CAP
     probs = [sparse_match_problem(64, 200, 4000, 10, 30, seed=8), random_refs_problem(50, 2, 20, 40, seed=9)]
     seeds, offsets, Ns = [41, 42], [0, 5], [100000, 3000]
-    b = make_batch(rsr, probs, seeds, offsets, Ns)
+    P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=POPC) for p in probs]
+    P[0].extra_flags = RSR_FLAG_TEST_DEEP_CAP
+    b = rsr.Batch(P, seeds, offsets, Ns)
     rsr.rsr_batch(b)
     torch.cuda.synchronize()
     counts = b.counts3.cpu().numpy()
     X = O.sample(probs[0].pmf, seeds[0], offsets[0], Ns[0])
     lab, cnt = O.classify(X, probs[0].ref_L, probs[0].ref_U)
-    assert cnt[2] > 40000          # far more unresolved samples than one queue holds
+    assert cnt[2] > 40 * 1024       # far more unresolved samples than the queue holds
     for s, p in enumerate(probs):
         if s:
             X = O.sample(p.pmf, seeds[s], offsets[s], Ns[s])
