@@ -97,14 +97,15 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
         *cnt_out = (int)((R - base) < (int64_t)kChunk ? (R - base) : (int64_t)kChunk);
         return (up ? d.popc_U : d.popc_L) + base * WB;
     };
+    const bool use_lg = d.popc_LG != nullptr;
     auto issue = [&](int buf, bool up, int64_t c) {
         int cnt_c;
         const uint32_t *rows = chunk_refs(up, c, &cnt_c);
-        const bool ix = use_idx && up;
+        const bool ix = use_idx && up, lg = use_lg && !up;
+        const uint32_t *skip = ix ? d.popc_UA + (size_t)c * WB : (lg ? d.popc_LG + (size_t)c * 2 * WB : nullptr);
         load_chunk_async<WB, kThreads>(s_buf + buf * (kChunk * kMaxWB), ix,
-                                       ix ? d.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, kenc,
-                                       ix ? d.popc_UA + (size_t)c * WB : nullptr, s_and + buf * kMaxWB, rows, cnt_c,
-                                       tid);
+                                       ix ? d.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, kenc, skip,
+                                       ix ? WB : 2 * WB, s_and + buf * 2 * kMaxWB, rows, cnt_c, tid);
     };
     issue((int)(step0 & 1), upper, ci);
     // ---- sample and encode (thermometer words, one column per thread) ----
@@ -215,11 +216,13 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
             walk.next(&up_next, &ci_next);
             issue((int)((step + 1) & 1), up_next, ci_next);
         }
-        // per-lane scan while many lanes are unresolved, cooperative warp scan otherwise
-        const unsigned active = __ballot_sync(0xffffffffu, !done);
+        // per-lane scan while many lanes are unresolved, cooperative warp scan otherwise;
+        // in a lower chunk only the lanes its skip rows do not rule out
+        const bool skip = !done && !upper && use_lg && lower_chunk_ruled_out<WB>(t, s_and + cur_buf * 2 * kMaxWB);
+        const unsigned active = __ballot_sync(0xffffffffu, !done && !skip);
         if (idx_chunk) {
             // a sample lacking a bit of the chunk's AND row dominates none of its references
-            const bool ruled = !done && chunk_ruled_out<WB>(t, s_and + cur_buf * kMaxWB);
+            const bool ruled = !done && chunk_ruled_out<WB>(t, s_and + cur_buf * 2 * kMaxWB);
             const unsigned need = __ballot_sync(0xffffffffu, !done && !ruled);
             if (__popc(need) > kCoopIdx) {
                 unsigned long long ops_unused = 0;
@@ -243,7 +246,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
                 __syncwarp();  // the columns read above are rewritten by their lanes for the next item
             }
         } else if (__popc(active) > kCoopLanes) {
-            if (!done) {
+            if (!done && !skip) {
                 bool m = false;
                 if (upper) {
                     for (int r = 0; r < cnt; ++r) {
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
-    __shared__ uint32_t s_and[2 * kMaxWB];   // AND rows of the staged index chunks
+    __shared__ uint32_t s_and[4 * kMaxWB];   // skip rows of the two staged chunks (AND row, guard row)
     const int tid = threadIdx.x;
     const BatchSmem m = batch_smem(smem);
     const uint64_t round = *((volatile unsigned long long *)&hdr->round);
@@ -494,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_deep_kernel(const BatchDesc
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
-    __shared__ uint32_t s_and[2 * kMaxWB];
+    __shared__ uint32_t s_and[4 * kMaxWB];
     const int tid = threadIdx.x;
     const BatchSmem m = batch_smem(smem);
     const uint64_t round = *((volatile unsigned long long *)&hdr->round);

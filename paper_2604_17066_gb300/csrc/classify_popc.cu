@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             const bool ix = use_idx && up;
             load_chunk_async<WB, kThreads>(s_buf + buf * (kChunk * WB), ix,
                                            ix ? p.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, p.kenc,
-                                           ix ? p.popc_UA + (size_t)c * WB : nullptr, s_and[buf], rows, cnt_c, tid);
+                                           ix ? p.popc_UA + (size_t)c * WB : nullptr, WB, s_and[buf], rows, cnt_c,
+                                           tid);
         };
         if (kBufs<WB>() == 2) {
             __syncthreads();            // every thread is done with the previous tile's buffers

@@ -150,23 +150,41 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Stage one chunk into shared memory, without waiting: an index chunk (kenc
-// rows of 8 words, from idx_src, and its AND row of WB words, from and_src) or
-// cnt bit-packed references of WB words (from rows_src).  Every address is 16-byte aligned: chunks start at
-// multiples of 256 references in 256-byte aligned regions.  The caller waits
-// with cp_async_wait_all() and a block barrier before reading.
+// rows of 8 words, from idx_src) or cnt bit-packed references of WB words
+// (from rows_src), and the chunk's and_words words of skip rows (from and_src
+// when not NULL: an index chunk's AND row, or a lower chunk's AND and guard
+// rows; and_words <= nthreads).  Every address is 16-byte aligned: chunks start
+// at multiples of 256 references in 256-byte aligned regions.  The caller
+// waits with cp_async_wait_all() and a block barrier before reading.
 template <int WB, int nthreads>
 __device__ __forceinline__ void load_chunk_async(uint32_t *dst, bool idx_chunk, const uint32_t *idx_src, int kenc,
-                                                 const uint32_t *and_src, uint32_t *and_dst,
+                                                 const uint32_t *and_src, int and_words, uint32_t *and_dst,
                                                  const uint32_t *rows_src, int cnt, int tid) {
+    if (and_src && tid < and_words) cp_async4(and_dst + tid, and_src + tid);
     if (idx_chunk) {
         for (int i = tid; i < kenc * 2; i += nthreads) cp_async16(dst + 4 * i, idx_src + 4 * i);
-        if (tid < WB) cp_async4(and_dst + tid, and_src + tid);   // the chunk's AND row
     } else {
         const int nw = cnt * WB, n16 = nw >> 2;
         for (int i = tid; i < n16; i += nthreads) cp_async16(dst + 4 * i, rows_src + 4 * i);
         for (int i = 4 * n16 + tid; i < nw; i += nthreads) cp_async4(dst + i, rows_src + i);
     }
     cp_async_commit();
+}
+
+// Lower chunk skip (rows ag: the AND of the chunk's forbidden-bit rows, then
+// the OR of their guard bits, all zero for no guard test): does the sample
+// have a 1 at a bit every reference of the chunk forbids, or a 1 at every
+// guard of the chunk?  Then it lies below none of them.
+template <int WB>
+__device__ __forceinline__ bool lower_chunk_ruled_out(const uint32_t (&t)[WB], const uint32_t *ag) {
+    uint32_t hit = 0u, miss = 0u, any = 0u;
+#pragma unroll
+    for (int w = 0; w < WB; ++w) {
+        hit |= t[w] & ag[w];
+        miss |= ag[WB + w] & ~t[w];
+        any |= ag[WB + w];
+    }
+    return hit != 0u || (any != 0u && miss == 0u);
 }
 
 // Does the sample (words t) lack a bit that every reference of the chunk has

@@ -16,6 +16,7 @@ struct BatchDesc {
     const uint32_t *popc_L, *popc_U;     // [R][words_b]
     const uint32_t *popc_UT;             // component-major index of the upper set, or NULL
     const uint32_t *popc_UA;             // per index chunk: AND of its references
+    const uint32_t *popc_LG;             // per lower chunk: AND row and guard row ([2][words_b]), or NULL
     const int32_t *overlap;              // precedence pre-check result
     uint8_t *labels;                     // [N] or NULL
     unsigned long long *counts3;         // [3]

@@ -329,10 +329,11 @@ void ordering_tables(const rsr_problem *p, std::vector<float> &tab) {
 
 // Reference order: decreasing probability of the region each reference
 // dominates under the current pmf, so that early exit meets a match sooner.
-// Labels do not depend on the order.  Writes the permutation to d_perm;
-// synchronises the stream (the scores come back to the host for sorting).
+// Labels do not depend on the order.  Writes the permutation to d_perm (and to
+// *idx_out if given); synchronises the stream (the scores come back to the host
+// for sorting).
 int order_references(const uint8_t *refs, int64_t R, int n, int K, const float *d_table, float *d_score,
-                     int32_t *d_perm, cudaStream_t s) {
+                     int32_t *d_perm, cudaStream_t s, std::vector<int32_t> *idx_out = nullptr) {
     if (R <= 0) return RSR_OK;
     std::vector<float> sc((size_t)R);
     RSR_CUDA(launch_score_refs(refs, R, n, K, d_table, d_score, s));
@@ -342,6 +343,7 @@ int order_references(const uint8_t *refs, int64_t R, int n, int K, const float *
     for (int64_t r = 0; r < R; ++r) idx[(size_t)r] = (int32_t)r;
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return sc[(size_t)a] > sc[(size_t)b]; });
     RSR_CUDA(cudaMemcpyAsync(d_perm, idx.data(), sizeof(int32_t) * (size_t)R, cudaMemcpyHostToDevice, s));
+    if (idx_out) *idx_out = std::move(idx);
     return RSR_OK;
 }
 
@@ -409,6 +411,102 @@ int build_upper_index(const rsr_problem *p, const uint32_t *pU, int64_t R_U, int
         perm = d_perm;
     }
     RSR_CUDA(launch_encode_index(pU, perm, R_U, words_b, kenc, out_index, out_and, s));
+    return RSR_OK;
+}
+
+// Lower set in guard order, and the rows of the lower chunk skip (bit-packed
+// rows).  A sample rules out a lower reference r (x <= r fails) exactly when
+// it has a 1 at one of r's forbidden bits, the thermometer bits that r lacks
+// (its encoded row).  The guard of r is its forbidden bit most likely to be 1
+// in a sample: (i, k) with P(x_i >= k) largest, ties to the lowest bit.  The
+// first chunk keeps the 256 most probable references (shallow matches are
+// found there); the rest is ordered by the rank of its guard, stably, so that
+// a chunk holds few distinct guards.  Per chunk c, ag[c] holds two rows of
+// `words` words: the AND of its references' rows (a sample with a 1 there
+// rules out the whole chunk) and the OR of their guards (a sample with all of
+// these bits 1 rules out the whole chunk; all zero, i.e. no test, where some
+// reference has no forbidden bit).  Labels do not depend on the order, and
+// both tests hold whatever guard each reference gets.  prob_idx: the order pL
+// was encoded through (rows of problem->ref_L); d_perm: scratch of R_L
+// entries.  Synchronises the stream.
+int guard_lower(const rsr_problem *p, uint32_t *pL, int words, const std::vector<int32_t> &prob_idx,
+                int32_t *d_perm, uint32_t *d_ag, cudaStream_t s) {
+    const int64_t R = p->R_L;
+    if (R <= 0) return RSR_OK;
+    const int K = p->K, km1 = K - 1, kenc = p->n * km1;
+    // bits by decreasing P(t_j = 1) = P(x_i >= k), ties by position
+    std::vector<std::pair<double, int>> pj;
+    pj.reserve((size_t)kenc);
+    std::vector<double> up((size_t)K);
+    for (int i = 0; i < p->n; ++i) {
+        double sfx = 0.0;
+        for (int v = K - 1; v >= 1; --v) {
+            sfx += p->pmf[(size_t)i * K + v];
+            up[(size_t)v] = sfx;
+        }
+        for (int k = 1; k <= km1; ++k) pj.push_back({up[(size_t)k], i * km1 + (k - 1)});
+    }
+    std::stable_sort(pj.begin(), pj.end(), [](const std::pair<double, int> &a, const std::pair<double, int> &b) {
+        return a.first > b.first;
+    });
+    std::vector<int32_t> rank((size_t)kenc);
+    for (int r = 0; r < kenc; ++r) rank[(size_t)pj[(size_t)r].second] = r;
+    std::vector<uint32_t> rows((size_t)R * words);
+    RSR_CUDA(cudaMemcpyAsync(rows.data(), pL, 4 * rows.size(), cudaMemcpyDeviceToHost, s));
+    RSR_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> gbit((size_t)R, -1);   // guard bit of each row (-1: none)
+    for (int64_t r = 0; r < R; ++r) {
+        int best = -1, best_rank = kenc;
+        for (int w = 0; w < words; ++w) {
+            uint32_t z = rows[(size_t)r * words + w];
+            while (z) {
+                const int j = 32 * w + __builtin_ctz(z);
+                z &= z - 1u;
+                if (j < kenc && rank[(size_t)j] < best_rank) {
+                    best_rank = rank[(size_t)j];
+                    best = j;
+                }
+            }
+        }
+        gbit[(size_t)r] = best;
+    }
+    // stable counting sort of rows [head, R) by guard rank (no guard: last)
+    const int64_t head = std::min<int64_t>(R, 256);
+    auto key = [&](int64_t r) { return gbit[(size_t)r] < 0 ? kenc : rank[(size_t)gbit[(size_t)r]]; };
+    std::vector<int64_t> cnt((size_t)kenc + 2, 0);
+    for (int64_t r = head; r < R; ++r) ++cnt[(size_t)key(r) + 1];
+    for (int v = 0; v <= kenc; ++v) cnt[(size_t)v + 1] += cnt[(size_t)v];
+    std::vector<int32_t> order((size_t)R);
+    for (int64_t r = 0; r < head; ++r) order[(size_t)r] = (int32_t)r;
+    for (int64_t r = head; r < R; ++r) order[(size_t)(head + cnt[(size_t)key(r)]++)] = (int32_t)r;
+    bool moved = false;
+    for (int64_t r = 0; r < R && !moved; ++r) moved = order[(size_t)r] != (int32_t)r;
+    std::vector<int32_t> composed;
+    if (moved) {
+        composed.resize((size_t)R);
+        for (int64_t k = 0; k < R; ++k) composed[(size_t)k] = prob_idx[(size_t)order[(size_t)k]];
+        RSR_CUDA(cudaMemcpyAsync(d_perm, composed.data(), sizeof(int32_t) * (size_t)R, cudaMemcpyHostToDevice, s));
+        RSR_CUDA(launch_encode_popc(p->ref_L, R, p->n, km1, words, true, pL, s, d_perm));
+    }
+    const int64_t nc = (R + 255) / 256;
+    std::vector<uint32_t> ag((size_t)nc * 2 * words, 0u);
+    for (int64_t c = 0; c < nc; ++c) {
+        uint32_t *a = ag.data() + (size_t)c * 2 * words, *g = a + words;
+        for (int w = 0; w < words; ++w) a[w] = 0xffffffffu;
+        bool guardless = false;
+        for (int64_t k = 256 * c; k < std::min<int64_t>(R, 256 * (c + 1)); ++k) {
+            const int64_t r = order[(size_t)k];
+            for (int w = 0; w < words; ++w) a[w] &= rows[(size_t)r * words + w];
+            const int j = gbit[(size_t)r];
+            if (j < 0) guardless = true;
+            else g[j >> 5] |= 1u << (j & 31);
+        }
+        if (guardless)
+            for (int w = 0; w < words; ++w) g[w] = 0u;
+    }
+    RSR_CUDA(cudaMemcpyAsync(d_ag, ag.data(), 4 * ag.size(), cudaMemcpyHostToDevice, s));
+    // the host vectors must outlive the copies
+    RSR_CUDA(cudaStreamSynchronize(s));
     return RSR_OK;
 }
 
@@ -772,7 +870,8 @@ namespace {
 struct BatchLayout {
     size_t off_descs = 0, off_begin = 0, off_deep_begin = 0, off_tc_descs = 0, off_tc_begin = 0, off_tune = 0,
            off_table = 0, off_score = 0, off_perm = 0, total = 0;
-    std::vector<size_t> off_hdr, off_thr, off_pL, off_pU, off_pUT, off_pUA, off_bit, off_lc, off_tgrad, off_deep;
+    std::vector<size_t> off_hdr, off_thr, off_pL, off_pLG, off_pU, off_pUT, off_pUA, off_bit, off_lc, off_tgrad,
+        off_deep;
     std::vector<size_t> off_tcL, off_tcU;   // FP8 tiles of the scenarios that may run on the pair kernel (else 0)
     std::vector<int> words_b, tc_kpad;
     std::vector<int64_t> deep_cap;          // deep-queue entries per scenario
@@ -830,6 +929,8 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S, const int64_t *Ns)
         off = align256(off + 8 * (size_t)p.n * km1);
         B.off_pL.push_back(off);
         off = align256(off + 4 * (size_t)p.R_L * wb);
+        B.off_pLG.push_back(off);  // per lower chunk: AND row and guard row
+        off = align256(off + 4 * (size_t)((p.R_L + 255) / 256) * 2 * wb);
         B.off_pU.push_back(off);
         off = align256(off + 4 * (size_t)p.R_U * wb);
         B.off_pUT.push_back(off);  // component-major index of the upper set
@@ -1023,11 +1124,15 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         RSR_CUDA(cudaMemcpyAsync(d_table, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s));
         const WsLayout Lk = layout_of(&p);
         const bool tc_enc = B.off_tcL[k] != 0 && tc2_available(Lk.tc_kpad);
-        if ((st = order_references(p.ref_L, p.R_L, p.n, p.K, d_table, d_score, d_perm, s)) != RSR_OK) return st;
+        std::vector<int32_t> prob_idx;
+        if ((st = order_references(p.ref_L, p.R_L, p.n, p.K, d_table, d_score, d_perm, s, &prob_idx)) != RSR_OK)
+            return st;
         RSR_CUDA(launch_encode_popc(p.ref_L, p.R_L, p.n, km1, B.words_b[k], true, pL, s, d_perm));
         if (tc_enc)
             RSR_CUDA(launch_encode_tc(p.ref_L, p.R_L, Lk.tc_rows_L, p.n, km1, Lk.tc_kpad, false,
                                       reinterpret_cast<uint8_t *>(base + B.off_tcL[k]), s, d_perm));
+        uint32_t *pLG = reinterpret_cast<uint32_t *>(base + B.off_pLG[k]);
+        if ((st = guard_lower(&p, pL, B.words_b[k], prob_idx, d_perm, pLG, s)) != RSR_OK) return st;
         if ((st = order_references(p.ref_U, p.R_U, p.n, p.K, d_table + (size_t)p.n * p.K, d_score, d_perm, s)) !=
             RSR_OK)
             return st;
@@ -1057,6 +1162,7 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.popc_U = pU;
         d.popc_UT = (p.R_U > 0 && !(p.flags & RSR_FLAG_NO_INDEX)) ? pUT : nullptr;
         d.popc_UA = d.popc_UT ? pUA : nullptr;
+        d.popc_LG = (p.R_L > 0 && !(p.flags & RSR_FLAG_NO_INDEX)) ? pLG : nullptr;
         d.overlap = &hs->overlap;
         d.labels = labels_or_null ? labels_or_null[k] : nullptr;
         d.counts3 = reinterpret_cast<unsigned long long *>(counts3xS + 3 * (size_t)k);
