@@ -67,12 +67,16 @@ typedef enum rsr_path {
 
 /* rsr_problem.flags */
 #define RSR_FLAG_DENSE 1u  /* test every sample against every reference (no early exit) */
-/* Bit-packed path, early-exit mode: scan the upper set reference by reference
- * instead of through its component-major index.  The index (built by
- * rsr_prepare) tests a chunk of 256 upper references with one 256-bit OR per
- * component of the sample below its top state, after a direct test of the 16
- * most probable upper references; labels, counts and gradient counts are the
- * same either way. */
+/* Bit-packed path, early-exit mode: scan both sets reference by reference,
+ * without the upper set's component-major index and the lower set's chunk
+ * skip.  The index (built by rsr_prepare) tests a chunk of 256 upper
+ * references with one 256-bit OR per component of the sample below its top
+ * state, after a direct test of the 16 most probable upper references.  The
+ * chunk skip passes over a chunk of 256 lower references when the sample has a
+ * 1 at a thermometer bit that all of them lack, or at every guard bit of the
+ * chunk (each lower reference's guard: the bit it lacks that is most likely 1;
+ * rsr_prepare groups the lower references after the 256 most probable by
+ * guard).  Labels, counts and gradient counts are the same either way. */
 #define RSR_FLAG_NO_INDEX 2u
 /* Failure-detection test hook (tensor-core path only): the reference producer
  * never starts, so the kernel's bounded waits run out after about 10 ms; the
@@ -156,10 +160,12 @@ RSR_API int rsr_update_pmf(const rsr_problem *problem, void *ws, size_t ws_bytes
  *   exec_tests_or_null  : device int64[2]; [0] += reference tests actually executed
  *                         (tiles issued x tile size on the tensor path; on the
  *                         bit-packed path every reference of an upper chunk that
- *                         the index test visits counts); [1] += the 32-bit logic
+ *                         the index test visits, and of a lower chunk that the
+ *                         chunk skip passes over, counts); [1] += the 32-bit logic
  *                         operations the bit-packed path issued on reference data:
  *                         one per word of each scanned reference test, one per
- *                         word of each chunk AND-row test, 4 per index row ORed
+ *                         word of each chunk AND-row test, two per word of each
+ *                         lower chunk-skip test, 4 per index row ORed
  *                         by one lane (8 words, two rows per three-input OR) plus
  *                         8 per encoding word it visits, 1 per index word ORed in
  *                         the warp-cooperative test (0 on the tensor path).

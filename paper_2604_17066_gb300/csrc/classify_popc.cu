@@ -98,12 +98,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     uint32_t *s_hot = s_cum + WB * 32;      // the first kHot upper references (index mode)
     uint32_t *s_first = s_hot + kHot * WB;  // component start bits per encoding word (index mode)
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
-    __shared__ uint32_t s_and[2][kMaxWords];   // AND rows of the staged index chunks
+    __shared__ uint32_t s_and[2][2 * kMaxWords];   // skip rows of the staged chunks (index AND row; lower AND, guard rows)
     __shared__ unsigned long long s_cnt[3];
     __shared__ unsigned long long s_exec, s_ops;
     __shared__ unsigned int s_fz;           // I^L samples counted by their zero bits
 
     const bool use_idx = p.popc_UT != nullptr && !p.dense && p.R_U > 0;
+    const bool use_lg = p.popc_LG != nullptr && !p.dense && p.R_L > 0;   // lower chunk skip rows
     const int hotc = use_idx ? (int)(p.R_U < kHot ? p.R_U : kHot) : 0;
     // binary states: 32-bit thresholds and never-bits in the same region
     uint32_t *s_t32 = reinterpret_cast<uint32_t *>(smem);
@@ -150,11 +151,11 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
         auto issue = [&](int buf, bool up, int64_t c) {
             int cnt_c;
             const uint32_t *rows = chunk_refs(up, c, &cnt_c);
-            const bool ix = use_idx && up;
+            const bool ix = use_idx && up, lg = use_lg && !up;
+            const uint32_t *skip = ix ? p.popc_UA + (size_t)c * WB : (lg ? p.popc_LG + (size_t)c * 2 * WB : nullptr);
             load_chunk_async<WB, kThreads>(s_buf + buf * (kChunk * WB), ix,
-                                           ix ? p.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, p.kenc,
-                                           ix ? p.popc_UA + (size_t)c * WB : nullptr, WB, s_and[buf], rows, cnt_c,
-                                           tid);
+                                           ix ? p.popc_UT + (size_t)c * kIdxChunk * WB : nullptr, p.kenc, skip,
+                                           ix ? WB : 2 * WB, s_and[buf], rows, cnt_c, tid);
         };
         if (kBufs<WB>() == 2) {
             __syncthreads();            // every thread is done with the previous tile's buffers
@@ -283,12 +284,19 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                     __syncwarp();  // the columns read above are rewritten by their lanes for the next tile
                 }
             } else {
-                // Early-exit mode.  While many lanes of the warp are unresolved each lane
-                // scans for its own sample; once few remain, the warp scans cooperatively,
-                // one unresolved sample at a time, 32 references per step.
-                const unsigned active = __ballot_sync(0xffffffffu, !done);
+                // Early-exit mode.  In a lower chunk a lane whose sample the chunk's skip
+                // rows rule out passes over it.  While many lanes of the warp are
+                // unresolved each lane scans for its own sample; once few remain, the warp
+                // scans cooperatively, one unresolved sample at a time, 32 references per step.
+                bool skip = false;
+                if (!done && !upper && use_lg) {
+                    skip = lower_chunk_ruled_out<WB>(t, s_and[cur_buf]);
+                    my_ops += 2 * WB;   // the skip-row test
+                    if (skip) my_exec += (unsigned long long)cnt;
+                }
+                const unsigned active = __ballot_sync(0xffffffffu, !done && !skip);
                 if (__popc(active) > kCoopLanes) {
-                    if (!done) {
+                    if (!done && !skip) {
                         int r = 0;
                         bool m = false;
                         if (upper) {

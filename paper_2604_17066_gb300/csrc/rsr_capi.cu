@@ -273,6 +273,9 @@ ClassifyParams make_params(const rsr_problem *p, const WsLayout &L, void *ws) {
     const bool idx = p->R_U > 0 && !(p->flags & RSR_FLAG_NO_INDEX);
     c.popc_UT = idx ? reinterpret_cast<const uint32_t *>(base + L.off_popc_UT) : nullptr;
     c.popc_UA = idx ? reinterpret_cast<const uint32_t *>(base + L.off_popc_UA) : nullptr;
+    c.popc_LG = (p->R_L > 0 && !(p->flags & RSR_FLAG_NO_INDEX))
+                    ? reinterpret_cast<const uint32_t *>(base + L.off_popc_LG)
+                    : nullptr;
     c.tc_L = reinterpret_cast<const uint8_t *>(base + L.off_tc_L);
     c.tc_U = reinterpret_cast<const uint8_t *>(base + L.off_tc_U);
     c.R_L = p->R_L;
@@ -615,14 +618,19 @@ int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_strea
     ordering_tables(problem, tab);
     RSR_CUDA(cudaMemcpyAsync(d_table, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice, s));
     const bool tc_enc = tc_supported() && L.tc_kpad <= tc_max_kpad();
-    // lower set: order, then encode through the order (the next ordering waits for these encodes)
-    if ((st = order_references(problem->ref_L, problem->R_L, problem->n, problem->K, d_table, d_score, d_perm, s)) !=
-        RSR_OK)
+    // lower set: order, then encode through the order (the next ordering waits for these encodes);
+    // the bit-packed rows then go into guard order
+    std::vector<int32_t> prob_idx;
+    if ((st = order_references(problem->ref_L, problem->R_L, problem->n, problem->K, d_table, d_score, d_perm, s,
+                               &prob_idx)) != RSR_OK)
         return st;
     RSR_CUDA(launch_encode_popc(problem->ref_L, problem->R_L, problem->n, km1, L.words, true, pL, s, d_perm));
     if (tc_enc)
         RSR_CUDA(launch_encode_tc(problem->ref_L, problem->R_L, L.tc_rows_L, problem->n, km1, L.tc_kpad, false,
                                   reinterpret_cast<uint8_t *>(base + L.off_tc_L), s, d_perm));
+    if ((st = guard_lower(problem, pL, L.words, prob_idx, d_perm,
+                          reinterpret_cast<uint32_t *>(base + L.off_popc_LG), s)) != RSR_OK)
+        return st;
     // upper set
     if ((st = order_references(problem->ref_U, problem->R_U, problem->n, problem->K,
                                d_table + (size_t)problem->n * problem->K, d_score, d_perm, s)) != RSR_OK)

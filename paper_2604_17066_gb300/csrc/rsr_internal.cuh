@@ -201,6 +201,7 @@ struct WsLayout {
     size_t off_perm = 0;        // int32 [max(R_L, R_U)]: reference order (ordering)
     size_t off_popc_UT = 0;     // uint32 [ceil(R_U/256)][32*words][8]: component-major index of the upper set
     size_t off_popc_UA = 0;     // uint32 [ceil(R_U/256)][words]: per index chunk, the AND of its references
+    size_t off_popc_LG = 0;     // uint32 [ceil(R_L/256)][2][words]: per lower chunk, AND row and guard row
     size_t total = 0;
 };
 
@@ -246,6 +247,8 @@ inline WsLayout make_layout(int32_t n, int32_t K, int64_t R_L, int64_t R_U, int3
     off = align256(off + sizeof(uint32_t) * (size_t)((R_U + 255) / 256) * 256 * L.words);
     L.off_popc_UA = off;
     off = align256(off + sizeof(uint32_t) * (size_t)((R_U + 255) / 256) * L.words);
+    L.off_popc_LG = off;
+    off = align256(off + sizeof(uint32_t) * (size_t)((R_L + 255) / 256) * 2 * L.words);
     L.total = off;
     return L;
 }
@@ -260,6 +263,7 @@ struct ClassifyParams {
     const uint32_t *popc_L, *popc_U;   // bit-packed references
     const uint32_t *popc_UT;           // component-major index of the upper set, or NULL (no index)
     const uint32_t *popc_UA;           // per index chunk: AND of its references (with popc_UT)
+    const uint32_t *popc_LG;           // per lower chunk: AND row and guard row ([2][words]), or NULL
     const uint8_t *tc_L, *tc_U;        // FP8 reference tiles
     int64_t R_L, R_U;
     int32_t tc_kpad;
