@@ -221,6 +221,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
         const int64_t tiles_U = (p.R_U + kPairRefs - 1) / kPairRefs;
         const int64_t tiles_L = (p.R_L + kPairRefs - 1) / kPairRefs;
         const int64_t T = tiles_U + tiles_L;
+        // Every other item of a pair walks the B tiles backwards.  The pairs take their
+        // items in step, so at any time they read about the same tiles, and the tiles a
+        // sweep read last are still in L2 when the next sweep starts on them.  Dense
+        // labels do not depend on the order of the tiles.
+        const bool rev = (((item - (int64_t)cluster_id_x()) / (int64_t)cluster_count_x()) & 1) != 0;
         const uint32_t half_bytes = (uint32_t)kHalfRefs * kp;
         int32_t *err = &p.hdr->error;
         const long long budget = p.test_stall ? kTestWaitCycles : kWaitCycles;
@@ -236,7 +241,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                     if (!mbar_wait(&ctl.empty[st_stage], st_phase ^ 1u, abort_flag, err, budget)) break;
                     bool up;
                     int64_t ti;
-                    chunk_at(j, tiles_U, tiles_L, overlap, &up, &ti);
+                    chunk_at(rev ? T - 1 - j : j, tiles_U, tiles_L, overlap, &up, &ti);
                     const uint8_t *src = (up ? p.tc_U : p.tc_L) + (size_t)(2 * ti + rank) * half_bytes;
                     mbar_arrive_expect_tx(&ctl.full[st_stage], half_bytes);
                     bulk_g2s(sStage + (size_t)st_stage * stage_stride, src, half_bytes, &ctl.full[st_stage]);
@@ -305,7 +310,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 bool is_upper;
                 int64_t ti;
-                chunk_at(j, tiles_U, tiles_L, overlap, &is_upper, &ti);
+                chunk_at(rev ? T - 1 - j : j, tiles_U, tiles_L, overlap, &is_upper, &ti);
                 // V >= 0 against lower references and V <= 0 against upper ones (padding
                 // rows give +1 / -1), so "some V = 0" is min V < 0.5 on a lower tile and
                 // max V > -0.5 on an upper tile
