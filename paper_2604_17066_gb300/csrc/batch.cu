@@ -118,40 +118,13 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
         else
             for (int w = 0; w < WB; ++w) s_tw[w * kThreads + tid] = 0u;
     } else {
-        uint32_t *col = s_tw + tid;
-        int w = 0, pos = 0;
-        uint32_t cur = 0;
-        if (valid) {
-            const uint64_t h = d.offset + round * (uint64_t)d.N + (uint64_t)hl;
-            // two independent Philox blocks per iteration (instruction-level parallelism)
-            for (int q = 0; 4 * q < d.n; q += 2) {
-                const U32x4 ra = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)q, 0u, key0, key1);
-                const U32x4 rb = philox4x32_10((uint32_t)h, (uint32_t)(h >> 32), (uint32_t)(q + 1), 0u, key0, key1);
-                const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int i = 4 * q + c;
-                    if (i >= d.n) break;
-                    const uint32_t x = state_from_uniform(us[c], s_thr + (size_t)i * d.km1, d.km1);
-                    const uint32_t bits = (1u << x) - 1u;
-                    cur |= bits << pos;
-                    const int np = pos + d.km1;
-                    if (np >= 32) {
-                        col[w * kThreads] = cur;
-                        ++w;
-                        cur = (np > 32) ? (bits >> (32 - pos)) : 0u;
-                        pos = np - 32;
-                    } else {
-                        pos = np;
-                    }
-                }
-            }
-            if (pos > 0) {
-                col[w * kThreads] = cur;
-                ++w;
-            }
-        }
-        for (; w < WB; ++w) col[w * kThreads] = 0u;
+        // multi-state: 32-bit tables and never words (multi_tables_to_smem) in the s_thr region
+        const uint32_t *s_t32k = reinterpret_cast<const uint32_t *>(s_thr);
+        if (valid)
+            sample_multi_words<WB, kThreads>(d.offset + round * (uint64_t)d.N + (uint64_t)hl, key0, key1, d.n, d.km1,
+                                             s_t32k, s_tw + tid);
+        else
+            for (int w = 0; w < WB; ++w) s_tw[w * kThreads + tid] = 0u;
     }
     uint32_t t[WB];
 #pragma unroll
@@ -399,7 +372,8 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
             uint32_t *s_t32 = reinterpret_cast<uint32_t *>(m.thr);   // [512] + never-words [16]
             binary_tables_to_smem(d.thr, d.n, s_t32, s_t32 + 512, tid, kThreads);
         } else {
-            for (int i = tid; i < nthr; i += kThreads) m.thr[i] = d.thr[i];
+            // 32-bit tables: at most 512 + 7 * 15 + 16 words of the 1024 in the region
+            multi_tables_to_smem(d.thr, d.n, d.km1, reinterpret_cast<uint32_t *>(m.thr), tid, kThreads);
         }
         for (int j = tid; j < d.words_b * 32; j += kThreads) m.cum[j] = 0u;
         if (d.popc_UT) {

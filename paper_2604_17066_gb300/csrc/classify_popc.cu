@@ -88,8 +88,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int nthr = p.n * p.km1;
-    unsigned long long *s_thr = reinterpret_cast<unsigned long long *>(smem);
+    // smem starts with the sampler's 32-bit threshold tables and never words (kMaxKenc * 8 bytes)
     uint32_t *s_tw = reinterpret_cast<uint32_t *>(smem + (size_t)kMaxKenc * 8);
     uint32_t *s_buf = s_tw + WB * kThreads;           // kBufs chunk buffers of kChunk * WB words
     // per thermometer bit: one bits of I^L samples counted by ballots, minus zero bits
@@ -106,13 +105,13 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     const bool use_idx = p.popc_UT != nullptr && !p.dense && p.R_U > 0;
     const bool use_lg = p.popc_LG != nullptr && !p.dense && p.R_L > 0;   // lower chunk skip rows
     const int hotc = use_idx ? (int)(p.R_U < kHot ? p.R_U : kHot) : 0;
-    // binary states: 32-bit thresholds and never-bits in the same region
+    // 32-bit thresholds and never words: binary (never words at kMaxKenc) or multi-state
+    // (multi_tables_to_smem's layout, at most kMaxKenc + 7 (K-1) + 32 words)
     uint32_t *s_t32 = reinterpret_cast<uint32_t *>(smem);
     uint32_t *s_never = s_t32 + kMaxKenc;
     const bool binary = p.km1 == 1;
     if (binary) binary_tables_to_smem(p.thr, p.n, s_t32, s_never, tid, kThreads);
-    else
-        for (int i = tid; i < nthr; i += kThreads) s_thr[i] = p.thr[i];
+    else multi_tables_to_smem(p.thr, p.n, p.km1, s_t32, tid, kThreads);   // 32-bit tables and never words
     if (use_idx) {
         for (int i = tid; i < hotc * WB; i += kThreads) s_hot[i] = p.popc_U[i];
         for (int w = tid; w < WB; w += kThreads) s_first[w] = component_first_bits(p.km1, p.kenc, w);
@@ -172,19 +171,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                 const uint8_t *row = p.samples + hl * (int64_t)p.n;
                 for (int i = 0; i < p.n; ++i) ww.put(row[i]);
             } else {
-                const uint64_t h = p.offset + (uint64_t)hl;
-                const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
-                // two independent Philox blocks per iteration (instruction-level parallelism)
-                for (int q = 0; 4 * q < p.n; q += 2) {
-                    const U32x4 ra = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
-                    const U32x4 rb = philox4x32_10(h0, h1, (uint32_t)(q + 1), 0u, key0, key1);
-                    const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int i = 4 * q + c;
-                        if (i < p.n) ww.put(state_from_uniform(us[c], s_thr + (size_t)i * p.km1, p.km1));
-                    }
-                }
+                sample_multi_words<WB, kThreads>(p.offset + (uint64_t)hl, key0, key1, p.n, p.km1, s_t32, s_tw + tid);
+                ww.w = WB;  // every word written
             }
         }
         ww.flush(WB);

@@ -109,6 +109,85 @@ __device__ __forceinline__ void sample_binary_words(uint64_t h, uint32_t key0, u
     for (; w < WB; ++w) col[w * stride] = 0u;
 }
 
+// Multi-state components (K > 2): thermometer bit j = i(K-1) + k-1 is
+// [u_i >= T_{i,k}], T <= 2^32.  As for binary states, each threshold is kept
+// as 32 bits, T32 = min(T, 2^32 - 1), with a never bit for T = 2^32 (the bit
+// is then 0 for every u < 2^32).  Thresholds do not decrease in k, so a
+// component's never bits are its top bits and its bits stay a thermometer.
+// Layout: s_t32k[k * npad + i] with npad = roundup(n, 8), so that one level's
+// thresholds of eight consecutive components load as two 16-byte words; the
+// never-words (one bit per thermometer bit, ceil(n(K-1)/32) words) follow at
+// s_t32k + (K-1) * npad.  Needs (K-1) * npad + ceil(n(K-1)/32) words.
+__device__ __forceinline__ void multi_tables_to_smem(const unsigned long long *__restrict__ thr, int n, int km1,
+                                                     uint32_t *s_t32k, int tid, int nthreads) {
+    const int npad = (n + 7) & ~7, kenc = n * km1;
+    for (int e = tid; e < km1 * npad; e += nthreads) {
+        const int k = e / npad, i = e - k * npad;
+        const unsigned long long T = i < n ? thr[(size_t)i * km1 + k] : (1ull << 32);
+        s_t32k[e] = T >= (1ull << 32) ? 0xffffffffu : (uint32_t)T;
+    }
+    uint32_t *s_never = s_t32k + km1 * npad;
+    for (int w = tid; 32 * w < kenc; w += nthreads) {
+        uint32_t m = 0u;
+        for (int b = 0; b < 32 && 32 * w + b < kenc; ++b)
+            if (thr[32 * w + b] >= (1ull << 32)) m |= 1u << b;
+        s_never[w] = m;
+    }
+}
+
+// Philox-sample a multi-state state straight into its thermometer words,
+// eight components per step (x_i = #{k : u_i >= T32_{i,k}}, then x_i ones at
+// bits i(K-1) ..), never bits cleared as each word is written to
+// col[w * stride]; words up to WB - 1 beyond the state are zeroed.  Same draws
+// and words as state_from_uniform() with thresholds held in 64 bits.
+template <int WB, int stride>
+__device__ __forceinline__ void sample_multi_words(uint64_t h, uint32_t key0, uint32_t key1, int n, int km1,
+                                                   const uint32_t *s_t32k, uint32_t *col) {
+    const int npad = (n + 7) & ~7;
+    const uint32_t *s_never = s_t32k + km1 * npad;
+    const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
+    uint32_t cur = 0u;
+    int pos = 0, w = 0;
+    for (int q = 0; 4 * q < n; q += 2) {
+        const U32x4 ra = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
+        const U32x4 rb = philox4x32_10(h0, h1, (uint32_t)(q + 1), 0u, key0, key1);
+        const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+        uint32_t x[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        for (int k = 0; k < km1; ++k) {
+            const uint4 ta = *reinterpret_cast<const uint4 *>(s_t32k + k * npad + 4 * q);
+            const uint4 tb = *reinterpret_cast<const uint4 *>(s_t32k + k * npad + 4 * q + 4);
+            x[0] += us[0] >= ta.x ? 1u : 0u;
+            x[1] += us[1] >= ta.y ? 1u : 0u;
+            x[2] += us[2] >= ta.z ? 1u : 0u;
+            x[3] += us[3] >= ta.w ? 1u : 0u;
+            x[4] += us[4] >= tb.x ? 1u : 0u;
+            x[5] += us[5] >= tb.y ? 1u : 0u;
+            x[6] += us[6] >= tb.z ? 1u : 0u;
+            x[7] += us[7] >= tb.w ? 1u : 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (4 * q + c >= n) break;
+            const uint32_t bits = (1u << x[c]) - 1u;   // x <= K-1 <= 15
+            cur |= bits << pos;
+            const int np = pos + km1;
+            if (np >= 32) {
+                col[w * stride] = cur & ~s_never[w];
+                ++w;
+                cur = (np > 32) ? (bits >> (32 - pos)) : 0u;
+                pos = np - 32;
+            } else {
+                pos = np;
+            }
+        }
+    }
+    if (pos > 0) {
+        col[w * stride] = cur & ~s_never[w];
+        ++w;
+    }
+    for (; w < WB; ++w) col[w * stride] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // Visiting order of the two reference sets, in chunks (tiles) of references.
 // Without an overlapping pair (no upper reference below a lower one) a sample
