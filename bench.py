@@ -448,6 +448,7 @@ def bench_c2_popc(rsr, torch, meas, reps=5):
     N = 1_000_000
     P = rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=rsr.RSR_PATH_POPC)
     sess = rsr.Session(P)
+    rsr.rsr_autotune(P, sess.ws)   # the first-pass budget (k0) of the two-pass kernel
     counts = torch.zeros(3, dtype=torch.int64, device="cuda")
     ex = torch.zeros(2, dtype=torch.int64, device="cuda")
     labels = torch.empty(N, dtype=torch.uint8, device="cuda")
@@ -714,6 +715,9 @@ def main():
     sess = rsr.Session(P)
     torch.cuda.synchronize()
     prep_ms = 1000 * (time.perf_counter() - t0)
+    if args.workload == "c2":
+        # the bit-packed path's first-pass budget, tuned on this problem (not timed)
+        rsr.rsr_autotune(P, sess.ws)
     overlap = sess.overlap()
     offset, n_rank = shard_range(N, rank, world)
     dev = torch.device("cuda", local)

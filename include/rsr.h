@@ -87,6 +87,10 @@ typedef enum rsr_path {
  * samples, so that tiles find it full and finish their walk themselves (the
  * fallback a queue of one entry per sample never needs). */
 #define RSR_FLAG_TEST_DEEP_CAP 0x200u
+/* Test hook (bit-packed path, early exit): two passes whenever the workspace
+ * holds a deep queue, whatever N (without it, calls of fewer than 2^19 samples
+ * run one pass). */
+#define RSR_FLAG_TEST_TWO_PASS 0x400u
 
 /*
  * One classification problem for a threshold m' (Sec. 3.2-3.3).
@@ -121,8 +125,13 @@ typedef struct rsr_estimate_out {
 } rsr_estimate_out;
 
 /*
- * Workspace bytes needed to classify up to N samples of `problem` (N only
- * bounds nothing today; it is reserved).  0 on invalid input.
+ * Workspace bytes for `problem` with a deep queue for calls of up to N
+ * samples: the prepared references, then (N > 0) a queue of min(N, 2^22)
+ * sample indices for the bit-packed path's second pass.  Any workspace of at
+ * least rsr_workspace_size(problem, 0) bytes serves calls of any N: the queue
+ * is whatever the workspace holds beyond that size (none: one pass), and a
+ * tile whose samples would overflow it finishes their walk itself.  0 on
+ * invalid input (or N < 0).
  */
 RSR_API size_t rsr_workspace_size(const rsr_problem *problem, int64_t N);
 
@@ -133,7 +142,9 @@ RSR_API size_t rsr_workspace_size(const rsr_problem *problem, int64_t N);
  * (bit-packed thermometer words; FP8 0/1 tiles in the tensor-core
  * shared-memory layout), builds the component-major index of the upper set
  * with one AND row per chunk of 256 references (in a clustered order when a
- * few binary components fail far more often than the rest), and runs the
+ * few binary components fail far more often than the rest), orders the lower
+ * set's bit-packed rows by guard after its 256 most probable references, with
+ * an AND row and a guard row per chunk (RSR_FLAG_NO_INDEX), and runs the
  * precedence pre-check (does any upper reference lie below a lower
  * reference?  Algorithm 1 lets lower win; if no pair overlaps, the kernels may
  * stop at the first match in either set).  None of these orders changes a
@@ -170,7 +181,12 @@ RSR_API int rsr_update_pmf(const rsr_problem *problem, void *ws, size_t ws_bytes
  *                         8 per encoding word it visits, 1 per index word ORed in
  *                         the warp-cooperative test (0 on the tensor path).
  * `ws` must be prepared for this problem and pmf (else RSR_ERR_NOT_PREPARED).
- * Capturable in a CUDA graph.
+ * On the bit-packed path in early-exit mode, when `ws` holds a deep queue (see
+ * rsr_workspace_size), the call is two launches after a memset of the queue's
+ * count: the first walks k0 reference chunks per 256-sample tile (k0 from
+ * rsr_autotune for this problem shape, else 2) and queues the samples still
+ * unresolved; the second finishes them 256 at a time.  Labels, counts and
+ * gradient counts are those of one pass.  Capturable in a CUDA graph.
  */
 RSR_API int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N,
                  const uint8_t *samples_or_null, uint8_t *labels_or_null, int64_t *counts3,
@@ -293,7 +309,10 @@ RSR_API int rsr_batch_grad(const rsr_problem *problems, int32_t S, const int64_t
  * Time both classifier paths on a slice of `problem` (prepared in `ws`; 2^18
  * samples in dense mode, 2^20 in early-exit mode) and remember the faster one
  * for RSR_PATH_AUTO on problems with the same n, K, density flag and
- * reference-count bucket (power of two).  *chosen_path receives it.
+ * reference-count bucket (power of two).  *chosen_path receives it.  When the
+ * bit-packed path wins in early-exit mode and `ws` holds a deep queue, its
+ * first-pass budget k0 in {0 (one pass), 2, 4, 8, 16} is timed too and
+ * remembered for the same shapes (used by rsr_classify whatever the path).
  * Synchronises `stream`.
  * Tuning cache: when the environment variable RSR_TUNE_CACHE names a file,
  * decisions (this one, and those of rsr_batch_autotune) are also kept there as

@@ -24,6 +24,7 @@ RSR_FLAG_DENSE = 1
 RSR_FLAG_NO_INDEX = 2
 RSR_FLAG_TEST_STALL = 0x100
 RSR_FLAG_TEST_DEEP_CAP = 0x200
+RSR_FLAG_TEST_TWO_PASS = 0x400
 
 
 class rsr_problem(ctypes.Structure):

@@ -165,10 +165,12 @@ class Session:
     estimate, and differentiate, reusing the encoded references (the references
     stay valid when the pmf changes, Sec. 5)."""
 
-    def __init__(self, problem: Problem, stream=None):
+    def __init__(self, problem: Problem, stream=None, max_samples: int = 1 << 20):
+        # the workspace holds a deep queue for calls of up to max_samples samples
+        # (the bit-packed path's second pass; larger calls defer fewer samples)
         self.problem = problem
         self.stream = stream
-        self.ws = alloc_workspace(problem)
+        self.ws = alloc_workspace(problem, max_samples)
         rsr_prepare(problem, self.ws, stream)
 
     def set_pmf(self, pmf) -> None:

@@ -59,6 +59,7 @@ struct Prepared {
 std::mutex g_mu;
 std::unordered_map<const void *, Prepared> g_prepared;
 std::unordered_map<uint64_t, int> g_tuned;  // rsr_autotune decisions for RSR_PATH_AUTO
+std::unordered_map<uint64_t, int> g_k0;     // rsr_autotune: first-pass chunk steps of the bit-packed path
 
 // Problems that share n, K, density and a reference-count bucket (powers of 2) share a decision.
 uint64_t tune_key(const rsr_problem *p) {
@@ -211,6 +212,57 @@ void remember_path(const rsr_problem *p, int path) {
         g_tuned[tune_key(p)] = path;
     }
     cache_put(path_cache_key(p), {path});
+}
+
+// First-pass chunk steps of the bit-packed early-exit path: rsr_autotune's
+// choice for this problem shape (this process, or the tuning cache), else
+// kClassifyDefaultK0.
+std::string k0_cache_key(const rsr_problem *p) { return "k0/" + path_cache_key(p).substr(5); }
+
+void remember_k0(const rsr_problem *p, int k0) {
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_k0[tune_key(p)] = k0;
+    }
+    cache_put(k0_cache_key(p), {k0});
+}
+
+int classify_k0(const rsr_problem *p) {
+    {
+        std::lock_guard<std::mutex> g(g_mu);
+        auto it = g_k0.find(tune_key(p));
+        if (it != g_k0.end()) return it->second;
+    }
+    std::vector<long long> cached;
+    if (cache_get(k0_cache_key(p), &cached) && cached.size() == 1 && cached[0] >= 0 && cached[0] <= 4096) {
+        std::lock_guard<std::mutex> g(g_mu);
+        g_k0[tune_key(p)] = (int)cached[0];
+        return (int)cached[0];
+    }
+    return kClassifyDefaultK0;
+}
+
+// The deep queue of the two-pass bit-packed path lives in the workspace beyond
+// the prepared layout: a 256-byte count line, then int64 entries, as many as fit
+// (at most kClassifyDeepCap).  A workspace of exactly the layout's size has none
+// and runs one pass.
+size_t deep_queue_bytes(int64_t N) {
+    if (N <= 0) return 0;
+    return align256(256 + 8 * (size_t)std::min<int64_t>(N, kClassifyDeepCap));
+}
+
+void set_deep_queue(ClassifyParams &c, const rsr_problem *p, const WsLayout &L, void *ws, size_t ws_bytes) {
+    c.deep = nullptr;
+    c.deep_count = nullptr;
+    c.deep_cap = 0;
+    c.k0 = 0;
+    if (ws_bytes < L.total + 256 + 8 * 256) return;
+    char *base = static_cast<char *>(ws);
+    c.deep_count = reinterpret_cast<unsigned long long *>(base + L.total);
+    c.deep = reinterpret_cast<int64_t *>(base + L.total + 256);
+    c.deep_cap = std::min<int64_t>((int64_t)((ws_bytes - L.total - 256) / 8), kClassifyDeepCap);
+    c.k0 = classify_k0(p);
+    c.two_pass_min_n = (p->flags & RSR_FLAG_TEST_TWO_PASS) ? 1 : kTwoPassMinN;
 }
 
 int validate(const rsr_problem *p) {
@@ -592,9 +644,8 @@ using namespace rsr;
 extern "C" {
 
 size_t rsr_workspace_size(const rsr_problem *problem, int64_t N) {
-    (void)N;
-    if (validate(problem) != RSR_OK) return 0;
-    return layout_of(problem).total;
+    if (validate(problem) != RSR_OK || N < 0) return 0;
+    return layout_of(problem).total + deep_queue_bytes(N);
 }
 
 int rsr_prepare(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stream_t stream) {
@@ -694,6 +745,7 @@ int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t offset, int
     c.counts3 = reinterpret_cast<unsigned long long *>(counts3);
     c.grad_counts = reinterpret_cast<unsigned long long *>(grad_counts_or_null);
     c.exec_tests = reinterpret_cast<unsigned long long *>(exec_tests_or_null);
+    set_deep_queue(c, problem, L, ws, ws_bytes);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int path = choose_path(problem);
     if (path == RSR_PATH_TC) {
@@ -811,6 +863,7 @@ int rsr_level_pmf(const rsr_problem *problems, int32_t n_boundaries, void *const
         c.offset = offset;
         c.labels = labels_scratch + (size_t)b * N;
         c.counts3 = reinterpret_cast<unsigned long long *>(counts3_per_boundary + 3 * b);
+        set_deep_queue(c, &problems[b], L, ws[b], ws_bytes[b]);
         if (choose_path(&problems[b]) == RSR_PATH_TC) {
             if (!tc_supported() || L.tc_kpad > tc_max_kpad()) return RSR_ERR_UNSUPPORTED;
             RSR_CUDA(launch_classify_tc(c, s));
@@ -1520,14 +1573,12 @@ int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stre
     c.seed = 0x5EEDull;
     c.offset = 0;
     c.counts3 = reinterpret_cast<WsHeader *>(ws)->tune_counts;
+    set_deep_queue(c, problem, L, ws, ws_bytes);
     cudaEvent_t e0, e1;
     RSR_CUDA(cudaEventCreate(&e0));
     RSR_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_path = RSR_PATH_POPC;
-    const bool tc_ok = tc_supported() && L.tc_kpad <= tc_max_kpad();
-    for (int path = RSR_PATH_POPC; path <= RSR_PATH_TC; ++path) {
-        if (path == RSR_PATH_TC && !tc_ok) continue;
+    // two timed runs after one untimed
+    auto timed3 = [&](int path, float *out) -> int {
         float sum = 0.0f;
         for (int rep = 0; rep < 3; ++rep) {
             RSR_CUDA(cudaEventRecord(e0, s));
@@ -1538,13 +1589,40 @@ int rsr_autotune(const rsr_problem *problem, void *ws, size_t ws_bytes, rsr_stre
             RSR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             if (rep > 0) sum += ms;
         }
+        *out = sum;
+        return RSR_OK;
+    };
+    float best = 1e30f;
+    int best_path = RSR_PATH_POPC;
+    const bool tc_ok = tc_supported() && L.tc_kpad <= tc_max_kpad();
+    for (int path = RSR_PATH_POPC; path <= RSR_PATH_TC; ++path) {
+        if (path == RSR_PATH_TC && !tc_ok) continue;
+        float sum = 0.0f;
+        if ((st = timed3(path, &sum)) != RSR_OK) break;
         if (sum < best) {
             best = sum;
             best_path = path;
         }
     }
+    // the bit-packed path in early-exit mode with a deep queue: its first-pass budget
+    if (st == RSR_OK && best_path == RSR_PATH_POPC && !c.dense && c.deep_cap > 0) {
+        static const int k0s[] = {0, 2, 4, 8, 16};
+        float best_k = 1e30f;
+        int best_k0 = c.k0;
+        for (int k0 : k0s) {
+            c.k0 = k0;
+            float sum = 0.0f;
+            if ((st = timed3(RSR_PATH_POPC, &sum)) != RSR_OK) break;
+            if (sum < best_k) {
+                best_k = sum;
+                best_k0 = k0;
+            }
+        }
+        if (st == RSR_OK) remember_k0(problem, best_k0);
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (st != RSR_OK) return st;
     remember_path(problem, best_path);
     if (chosen_path) *chosen_path = best_path;
     return RSR_OK;

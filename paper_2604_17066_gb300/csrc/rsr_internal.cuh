@@ -14,6 +14,9 @@ namespace rsr {
 // ---------------------------------------------------------------------------
 constexpr int kMaxK = 16;
 constexpr int kMaxKenc = 1024;                 // n*(K-1) thermometer bits
+constexpr int kClassifyDefaultK0 = 2;          // first-pass chunk steps of the two-pass bit-packed path
+constexpr int64_t kTwoPassMinN = int64_t(1) << 19;   // calls with fewer samples run one pass
+constexpr int64_t kClassifyDeepCap = int64_t(1) << 22;   // deep-queue entries at most (32 MB)
 constexpr int kMaxWords = kMaxKenc / 32;       // 32-bit words per encoded state
 constexpr int kTcKPad = 32;                    // FP8 MMA K step (bytes)
 
@@ -115,7 +118,7 @@ __device__ __forceinline__ void sample_binary_words(uint64_t h, uint32_t key0, u
 // is then 0 for every u < 2^32).  Thresholds do not decrease in k, so a
 // component's never bits are its top bits and its bits stay a thermometer.
 // Layout: s_t32k[k * npad + i] with npad = roundup(n, 8), so that one level's
-// thresholds of eight consecutive components load as two 16-byte words; the
+// thresholds of four consecutive components load as one 16-byte word; the
 // never-words (one bit per thermometer bit, ceil(n(K-1)/32) words) follow at
 // s_t32k + (K-1) * npad.  Needs (K-1) * npad + ceil(n(K-1)/32) words.
 __device__ __forceinline__ void multi_tables_to_smem(const unsigned long long *__restrict__ thr, int n, int km1,
@@ -135,11 +138,14 @@ __device__ __forceinline__ void multi_tables_to_smem(const unsigned long long *_
     }
 }
 
-// Philox-sample a multi-state state straight into its thermometer words,
-// eight components per step (x_i = #{k : u_i >= T32_{i,k}}, then x_i ones at
-// bits i(K-1) ..), never bits cleared as each word is written to
+// Philox-sample a multi-state state straight into its thermometer words, four
+// components (one Philox block) per step (x_i = #{k : u_i >= T32_{i,k}}, then
+// x_i ones at bits i(K-1) ..), never bits cleared as each word is written to
 // col[w * stride]; words up to WB - 1 beyond the state are zeroed.  Same draws
-// and words as state_from_uniform() with thresholds held in 64 bits.
+// and words as state_from_uniform() with thresholds held in 64 bits.  (One
+// block per step, not two as for binary states: the level compares give the
+// step its parallelism, and the kernels that inline this stay within their
+// register budget.)
 template <int WB, int stride>
 __device__ __forceinline__ void sample_multi_words(uint64_t h, uint32_t key0, uint32_t key1, int n, int km1,
                                                    const uint32_t *s_t32k, uint32_t *col) {
@@ -148,27 +154,21 @@ __device__ __forceinline__ void sample_multi_words(uint64_t h, uint32_t key0, ui
     const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
     uint32_t cur = 0u;
     int pos = 0, w = 0;
-    for (int q = 0; 4 * q < n; q += 2) {
-        const U32x4 ra = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
-        const U32x4 rb = philox4x32_10(h0, h1, (uint32_t)(q + 1), 0u, key0, key1);
-        const uint32_t us[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-        uint32_t x[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    for (int q = 0; 4 * q < n; ++q) {
+        const U32x4 r = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
+        uint32_t x0 = 0u, x1 = 0u, x2 = 0u, x3 = 0u;
         for (int k = 0; k < km1; ++k) {
-            const uint4 ta = *reinterpret_cast<const uint4 *>(s_t32k + k * npad + 4 * q);
-            const uint4 tb = *reinterpret_cast<const uint4 *>(s_t32k + k * npad + 4 * q + 4);
-            x[0] += us[0] >= ta.x ? 1u : 0u;
-            x[1] += us[1] >= ta.y ? 1u : 0u;
-            x[2] += us[2] >= ta.z ? 1u : 0u;
-            x[3] += us[3] >= ta.w ? 1u : 0u;
-            x[4] += us[4] >= tb.x ? 1u : 0u;
-            x[5] += us[5] >= tb.y ? 1u : 0u;
-            x[6] += us[6] >= tb.z ? 1u : 0u;
-            x[7] += us[7] >= tb.w ? 1u : 0u;
+            const uint4 t = *reinterpret_cast<const uint4 *>(s_t32k + k * npad + 4 * q);
+            x0 += r.x >= t.x ? 1u : 0u;
+            x1 += r.y >= t.y ? 1u : 0u;
+            x2 += r.z >= t.z ? 1u : 0u;
+            x3 += r.w >= t.w ? 1u : 0u;
         }
+        const uint32_t xs[4] = {x0, x1, x2, x3};
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < 4; ++c) {
             if (4 * q + c >= n) break;
-            const uint32_t bits = (1u << x[c]) - 1u;   // x <= K-1 <= 15
+            const uint32_t bits = (1u << xs[c]) - 1u;   // x <= K-1 <= 15
             cur |= bits << pos;
             const int np = pos + km1;
             if (np >= 32) {
@@ -353,6 +353,13 @@ struct ClassifyParams {
     WsHeader *hdr;
     int32_t dense;
     int32_t test_stall;                // RSR_FLAG_TEST_STALL: the producer never starts
+    // bit-packed early-exit mode, two passes (NULL / 0: one pass)
+    int64_t *deep;                     // [deep_cap] deep queue: indices of the samples the first pass defers
+    unsigned long long *deep_count;    // samples appended to the queue (may exceed deep_cap)
+    int64_t deep_cap;
+    int32_t k0;                        // chunk steps of the first pass (0: one pass)
+    int64_t two_pass_min_n;            // fewer samples: one pass (kTwoPassMinN; 1 under RSR_FLAG_TEST_TWO_PASS)
+    int32_t deep_pass;                 // set by the launcher for the second pass
 };
 
 }  // namespace rsr
