@@ -739,6 +739,8 @@ def main():
     c2 = torch.zeros(2, dtype=torch.int64, device=dev)
     stage2_ms = []
 
+    classify_launches = rsr.rsr_classify_plan(P, n_rank, sess.ws)[1]
+
     def step(k, grad=True, ev=None):
         counts.zero_()
         gcounts.zero_()
@@ -760,7 +762,9 @@ def main():
             rsr.rsr_grad(P, 1, off, n_rank, gcounts, sess.ws, u_lower_idx=uidx[:n_ul] if n_ul else None,
                          stream=stream)
         est = rsr.rsr_estimate(counts.cpu().numpy(), n_rank, n_ul)
-        step.last_launches = 1 + (system is not None) + (grad and n_ul > 0)   # classify, resolve, correction
+        # classify (one launch, two for the bit-packed path's two passes), resolve,
+        # and rsr_grad's index check and correction
+        step.last_launches = classify_launches + (system is not None) + (2 if (grad and n_ul > 0) else 0)
         return est
 
     for k in range(args.warmup):

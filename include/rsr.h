@@ -194,6 +194,15 @@ RSR_API int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t off
                  void *ws, size_t ws_bytes, rsr_stream_t stream);
 
 /*
+ * What rsr_classify would run for N samples of `problem` in a prepared
+ * workspace of ws_bytes bytes (host only, no device work): out[0] = the path
+ * (RSR_PATH_POPC or RSR_PATH_TC, after RSR_PATH_AUTO's decision), out[1] = the
+ * kernel launches (0 for N = 0; 2 when the bit-packed path runs two passes),
+ * out[2] = the first pass's chunk-step budget k0 (0: one pass).
+ */
+RSR_API int rsr_classify_plan(const rsr_problem *problem, int64_t N, size_t ws_bytes, int32_t out[3]);
+
+/*
  * Estimates on the host from counts3 (host int64[3]) and H = N (Sec. 3.3):
  * p_hat = count/H and delta_hat = sqrt((1 - p)/(H p)); n_u_lower = number of
  * unclassified samples that Phi resolved to S <= m' (Sec. 3.5 Stage 2; pass 0

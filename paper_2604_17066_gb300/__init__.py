@@ -10,7 +10,7 @@ from __future__ import annotations
 
 __all__ = [
     "Problem", "Session", "RSRProb", "RSRError", "alloc_workspace",
-    "rsr_workspace_size", "rsr_prepare", "rsr_update_pmf", "rsr_classify", "rsr_estimate",
+    "rsr_workspace_size", "rsr_prepare", "rsr_update_pmf", "rsr_classify", "rsr_classify_plan", "rsr_estimate",
     "rsr_grad", "rsr_sample", "rsr_workspace_status",
     "Batch", "rsr_batch_prepare", "rsr_batch", "rsr_batch_autotune", "rsr_autotune",
     "rsr_classify_static", "rsr_batch_grad", "System", "rsr_resolve",

@@ -122,6 +122,15 @@ def rsr_classify(problem: Problem, seed: int, offset: int, N: int, ws: torch.Ten
                                    _stream(stream)), "rsr_classify")
 
 
+def rsr_classify_plan(problem: Problem, N: int, ws: torch.Tensor):
+    """(path, kernel launches, k0) that rsr_classify would use for N samples
+    in the prepared workspace ws (host only)."""
+    out = np.zeros(3, dtype=np.int32)
+    s = problem.struct()
+    check(_lib.load().rsr_classify_plan(ctypes.byref(s), int(N), ws.numel(), out.ctypes.data), "rsr_classify_plan")
+    return int(out[0]), int(out[1]), int(out[2])
+
+
 def rsr_estimate(counts3, N: int, n_u_lower: int = 0) -> dict:
     c = np.ascontiguousarray(np.asarray(counts3, dtype=np.int64).reshape(3))
     out = rsr_estimate_out()

@@ -59,6 +59,15 @@ struct Shared {
     unsigned int warp_pend[kThreads / 32];
 };
 
+// The multi-state sampler as a call: inlined, its registers would add to the
+// walk's in this one kernel for every scenario (spills 180 -> 400 bytes in
+// batch_kernel); called, it keeps its own (224 bytes).
+template <int WB>
+__device__ __noinline__ void sample_multi_call(uint64_t h, uint32_t key0, uint32_t key1, int n, int km1,
+                                               const uint32_t *s_t32k, uint32_t *col) {
+    sample_multi_words<WB, kThreads>(h, key0, key1, n, km1, s_t32k, col);
+}
+
 // One item.  First pass (deep == nullptr): samples tile*256 + tid, chunk steps
 // 0 .. k0-1 (all steps if k0 = 0), then the unresolved samples go to the deep
 // queue.  Second pass: the sample whose local index is deep[tid] (none if
@@ -121,8 +130,8 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
         // multi-state: 32-bit tables and never words (multi_tables_to_smem) in the s_thr region
         const uint32_t *s_t32k = reinterpret_cast<const uint32_t *>(s_thr);
         if (valid)
-            sample_multi_words<WB, kThreads>(d.offset + round * (uint64_t)d.N + (uint64_t)hl, key0, key1, d.n, d.km1,
-                                             s_t32k, s_tw + tid);
+            sample_multi_call<WB>(d.offset + round * (uint64_t)d.N + (uint64_t)hl, key0, key1, d.n, d.km1, s_t32k,
+                                  s_tw + tid);
         else
             for (int w = 0; w < WB; ++w) s_tw[w * kThreads + tid] = 0u;
     }

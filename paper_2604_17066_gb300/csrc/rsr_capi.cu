@@ -757,6 +757,24 @@ int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t offset, int
     return RSR_OK;
 }
 
+int rsr_classify_plan(const rsr_problem *problem, int64_t N, size_t ws_bytes, int32_t out[3]) {
+    int st = validate(problem);
+    if (st != RSR_OK) return st;
+    if (N < 0 || !out) return RSR_ERR_INVALID_ARG;
+    const WsLayout L = layout_of(problem);
+    if (ws_bytes < L.total) return RSR_ERR_WORKSPACE;
+    const int path = choose_path(problem);
+    const bool dense = (problem->flags & RSR_FLAG_DENSE) != 0;
+    const bool queue = ws_bytes >= L.total + 256 + 8 * 256;   // as set_deep_queue
+    const int k0 = queue ? classify_k0(problem) : 0;
+    const int64_t min_n = (problem->flags & RSR_FLAG_TEST_TWO_PASS) ? 1 : kTwoPassMinN;
+    const bool two = path != RSR_PATH_TC && !dense && queue && k0 > 0 && N >= min_n;
+    out[0] = path;
+    out[1] = N == 0 ? 0 : (two ? 2 : 1);
+    out[2] = two ? k0 : 0;
+    return RSR_OK;
+}
+
 int rsr_estimate(const int64_t counts3[3], int64_t N, int64_t n_u_lower, rsr_estimate_out *out) {
     if (!counts3 || !out || N <= 0 || n_u_lower < 0 || n_u_lower > counts3[2] || counts3[0] < 0 ||
         counts3[1] < 0 || counts3[2] < 0 || counts3[0] + counts3[1] + counts3[2] != N)
