@@ -543,6 +543,22 @@ def cpu_baseline(prob, seed, n_sample, offset=0):
     return n_sample / dt, dt
 
 
+def c5_cpu_baseline(N_each=5000, stride=16):
+    """The oracle as it stands on one host core over a bounded sample of the
+    batched workload: N_each samples of every stride-th scenario."""
+    import workloads.large as L
+    probs = L.c5_batch()
+    tot_n, tot_t, k = 0, 0.0, 0
+    for s in range(0, len(probs), stride):
+        _, dt = cpu_baseline(probs[s], 1000 + s, N_each)
+        tot_n += N_each
+        tot_t += dt
+        k += 1
+    return {"value": tot_n / tot_t, "unit": "samples/s", "cores": 1, "kind": "oracle",
+            "sample": "%d samples of each of %d scenarios (every %dth of 256), one core, %.1f s"
+                      % (N_each, k, stride, tot_t)}
+
+
 def run_reference(args):
     """--impl reference: the oracle timed on the host cores on the same workload."""
     rank = int(os.environ.get("RANK", "0"))
@@ -643,6 +659,8 @@ def run_batch_line(args):
             "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32 bit-packed", "data": "synthetic", "config": {"workload": res["workload"]},
             "clocks": clk.summary(), "batch": res}
+    if not args.quick:
+        line["cpu_baseline"] = c5_cpu_baseline()
     print(json.dumps(line), flush=True)
     return 0
 
