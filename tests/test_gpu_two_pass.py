@@ -82,3 +82,23 @@ def test_two_pass_after_autotune(rsr):
     assert np.array_equal(got["labels"], lab)
     assert np.array_equal(got["counts3"], cnt)
     assert np.array_equal(got["grad_counts"].reshape(prob.n, prob.K), C)
+
+
+def test_two_pass_with_an_overlapping_pair(rsr):
+    """An upper reference below a lower one: every lower chunk comes first
+    (lower takes precedence, Algorithm 1), so the first pass's k0 steps are all
+    lower chunks and the deferred samples resume there."""
+    import workloads as W
+    prob = sparse_match_problem(80, 600, 3000, 6, 24, seed=21)   # three lower chunks, rarely matched
+    extra_U = prob.ref_L[:1].copy()
+    extra_U[0, :5] = 0
+    bad = W.Problem("overlapping", prob.pmf, prob.ref_L, np.concatenate([prob.ref_U, extra_U]))
+    assert O.count_overlaps(bad.ref_L, bad.ref_U) > 0
+    sess = session_with_queue(rsr, bad, 1 << 20)
+    assert sess.overlap()
+    N = 9000
+    lab, cnt, C = oracle_of(bad, 6, 123, N)
+    got = run(sess, 6, 123, N)
+    assert np.array_equal(got["labels"], lab)
+    assert np.array_equal(got["counts3"], cnt)
+    assert np.array_equal(got["grad_counts"].reshape(bad.n, bad.K), C)
