@@ -402,7 +402,11 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
     no_index_ms = ev[0].elapsed_time(ev[1]) / reps
     del bn
     R = [p.R_L + p.R_U for p in P]
+    # the generator alone: the Philox4x32-10 blocks both paths draw, at the measured rate
+    philox_blocks = sum(N * ((p.n + 3) // 4) for p in P)
+    philox_ms = 1e3 * philox_blocks / rsr.rsr_measure_philox_rate()
     return {"workload": "c5_256_scenarios_N%d" % N, "scenarios": S, "refs_total": int(sum(R)),
+            "philox_blocks": philox_blocks, "philox_floor_ms": philox_ms,
             "batched_no_index_ms": no_index_ms,
             "batched_ms": batched_ms, "per_scenario_ms": plain_ms, "speedup_kernels": plain_ms / batched_ms,
             "per_scenario_kernel_sum_ms": kernel_sum_ms, "per_scenario_gaps_ms": plain_ms - kernel_sum_ms,
@@ -422,6 +426,8 @@ def popc_roofline(rsr, n, K, n_samples, kern_ms, word_ops, meas=None):
     words, index rows).  Peak: this mix at the LOP3 and IMAD.WIDE rates measured
     on this GPU (time bound = max(ALU ops / LOP3 rate, IMAD ops / IMAD rate))."""
     meas = meas or rsr.rsr_measure_int_peak()
+    if "philox_blocks_per_s" not in meas:
+        meas = dict(meas, philox_blocks_per_s=rsr.rsr_measure_philox_rate())
     blocks = n_samples * ((n + 3) // 4)
     imad_ops = 20.0 * blocks
     alu_ops = 60.0 * blocks + n_samples * n * (K - 1) + float(word_ops)
@@ -433,6 +439,8 @@ def popc_roofline(rsr, n, K, n_samples, kern_ms, word_ops, meas=None):
             "traffic": None, "issued_word_ops": float(word_ops), "philox_blocks": float(blocks),
             "measured_lop3_tops": meas["lop3_ops_per_s"] / 1e12,
             "measured_imad_wide_tops": meas["imad_ops_per_s"] / 1e12,
+            "measured_philox_blocks_per_s": meas["philox_blocks_per_s"],
+            "philox_floor_ms": 1e3 * blocks / meas["philox_blocks_per_s"],
             "note": "integer-op model on issued operations (per Philox block 20 IMAD.WIDE + 60 ALU ops, n(K-1) "
                     "compares per sample, the kernel's own count of logic operations on reference data); peak = "
                     "this mix at the LOP3 and IMAD.WIDE rates measured on this GPU (rsr_measure_int_peak)"}

@@ -543,6 +543,16 @@ RSR_API int rsr_stage1(const rsr_problem *problem, const rsr_system *system, con
 RSR_API int rsr_measure_int_peak(double *lop3_ops_per_s, double *imad_ops_per_s, rsr_stream_t stream);
 
 /*
+ * Measured rate of the samplers' generator on the current GPU (not a step of
+ * the method): Philox4x32-10 blocks per second on a full grid (8 blocks of 256
+ * threads per SM, eight independent counters per thread), the library's own
+ * implementation, timed on the second of two launches.
+ *   blocks_per_s : host double[1].
+ * Synchronous (waits for its own kernels on `stream`); allocates nothing.
+ */
+RSR_API int rsr_measure_philox_rate(double *blocks_per_s, rsr_stream_t stream);
+
+/*
  * Measured dense FP8 tensor-core rate of the current GPU, for the roofline of
  * the tensor-core classifiers (not a step of the method; the paper has no
  * counterpart).  One CTA per SM issues tcgen05.mma.kind::f8f6f4 (K = 32, E4M3

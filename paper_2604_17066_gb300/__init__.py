@@ -15,6 +15,7 @@ __all__ = [
     "Batch", "rsr_batch_prepare", "rsr_batch", "rsr_batch_autotune", "rsr_autotune",
     "rsr_classify_static", "rsr_batch_grad", "System", "rsr_resolve",
     "rsr_boundary_search", "rsr_nondominated", "rsr_stage1", "rsr_level_pmf", "rsr_measure_int_peak", "rsr_measure_fp8_peak",
+    "rsr_measure_philox_rate",
     "RSR_PHI_ST_CONNECTIVITY", "RSR_PHI_ST_MAXFLOW_LEVELS", "RSR_PHI_GLOBAL_CONNECTIVITY",
     "RSR_PHI_GLOBAL_CONN_LEVEL", "RSR_SEARCH_INDEX_ORDER", "RSR_SEARCH_PERMUTED",
     "RSR_PATH_AUTO", "RSR_PATH_POPC", "RSR_PATH_TC", "RSR_FLAG_DENSE", "RSR_FLAG_NO_INDEX",

@@ -98,6 +98,7 @@ _I32, _I64, _U64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
 _PROB = ctypes.POINTER(rsr_problem)
 SIGNATURES = {
     "rsr_measure_int_peak": (ctypes.c_int, [_P, _P, _P]),
+    "rsr_measure_philox_rate": (ctypes.c_int, [_P, _P]),
     "rsr_measure_fp8_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_double, _P, _P, _P]),
     "rsr_classify_plan": (ctypes.c_int, [_PROB, _I64, ctypes.c_size_t, _P]),
     "rsr_workspace_size": (ctypes.c_size_t, [_PROB, _I64]),

@@ -496,6 +496,14 @@ def rsr_measure_int_peak(stream=None) -> dict:
     return {"lop3_ops_per_s": lop3.value, "imad_ops_per_s": imad.value}
 
 
+def rsr_measure_philox_rate(stream=None) -> float:
+    """rsr_measure_philox_rate: Philox4x32-10 blocks per second of the library's
+    generator on the current GPU."""
+    rate = ctypes.c_double(0.0)
+    check(_lib.load().rsr_measure_philox_rate(ctypes.addressof(rate), _stream(stream)), "rsr_measure_philox_rate")
+    return rate.value
+
+
 def rsr_measure_fp8_peak(seconds: float = 0.0, cta_pair: bool = False, stream=None) -> dict:
     """rsr_measure_fp8_peak: measured dense FP8 tensor-core rate of the current
     GPU (tcgen05.mma kind::f8f6f4, E4M3 operands, FP32 accumulation), in

@@ -73,6 +73,25 @@ __global__ void __launch_bounds__(kPeakThreads) imad_peak_kernel(uint32_t seed) 
     if ((uint32_t)x == 0x5EED5EEDu) g_peak_sink = (uint32_t)x;
 }
 
+// Philox4x32-10 blocks (the samplers' generator, rsr_internal.cuh) with eight
+// independent counters per thread: the generator's own rate, which issue
+// slots, not the multiplier alone, bound (each round is two wide products, two
+// three-input XORs and two key additions).
+constexpr int kPhiloxIters = 1 << 10;
+
+__global__ void __launch_bounds__(kPeakThreads) philox_rate_kernel(uint32_t seed) {
+    const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0u;
+    for (int i = 0; i < kPhiloxIters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) {
+            const U32x4 r = philox4x32_10(gid, (uint32_t)i, (uint32_t)k, 0u, seed, ~seed);
+            acc ^= r.x ^ r.y ^ r.z ^ r.w;
+        }
+    }
+    if (acc == 0x5EED5EEDu) g_peak_sink = acc;
+}
+
 constexpr int kMmaM = 128, kMmaN = 256;
 constexpr int kMmaKBytes = 128;           // four K steps of 32 E4M3 values per iteration
 constexpr int kFp8Threads = 128;
@@ -269,6 +288,34 @@ extern "C" int rsr_measure_fp8_peak(int32_t cta_pair, double seconds, double *bu
         if (e != cudaSuccess) return cuda_fail(e, "rsr_measure_fp8_peak");
         if (err != 0) return RSR_ERR_TIMEOUT;
     }
+    return st;
+}
+
+extern "C" int rsr_measure_philox_rate(double *blocks_per_s, rsr_stream_t stream) {
+    if (!blocks_per_s) return RSR_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int grid = device_sm_count() * kPeakBlocksPerSM;
+    const double blocks = (double)grid * kPeakThreads * (double)kPhiloxIters * kChains;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "rsr_measure_philox_rate");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "rsr_measure_philox_rate");
+    }
+    int st = RSR_OK;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 2 && st == RSR_OK; ++rep) {
+        cudaEventRecord(e0, s);
+        philox_rate_kernel<<<grid, kPeakThreads, 0, s>>>(0x1234u + rep);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) st = cuda_fail(e, "rsr_measure_philox_rate");
+    }
+    if (st == RSR_OK) *blocks_per_s = blocks / (ms / 1000.0);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     return st;
 }
 

@@ -192,3 +192,12 @@ def test_measured_integer_peaks_are_plausible(rsr):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     for k in ("lop3_ops_per_s", "imad_ops_per_s"):
         assert sms * 16 * 0.5e9 < m[k] < sms * 256 * 3e9, (k, m[k])
+
+
+def test_measured_philox_rate_is_plausible(rsr):
+    """rsr_measure_philox_rate (the samplers' generator alone) returns between
+    0.1 and 16 Philox4x32-10 blocks per SM per cycle at 0.5-3 GHz: each block is
+    20 wide products and about 40 other integer ops."""
+    rate = rsr.rsr_measure_philox_rate()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert sms * 0.1 * 0.5e9 < rate < sms * 16 * 3e9, rate
