@@ -55,6 +55,7 @@ struct Shared {
     unsigned long long cnt[3];
     unsigned int fz;   // I^L samples of the item counted by their zero bits
     int last;
+    int changed;                 // the item's scenario differs from the block's previous one
     long long deep_pos;          // the item's reservation in its scenario's deep queue
     unsigned int warp_pend[kThreads / 32];
 };
@@ -367,7 +368,8 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
                 const int mid = (lo + hi + 1) >> 1;
                 if (begin[mid] <= item) lo = mid; else hi = mid - 1;
             }
-            if (lo != sh.scenario) {
+            sh.changed = lo != sh.scenario;
+            if (sh.changed) {
                 sh.scenario = lo;
                 sh.d = descs[lo];
             }
@@ -377,19 +379,23 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
         __syncthreads();
         const BatchDesc &d = sh.d;
         const int nthr = d.n * d.km1;
-        if (d.km1 == 1) {
-            uint32_t *s_t32 = reinterpret_cast<uint32_t *>(m.thr);   // [512] + never-words [16]
-            binary_tables_to_smem(d.thr, d.n, s_t32, s_t32 + 512, tid, kThreads);
-        } else {
-            // 32-bit tables: at most 512 + 7 * 15 + 16 words of the 1024 in the region
-            multi_tables_to_smem(d.thr, d.n, d.km1, reinterpret_cast<uint32_t *>(m.thr), tid, kThreads);
+        // the scenario's tables stay in shared memory while the block's items stay in it
+        // (items only read them)
+        if (sh.changed) {
+            if (d.km1 == 1) {
+                uint32_t *s_t32 = reinterpret_cast<uint32_t *>(m.thr);   // [512] + never-words [16]
+                binary_tables_to_smem(d.thr, d.n, s_t32, s_t32 + 512, tid, kThreads);
+            } else {
+                // 32-bit tables: at most 512 + 7 * 15 + 16 words of the 1024 in the region
+                multi_tables_to_smem(d.thr, d.n, d.km1, reinterpret_cast<uint32_t *>(m.thr), tid, kThreads);
+            }
+            if (d.popc_UT) {
+                const int hotw = (int)(d.R_U < kHot ? d.R_U : kHot) * d.words_b;
+                for (int i = tid; i < hotw; i += kThreads) m.hot[i] = d.popc_U[i];
+                for (int w = tid; w < d.words_b; w += kThreads) m.first[w] = component_first_bits(d.km1, nthr, w);
+            }
         }
         for (int j = tid; j < d.words_b * 32; j += kThreads) m.cum[j] = 0u;
-        if (d.popc_UT) {
-            const int hotw = (int)(d.R_U < kHot ? d.R_U : kHot) * d.words_b;
-            for (int i = tid; i < hotw; i += kThreads) m.hot[i] = d.popc_U[i];
-            for (int w = tid; w < d.words_b; w += kThreads) m.first[w] = component_first_bits(d.km1, nthr, w);
-        }
         __syncthreads();
         const int64_t k = item - begin[sh.scenario];   // tile, or group of queued samples
         const int64_t *deep = nullptr;
