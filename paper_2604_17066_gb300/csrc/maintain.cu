@@ -6,11 +6,14 @@
 //   t(r_j) AND NOT t(r_i) = 0, and r_j = r_i iff the words are equal.  One
 //   reference per thread against the set streamed through shared memory (the
 //   same shape as the bit-packed classifier), a block leaving as soon as all
-//   of its references are known to be dominated.
+//   of its references are known to be dominated; a (bit count, hash) key per
+//   row skips the pairs that cannot dominate.
 // * Selection: the first `limit` indices i (ascending) with flags[i] == value,
 //   in three launches (per-tile counts, one-block exclusive scan of the
 //   counts, ballot-ranked scatter).  Stage 1 uses it to pick unclassified
 //   samples as search starts and to compact reference rows in order.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "rsr_internal.cuh"
@@ -25,28 +28,69 @@ constexpr int kSelTile = 4096;
 constexpr int kSelThreads = 256;
 constexpr int kScanThreads = 1024;
 
-// keep[j] for the candidates j in [c0, c1): no row i in [d0, d1), i != j, dominates
-// row j, and none equals it with i < j (indices are global rows of enc).
+// Row key for the pair filter: the number of thermometer bits (the sum of the
+// states) and a 32-bit hash of the words.
+template <int WB>
+__device__ __forceinline__ void row_key(const uint32_t *row, uint32_t *pop, uint32_t *hash) {
+    uint32_t c = 0u, h = 0x811C9DC5u;
+#pragma unroll
+    for (int w = 0; w < WB; ++w) {
+        c += __popc(row[w]);
+        h = (h ^ row[w]) * 0x01000193u;
+        h ^= h >> 15;
+    }
+    *pop = c;
+    *hash = h;
+}
+
+// Clears keep[j] for the candidates j in [c0, c1) that a row i in this block's
+// slice of [d0, d1) dominates, or equals with i < j (indices are global rows of
+// enc; keep[] is set to 1 before the launch).  Blocks along y take consecutive
+// slices of `slice` rows, so a few candidates against many rows still fill the
+// machine; a candidate that another slice has already cleared is skipped.
+// Pair filter, exact: a row that makes row j redundant has fewer thermometer
+// bits (upper set: r_i <= r_j; lower set: r_i >= r_j, so more bits), or as many
+// and then equals row j.  So rows with more (upper) or fewer (lower) bits are
+// skipped, and rows with as many bits are tested only when their hashes agree.
+// The keys of each staged chunk are computed once in shared memory.  (Upper
+// references that are spanning trees of one graph all have the same number of
+// bits: then only equal hashes reach the word test.)
 template <int WB>
 __global__ void __launch_bounds__(kNdThreads) nondominated_kernel(const uint32_t *__restrict__ enc, int64_t c0,
-                                                                  int64_t c1, int64_t d0, int64_t d1, int upper,
-                                                                  uint8_t *__restrict__ keep,
-                                                                  unsigned long long *n_keep) {
+                                                                  int64_t c1, int64_t d0, int64_t d1, int64_t slice,
+                                                                  int upper, uint8_t *keep) {
     __shared__ __align__(16) uint32_t s_ref[kNdThreads * WB];
+    __shared__ uint32_t s_pop[kNdThreads], s_hash[kNdThreads];
     const int64_t j = c0 + (int64_t)blockIdx.x * kNdThreads + threadIdx.x;
+    const int64_t e0 = d0 + (int64_t)blockIdx.y * slice;
+    const int64_t e1 = (d1 - e0) < slice ? d1 : e0 + slice;
     uint32_t a[WB];
 #pragma unroll
     for (int w = 0; w < WB; ++w) a[w] = (j < c1) ? enc[j * WB + w] : 0u;
-    bool done = !(j < c1);      // dominated, or no reference in this slot
-    for (int64_t base = d0; base < d1; base += kNdThreads) {
+    uint32_t pop_j, hash_j;
+    row_key<WB>(a, &pop_j, &hash_j);
+    // no reference in this slot, or already dominated (by another slice)
+    bool done = !(j < c1) || *((volatile const uint8_t *)&keep[j]) == 0;
+    bool dominated = false;     // found here
+    for (int64_t base = e0; base < e1; base += kNdThreads) {
         if (__syncthreads_and(done)) break;
-        const int cnt = (int)((d1 - base) < kNdThreads ? (d1 - base) : kNdThreads);
+        const int cnt = (int)((e1 - base) < kNdThreads ? (e1 - base) : kNdThreads);
         for (int idx = threadIdx.x; idx < cnt * WB; idx += kNdThreads) s_ref[idx] = enc[base * WB + idx];
+        __syncthreads();
+        if ((int)threadIdx.x < cnt) {
+            uint32_t row[WB];
+#pragma unroll
+            for (int w = 0; w < WB; ++w) row[w] = s_ref[threadIdx.x * WB + w];
+            row_key<WB>(row, &s_pop[threadIdx.x], &s_hash[threadIdx.x]);
+        }
         __syncthreads();
         if (!done) {
             for (int r = 0; r < cnt; ++r) {
                 const int64_t i = base + r;
                 if (i == j) continue;
+                const uint32_t pi = s_pop[r];
+                if (upper ? (pi > pop_j) : (pi < pop_j)) continue;
+                if (pi == pop_j && s_hash[r] != hash_j) continue;
                 uint32_t viol = 0u, diff = 0u;
 #pragma unroll
                 for (int w = 0; w < WB; ++w) {
@@ -56,24 +100,53 @@ __global__ void __launch_bounds__(kNdThreads) nondominated_kernel(const uint32_t
                 }
                 if (viol == 0u && (diff != 0u || i < j)) {
                     done = true;
+                    dominated = true;
                     break;
                 }
             }
         }
     }
-    if (j < c1) {
-        keep[j] = done ? 0 : 1;
-        if (!done) atomicAdd(n_keep, 1ull);
-    }
+    if (dominated) keep[j] = 0;
 }
+
+// *n_keep += the number of ones in keep[c0, c1).
+__global__ void __launch_bounds__(kNdThreads) count_keep_kernel(const uint8_t *__restrict__ keep, int64_t c0,
+                                                                int64_t c1, unsigned long long *n_keep) {
+    unsigned c = 0u;
+    for (int64_t i = c0 + (int64_t)blockIdx.x * kNdThreads + threadIdx.x; i < c1;
+         i += (int64_t)gridDim.x * kNdThreads)
+        c += keep[i];
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(n_keep, (unsigned long long)c);
+}
+
+// Candidates [c0, c1) against rows [d0, d1): keep[c0, c1) set to 1, then cleared
+// for the dominated ones.  The rows are split into slices (multiples of the
+// block's 256) so that the grid holds about kNdTargetBlocks blocks.
+constexpr int64_t kNdTargetBlocks = 2048;
 
 template <int WB>
 cudaError_t launch_nd_wb(const uint32_t *enc, int64_t c0, int64_t c1, int64_t d0, int64_t d1, bool upper,
-                         uint8_t *keep, unsigned long long *n_keep, cudaStream_t s) {
+                         uint8_t *keep, cudaStream_t s) {
     const int64_t blocks = (c1 - c0 + kNdThreads - 1) / kNdThreads;
     if (blocks <= 0) return cudaSuccess;
-    nondominated_kernel<WB><<<(unsigned)blocks, kNdThreads, 0, s>>>(enc, c0, c1, d0, d1, upper ? 1 : 0, keep,
-                                                                     n_keep);
+    cudaError_t e = cudaMemsetAsync(keep + c0, 1, (size_t)(c1 - c0), s);
+    if (e != cudaSuccess || d1 <= d0) return e;
+    const int64_t chunks = (d1 - d0 + kNdThreads - 1) / kNdThreads;
+    int64_t slices = std::max<int64_t>(1, std::min<int64_t>(chunks, kNdTargetBlocks / blocks));
+    slices = std::min<int64_t>(slices, 65535);
+    const int64_t slice = ((chunks + slices - 1) / slices) * kNdThreads;
+    slices = (d1 - d0 + slice - 1) / slice;
+    nondominated_kernel<WB><<<dim3((unsigned)blocks, (unsigned)slices), kNdThreads, 0, s>>>(
+        enc, c0, c1, d0, d1, slice, upper ? 1 : 0, keep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_keep(const uint8_t *keep, int64_t c0, int64_t c1, unsigned long long *n_keep,
+                              cudaStream_t s) {
+    if (c1 <= c0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((c1 - c0 + kNdThreads - 1) / kNdThreads, 1024);
+    count_keep_kernel<<<(unsigned)blocks, kNdThreads, 0, s>>>(keep, c0, c1, n_keep);
     return cudaGetLastError();
 }
 
@@ -161,18 +234,18 @@ __global__ void gather_rows_kernel(const uint8_t *__restrict__ src, const int64_
 
 namespace {
 cudaError_t launch_nd_range(const uint32_t *enc, int64_t c0, int64_t c1, int64_t d0, int64_t d1, int words_b,
-                            bool upper, uint8_t *keep, unsigned long long *n_keep, cudaStream_t s) {
+                            bool upper, uint8_t *keep, cudaStream_t s) {
     switch (words_b) {
-        case 1: return launch_nd_wb<1>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 2: return launch_nd_wb<2>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 4: return launch_nd_wb<4>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 6: return launch_nd_wb<6>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 8: return launch_nd_wb<8>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 10: return launch_nd_wb<10>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 12: return launch_nd_wb<12>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 16: return launch_nd_wb<16>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 24: return launch_nd_wb<24>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
-        case 32: return launch_nd_wb<32>(enc, c0, c1, d0, d1, upper, keep, n_keep, s);
+        case 1: return launch_nd_wb<1>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 2: return launch_nd_wb<2>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 4: return launch_nd_wb<4>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 6: return launch_nd_wb<6>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 8: return launch_nd_wb<8>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 10: return launch_nd_wb<10>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 12: return launch_nd_wb<12>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 16: return launch_nd_wb<16>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 24: return launch_nd_wb<24>(enc, c0, c1, d0, d1, upper, keep, s);
+        case 32: return launch_nd_wb<32>(enc, c0, c1, d0, d1, upper, keep, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -181,7 +254,9 @@ cudaError_t launch_nd_range(const uint32_t *enc, int64_t c0, int64_t c1, int64_t
 cudaError_t launch_nondominated(const uint32_t *enc, int64_t R, int words_b, bool upper, uint8_t *keep,
                                 unsigned long long *n_keep, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
-    return launch_nd_range(enc, 0, R, 0, R, words_b, upper, keep, n_keep, s);
+    cudaError_t e = launch_nd_range(enc, 0, R, 0, R, words_b, upper, keep, s);
+    if (e != cudaSuccess) return e;
+    return launch_count_keep(keep, 0, R, n_keep, s);
 }
 
 // Rows [0, R_old) are already non-dominated among themselves (no row dominates
@@ -192,9 +267,10 @@ cudaError_t launch_nondominated(const uint32_t *enc, int64_t R, int words_b, boo
 cudaError_t launch_nondominated_appended(const uint32_t *enc, int64_t R_old, int64_t R, int words_b, bool upper,
                                          uint8_t *keep, unsigned long long *n_keep, cudaStream_t s) {
     if (R <= 0) return cudaSuccess;
-    cudaError_t e = launch_nd_range(enc, 0, R_old, R_old, R, words_b, upper, keep, n_keep, s);
+    cudaError_t e = launch_nd_range(enc, 0, R_old, R_old, R, words_b, upper, keep, s);
     if (e != cudaSuccess) return e;
-    return launch_nd_range(enc, R_old, R, 0, R, words_b, upper, keep, n_keep, s);
+    if ((e = launch_nd_range(enc, R_old, R, 0, R, words_b, upper, keep, s)) != cudaSuccess) return e;
+    return launch_count_keep(keep, 0, R, n_keep, s);
 }
 
 size_t select_scratch_bytes(int64_t N) {
