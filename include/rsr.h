@@ -125,13 +125,13 @@ typedef struct rsr_estimate_out {
 } rsr_estimate_out;
 
 /*
- * Workspace bytes for `problem` with a deep queue for calls of up to N
- * samples: the prepared references, then (N > 0) a queue of min(N, 2^22)
- * sample indices for the bit-packed path's second pass.  Any workspace of at
- * least rsr_workspace_size(problem, 0) bytes serves calls of any N: the queue
- * is whatever the workspace holds beyond that size (none: one pass), and a
- * tile whose samples would overflow it finishes their walk itself.  0 on
- * invalid input (or N < 0).
+ * Workspace bytes for `problem` with deep queues for calls of up to N
+ * samples: the prepared references, then (N > 0) two queues of min(N, 2^22)
+ * sample indices each for the bit-packed path's staged passes.  Any workspace
+ * of at least rsr_workspace_size(problem, 0) bytes serves calls of any N: the
+ * queues are whatever the workspace holds beyond that size (none: one pass),
+ * and a tile whose samples would overflow a queue finishes their walk itself.
+ * 0 on invalid input (or N < 0).
  */
 RSR_API size_t rsr_workspace_size(const rsr_problem *problem, int64_t N);
 
@@ -181,12 +181,15 @@ RSR_API int rsr_update_pmf(const rsr_problem *problem, void *ws, size_t ws_bytes
  *                         8 per encoding word it visits, 1 per index word ORed in
  *                         the warp-cooperative test (0 on the tensor path).
  * `ws` must be prepared for this problem and pmf (else RSR_ERR_NOT_PREPARED).
- * On the bit-packed path in early-exit mode, when `ws` holds a deep queue (see
- * rsr_workspace_size), the call is two launches after a memset of the queue's
- * count: the first walks k0 reference chunks per 256-sample tile (k0 from
- * rsr_autotune for this problem shape, else 2) and queues the samples still
- * unresolved; the second finishes them 256 at a time.  Labels, counts and
- * gradient counts are those of one pass.  Capturable in a CUDA graph.
+ * On the bit-packed path in early-exit mode, for N >= 2^19 samples, when `ws`
+ * holds deep queues (see rsr_workspace_size), the call runs in stages, one
+ * launch each (after a memset of the count of the queue it fills): the first
+ * walks k0 reference chunks per 256-sample tile (k0 from rsr_autotune for this
+ * problem shape, else 2) and queues the samples still unresolved; each later
+ * stage takes the queued samples 256 at a time and walks on to four times the
+ * chunk step it starts at, queueing again, and the last walks to the end
+ * (rsr_classify_plan gives the count).  Labels, counts and gradient counts are
+ * those of one pass.  Capturable in a CUDA graph.
  */
 RSR_API int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t offset, int64_t N,
                  const uint8_t *samples_or_null, uint8_t *labels_or_null, int64_t *counts3,
@@ -197,7 +200,7 @@ RSR_API int rsr_classify(const rsr_problem *problem, uint64_t seed, uint64_t off
  * What rsr_classify would run for N samples of `problem` in a prepared
  * workspace of ws_bytes bytes (host only, no device work): out[0] = the path
  * (RSR_PATH_POPC or RSR_PATH_TC, after RSR_PATH_AUTO's decision), out[1] = the
- * kernel launches (0 for N = 0; 2 when the bit-packed path runs two passes),
+ * kernel launches (0 for N = 0; one per stage when the bit-packed path runs in stages),
  * out[2] = the first pass's chunk-step budget k0 (0: one pass).
  */
 RSR_API int rsr_classify_plan(const rsr_problem *problem, int64_t N, size_t ws_bytes, int32_t out[3]);

@@ -83,9 +83,9 @@ struct WordWriter {
     }
 };
 
-// kDeep: the two-pass form (first pass with deferral, or the second pass); the
-// one-pass launches run an instantiation without it, which keeps the walk's
-// register budget.
+// kDeep: the staged form (a pass that reads the call's tiles or a queue, and may
+// queue the samples it leaves unresolved); the one-pass launches run an
+// instantiation without it, which keeps the walk's register budget.
 template <int WB, bool kDeep>
 __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel(const ClassifyParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     __shared__ unsigned long long s_cnt[3];
     __shared__ unsigned long long s_exec, s_ops;
     __shared__ unsigned int s_fz;           // I^L samples counted by their zero bits
-    __shared__ unsigned int s_pend[kThreads / 32];   // first pass: unresolved samples per warp at step k0
-    __shared__ long long s_deep_pos;                 // first pass: the tile's reservation in the deep queue
+    __shared__ unsigned int s_pend[kThreads / 32];   // unresolved samples per warp at the pass's last step
+    __shared__ long long s_deep_pos;                 // the tile's reservation in the output queue
 
-    // second pass: nothing to do for blocks beyond the queued groups (before any set-up)
-    if (kDeep && p.deep_pass != 0) {
-        const unsigned long long q = *((volatile const unsigned long long *)p.deep_count);
+    // a pass over a queue: nothing to do for blocks beyond its groups (before any set-up)
+    if (kDeep && p.q_in >= 0) {
+        const unsigned long long q = *((volatile const unsigned long long *)(p.deep_count + p.q_in));
         const unsigned long long queued_now = q < (unsigned long long)p.deep_cap ? q : (unsigned long long)p.deep_cap;
         if ((unsigned long long)blockIdx.x * kThreads >= queued_now) return;
     }
@@ -142,28 +142,34 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
     unsigned long long my_cnt0 = 0, my_cnt1 = 0, my_cnt2 = 0, my_exec = 0;
     unsigned long long my_ops = 0;   // 32-bit logic operations on reference data (scan words, AND rows, index rows)
 
-    // Two passes in early-exit mode with a deep queue (p.k0 > 0): the first walks
-    // at most k0 chunk steps per tile and queues the samples still unresolved; the
-    // second (p.deep_pass) takes them 256 at a time and finishes their walks.
-    const bool second = kDeep && p.deep_pass != 0;
+    // Staged passes in early-exit mode (kDeep): a pass walks chunk steps
+    // [step_lo, step_hi) for the call's tiles (q_in < 0, step_lo = 0) or for the
+    // samples queue q_in holds, 256 at a time, and queues the samples still
+    // unresolved at step_hi into queue q_out for the next pass (none in the last).
+    const bool second = kDeep && p.q_in >= 0;
     const int64_t nU = (p.R_U + kChunk - 1) / kChunk, nL = (p.R_L + kChunk - 1) / kChunk;
     const int64_t nsteps = nU + nL;
-    const bool defer = kDeep && !p.dense && p.k0 > 0 && p.deep != nullptr && p.deep_cap > 0;
-    const int64_t k0 = defer && (int64_t)p.k0 < nsteps ? (int64_t)p.k0 : nsteps;
-    const int64_t step0 = second ? k0 : 0;
+    const bool defer = kDeep && !p.dense && p.q_out >= 0 && p.deep != nullptr && p.deep_cap > 0;
+    const int64_t step0 = second ? (p.step_lo < nsteps ? p.step_lo : nsteps) : 0;
+    const int64_t lim0 = defer && p.step_hi < nsteps ? p.step_hi : nsteps;
+    const int64_t *q_in = second ? p.deep + (size_t)p.q_in * p.deep_cap : nullptr;
+    int64_t *q_out = defer ? p.deep + (size_t)p.q_out * p.deep_cap : nullptr;
+    unsigned long long *q_out_count = defer ? p.deep_count + p.q_out : nullptr;
     const int64_t queued =
-        second ? (int64_t)min(*((volatile const unsigned long long *)p.deep_count), (unsigned long long)p.deep_cap) : 0;
+        second ? (int64_t)min(*((volatile const unsigned long long *)(p.deep_count + p.q_in)),
+                              (unsigned long long)p.deep_cap)
+               : 0;
     const int64_t ntiles = second ? (queued + kThreads - 1) / kThreads : (p.N + kThreads - 1) / kThreads;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         int64_t hl = tile * kThreads + tid;
-        if (second) hl = hl < queued ? p.deep[hl] : -1;   // -1: a voided entry or no entry
+        if (second) hl = hl < queued ? q_in[hl] : -1;   // -1: a voided entry or no entry
         const bool valid = hl >= 0 && hl < p.N;
         ChunkWalk walk(nU, nL, overlap, use_idx);
         bool upper = false;
         int64_t ci = 0;
-        for (int64_t i = 0; i < step0; ++i) walk.next(&upper, &ci);   // the second pass resumes at step k0
+        for (int64_t i = 0; i < step0; ++i) walk.next(&upper, &ci);   // a later pass resumes at step_lo
         walk.next(&upper, &ci);   // step0 < nsteps: some reference exists, and nothing is queued at nsteps
-        int64_t lim = second ? nsteps : k0;
+        int64_t lim = lim0;
         bool deferred = false;
         auto chunk_refs = [&](bool up, int64_t c, int *cnt_out) {
             const int64_t R = up ? p.R_U : p.R_L;
@@ -230,9 +236,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             const bool all_done = __syncthreads_and(done);  // chunk `step` visible; chunk step-1 consumed
             if (all_done && !p.dense) break;
             if (kDeep && step == lim) {
-                // First pass, budget spent: queue the unresolved samples (a block-wide
-                // reservation).  An unresolved sample has no match so far: with an
-                // overlapping pair a lower match is final and upper chunks come last.
+                // The pass's steps are spent: queue the unresolved samples for the next
+                // pass (a block-wide reservation).  An unresolved sample has no match so
+                // far: with an overlapping pair a lower match is final and upper chunks
+                // come last.
                 const bool pend = !done;
                 const unsigned wb = __ballot_sync(0xffffffffu, pend);
                 if (lane == 0) s_pend[tid >> 5] = (unsigned)__popc(wb);
@@ -244,19 +251,19 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
                     before += (w < (tid >> 5)) ? c : 0;
                     total += c;
                 }
-                if (tid == 0) s_deep_pos = (long long)atomicAdd(p.deep_count, (unsigned long long)total);
+                if (tid == 0) s_deep_pos = (long long)atomicAdd(q_out_count, (unsigned long long)total);
                 __syncthreads();
                 const long long pos = s_deep_pos;
                 if (pos + total <= (long long)p.deep_cap) {
                     if (pend) {
-                        p.deep[pos + before + __popc(wb & ((1u << lane) - 1u))] = hl;
+                        q_out[pos + before + __popc(wb & ((1u << lane) - 1u))] = hl;
                         deferred = true;
                     }
                     break;
                 }
                 // the queue is full: void this reservation's slots below the capacity, walk on here
                 for (long long k = tid; k < total && pos + k < (long long)p.deep_cap; k += kThreads)
-                    p.deep[pos + k] = -1;
+                    q_out[pos + k] = -1;
                 lim = nsteps;
             }
             const int cur_buf = kBufs<WB>() == 2 ? (int)(step & 1) : 0;
@@ -405,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(WB)) classify_popc_kernel
             ci = ci_next;
         }
         const int label = mL ? 0 : (mU ? 1 : 2);
-        const bool final_ = valid && !deferred;   // a deferred sample is counted by the second pass
+        const bool final_ = valid && !deferred;   // a deferred sample is counted by a later pass
         if (final_) {
             if (p.labels) p.labels[hl] = (uint8_t)label;
             my_cnt0 += label == 0;
@@ -526,7 +533,7 @@ int popc_word_bucket(int words) {
 
 namespace {
 cudaError_t launch_words(const ClassifyParams &p, cudaStream_t s) {
-    const bool deep = p.k0 > 0;   // the two-pass form (the launcher clears k0 for one pass)
+    const bool deep = p.k0 > 0;   // the staged form (the launcher clears k0 for one pass)
     switch (p.words) {
         case 1: return deep ? launch_wb<1, true>(p, s) : launch_wb<1, false>(p, s);
         case 2: return deep ? launch_wb<2, true>(p, s) : launch_wb<2, false>(p, s);
@@ -543,28 +550,46 @@ cudaError_t launch_words(const ClassifyParams &p, cudaStream_t s) {
 }
 }  // namespace
 
-// One pass, or in early-exit mode with a deep queue, k0 > 0 and at least
-// two_pass_min_n samples (kTwoPassMinN) two: the queue's count is cleared, the first pass walks
-// k0 chunk steps per tile and queues the samples still unresolved, the second
-// finishes them (a memset and two launches, all on stream s).  Below that size
-// the second launch and the memset cost more than the deferral saves (the 256
-// hazard scenarios at 2e5 samples each: 37.5 ms against 34.2 ms in one pass).
+// One pass, or in early-exit mode with deep queues, k0 > 0 and at least
+// two_pass_min_n samples (kTwoPassMinN) staged passes (staged_passes()): the
+// first walks chunk steps [0, k0) of the call's tiles, each later one takes the
+// samples the previous one queued, 256 at a time, and walks kDeferGrowth times
+// as far as the step it starts at (next_stage_end); the last walks to the end.  Two queues
+// alternate; each pass that queues clears its queue's count first (a memset and
+// a launch per pass, all on stream s; a pass whose queue is empty returns at
+// once).  Below that size the extra launches and memsets cost more than the
+// deferral saves (the 256 hazard scenarios at 2e5 samples each: 37.5 ms in two
+// passes against 34.2 ms in one).
 cudaError_t launch_classify_popc(const ClassifyParams &p, cudaStream_t s) {
-    if (p.dense || p.k0 <= 0 || !p.deep || !p.deep_count || p.deep_cap <= 0 ||
-        p.N < p.two_pass_min_n) {
+    const int64_t nsteps = (p.R_U + kChunk - 1) / kChunk + (p.R_L + kChunk - 1) / kChunk;
+    if (p.dense || p.k0 <= 0 || !p.deep || !p.deep_count || p.deep_cap <= 0 || p.N < p.two_pass_min_n ||
+        staged_passes(nsteps, p.k0) < 2) {
         ClassifyParams one = p;
         one.k0 = 0;
-        one.deep_pass = 0;
+        one.q_in = one.q_out = -1;
+        one.step_lo = 0;
+        one.step_hi = nsteps;
         return launch_words(one, s);
     }
-    cudaError_t e = cudaMemsetAsync(p.deep_count, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return e;
-    ClassifyParams first = p;
-    first.deep_pass = 0;
-    if ((e = launch_words(first, s)) != cudaSuccess) return e;
-    ClassifyParams second = p;
-    second.deep_pass = 1;
-    return launch_words(second, s);
+    int64_t lo = 0, hi = p.k0;
+    int q_in = -1, q_out = 0;
+    while (true) {
+        const bool last = hi >= nsteps;
+        ClassifyParams c = p;
+        c.q_in = q_in;
+        c.q_out = last ? -1 : q_out;
+        c.step_lo = lo;
+        c.step_hi = last ? nsteps : hi;
+        cudaError_t e;
+        if (!last && (e = cudaMemsetAsync(p.deep_count + q_out, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+            return e;
+        if ((e = launch_words(c, s)) != cudaSuccess) return e;
+        if (last) return cudaSuccess;
+        lo = hi;
+        hi = next_stage_end(hi, nsteps);
+        q_in = q_out;
+        q_out ^= 1;
+    }
 }
 
 }  // namespace rsr

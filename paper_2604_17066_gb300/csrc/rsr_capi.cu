@@ -242,13 +242,13 @@ int classify_k0(const rsr_problem *p) {
     return kClassifyDefaultK0;
 }
 
-// The deep queue of the two-pass bit-packed path lives in the workspace beyond
-// the prepared layout: a 256-byte count line, then int64 entries, as many as fit
-// (at most kClassifyDeepCap).  A workspace of exactly the layout's size has none
-// and runs one pass.
+// The deep queues of the staged bit-packed path live in the workspace beyond
+// the prepared layout: a 256-byte line with the two counts, then two queues of
+// int64 entries, as many as fit (at most kClassifyDeepCap each).  A workspace of
+// exactly the layout's size has none and runs one pass.
 size_t deep_queue_bytes(int64_t N) {
     if (N <= 0) return 0;
-    return align256(256 + 8 * (size_t)std::min<int64_t>(N, kClassifyDeepCap));
+    return align256(256 + 2 * 8 * (size_t)std::min<int64_t>(N, kClassifyDeepCap));
 }
 
 void set_deep_queue(ClassifyParams &c, const rsr_problem *p, const WsLayout &L, void *ws, size_t ws_bytes) {
@@ -256,11 +256,11 @@ void set_deep_queue(ClassifyParams &c, const rsr_problem *p, const WsLayout &L, 
     c.deep_count = nullptr;
     c.deep_cap = 0;
     c.k0 = 0;
-    if (ws_bytes < L.total + 256 + 8 * 256) return;
+    if (ws_bytes < L.total + 256 + 2 * 8 * 256) return;
     char *base = static_cast<char *>(ws);
     c.deep_count = reinterpret_cast<unsigned long long *>(base + L.total);
     c.deep = reinterpret_cast<int64_t *>(base + L.total + 256);
-    c.deep_cap = std::min<int64_t>((int64_t)((ws_bytes - L.total - 256) / 8), kClassifyDeepCap);
+    c.deep_cap = std::min<int64_t>((int64_t)((ws_bytes - L.total - 256) / 16), kClassifyDeepCap);
     c.k0 = classify_k0(p);
     c.two_pass_min_n = (p->flags & RSR_FLAG_TEST_TWO_PASS) ? 1 : kTwoPassMinN;
 }
@@ -765,13 +765,14 @@ int rsr_classify_plan(const rsr_problem *problem, int64_t N, size_t ws_bytes, in
     if (ws_bytes < L.total) return RSR_ERR_WORKSPACE;
     const int path = choose_path(problem);
     const bool dense = (problem->flags & RSR_FLAG_DENSE) != 0;
-    const bool queue = ws_bytes >= L.total + 256 + 8 * 256;   // as set_deep_queue
+    const bool queue = ws_bytes >= L.total + 256 + 2 * 8 * 256;   // as set_deep_queue
     const int k0 = queue ? classify_k0(problem) : 0;
     const int64_t min_n = (problem->flags & RSR_FLAG_TEST_TWO_PASS) ? 1 : kTwoPassMinN;
-    const bool two = path != RSR_PATH_TC && !dense && queue && k0 > 0 && N >= min_n;
+    const int64_t nsteps = (problem->R_U + 255) / 256 + (problem->R_L + 255) / 256;
+    const int passes = (path != RSR_PATH_TC && !dense && queue && k0 > 0 && N >= min_n) ? staged_passes(nsteps, k0) : 1;
     out[0] = path;
-    out[1] = N == 0 ? 0 : (two ? 2 : 1);
-    out[2] = two ? k0 : 0;
+    out[1] = N == 0 ? 0 : passes;
+    out[2] = passes > 1 ? k0 : 0;
     return RSR_OK;
 }
 

@@ -353,13 +353,31 @@ struct ClassifyParams {
     WsHeader *hdr;
     int32_t dense;
     int32_t test_stall;                // RSR_FLAG_TEST_STALL: the producer never starts
-    // bit-packed early-exit mode, two passes (NULL / 0: one pass)
-    int64_t *deep;                     // [deep_cap] deep queue: indices of the samples the first pass defers
-    unsigned long long *deep_count;    // samples appended to the queue (may exceed deep_cap)
-    int64_t deep_cap;
+    // bit-packed early-exit mode, staged passes (NULL / 0: one pass)
+    int64_t *deep;                     // [2][deep_cap]: two queues of the indices of deferred samples
+    unsigned long long *deep_count;    // [2]: entries appended to each queue (may exceed deep_cap)
+    int64_t deep_cap;                  // entries per queue
     int32_t k0;                        // chunk steps of the first pass (0: one pass)
     int64_t two_pass_min_n;            // fewer samples: one pass (kTwoPassMinN; 1 under RSR_FLAG_TEST_TWO_PASS)
-    int32_t deep_pass;                 // set by the launcher for the second pass
+    // set by the launcher for each pass
+    int32_t q_in, q_out;               // queue read (-1: the call's tiles) and written (-1: none)
+    int64_t step_lo, step_hi;          // the chunk steps this pass walks: [step_lo, step_hi)
 };
+
+// Stages of the staged bit-packed path: the first walks chunk steps [0, k0), each
+// later one kDeferGrowth times as far as the step it starts at, the last to the
+// end; a stage that would end past half of the steps walks to the end instead
+// (no short last stage).
+constexpr int kDeferGrowth = 4;
+inline int64_t next_stage_end(int64_t hi, int64_t nsteps) {
+    const int64_t next = hi * kDeferGrowth;
+    return 2 * next > nsteps ? nsteps : next;
+}
+inline int staged_passes(int64_t nsteps, int64_t k0) {
+    if (k0 <= 0 || k0 >= nsteps) return 1;
+    int passes = 1;
+    for (int64_t hi = k0; hi < nsteps; hi = next_stage_end(hi, nsteps)) ++passes;
+    return passes;
+}
 
 }  // namespace rsr

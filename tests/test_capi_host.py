@@ -165,14 +165,15 @@ def test_stage1_entry_points_reject_bad_arguments(lib):
 
 
 def test_classify_plan_on_the_host(lib):
-    """rsr_classify_plan reports the launches rsr_classify makes: one pass, two
-    passes with a deep queue from 2^19 samples (or under the test flag), none
-    for N = 0, one on the dense path; a workspace below the layout is refused."""
+    """rsr_classify_plan reports the launches rsr_classify makes: one pass, or
+    with deep queues from 2^19 samples (or under the test flag) one pass per
+    stage (24 chunk steps at k0 = 2: steps [0, 2), [2, 8), [8, 24)), none for
+    N = 0, one on the dense path; a workspace below the layout is refused."""
     from paper_2604_17066_gb300 import _lib
     s, pmf = _problem_struct(n=100, K=2, R_L=3000, R_U=3000, path=_lib.RSR_PATH_POPC)
     base = lib.rsr_workspace_size(ctypes.byref(s), 0)
     queue = lib.rsr_workspace_size(ctypes.byref(s), 1 << 20)
-    assert queue >= base + 8 * (1 << 20) and queue % 256 == 0
+    assert queue >= base + 2 * 8 * (1 << 20) and queue % 256 == 0
     out = np.zeros(3, dtype=np.int32)
 
     def plan(N, ws_bytes):
@@ -180,11 +181,11 @@ def test_classify_plan_on_the_host(lib):
         return st, tuple(int(v) for v in out)
 
     assert plan(1 << 20, base) == (0, (_lib.RSR_PATH_POPC, 1, 0))        # no queue: one pass
-    assert plan(1 << 20, queue) == (0, (_lib.RSR_PATH_POPC, 2, 2))       # two passes, default k0
+    assert plan(1 << 20, queue) == (0, (_lib.RSR_PATH_POPC, 3, 2))       # staged passes, default k0
     assert plan((1 << 19) - 1, queue) == (0, (_lib.RSR_PATH_POPC, 1, 0))  # small calls: one pass
     assert plan(0, queue)[1][1] == 0
     s.flags = _lib.RSR_FLAG_TEST_TWO_PASS
-    assert plan(1000, queue) == (0, (_lib.RSR_PATH_POPC, 2, 2))
+    assert plan(1000, queue) == (0, (_lib.RSR_PATH_POPC, 3, 2))
     s.flags = _lib.RSR_FLAG_DENSE
     assert plan(1 << 20, queue)[1][1] == 1
     s.flags = 0

@@ -1,7 +1,8 @@
-"""GPU parity of the single-problem bit-packed path in two passes: the first
-pass walks k0 chunk steps per tile and queues the samples still unresolved in
-the workspace's deep queue, the second finishes them (at any N under a test
-flag; by default from 2^19 samples, as in the full-size tests).  Labels, counts and
+"""GPU parity of the single-problem bit-packed path in stages: the first pass
+walks k0 chunk steps per tile and queues the samples still unresolved in one of
+the workspace's two deep queues, each later pass takes them 256 at a time and
+walks four times as far, queueing again, the last to the end (at any N under a
+test flag; by default from 2^19 samples, as in the full-size tests).  Labels, counts and
 gradient counts equal the oracle's and the one-pass kernel's (a workspace
 without a queue), with Philox samples and with given states, when the queue
 overflows (its tiles finish the walk themselves), and after rsr_autotune picks
@@ -42,6 +43,8 @@ PROBS = {
     # first matches thousands of references deep, multi-state
     "deep_k3": lambda: deep_refs_problem(100, 3, 30, 2000, seed=77),
     "deep_k5": lambda: deep_refs_problem(47, 5, 7, 1500, seed=78),
+    # 122 chunk steps: stages [0, 2), [2, 8), [8, 32), [32, 122)
+    "many_chunks": lambda: sparse_match_problem(80, 300, 30000, 6, 24, seed=6),
 }
 
 
