@@ -330,7 +330,7 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
     seeds, offsets, Ns = [1000 + s for s in range(S)], [0] * S, [N] * S
     t0 = time.perf_counter()
     b = rsr.Batch(P, seeds, offsets, Ns, labels=True, grad=True)
-    grid, order, k0, n_tc = rsr.rsr_batch_autotune(b)
+    grid, order, k0, n_tc, staged = rsr.rsr_batch_autotune(b)
     prep_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
@@ -414,7 +414,8 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
             "batched_fwd_grad_round_ms": batched_round_ms, "per_scenario_fwd_grad_round_ms": plain_round_ms,
             "speedup_fwd_grad_round": plain_round_ms / batched_round_ms,
             "samples_per_s": S * N / (batched_ms / 1000.0), "autotune_grid": grid,
-            "autotune_order": "longest-first" if order == 0 else "as-given", "autotune_k0": k0, "autotune_tc_scenarios": n_tc,
+            "autotune_order": "longest-first" if order == 0 else "as-given", "autotune_k0": k0,
+            "autotune_staged": staged, "autotune_tc_scenarios": n_tc,
             "prepare_s": prep_s}
 
 

@@ -285,12 +285,15 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  * rsr_batch_autotune       : first picks the path of every dense RSR_PATH_AUTO scenario by timing
  *                            the pair kernel and the bit-packed kernel on a slice of its samples
  *                            (scenarios of one shape share the timing), then times the first
- *                            pass's chunk budget k0 (0 = no second pass, 2, 4, 8, 16, 32), work
- *                            orders and grid sizes, on the prepared batch (writing only into the
- *                            workspace's scratch, never the caller's outputs), keeps the fastest
- *                            for later rsr_batch calls and resets the round to 0; chosen[0] =
- *                            grid, chosen[1] = order (0 = longest first, 1 = as given), chosen[2]
- *                            = k0 (8 until tuned), chosen[3] = scenarios on the tensor cores.
+ *                            pass's chunk budget k0 (0 = no second pass, 2, 4, 8, 16, 32) with
+ *                            either one later stage to the end or stages that each walk four
+ *                            times as far as they start (staged), then work orders and grid
+ *                            sizes, on the prepared batch (writing only into the workspace's
+ *                            scratch, never the caller's outputs), keeps the fastest for later
+ *                            rsr_batch calls and resets the round to 0; chosen[0] = grid,
+ *                            chosen[1] = order (0 = longest first, 1 = as given), chosen[2] = k0
+ *                            (8 until tuned), chosen[3] = scenarios on the tensor cores,
+ *                            chosen[4] = staged (0 until tuned).
  *                            Synchronises `stream`.  With RSR_TUNE_CACHE set (see rsr_autotune)
  *                            the choices are read from and written to the tuning cache.
  */
@@ -305,7 +308,7 @@ RSR_API int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *se
 RSR_API int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
                                const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
                                int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws,
-                               size_t ws_bytes, rsr_stream_t stream, int32_t chosen[4]);
+                               size_t ws_bytes, rsr_stream_t stream, int32_t chosen[5]);
 
 /*
  * Gradients of every scenario of a batch from its per-state I^L counts (the

@@ -280,14 +280,15 @@ def rsr_batch(batch: Batch, stream=None) -> None:
 
 
 def rsr_batch_autotune(batch: Batch, stream=None):
-    """Tunes the batch's launches; returns (grid, order, k0, n_tc): blocks of
-    the bit-packed persistent grid, work order (0 = longest scenarios first,
-    1 = as given), the first pass's reference-chunk budget (0 = one pass) and
-    the number of scenarios on the tensor-core pair kernel."""
-    chosen = np.zeros(4, dtype=np.int32)
+    """Tunes the batch's launches; returns (grid, order, k0, n_tc, staged):
+    blocks of the bit-packed persistent grid, work order (0 = longest scenarios
+    first, 1 = as given), the first pass's reference-chunk budget (0 = one
+    pass), the number of scenarios on the tensor-core pair kernel, and whether
+    the later passes are staged (1) or one stage to the end (0)."""
+    chosen = np.zeros(5, dtype=np.int32)
     check(_lib.load().rsr_batch_autotune(*batch.args(), _stream(stream if stream is not None else batch.stream),
                                          chosen.ctypes.data), "rsr_batch_autotune")
-    return int(chosen[0]), int(chosen[1]), int(chosen[2]), int(chosen[3])
+    return int(chosen[0]), int(chosen[1]), int(chosen[2]), int(chosen[3]), int(chosen[4])
 
 
 def rsr_batch_grad(batch: Batch, stream=None):

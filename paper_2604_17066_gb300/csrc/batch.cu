@@ -29,6 +29,8 @@
 // scratch and the queues, resets the work counters and advances the round, so
 // the same two launches can be replayed (e.g. from a CUDA graph) on the next
 // N_s samples of every scenario without any host work.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "popc_index.cuh"
@@ -69,12 +71,13 @@ __device__ __noinline__ void sample_multi_call(uint64_t h, uint32_t key0, uint32
     sample_multi_words<WB, kThreads>(h, key0, key1, n, km1, s_t32k, col);
 }
 
-// One item.  First pass (deep == nullptr): samples tile*256 + tid, chunk steps
-// 0 .. k0-1 (all steps if k0 = 0), then the unresolved samples go to the deep
-// queue.  Second pass: the sample whose local index is deep[tid] (none if
-// tid >= n_deep or the entry is negative), chunk steps from k0 on.
+// One item.  First pass (deep == nullptr): samples tile*256 + tid.  A later
+// stage: the sample whose local index is deep[tid] (none if tid >= n_deep or
+// the entry is negative).  Chunk steps [step0, lim); the samples still
+// unresolved at lim go to queue q_sel (0 or 1; -1: lim is the end).
 template <int WB>
-__device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *deep, int n_deep, uint64_t round,
+__device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *deep, int n_deep, int step0_in,
+                              int lim_in, int q_sel, uint64_t round,
                               const unsigned long long *s_thr, uint32_t *s_tw, uint32_t *s_buf, uint32_t *s_cum,
                               const uint32_t *s_hot, const uint32_t *s_first, const uint32_t *s_zero,
                               uint32_t *s_and, Shared &sh) {
@@ -95,10 +98,9 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
     ChunkWalk walk(nU, nL, overlap, use_idx);
     bool upper = false;
     int64_t ci = 0;
-    // first pass: steps [0, lim); second pass: steps [k0, nsteps) (the walk is replayed up to k0)
-    const int64_t k0 = d.k0 > 0 && (int64_t)d.k0 < nsteps ? (int64_t)d.k0 : nsteps;
-    const int64_t step0 = second ? k0 : 0;
-    int64_t lim = second ? nsteps : k0;
+    // steps [step0, lim): a later stage replays the walk up to its first step
+    const int64_t step0 = step0_in;
+    int64_t lim = lim_in;
     for (int64_t i = 0; i < step0; ++i) walk.next(&upper, &ci);
     walk.next(&upper, &ci);   // step0 < nsteps: some reference exists, and the second pass only runs below nsteps
     auto chunk_refs = [&](bool up, int64_t c, int *cnt_out) {
@@ -160,7 +162,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
         cp_async_wait_all();                       // this thread's copies of chunk `step`
         if (__syncthreads_and(done)) break;        // chunk `step` visible; chunk step-1 consumed
         if (step == lim) {
-            // First pass, budget spent: queue the unresolved samples for the second pass.
+            // The stage's steps are spent: queue the unresolved samples for the next stage.
             // (An unresolved sample has no match so far: with an overlapping pair a lower
             // match is final and upper chunks only follow the lower ones.)
             const bool pend = !done;
@@ -174,18 +176,19 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
                 before += (w < (tid >> 5)) ? c : 0;
                 total += c;
             }
-            if (tid == 0) sh.deep_pos = (long long)atomicAdd(d.deep_count, (unsigned long long)total);
+            int64_t *q_out = d.deep + (size_t)q_sel * d.deep_cap;
+            if (tid == 0) sh.deep_pos = (long long)atomicAdd(d.deep_count + q_sel, (unsigned long long)total);
             __syncthreads();
             const long long pos = sh.deep_pos;
             if (pos + total <= (long long)d.deep_cap) {
                 if (pend) {
-                    d.deep[pos + before + __popc(wb & ((1u << lane) - 1u))] = hl;
+                    q_out[pos + before + __popc(wb & ((1u << lane) - 1u))] = hl;
                     deferred = true;
                 }
                 break;
             }
             // the queue is full: void this reservation's slots below the capacity and walk on here
-            for (long long k = tid; k < total && pos + k < (long long)d.deep_cap; k += kThreads) d.deep[pos + k] = -1;
+            for (long long k = tid; k < total && pos + k < (long long)d.deep_cap; k += kThreads) q_out[pos + k] = -1;
             lim = nsteps;
         }
         const int cur_buf = (int)(step & 1);
@@ -351,10 +354,25 @@ __device__ __forceinline__ BatchSmem batch_smem(unsigned char *smem) {
 // The persistent item loop of one pass: items [begin[s], begin[s+1]) belong to
 // scenario s; first pass: item = tile, second pass: item = group of 256 queued
 // samples.  Counts are flushed per item.
+// The chunk steps of stage `stage` of a scenario (0: the first pass): the first
+// pass walks [0, k0) (everything if k0 = 0), each later stage from where the
+// previous one stopped to next_stage_end() (d.staged) or to the end; empty
+// (lo = nsteps) once done.
+__device__ __forceinline__ void stage_steps(const BatchDesc &d, int stage, int64_t *lo, int64_t *hi) {
+    const int64_t nsteps = (d.R_U + kChunk - 1) / kChunk + (d.R_L + kChunk - 1) / kChunk;
+    int64_t a = 0, b = (d.k0 > 0 && (int64_t)d.k0 < nsteps) ? (int64_t)d.k0 : nsteps;
+    for (int st = 0; st < stage; ++st) {
+        a = b;
+        b = (b >= nsteps || !d.staged) ? nsteps : next_stage_end(b, nsteps);
+    }
+    *lo = a;
+    *hi = b;
+}
+
 template <bool kSecond>
 __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__restrict__ begin, int S,
-                          int64_t total_items, unsigned long long *counter, uint64_t round, const BatchSmem &m,
-                          const uint32_t *s_zero, uint32_t *s_and, Shared &sh) {
+                          int64_t total_items, unsigned long long *counter, uint64_t round, int stage,
+                          const BatchSmem &m, const uint32_t *s_zero, uint32_t *s_and, Shared &sh) {
     const int tid = threadIdx.x;
     while (true) {
         if (tid == 0) sh.item = (long long)atomicAdd(counter, 1ull);
@@ -401,12 +419,23 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
         const int64_t *deep = nullptr;
         int n_deep = 0;
         if (kSecond) {
-            const int64_t queued = (int64_t)min(*((volatile unsigned long long *)d.deep_count),
+            // this stage reads the queue the previous one filled
+            const int q_in = (stage - 1) & 1;
+            const int64_t queued = (int64_t)min(*((volatile unsigned long long *)(d.deep_count + q_in)),
                                                 (unsigned long long)d.deep_cap);
-            deep = d.deep + k * kThreads;
+            deep = d.deep + (size_t)q_in * d.deep_cap + k * kThreads;
             n_deep = (int)min((int64_t)kThreads, queued - k * kThreads);
         }
-#define RSR_ITEM(WBV) classify_item<WBV>(d, k, deep, n_deep, round, m.thr, m.tw, m.buf, m.cum, m.hot, m.first, s_zero, s_and, sh)
+        int64_t step_lo, step_hi;
+        stage_steps(d, stage, &step_lo, &step_hi);
+        const int64_t nsteps_d = (d.R_U + kChunk - 1) / kChunk + (d.R_L + kChunk - 1) / kChunk;
+        // chunk steps stay below 2^24 (R < 2^31): 32 bits carry them
+        const int step0 = kSecond ? (int)(step_lo < nsteps_d ? step_lo : nsteps_d) : 0;
+        const int q_sel = step_hi < nsteps_d ? (stage & 1) : -1;
+        const int lim = (int)(q_sel >= 0 ? step_hi : nsteps_d);
+#define RSR_ITEM(WBV)                                                                                           \
+    classify_item<WBV>(d, k, deep, n_deep, step0, lim, q_sel, round, m.thr, m.tw, m.buf, m.cum, m.hot, m.first, \
+                       s_zero, s_and, sh)
         switch (d.words_b) {
             case 1: RSR_ITEM(1); break;
             case 2: RSR_ITEM(2); break;
@@ -443,8 +472,22 @@ __device__ __forceinline__ bool last_block(unsigned int *done_counter, Shared &s
     return true;
 }
 
-// First pass.  Its last block lays out the second pass's items (groups of 256
-// queued samples per scenario) and re-arms the first pass's counters.
+// Items of the next stage (groups of 256 queued samples per scenario) from the
+// counts of queue q; one thread.
+__device__ void lay_out_stage(const BatchDesc *descs, int S, int q, int64_t *deep_begin, BatchHeader *hdr) {
+    int64_t acc = 0;
+    for (int s = 0; s < S; ++s) {
+        deep_begin[s] = acc;
+        const unsigned long long c = *((volatile unsigned long long *)(descs[s].deep_count + q));
+        const int64_t queued = (int64_t)(c < (unsigned long long)descs[s].deep_cap ? c : descs[s].deep_cap);
+        acc += (queued + kThreads - 1) / kThreads;
+    }
+    deep_begin[S] = acc;
+    hdr->deep_total = acc;
+}
+
+// First pass (stage 0).  Its last block lays out stage 1's items and re-arms the
+// first pass's counters.
 __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__restrict__ descs,
                                                              const int64_t *__restrict__ item_begin, int S,
                                                              int64_t total_items, BatchHeader *hdr,
@@ -459,30 +502,24 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(const BatchDesc *__r
     if (tid == 0) sh.scenario = -1;
     if (tid < kIdxWords) s_zero[tid] = 0u;
     __syncthreads();
-    item_loop<false>(descs, item_begin, S, total_items, &hdr->next_item, round, m, s_zero, s_and, sh);
+    item_loop<false>(descs, item_begin, S, total_items, &hdr->next_item, round, 0, m, s_zero, s_and, sh);
     if (!last_block(&hdr->blocks_done, sh)) return;
     if (tid == 0) {
-        int64_t acc = 0;
-        for (int s = 0; s < S; ++s) {
-            deep_begin[s] = acc;
-            const unsigned long long q = *((volatile unsigned long long *)descs[s].deep_count);
-            const int64_t queued = (int64_t)(q < (unsigned long long)descs[s].deep_cap ? q : descs[s].deep_cap);
-            acc += (queued + kThreads - 1) / kThreads;
-        }
-        deep_begin[S] = acc;
-        hdr->deep_total = acc;
+        lay_out_stage(descs, S, 0, deep_begin, hdr);
         hdr->next_item = 0ull;
         hdr->blocks_done = 0u;
         __threadfence();
     }
 }
 
-// Second pass.  Its last block converts the I^L bit counts to per-state
-// gradient counts, zeroes the scratch and the queues, re-arms its counters and
-// advances the round.
+// Stage `stage` >= 1 over the queued samples (queue (stage-1) & 1, filling
+// queue stage & 1).  Its last block clears the count of the queue it read; then
+// it lays out the next stage's items, or, in the last stage (final != 0),
+// converts the I^L bit counts to per-state gradient counts, zeroes the scratch
+// and both queue counts, re-arms the counters and advances the round.
 __global__ void __launch_bounds__(kThreads, 4) batch_deep_kernel(const BatchDesc *__restrict__ descs,
-                                                                  const int64_t *__restrict__ deep_begin, int S,
-                                                                  BatchHeader *hdr) {
+                                                                  int64_t *deep_begin, int S, BatchHeader *hdr,
+                                                                  int stage, int final) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Shared sh;
     __shared__ __align__(16) uint32_t s_zero[kIdxWords];
@@ -494,8 +531,18 @@ __global__ void __launch_bounds__(kThreads, 4) batch_deep_kernel(const BatchDesc
     if (tid == 0) sh.scenario = -1;
     if (tid < kIdxWords) s_zero[tid] = 0u;
     __syncthreads();
-    item_loop<true>(descs, deep_begin, S, total, &hdr->next_deep, round, m, s_zero, s_and, sh);
+    item_loop<true>(descs, deep_begin, S, total, &hdr->next_deep, round, stage, m, s_zero, s_and, sh);
     if (!last_block(&hdr->blocks_done2, sh)) return;
+    if (!final) {
+        if (tid == 0) {
+            for (int s = 0; s < S; ++s) descs[s].deep_count[(stage - 1) & 1] = 0ull;   // read by this stage
+            lay_out_stage(descs, S, stage & 1, deep_begin, hdr);
+            hdr->next_deep = 0ull;
+            hdr->blocks_done2 = 0u;
+            __threadfence();
+        }
+        return;
+    }
     for (int s = 0; s < S; ++s) {
         const BatchDesc &d = descs[s];
         if (d.bitcnt) {
@@ -516,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 4) batch_deep_kernel(const BatchDesc
             for (int j = tid; j < d.n * d.km1; j += kThreads) d.bitcnt[j] = 0u;
             if (tid == 0) *d.lcount = 0ull;
         }
-        if (tid == 0) *d.deep_count = 0ull;
+        if (tid == 0) d.deep_count[0] = d.deep_count[1] = 0ull;
     }
     if (tid == 0) {
         hdr->next_deep = 0ull;
@@ -553,14 +600,27 @@ cudaError_t batch_max_grid(int *blocks_per_sm) {
 // batch is prepared), so a launch issues nothing but the two kernels and can
 // be captured.  The second pass always runs: it also closes the round.
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
-                         BatchHeader *hdr, int64_t *deep_begin, int grid, cudaStream_t s) {
+                         BatchHeader *hdr, int64_t *deep_begin, int n_stages, int grid, cudaStream_t s) {
     const size_t smem = batch_kernel_smem();
-    if (grid <= 0) grid = 1;   // both passes run even without bit-packed items: the second closes the round
+    if (grid <= 0) grid = 1;   // every launch runs even without bit-packed items: the last closes the round
+    if (n_stages < 1) n_stages = 1;
     batch_kernel<<<grid, kThreads, smem, s>>>(descs, item_begin, S, total_items, hdr, deep_begin);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    batch_deep_kernel<<<grid, kThreads, smem, s>>>(descs, deep_begin, S, hdr);
-    return cudaGetLastError();
+    for (int st = 1; st <= n_stages && e == cudaSuccess; ++st) {
+        batch_deep_kernel<<<grid, kThreads, smem, s>>>(descs, deep_begin, S, hdr, st, st == n_stages ? 1 : 0);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+int batch_stages(const BatchDesc *descs, int S) {
+    int stages = 1;
+    for (int k = 0; k < S; ++k) {
+        if (descs[k].path == RSR_PATH_TC) continue;   // on the pair kernel
+        const int64_t nsteps = (descs[k].R_U + kChunk - 1) / kChunk + (descs[k].R_L + kChunk - 1) / kChunk;
+        stages = std::max(stages, descs[k].staged ? staged_passes(nsteps, descs[k].k0) - 1 : 1);
+    }
+    return stages;
 }
 
 }  // namespace rsr

@@ -23,10 +23,11 @@ struct BatchDesc {
     unsigned long long *grad_counts;     // [n*K] or NULL
     uint32_t *bitcnt;                    // [n*(K-1)] I^L per-bit scratch, or NULL
     unsigned long long *lcount;          // I^L count scratch
-    int64_t *deep;                       // [deep_cap] deep queue: local indices of deferred samples
-    unsigned long long *deep_count;      // samples appended to the queue (may exceed deep_cap)
-    int64_t deep_cap;
+    int64_t *deep;                       // [2][deep_cap] two queues: local indices of deferred samples
+    unsigned long long *deep_count;      // [2] samples appended to each queue (may exceed deep_cap)
+    int64_t deep_cap;                    // entries per queue
     int32_t k0;                          // chunk steps of the first pass (0 = all)
+    int32_t staged;                      // later stages grow by kDeferGrowth (0: one stage to the end)
     int32_t path;                        // RSR_PATH_POPC, or RSR_PATH_TC: the scenario runs on the pair kernel
 };
 
@@ -36,8 +37,8 @@ struct BatchHeader {
     unsigned int blocks_done;       // first pass: finished blocks
     unsigned int blocks_done2;      // second pass: finished blocks
     unsigned long long round;       // launch pairs since prepare: sample window index
-    unsigned long long next_deep;   // second pass: work counter
-    long long deep_total;           // second pass: items (groups of 256 queued samples)
+    unsigned long long next_deep;   // later stages: work counter
+    long long deep_total;           // the next stage's items (groups of 256 queued samples)
     unsigned long long reserved[27];
 };
 static_assert(sizeof(BatchHeader) == 256, "batch header is one 256-byte line");
@@ -45,10 +46,13 @@ static_assert(sizeof(BatchHeader) == 256, "batch header is one 256-byte line");
 size_t batch_kernel_smem();
 int batch_max_words();
 cudaError_t batch_max_grid(int *blocks_per_sm);
-// Both passes: the tile pass, then the pass over the queued deep samples
-// (deep_begin: workspace int64[S+1], written by the first pass).
+// The tile pass, then n_stages stages over the queued deep samples (deep_begin:
+// workspace int64[S+1], written by the launch before each stage).
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
-                         BatchHeader *hdr, int64_t *deep_begin, int grid, cudaStream_t s);
+                         BatchHeader *hdr, int64_t *deep_begin, int n_stages, int grid, cudaStream_t s);
+// Stages after the tile pass for these descriptors (host copies): the most any
+// bit-packed scenario needs (staged_passes() - 1), at least one.
+int batch_stages(const BatchDesc *descs, int S);
 constexpr int64_t kBatchDeepCap = int64_t(1) << 22;   // deep-queue entries per scenario at most (32 MB)
 constexpr int64_t kBatchTestDeepCap = 1024;           // with RSR_FLAG_TEST_DEEP_CAP (test hook)
 constexpr int kBatchDefaultK0 = 8;         // first-pass chunk steps before rsr_batch_autotune picks them

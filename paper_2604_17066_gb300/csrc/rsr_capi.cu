@@ -1023,9 +1023,9 @@ BatchLayout batch_layout(const rsr_problem *probs, int32_t S, const int64_t *Ns)
         off = align256(off + 8);
         B.off_tgrad.push_back(off);  // tuning scratch: gradient counts
         off = align256(off + 8 * (size_t)p.n * p.K);
-        B.off_deep.push_back(off);   // deep-queue count (8 bytes) and the queue
+        B.off_deep.push_back(off);   // the two deep-queue counts (16 bytes) and the two queues
         B.deep_cap.push_back(deep_cap_of(p, Ns[s]));
-        off = align256(off + 8 + 8 * (size_t)B.deep_cap.back());
+        off = align256(off + 16 + 2 * 8 * (size_t)B.deep_cap.back());
         const WsLayout L = layout_of(&p);
         B.tc_kpad.push_back(L.tc_kpad);
         if (batch_tc_eligible(p)) {
@@ -1250,9 +1250,10 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.bitcnt = d.grad_counts ? reinterpret_cast<uint32_t *>(base + B.off_bit[k]) : nullptr;
         d.lcount = reinterpret_cast<unsigned long long *>(base + B.off_lc[k]);
         d.deep_count = reinterpret_cast<unsigned long long *>(base + B.off_deep[k]);
-        d.deep = reinterpret_cast<int64_t *>(base + B.off_deep[k] + 8);
+        d.deep = reinterpret_cast<int64_t *>(base + B.off_deep[k] + 16);
         d.deep_cap = B.deep_cap[k];
         d.k0 = kBatchDefaultK0;
+        d.staged = 0;
         // pair-kernel parameters (dense); the path: RSR_PATH_TC where asked for, a tuned
         // decision for RSR_PATH_AUTO (else the reference-count rule of choose_path)
         ClassifyParams c{};
@@ -1332,7 +1333,7 @@ int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, con
     RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
                           reinterpret_cast<const int64_t *>(base + B.off_begin), S, bp.total_items,
                           reinterpret_cast<BatchHeader *>(base), reinterpret_cast<int64_t *>(base + B.off_deep_begin),
-                          bp.grid, s));
+                          batch_stages(bp.descs.data(), S), bp.grid, s));
     return RSR_OK;
 }
 
@@ -1453,16 +1454,20 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     char hex[32];
     snprintf(hex, sizeof(hex), "%016llx", (unsigned long long)shape);
     const std::string batch_key = "batch/" + device_tag() + "/S" + std::to_string(S) + "/" + hex;
-    int best_grid = bp.grid, best_order = 0, best_k0 = bp.k0;
+    int best_grid = bp.grid, best_order = 0, best_k0 = bp.k0, best_staged = 0;
     std::vector<long long> cached;
-    if (cache_get(batch_key, &cached) && cached.size() == 3 && cached[0] >= 1 && (cached[1] == 0 || cached[1] == 1) &&
-        cached[2] >= 0) {
+    if (cache_get(batch_key, &cached) && cached.size() == 4 && cached[0] >= 1 && (cached[1] == 0 || cached[1] == 1) &&
+        cached[2] >= 0 && (cached[3] == 0 || cached[3] == 1)) {
         best_grid = (int)cached[0];
         best_order = (int)cached[1];
         best_k0 = (int)cached[2];
+        best_staged = (int)cached[3];
     } else {
-        auto time_config = [&](int ord, int bps, int k0, float *ms_out, int64_t *grid_out) -> int {
-            for (int k = 0; k < S; ++k) scratch[k].k0 = k0;
+        auto time_config = [&](int ord, int bps, int k0, int staged, float *ms_out, int64_t *grid_out) -> int {
+            for (int k = 0; k < S; ++k) {
+                scratch[k].k0 = k0;
+                scratch[k].staged = staged;
+            }
             std::vector<int64_t> begin;
             int64_t total = 0;
             int st2 = upload_schedule(ws, B, scratch, ord ? natural : lpt, begin, total, s);
@@ -1473,19 +1478,25 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
                 return launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
                                     reinterpret_cast<const int64_t *>(base + B.off_begin), S, total,
                                     reinterpret_cast<BatchHeader *>(base),
-                                    reinterpret_cast<int64_t *>(base + B.off_deep_begin), grid, s);
+                                    reinterpret_cast<int64_t *>(base + B.off_deep_begin),
+                                    batch_stages(scratch.data(), S), grid, s);
             }, ms_out);
         };
         float best = 1e30f;
+        // the first pass's budget, with one later stage to the end or staged later passes
         static const int kK0[] = {0, 2, 4, 8, 16, 32};
-        for (int k0 : kK0) {
-            float ms = 0.0f;
-            int64_t grid = 0;
-            if ((st = time_config(0, occ, k0, &ms, &grid)) != RSR_OK) return st;
-            if (ms < best) {
-                best = ms;
-                best_k0 = k0;
-                best_grid = (int)grid;
+        for (int staged = 0; staged < 2; ++staged) {
+            for (int k0 : kK0) {
+                if (staged && k0 == 0) continue;   // nothing is deferred: the same launches
+                float ms = 0.0f;
+                int64_t grid = 0;
+                if ((st = time_config(0, occ, k0, staged, &ms, &grid)) != RSR_OK) return st;
+                if (ms < best) {
+                    best = ms;
+                    best_k0 = k0;
+                    best_staged = staged;
+                    best_grid = (int)grid;
+                }
             }
         }
         for (int ord = 0; ord < 2; ++ord) {
@@ -1493,7 +1504,7 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
                 if (ord == 0 && bps == occ) continue;   // timed above
                 float ms = 0.0f;
                 int64_t grid = 0;
-                if ((st = time_config(ord, bps, best_k0, &ms, &grid)) != RSR_OK) return st;
+                if ((st = time_config(ord, bps, best_k0, best_staged, &ms, &grid)) != RSR_OK) return st;
                 if (ms < best) {
                     best = ms;
                     best_grid = (int)grid;
@@ -1501,13 +1512,16 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
                 }
             }
         }
-        cache_put(batch_key, {best_grid, best_order, best_k0});
+        cache_put(batch_key, {best_grid, best_order, best_k0, best_staged});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // the caller's descriptors with the chosen paths and k0, in the chosen order; round 0
     std::vector<BatchDesc> tuned = bp.descs;
-    for (int k = 0; k < S; ++k) tuned[k].k0 = best_k0;
+    for (int k = 0; k < S; ++k) {
+        tuned[k].k0 = best_k0;
+        tuned[k].staged = best_staged;
+    }
     std::vector<int64_t> begin;
     int64_t total = 0;
     if ((st = upload_schedule(ws, B, tuned, best_order ? natural : lpt, begin, total, s)) != RSR_OK) return st;
@@ -1517,7 +1531,7 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     for (int k = 0; k < S; ++k) {
         RSR_CUDA(cudaMemsetAsync(base + B.off_lc[k], 0, 8, s));
         RSR_CUDA(cudaMemsetAsync(base + B.off_bit[k], 0, 4 * (size_t)problems[k].n * (problems[k].K - 1), s));
-        RSR_CUDA(cudaMemsetAsync(base + B.off_deep[k], 0, 8, s));
+        RSR_CUDA(cudaMemsetAsync(base + B.off_deep[k], 0, 16, s));
     }
     RSR_CUDA(cudaStreamSynchronize(s));
     if (chosen) {
@@ -1525,6 +1539,7 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
         chosen[1] = best_order;
         chosen[2] = best_k0;
         chosen[3] = bp.n_tc;
+        chosen[4] = best_staged;
     }
     std::lock_guard<std::mutex> g(g_mu);
     BatchPrepared &ref = g_batches[ws];

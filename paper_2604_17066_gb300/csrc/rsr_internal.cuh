@@ -369,11 +369,11 @@ struct ClassifyParams {
 // end; a stage that would end past half of the steps walks to the end instead
 // (no short last stage).
 constexpr int kDeferGrowth = 4;
-inline int64_t next_stage_end(int64_t hi, int64_t nsteps) {
+__host__ __device__ inline int64_t next_stage_end(int64_t hi, int64_t nsteps) {
     const int64_t next = hi * kDeferGrowth;
     return 2 * next > nsteps ? nsteps : next;
 }
-inline int staged_passes(int64_t nsteps, int64_t k0) {
+__host__ __device__ inline int staged_passes(int64_t nsteps, int64_t k0) {
     if (k0 <= 0 || k0 >= nsteps) return 1;
     int passes = 1;
     for (int64_t hi = k0; hi < nsteps; hi = next_stage_end(hi, nsteps)) ++passes;

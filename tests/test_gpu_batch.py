@@ -97,8 +97,8 @@ def test_batch_replay_and_graph_capture(rsr):
 def test_batch_autotune_leaves_outputs_alone(rsr):
     probs, seeds, offsets, Ns = scenarios()
     b = make_batch(rsr, probs, seeds, offsets, Ns)
-    grid, order, k0, n_tc = rsr.rsr_batch_autotune(b)
-    assert grid >= 1 and order in (0, 1) and k0 in (0, 2, 4, 8, 16, 32) and n_tc == 0
+    grid, order, k0, n_tc, staged = rsr.rsr_batch_autotune(b)
+    assert grid >= 1 and order in (0, 1) and k0 in (0, 2, 4, 8, 16, 32) and n_tc == 0 and staged in (0, 1)
     torch.cuda.synchronize()
     assert int(b.counts3.abs().sum()) == 0
     assert all(int(t.abs().sum()) == 0 for t in b.grad_counts)
@@ -199,7 +199,7 @@ def test_mixed_path_batch_matches_oracle_before_and_after_autotune(rsr):
     torch.cuda.synchronize()
     check_batch_round(rsr, b, probs, seeds, offsets, Ns, 0)
     b2 = make_mixed_batch(rsr, probs, seeds, offsets, Ns, paths, dense)
-    grid, order, k0, n_tc = rsr.rsr_batch_autotune(b2)
+    grid, order, k0, n_tc, staged = rsr.rsr_batch_autotune(b2)
     assert n_tc >= 3                      # the three scenarios that ask for the tensor cores
     torch.cuda.synchronize()
     assert int(b2.counts3.abs().sum()) == 0
