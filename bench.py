@@ -789,7 +789,7 @@ def main():
             rsr.rsr_grad(P, 1, off, n_rank, gcounts, sess.ws, u_lower_idx=uidx[:n_ul] if n_ul else None,
                          stream=stream)
         est = rsr.rsr_estimate(counts.cpu().numpy(), n_rank, n_ul)
-        # classify (one launch, two for the bit-packed path's two passes), resolve,
+        # classify (one launch, one per stage on the bit-packed path's staged passes), resolve,
         # and rsr_grad's index check and correction
         step.last_launches = classify_launches + (system is not None) + (2 if (grad and n_ul > 0) else 0)
         return est

@@ -87,9 +87,9 @@ typedef enum rsr_path {
  * samples, so that tiles find it full and finish their walk themselves (the
  * fallback a queue of one entry per sample never needs). */
 #define RSR_FLAG_TEST_DEEP_CAP 0x200u
-/* Test hook (bit-packed path, early exit): two passes whenever the workspace
- * holds a deep queue, whatever N (without it, calls of fewer than 2^19 samples
- * run one pass). */
+/* Test hook (bit-packed path, early exit): staged passes whenever the
+ * workspace holds a deep queue, whatever N (without it, calls of fewer than
+ * 2^19 samples run one pass). */
 #define RSR_FLAG_TEST_TWO_PASS 0x400u
 
 /*
@@ -285,7 +285,7 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  * rsr_batch_autotune       : first picks the path of every dense RSR_PATH_AUTO scenario by timing
  *                            the pair kernel and the bit-packed kernel on a slice of its samples
  *                            (scenarios of one shape share the timing), then times the first
- *                            pass's chunk budget k0 (0 = no second pass, 2, 4, 8, 16, 32) with
+ *                            pass's chunk budget k0 (0 = no later stage, 2, 4, 8, 16, 32) with
  *                            either one later stage to the end or stages that each walk four
  *                            times as far as they start (staged), then work orders and grid
  *                            sizes, on the prepared batch (writing only into the workspace's

@@ -176,7 +176,7 @@ class Session:
 
     def __init__(self, problem: Problem, stream=None, max_samples: int = 1 << 20):
         # the workspace holds a deep queue for calls of up to max_samples samples
-        # (the bit-packed path's second pass; larger calls defer fewer samples)
+        # (the bit-packed path's later stages; larger calls defer fewer samples)
         self.problem = problem
         self.stream = stream
         self.ws = alloc_workspace(problem, max_samples)

@@ -18,17 +18,20 @@
 // other lanes idle.  The first pass (batch_kernel) therefore walks at most k0
 // chunks per tile; samples still unresolved then are appended to their
 // scenario's deep queue (a block-wide reservation; a tile whose reservation
-// would overflow the queue keeps walking itself).  The second pass
-// (batch_deep_kernel) takes the queued samples 256 at a time, regenerates
-// their states from Philox, and resumes the walk at chunk k0 with every lane
-// busy.  Labels, counts and gradient counts are the same as one pass would
-// give: the visiting order of the chunks is the same, and a sample is counted
-// once, in the pass that resolves it.  k0 = 0 runs everything in the first
-// pass.  I^L per-bit counts go to a scenario scratch counter; the last block of
-// the second pass converts them into the per-state gradient counts, zeroes the
-// scratch and the queues, resets the work counters and advances the round, so
-// the same two launches can be replayed (e.g. from a CUDA graph) on the next
-// N_s samples of every scenario without any host work.
+// would overflow the queue keeps walking itself).  The later stages
+// (batch_deep_kernel) take the queued samples 256 at a time, regenerate their
+// states from Philox, and resume the walk where the previous stage stopped
+// with every lane busy: either one stage to the last chunk, or (a staged
+// scenario) stages that each walk four times as far as they start and queue
+// again into the other of the scenario's two queues.  Labels, counts and
+// gradient counts are the same as one pass would give: the visiting order of
+// the chunks is the same, and a sample is counted once, in the pass that
+// resolves it.  k0 = 0 runs everything in the first pass.  I^L per-bit counts
+// go to a scenario scratch counter; the last block of the final stage converts
+// them into the per-state gradient counts, zeroes the scratch and the queues,
+// resets the work counters and advances the round, so the same launches can be
+// replayed (e.g. from a CUDA graph) on the next N_s samples of every scenario
+// without any host work.
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -102,7 +105,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
     const int64_t step0 = step0_in;
     int64_t lim = lim_in;
     for (int64_t i = 0; i < step0; ++i) walk.next(&upper, &ci);
-    walk.next(&upper, &ci);   // step0 < nsteps: some reference exists, and the second pass only runs below nsteps
+    walk.next(&upper, &ci);   // step0 < nsteps: some reference exists, and a later stage only runs below nsteps
     auto chunk_refs = [&](bool up, int64_t c, int *cnt_out) {
         const int64_t R = up ? d.R_U : d.R_L;
         const int64_t base = c * kChunk;
@@ -289,7 +292,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
         ci = ci_next;
     }
     cp_async_wait_all();   // the copy of a chunk that a finished walk did not reach
-    const bool final_ = valid && !deferred;   // resolved here (a deferred sample is counted by the second pass)
+    const bool final_ = valid && !deferred;   // resolved here (a deferred sample is counted by a later stage)
     const int label = mL ? 0 : (mU ? 1 : 2);
     if (final_ && d.labels) d.labels[hl] = (uint8_t)label;
     // counts
@@ -334,7 +337,7 @@ __device__ void classify_item(const BatchDesc &d, int64_t tile, const int64_t *d
     }
 }
 
-// Shared-memory carve-up of both passes.
+// Shared-memory carve-up of every pass.
 struct BatchSmem {
     unsigned long long *thr;   // [512] thresholds (or 32-bit binary tables and never-words)
     uint32_t *tw, *buf, *cum, *hot, *first;
@@ -351,9 +354,6 @@ __device__ __forceinline__ BatchSmem batch_smem(unsigned char *smem) {
     return m;
 }
 
-// The persistent item loop of one pass: items [begin[s], begin[s+1]) belong to
-// scenario s; first pass: item = tile, second pass: item = group of 256 queued
-// samples.  Counts are flushed per item.
 // The chunk steps of stage `stage` of a scenario (0: the first pass): the first
 // pass walks [0, k0) (everything if k0 = 0), each later stage from where the
 // previous one stopped to next_stage_end() (d.staged) or to the end; empty
@@ -369,6 +369,9 @@ __device__ __forceinline__ void stage_steps(const BatchDesc &d, int stage, int64
     *hi = b;
 }
 
+// The persistent item loop of one pass: items [begin[s], begin[s+1]) belong to
+// scenario s; first pass: item = tile, later stages: item = group of 256
+// queued samples.  Counts are flushed per item.
 template <bool kSecond>
 __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__restrict__ begin, int S,
                           int64_t total_items, unsigned long long *counter, uint64_t round, int stage,
@@ -597,8 +600,8 @@ cudaError_t batch_max_grid(int *blocks_per_sm) {
 }
 
 // The shared-memory attributes are set by batch_max_grid() (called when a
-// batch is prepared), so a launch issues nothing but the two kernels and can
-// be captured.  The second pass always runs: it also closes the round.
+// batch is prepared), so a launch issues nothing but the kernels and can be
+// captured.  The final stage always runs: it also closes the round.
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
                          BatchHeader *hdr, int64_t *deep_begin, int n_stages, int grid, cudaStream_t s) {
     const size_t smem = batch_kernel_smem();

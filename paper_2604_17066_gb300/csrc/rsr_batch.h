@@ -35,8 +35,8 @@ struct BatchDesc {
 struct BatchHeader {
     unsigned long long next_item;   // first pass: work counter
     unsigned int blocks_done;       // first pass: finished blocks
-    unsigned int blocks_done2;      // second pass: finished blocks
-    unsigned long long round;       // launch pairs since prepare: sample window index
+    unsigned int blocks_done2;      // later stages: finished blocks
+    unsigned long long round;       // launch sets since prepare: sample window index
     unsigned long long next_deep;   // later stages: work counter
     long long deep_total;           // the next stage's items (groups of 256 queued samples)
     unsigned long long reserved[27];
