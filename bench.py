@@ -351,6 +351,26 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
         g.replay()
         rsr.rsr_batch_grad(b)
     batched_round_ms = 1000 * (time.perf_counter() - t0) / reps
+    # where a block's time goes: one cycle-profiled launch set (the same kernels with
+    # clock64 marks per item; outside the timed region)
+    torch.cuda.synchronize()
+    prof = rsr.rsr_batch_profile(b).cpu().numpy().astype(np.float64)
+    R_s = np.array([p.R_L + p.R_U for p in P], dtype=np.float64)
+    heavy = R_s >= 1e4
+    first, later = prof[:, 1:4].sum(axis=0), prof[:, 5:8].sum(axis=0)
+    walk = prof[:, 3] + prof[:, 7]
+    tot = first.sum() + later.sum()
+    cycle_profile = {
+        "tile_pass_share": float(first.sum() / tot),
+        "tile_pass_setup_sample_walk": [float(x) for x in first / first.sum()],
+        "later_stages_setup_sample_walk": [float(x) for x in later / max(later.sum(), 1.0)],
+        "sample_share": float((first[1] + later[1]) / tot),
+        "walk_share": float((first[2] + later[2]) / tot),
+        "heavy_scenarios_R_ge_1e4": int(heavy.sum()),
+        "heavy_share_of_walk": float(walk[heavy].sum() / walk.sum()),
+        "heavy_share_of_samples": float(heavy.sum() / len(P)),
+        "later_stage_items": int(prof[:, 4].sum()), "tile_items": int(prof[:, 0].sum()),
+    }
     # per-scenario path
     sessions = [rsr.Session(p) for p in P]
     cur = torch.cuda.current_stream()
@@ -416,7 +436,7 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
             "samples_per_s": S * N / (batched_ms / 1000.0), "autotune_grid": grid,
             "autotune_order": "longest-first" if order == 0 else "as-given", "autotune_k0": k0,
             "autotune_staged": staged, "autotune_tc_scenarios": n_tc,
-            "prepare_s": prep_s}
+            "cycle_profile": cycle_profile, "prepare_s": prep_s}
 
 
 def popc_roofline(rsr, n, K, n_samples, kern_ms, word_ops, meas=None):

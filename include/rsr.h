@@ -274,14 +274,28 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  * rsr_batch_prepare        : thresholds, reference encodings, precedence pre-checks and the work
  *                            list (longest scenarios first) into `ws`; not capturable.
  * rsr_batch                : the pair-kernel launch (if any scenario runs on the tensor cores),
- *                            then two bit-packed persistent launches: every (scenario, 256-sample
+ *                            then the bit-packed persistent launches: every (scenario, 256-sample
  *                            tile) walks at most k0 reference chunks, and the samples still
- *                            unresolved then are queued and finished 256 at a time by the second
- *                            launch (same labels and counts as one walk; a tile that would
- *                            overflow a queue of more than 2^22 samples finishes its walk itself).  The arguments must equal those given
- *                            to rsr_batch_prepare (else RSR_ERR_NOT_PREPARED).  The launches re-arm
- *                            their own counters, so they can be captured once in a CUDA graph and
- *                            replayed.
+ *                            unresolved then are queued and taken 256 at a time by the later
+ *                            launches, one stage to the last chunk or (staged) stages that each
+ *                            walk four times as far as they start and queue again (same labels
+ *                            and counts as one walk; a tile that would overflow a queue of more
+ *                            than 2^22 samples finishes its walk itself).  The arguments must
+ *                            equal those given to rsr_batch_prepare (else RSR_ERR_NOT_PREPARED).
+ *                            The launches re-arm their own counters, so they can be captured
+ *                            once in a CUDA graph and replayed.
+ * rsr_batch_profile        : rsr_batch (the same outputs, and it advances the round) with a cycle
+ *                            profile of the bit-packed launches: cycles is a device uint64[S*8],
+ *                            zeroed by the call (stream-ordered), then per scenario s, at
+ *                            [8s + 0..3] for the tile pass and [8s + 4..7] for the later stages:
+ *                            items, and SM clock cycles (clock64 of each item's block, summed over
+ *                            items) spent from an item's start to its tables being ready (work
+ *                            counter, scenario lookup, table loads), from there to the block's
+ *                            first warp having written its samples (Philox sampling and
+ *                            encoding), and from there to the item's counts being flushed (the
+ *                            reference-chunk walk).  Scenarios on the tensor cores keep zeros.
+ *                            Blocks share their SM, so the cycles measure where a block's time
+ *                            goes, not SM time; the three parts give the split.
  * rsr_batch_autotune       : first picks the path of every dense RSR_PATH_AUTO scenario by timing
  *                            the pair kernel and the bit-packed kernel on a slice of its samples
  *                            (scenarios of one shape share the timing), then times the first
@@ -305,6 +319,10 @@ RSR_API int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint
 RSR_API int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
                       const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
                       int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream);
+RSR_API int rsr_batch_profile(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
+                              const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
+                              int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes,
+                              rsr_stream_t stream, uint64_t *cycles);
 RSR_API int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *seeds,
                                const uint64_t *offsets, const int64_t *Ns, uint8_t *const *labels_or_null,
                                int64_t *counts3xS, int64_t *const *grad_counts_or_null, void *ws,

@@ -12,7 +12,7 @@ __all__ = [
     "Problem", "Session", "RSRProb", "RSRError", "alloc_workspace",
     "rsr_workspace_size", "rsr_prepare", "rsr_update_pmf", "rsr_classify", "rsr_classify_plan", "rsr_estimate",
     "rsr_grad", "rsr_sample", "rsr_workspace_status",
-    "Batch", "rsr_batch_prepare", "rsr_batch", "rsr_batch_autotune", "rsr_autotune",
+    "Batch", "rsr_batch_prepare", "rsr_batch", "rsr_batch_profile", "rsr_batch_autotune", "rsr_autotune",
     "rsr_classify_static", "rsr_batch_grad", "System", "rsr_resolve",
     "rsr_boundary_search", "rsr_nondominated", "rsr_stage1", "rsr_level_pmf", "rsr_measure_int_peak", "rsr_measure_fp8_peak",
     "rsr_measure_philox_rate",

@@ -113,6 +113,7 @@ SIGNATURES = {
     "rsr_batch_prepare": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P]),
     "rsr_batch": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P]),
     "rsr_batch_autotune": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P, _P]),
+    "rsr_batch_profile": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P, _P, _P, _S, _P, _P]),
     "rsr_autotune": (ctypes.c_int, [_PROB, _P, _S, _P, _P]),
     "rsr_batch_grad": (ctypes.c_int, [_PROB, _I32, _P, _P, _P, _P, _P]),
     "rsr_classify_static": (ctypes.c_int, [_PROB, _U64, _U64, _I64, _P, _P, _P, _P, _P]),

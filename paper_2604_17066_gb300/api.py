@@ -279,6 +279,18 @@ def rsr_batch(batch: Batch, stream=None) -> None:
           "rsr_batch")
 
 
+def rsr_batch_profile(batch: Batch, stream=None) -> torch.Tensor:
+    """rsr_batch (same outputs; advances the round) with a cycle profile of the
+    bit-packed launches: a device int64 [S, 8] tensor, per scenario the tile
+    pass's items and its set-up, sampling and chunk-walk SM cycles (summed over
+    items, clock64 of each item's block), then the same four for the later
+    stages.  Tensor-core scenarios keep zeros."""
+    st = stream if stream is not None else batch.stream
+    cycles = torch.empty((batch.S, 8), dtype=torch.int64, device=batch.counts3.device)
+    check(_lib.load().rsr_batch_profile(*batch.args(), _stream(st), cycles.data_ptr()), "rsr_batch_profile")
+    return cycles
+
+
 def rsr_batch_autotune(batch: Batch, stream=None):
     """Tunes the batch's launches; returns (grid, order, k0, n_tc, staged):
     blocks of the bit-packed persistent grid, work order (0 = longest scenarios

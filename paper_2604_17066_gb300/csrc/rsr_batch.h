@@ -47,9 +47,18 @@ size_t batch_kernel_smem();
 int batch_max_words();
 cudaError_t batch_max_grid(int *blocks_per_sm);
 // The tile pass, then n_stages stages over the queued deep samples (deep_begin:
-// workspace int64[S+1], written by the launch before each stage).
+// workspace int64[S+1], written by the launch before each stage).  prof: null,
+// or a device [S][8] cycle profile the launches add to (per scenario: first
+// pass items, set-up, sampling and walk cycles, then the same for later stages).
 cudaError_t launch_batch(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
-                         BatchHeader *hdr, int64_t *deep_begin, int n_stages, int grid, cudaStream_t s);
+                         BatchHeader *hdr, int64_t *deep_begin, int n_stages, int grid, cudaStream_t s,
+                         unsigned long long *prof = nullptr);
+// The profiled variant (batch_prof.cu): its shared-memory attributes (lowering
+// *blocks_per_sm to its occupancy) and its launches (prof non-null).
+cudaError_t batch_prof_attributes(int *blocks_per_sm);
+cudaError_t launch_batch_prof(const BatchDesc *descs, const int64_t *item_begin, int S, int64_t total_items,
+                              BatchHeader *hdr, int64_t *deep_begin, int n_stages, int grid, cudaStream_t s,
+                              unsigned long long *prof);
 // Stages after the tile pass for these descriptors (host copies): the most any
 // bit-packed scenario needs (staged_passes() - 1), at least one.
 int batch_stages(const BatchDesc *descs, int S);

@@ -1303,9 +1303,11 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
     return RSR_OK;
 }
 
-int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+// rsr_batch's launches; prof: null, or the [S][8] cycle profile to add to.
+static int run_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
               const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
-              int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream) {
+              int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream,
+              unsigned long long *prof) {
     int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
     if (st != RSR_OK) return st;
     const BatchLayout B = batch_layout(problems, S, Ns);
@@ -1333,8 +1335,27 @@ int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, con
     RSR_CUDA(launch_batch(reinterpret_cast<const BatchDesc *>(base + B.off_descs),
                           reinterpret_cast<const int64_t *>(base + B.off_begin), S, bp.total_items,
                           reinterpret_cast<BatchHeader *>(base), reinterpret_cast<int64_t *>(base + B.off_deep_begin),
-                          batch_stages(bp.descs.data(), S), bp.grid, s));
+                          batch_stages(bp.descs.data(), S), bp.grid, s, prof));
     return RSR_OK;
+}
+
+int rsr_batch(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+              const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
+              int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream) {
+    return run_batch(problems, S, seeds, offsets, Ns, labels_or_null, counts3xS, grad_counts_or_null, ws, ws_bytes,
+                     stream, nullptr);
+}
+
+int rsr_batch_profile(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,
+                      const int64_t *Ns, uint8_t *const *labels_or_null, int64_t *counts3xS,
+                      int64_t *const *grad_counts_or_null, void *ws, size_t ws_bytes, rsr_stream_t stream,
+                      uint64_t *cycles) {
+    if (!cycles || S < 1) return RSR_ERR_INVALID_ARG;
+    const int st = validate_batch(problems, S, seeds, offsets, Ns, counts3xS);
+    if (st != RSR_OK) return st;
+    RSR_CUDA(cudaMemsetAsync(cycles, 0, sizeof(uint64_t) * 8 * (size_t)S, reinterpret_cast<cudaStream_t>(stream)));
+    return run_batch(problems, S, seeds, offsets, Ns, labels_or_null, counts3xS, grad_counts_or_null, ws, ws_bytes,
+                     stream, reinterpret_cast<unsigned long long *>(cycles));
 }
 
 int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *seeds, const uint64_t *offsets,

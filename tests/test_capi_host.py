@@ -191,3 +191,18 @@ def test_classify_plan_on_the_host(lib):
     s.flags = 0
     assert plan(1 << 20, base - 256)[0] == _lib.RSR_ERR_WORKSPACE
     assert plan(-1, queue)[0] == _lib.RSR_ERR_INVALID_ARG
+
+
+def test_batch_profile_rejects_bad_arguments(lib):
+    """rsr_batch_profile checks its cycle array and the batch's arguments on the
+    host, before any CUDA call."""
+    from paper_2604_17066_gb300 import _lib
+    s, pmf = _problem_struct(n=4, K=2, R_L=0, R_U=0)
+    fake = ctypes.c_void_p(0x10000)                    # never dereferenced
+    seeds = (ctypes.c_uint64 * 1)(1)
+    offs = (ctypes.c_uint64 * 1)(0)
+    Ns = (ctypes.c_int64 * 1)(1000)
+    call = lambda S, cycles: lib.rsr_batch_profile(ctypes.byref(s), S, seeds, offs, Ns, None, fake, None, fake,
+                                                   1 << 20, None, cycles)
+    assert call(1, None) == _lib.RSR_ERR_INVALID_ARG   # no cycle array
+    assert call(0, fake) == _lib.RSR_ERR_INVALID_ARG   # no scenario

@@ -1,9 +1,10 @@
 """GPU parity of the batched persistent launches (many scenarios; a tile pass
-and a pass over the queued deep samples): every scenario's labels, counts and
-gradient counts equal the single-problem path's and the oracle's, including a
-scenario whose samples mostly reach the second pass and one that overflows its
-deep queue; replays (direct and from a CUDA graph) advance to the next window
-of samples; autotuning never touches the caller's outputs."""
+and later stages over the queued deep samples): every scenario's labels,
+counts and gradient counts equal the single-problem path's and the oracle's,
+including a scenario whose samples mostly reach a later stage and one that
+overflows its deep queue; replays (direct and from a CUDA graph) advance to the
+next window of samples; autotuning never touches the caller's outputs; the
+cycle-profiled launch gives the same outputs."""
 import numpy as np
 import pytest
 import torch
@@ -48,6 +49,29 @@ def test_batch_matches_oracle_and_single_path(rsr):
         assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K), O.grad_counts(X, lab, p.K)), s
         single = run(make_session(rsr, p), seeds[s], offsets[s], Ns[s])
         assert np.array_equal(single["labels"], lab)
+
+
+def test_batch_profile_keeps_outputs_and_counts_items(rsr):
+    """rsr_batch_profile gives rsr_batch's outputs for the same round, and its
+    cycle profile counts one tile-pass item per 256 samples of each scenario,
+    positive cycles in each part of an item, and later-stage items only where
+    samples outlast the first pass's chunk budget (the sparse scenario)."""
+    probs, seeds, offsets, Ns = scenarios()
+    b1 = make_batch(rsr, probs, seeds, offsets, Ns)
+    b2 = make_batch(rsr, probs, seeds, offsets, Ns)
+    for _ in range(2):   # rounds 0 and 1
+        rsr.rsr_batch(b1)
+        prof = rsr.rsr_batch_profile(b2).cpu().numpy()
+        torch.cuda.synchronize()
+        assert np.array_equal(b1.counts3.cpu().numpy(), b2.counts3.cpu().numpy())
+        for s in range(len(probs)):
+            assert np.array_equal(b1.labels[s].cpu().numpy(), b2.labels[s].cpu().numpy()), s
+            assert np.array_equal(b1.grad_counts[s].cpu().numpy(), b2.grad_counts[s].cpu().numpy()), s
+        for s, N in enumerate(Ns):
+            assert prof[s, 0] == (N + 255) // 256, s
+            assert (prof[s, 1:4] > 0).all(), s
+            assert (prof[s, 5:8] > 0).all() if prof[s, 4] > 0 else (prof[s, 5:8] == 0).all(), s
+        assert prof[9, 4] > 0   # the sparse scenario queues samples for a later stage
 
 
 def test_batch_grad_matches_oracle(rsr):
