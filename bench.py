@@ -330,7 +330,7 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
     seeds, offsets, Ns = [1000 + s for s in range(S)], [0] * S, [N] * S
     t0 = time.perf_counter()
     b = rsr.Batch(P, seeds, offsets, Ns, labels=True, grad=True)
-    grid, order, k0, n_tc, staged = rsr.rsr_batch_autotune(b)
+    grid, order, k0, n_tc, staged, tiles = rsr.rsr_batch_autotune(b)
     prep_s = time.perf_counter() - t0
     stream = torch.cuda.Stream()
     g = torch.cuda.CUDAGraph()
@@ -369,7 +369,7 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
         "heavy_scenarios_R_ge_1e4": int(heavy.sum()),
         "heavy_share_of_walk": float(walk[heavy].sum() / walk.sum()),
         "heavy_share_of_samples": float(heavy.sum() / len(P)),
-        "later_stage_items": int(prof[:, 4].sum()), "tile_items": int(prof[:, 0].sum()),
+        "later_stage_groups": int(prof[:, 4].sum()), "tiles": int(prof[:, 0].sum()),
     }
     # per-scenario path
     sessions = [rsr.Session(p) for p in P]
@@ -435,7 +435,7 @@ def bench_batch(rsr, torch, N=200_000, reps=5):
             "speedup_fwd_grad_round": plain_round_ms / batched_round_ms,
             "samples_per_s": S * N / (batched_ms / 1000.0), "autotune_grid": grid,
             "autotune_order": "longest-first" if order == 0 else "as-given", "autotune_k0": k0,
-            "autotune_staged": staged, "autotune_tc_scenarios": n_tc,
+            "autotune_staged": staged, "autotune_tiles_per_item": tiles, "autotune_tc_scenarios": n_tc,
             "cycle_profile": cycle_profile, "prepare_s": prep_s}
 
 

@@ -91,6 +91,10 @@ typedef enum rsr_path {
  * workspace holds a deep queue, whatever N (without it, calls of fewer than
  * 2^19 samples run one pass). */
 #define RSR_FLAG_TEST_TWO_PASS 0x400u
+/* Test hook (batched bit-packed path): the scenario's first-pass work items
+ * hold three consecutive 256-sample tiles each instead of one, until
+ * rsr_batch_autotune picks the tiles per item for every scenario. */
+#define RSR_FLAG_TEST_TILES3 0x800u
 
 /*
  * One classification problem for a threshold m' (Sec. 3.2-3.3).
@@ -288,12 +292,13 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  *                            profile of the bit-packed launches: cycles is a device uint64[S*8],
  *                            zeroed by the call (stream-ordered), then per scenario s, at
  *                            [8s + 0..3] for the tile pass and [8s + 4..7] for the later stages:
- *                            items, and SM clock cycles (clock64 of each item's block, summed over
- *                            items) spent from an item's start to its tables being ready (work
- *                            counter, scenario lookup, table loads), from there to the block's
- *                            first warp having written its samples (Philox sampling and
- *                            encoding), and from there to the item's counts being flushed (the
- *                            reference-chunk walk).  Scenarios on the tensor cores keep zeros.
+ *                            tiles (groups of queued samples), and SM clock cycles (clock64 of
+ *                            the tile's block, summed over tiles) spent from a tile's start to
+ *                            its tables being ready (for an item's first tile: the work counter,
+ *                            scenario lookup and table loads), from there to the block's first
+ *                            warp having written its samples (Philox sampling and encoding), and
+ *                            from there to the tile's end (the reference-chunk walk; an item's
+ *                            last tile includes its count flush).  Scenarios on the tensor cores keep zeros.
  *                            Blocks share their SM, so the cycles measure where a block's time
  *                            goes, not SM time; the three parts give the split.
  * rsr_batch_autotune       : first picks the path of every dense RSR_PATH_AUTO scenario by timing
@@ -302,12 +307,16 @@ RSR_API int rsr_workspace_status(const void *ws, int32_t out[2], rsr_stream_t st
  *                            pass's chunk budget k0 (0 = no later stage, 2, 4, 8, 16, 32) with
  *                            either one later stage to the end or stages that each walk four
  *                            times as far as they start (staged), then work orders and grid
- *                            sizes, on the prepared batch (writing only into the workspace's
+ *                            sizes, then the first pass's tiles per work item (1, 2, 4, 8
+ *                            consecutive 256-sample tiles of a scenario: one work-counter
+ *                            atomic, scenario lookup, table load and count flush for all of
+ *                            them), on the prepared batch (writing only into the workspace's
  *                            scratch, never the caller's outputs), keeps the fastest for later
- *                            rsr_batch calls and resets the round to 0; chosen[0] = grid,
- *                            chosen[1] = order (0 = longest first, 1 = as given), chosen[2] = k0
- *                            (8 until tuned), chosen[3] = scenarios on the tensor cores,
- *                            chosen[4] = staged (0 until tuned).
+ *                            rsr_batch calls and resets the round to 0; chosen (host
+ *                            int32[6]): chosen[0] = grid, chosen[1] = order (0 = longest first,
+ *                            1 = as given), chosen[2] = k0 (8 until tuned), chosen[3] =
+ *                            scenarios on the tensor cores, chosen[4] = staged (0 until tuned),
+ *                            chosen[5] = tiles per first-pass item (1 until tuned).
  *                            Synchronises `stream`.  With RSR_TUNE_CACHE set (see rsr_autotune)
  *                            the choices are read from and written to the tuning cache.
  */

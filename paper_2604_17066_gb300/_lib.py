@@ -25,6 +25,7 @@ RSR_FLAG_NO_INDEX = 2
 RSR_FLAG_TEST_STALL = 0x100
 RSR_FLAG_TEST_DEEP_CAP = 0x200
 RSR_FLAG_TEST_TWO_PASS = 0x400
+RSR_FLAG_TEST_TILES3 = 0x800
 
 
 class rsr_problem(ctypes.Structure):

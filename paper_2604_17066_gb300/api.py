@@ -282,9 +282,9 @@ def rsr_batch(batch: Batch, stream=None) -> None:
 def rsr_batch_profile(batch: Batch, stream=None) -> torch.Tensor:
     """rsr_batch (same outputs; advances the round) with a cycle profile of the
     bit-packed launches: a device int64 [S, 8] tensor, per scenario the tile
-    pass's items and its set-up, sampling and chunk-walk SM cycles (summed over
+    pass's tiles and its set-up, sampling and chunk-walk SM cycles (summed over
     items, clock64 of each item's block), then the same four for the later
-    stages.  Tensor-core scenarios keep zeros."""
+    stages (groups of queued samples).  Tensor-core scenarios keep zeros."""
     st = stream if stream is not None else batch.stream
     cycles = torch.empty((batch.S, 8), dtype=torch.int64, device=batch.counts3.device)
     check(_lib.load().rsr_batch_profile(*batch.args(), _stream(st), cycles.data_ptr()), "rsr_batch_profile")
@@ -292,15 +292,16 @@ def rsr_batch_profile(batch: Batch, stream=None) -> torch.Tensor:
 
 
 def rsr_batch_autotune(batch: Batch, stream=None):
-    """Tunes the batch's launches; returns (grid, order, k0, n_tc, staged):
+    """Tunes the batch's launches; returns (grid, order, k0, n_tc, staged, tiles):
     blocks of the bit-packed persistent grid, work order (0 = longest scenarios
     first, 1 = as given), the first pass's reference-chunk budget (0 = one
-    pass), the number of scenarios on the tensor-core pair kernel, and whether
-    the later passes are staged (1) or one stage to the end (0)."""
-    chosen = np.zeros(5, dtype=np.int32)
+    pass), the number of scenarios on the tensor-core pair kernel, whether the
+    later passes are staged (1) or one stage to the end (0), and the
+    consecutive 256-sample tiles per first-pass work item."""
+    chosen = np.zeros(6, dtype=np.int32)
     check(_lib.load().rsr_batch_autotune(*batch.args(), _stream(stream if stream is not None else batch.stream),
                                          chosen.ctypes.data), "rsr_batch_autotune")
-    return int(chosen[0]), int(chosen[1]), int(chosen[2]), int(chosen[3]), int(chosen[4])
+    return tuple(int(x) for x in chosen)
 
 
 def rsr_batch_grad(batch: Batch, stream=None):

@@ -35,7 +35,10 @@ struct Shared {
     int changed;                 // the item's scenario differs from the block's previous one
     long long deep_pos;          // the item's reservation in its scenario's deep queue
     unsigned int warp_pend[kThreads / 32];
-    long long t_start, t_ready, t_sampled;   // cycle profile marks: item start, tables ready, warp 0's samples written
+    long long tile;                          // the tile (first pass) or queued group (later stage) run now
+    int left;                                // the item's tiles still to run after this one
+    int fresh;                               // this tile starts an item (counts and bit counts zeroed)
+    long long t_start, t_ready, t_sampled;   // cycle profile marks: tile start, tables ready, warp 0's samples written
 };
 
 // The multi-state sampler as a call: inlined, its registers would add to the
@@ -345,39 +348,61 @@ __device__ __forceinline__ void stage_steps(const BatchDesc &d, int stage, int64
 }
 
 // The persistent item loop of one pass: items [begin[s], begin[s+1]) belong to
-// scenario s; first pass: item = tile, later stages: item = group of 256
-// queued samples.  Counts are flushed per item.  With a cycle profile (prof:
-// [S][8]), thread 0 adds to its scenario's row, at [0] for the first pass and
-// [4] for a later stage: items, then SM cycles from the item's start to its
-// tables being ready (scenario lookup, table loads), from there to warp 0's
-// samples being written, and from there to the item's counts being flushed
-// (the chunk walk).
+// scenario s.  A first-pass item is d.tiles consecutive 256-sample tiles of
+// its scenario (one work-counter atomic, scenario lookup, table load and count
+// flush for all of them); a later-stage item is one group of 256 queued
+// samples.  The loop runs one tile per iteration and keeps its state (item,
+// tile, tiles left) in shared memory, so nothing of it is live across the
+// chunk walk.  With a cycle profile (prof: [S][8]), thread 0 adds to its
+// scenario's row, at [0] for the first pass and [4] for a later stage: tiles
+// (groups), then SM cycles from a tile's start to its tables being ready (work
+// counter, scenario lookup, table loads), from there to warp 0's samples being
+// written (sampling), and from there to the tile's end (the chunk walk; an
+// item's last tile includes its count flush).
 template <bool kSecond, bool kProf>
 __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__restrict__ begin, int S,
                           int64_t total_items, unsigned long long *counter, uint64_t round, int stage,
                           const BatchSmem &m, const uint32_t *s_zero, uint32_t *s_and, Shared &sh,
                           unsigned long long *prof) {
     const int tid = threadIdx.x;
+    if (tid == 0) sh.left = 0;
     while (true) {
         if (kProf && tid == 0) sh.t_start = clock64();
-        if (tid == 0) sh.item = (long long)atomicAdd(counter, 1ull);
+        if (tid == 0 && sh.left == 0) sh.item = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
         const long long item = sh.item;
         if (item >= total_items) break;
-        // scenario of this item: last s with begin[s] <= item
         if (tid == 0) {
-            int lo = 0, hi = S - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (begin[mid] <= item) lo = mid; else hi = mid - 1;
+            const int fresh = sh.left == 0;
+            if (fresh) {
+                // scenario of this item: last s with begin[s] <= item
+                int lo = 0, hi = S - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (begin[mid] <= item) lo = mid; else hi = mid - 1;
+                }
+                sh.changed = lo != sh.scenario;
+                if (sh.changed) {
+                    sh.scenario = lo;
+                    sh.d = descs[lo];
+                }
+                sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0ull;
+                sh.fz = 0u;
+                const int64_t k = item - begin[lo];
+                if (kSecond) {
+                    sh.tile = k;
+                    sh.left = 1;
+                } else {
+                    const int64_t ntiles = (sh.d.N + kThreads - 1) / kThreads;
+                    sh.tile = k * sh.d.tiles;
+                    sh.left = (int)min((int64_t)sh.d.tiles, ntiles - (int64_t)sh.tile);
+                }
+            } else {
+                sh.changed = 0;
+                sh.tile += 1;
             }
-            sh.changed = lo != sh.scenario;
-            if (sh.changed) {
-                sh.scenario = lo;
-                sh.d = descs[lo];
-            }
-            sh.cnt[0] = sh.cnt[1] = sh.cnt[2] = 0ull;
-            sh.fz = 0u;
+            sh.fresh = fresh;
+            sh.left -= 1;
         }
         __syncthreads();
         const BatchDesc &d = sh.d;
@@ -398,10 +423,11 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
                 for (int w = tid; w < d.words_b; w += kThreads) m.first[w] = component_first_bits(d.km1, nthr, w);
             }
         }
-        for (int j = tid; j < d.words_b * 32; j += kThreads) m.cum[j] = 0u;
+        if (sh.fresh)
+            for (int j = tid; j < d.words_b * 32; j += kThreads) m.cum[j] = 0u;
         __syncthreads();
         if (kProf && tid == 0) sh.t_ready = clock64();
-        const int64_t k = item - begin[sh.scenario];   // tile, or group of queued samples
+        const int64_t k = sh.tile;   // tile, or group of queued samples
         const int64_t *deep = nullptr;
         int n_deep = 0;
         if (kSecond) {
@@ -420,8 +446,8 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
         const int q_sel = step_hi < nsteps_d ? (stage & 1) : -1;
         const int lim = (int)(q_sel >= 0 ? step_hi : nsteps_d);
 #define RSR_ITEM(WBV)                                                                                           \
-    classify_item<WBV, kProf>(d, k, deep, n_deep, step0, lim, q_sel, round, m.thr, m.tw, m.buf, m.cum, m.hot, m.first, \
-                       s_zero, s_and, sh)
+    classify_item<WBV, kProf>(d, k, deep, n_deep, step0, lim, q_sel, round, m.thr, m.tw, m.buf, m.cum, m.hot, \
+                              m.first, s_zero, s_and, sh)
         switch (d.words_b) {
             case 1: RSR_ITEM(1); break;
             case 2: RSR_ITEM(2); break;
@@ -434,18 +460,20 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
         }
 #undef RSR_ITEM
         __syncthreads();
-        if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);
-        if (d.bitcnt && sh.cnt[0]) {
-            if (tid == 0) atomicAdd(d.lcount, sh.cnt[0]);
-            for (int j = tid; j < nthr; j += kThreads) {
-                const uint32_t ones = m.cum[j] + sh.fz;   // one bits of the item's I^L samples (mod 2^32)
-                if (ones) atomicAdd(&d.bitcnt[j], ones);
+        if (sh.left == 0) {   // the item's last tile: flush its counts
+            if (tid < 3 && sh.cnt[tid]) atomicAdd(&d.counts3[tid], sh.cnt[tid]);
+            if (d.bitcnt && sh.cnt[0]) {
+                if (tid == 0) atomicAdd(d.lcount, sh.cnt[0]);
+                for (int j = tid; j < nthr; j += kThreads) {
+                    const uint32_t ones = m.cum[j] + sh.fz;   // one bits of the item's I^L samples (mod 2^32)
+                    if (ones) atomicAdd(&d.bitcnt[j], ones);
+                }
             }
         }
         __syncthreads();
         if (kProf && tid == 0) {
             const long long t_end = clock64();
-            unsigned long long *row = prof + (size_t)sh.scenario * 8 + (kSecond ? 4 : 0);
+            unsigned long long *row = prof + (size_t)sh.d.id * 8 + (kSecond ? 4 : 0);
             atomicAdd(row + 0, 1ull);
             atomicAdd(row + 1, (unsigned long long)(sh.t_ready - sh.t_start));
             atomicAdd(row + 2, (unsigned long long)(sh.t_sampled - sh.t_ready));

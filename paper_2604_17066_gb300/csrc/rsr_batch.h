@@ -29,6 +29,9 @@ struct BatchDesc {
     int32_t k0;                          // chunk steps of the first pass (0 = all)
     int32_t staged;                      // later stages grow by kDeferGrowth (0: one stage to the end)
     int32_t path;                        // RSR_PATH_POPC, or RSR_PATH_TC: the scenario runs on the pair kernel
+    int32_t id;                          // the scenario's index in the caller's arrays (descriptors are in work order)
+    int32_t tiles;                       // first pass: consecutive 256-sample tiles per work item (>= 1)
+    int32_t pad_;
 };
 
 // Work counter and round of a batch workspace (256 bytes at its start).
@@ -64,6 +67,7 @@ cudaError_t launch_batch_prof(const BatchDesc *descs, const int64_t *item_begin,
 int batch_stages(const BatchDesc *descs, int S);
 constexpr int64_t kBatchDeepCap = int64_t(1) << 22;   // deep-queue entries per scenario at most (32 MB)
 constexpr int64_t kBatchTestDeepCap = 1024;           // with RSR_FLAG_TEST_DEEP_CAP (test hook)
+constexpr int kBatchMaxTiles = 8;          // first-pass tiles per work item that rsr_batch_autotune tries (1, 2, 4, 8)
 constexpr int kBatchDefaultK0 = 8;         // first-pass chunk steps before rsr_batch_autotune picks them
 
 }  // namespace rsr

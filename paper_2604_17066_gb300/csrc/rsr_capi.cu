@@ -1105,7 +1105,8 @@ int upload_schedule(void *ws, const BatchLayout &B, const std::vector<BatchDesc>
     for (int k = 0; k < S; ++k) {
         ordered[k] = descs[order[k]];
         begin[k] = total;
-        if (ordered[k].path != RSR_PATH_TC) total += (ordered[k].N + 255) / 256;   // pair-kernel scenarios: none
+        // first-pass items of d.tiles tiles each; pair-kernel scenarios: none
+        if (ordered[k].path != RSR_PATH_TC) total += ((ordered[k].N + 255) / 256 + ordered[k].tiles - 1) / ordered[k].tiles;
     }
     begin[S] = total;
     char *base = static_cast<char *>(ws);
@@ -1237,6 +1238,8 @@ int rsr_batch_prepare(const rsr_problem *problems, int32_t S, const uint64_t *se
         d.seed = seeds[k];
         d.offset = offsets[k];
         d.N = Ns[k];
+        d.id = k;
+        d.tiles = (p.flags & RSR_FLAG_TEST_TILES3) ? 3 : 1;   // until rsr_batch_autotune picks it
         d.thr = reinterpret_cast<const unsigned long long *>(base + B.off_thr[k]);
         d.popc_L = pL;
         d.popc_U = pU;
@@ -1475,19 +1478,22 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     char hex[32];
     snprintf(hex, sizeof(hex), "%016llx", (unsigned long long)shape);
     const std::string batch_key = "batch/" + device_tag() + "/S" + std::to_string(S) + "/" + hex;
-    int best_grid = bp.grid, best_order = 0, best_k0 = bp.k0, best_staged = 0;
+    int best_grid = bp.grid, best_order = 0, best_k0 = bp.k0, best_staged = 0, best_tiles = 1;
     std::vector<long long> cached;
-    if (cache_get(batch_key, &cached) && cached.size() == 4 && cached[0] >= 1 && (cached[1] == 0 || cached[1] == 1) &&
-        cached[2] >= 0 && (cached[3] == 0 || cached[3] == 1)) {
+    if (cache_get(batch_key, &cached) && cached.size() == 5 && cached[0] >= 1 && (cached[1] == 0 || cached[1] == 1) &&
+        cached[2] >= 0 && (cached[3] == 0 || cached[3] == 1) && cached[4] >= 1 && cached[4] <= kBatchMaxTiles) {
         best_grid = (int)cached[0];
         best_order = (int)cached[1];
         best_k0 = (int)cached[2];
         best_staged = (int)cached[3];
+        best_tiles = (int)cached[4];
     } else {
-        auto time_config = [&](int ord, int bps, int k0, int staged, float *ms_out, int64_t *grid_out) -> int {
+        auto time_config = [&](int ord, int bps, int k0, int staged, int tiles, float *ms_out,
+                               int64_t *grid_out) -> int {
             for (int k = 0; k < S; ++k) {
                 scratch[k].k0 = k0;
                 scratch[k].staged = staged;
+                scratch[k].tiles = tiles;
             }
             std::vector<int64_t> begin;
             int64_t total = 0;
@@ -1511,7 +1517,7 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
                 if (staged && k0 == 0) continue;   // nothing is deferred: the same launches
                 float ms = 0.0f;
                 int64_t grid = 0;
-                if ((st = time_config(0, occ, k0, staged, &ms, &grid)) != RSR_OK) return st;
+                if ((st = time_config(0, occ, k0, staged, 1, &ms, &grid)) != RSR_OK) return st;
                 if (ms < best) {
                     best = ms;
                     best_k0 = k0;
@@ -1520,20 +1526,34 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
                 }
             }
         }
+        int best_bps = occ;
         for (int ord = 0; ord < 2; ++ord) {
             for (int bps = 1; bps <= occ; bps *= 2) {
                 if (ord == 0 && bps == occ) continue;   // timed above
                 float ms = 0.0f;
                 int64_t grid = 0;
-                if ((st = time_config(ord, bps, best_k0, best_staged, &ms, &grid)) != RSR_OK) return st;
+                if ((st = time_config(ord, bps, best_k0, best_staged, 1, &ms, &grid)) != RSR_OK) return st;
                 if (ms < best) {
                     best = ms;
                     best_grid = (int)grid;
                     best_order = ord;
+                    best_bps = bps;
                 }
             }
         }
-        cache_put(batch_key, {best_grid, best_order, best_k0, best_staged});
+        // first-pass tiles per work item: fewer work-counter atomics, scenario lookups and
+        // table loads, against a coarser balance at the end of the pass
+        for (int tiles = 2; tiles <= kBatchMaxTiles; tiles *= 2) {
+            float ms = 0.0f;
+            int64_t grid = 0;
+            if ((st = time_config(best_order, best_bps, best_k0, best_staged, tiles, &ms, &grid)) != RSR_OK) return st;
+            if (ms < best) {
+                best = ms;
+                best_grid = (int)grid;
+                best_tiles = tiles;
+            }
+        }
+        cache_put(batch_key, {best_grid, best_order, best_k0, best_staged, best_tiles});
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1542,6 +1562,7 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
     for (int k = 0; k < S; ++k) {
         tuned[k].k0 = best_k0;
         tuned[k].staged = best_staged;
+        tuned[k].tiles = best_tiles;
     }
     std::vector<int64_t> begin;
     int64_t total = 0;
@@ -1561,6 +1582,7 @@ int rsr_batch_autotune(const rsr_problem *problems, int32_t S, const uint64_t *s
         chosen[2] = best_k0;
         chosen[3] = bp.n_tc;
         chosen[4] = best_staged;
+        chosen[5] = best_tiles;
     }
     std::lock_guard<std::mutex> g(g_mu);
     BatchPrepared &ref = g_batches[ws];

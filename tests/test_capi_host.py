@@ -47,7 +47,7 @@ def test_flags_match_the_header():
     from paper_2604_17066_gb300 import _lib
     text = open(os.path.join(ROOT, "include", "rsr.h")).read()
     for name in ("RSR_FLAG_DENSE", "RSR_FLAG_NO_INDEX", "RSR_FLAG_TEST_STALL", "RSR_FLAG_TEST_DEEP_CAP",
-                 "RSR_FLAG_TEST_TWO_PASS"):
+                 "RSR_FLAG_TEST_TWO_PASS", "RSR_FLAG_TEST_TILES3"):
         m = re.search(r"#define\s+%s\s+(0x[0-9a-fA-F]+|\d+)u" % name, text)
         assert m, name
         assert int(m.group(1), 0) == getattr(_lib, name), name

@@ -74,6 +74,33 @@ def test_batch_profile_keeps_outputs_and_counts_items(rsr):
         assert prof[9, 4] > 0   # the sparse scenario queues samples for a later stage
 
 
+def test_batch_items_of_three_tiles_match_oracle(rsr):
+    """First-pass work items of three consecutive tiles (the test hook; a ragged
+    last item where a scenario's tile count is not a multiple of three) give
+    the oracle's labels, counts and gradient counts, with later stages and
+    cycle profile unchanged in meaning."""
+    from paper_2604_17066_gb300._lib import RSR_FLAG_TEST_TILES3
+    probs, seeds, offsets, Ns = scenarios()
+    P = [rsr.Problem(p.pmf, p.ref_L, p.ref_U, path=POPC) for p in probs]
+    for k, pp in enumerate(P):
+        if k % 3 != 2:           # most scenarios on three-tile items, the rest on one-tile items
+            pp.extra_flags = RSR_FLAG_TEST_TILES3
+    b = rsr.Batch(P, seeds, offsets, Ns)
+    for r in range(2):
+        prof = rsr.rsr_batch_profile(b).cpu().numpy()
+        torch.cuda.synchronize()
+        counts = b.counts3.cpu().numpy()
+        for s, p in enumerate(probs):
+            X = O.sample(p.pmf, seeds[s], offsets[s] + r * Ns[s], Ns[s])
+            lab, cnt = O.classify(X, p.ref_L, p.ref_U)
+            assert np.array_equal(b.labels[s].cpu().numpy(), lab), (r, s)
+            assert prof[s, 0] == (Ns[s] + 255) // 256, (r, s)
+            if r == 0:
+                assert np.array_equal(counts[s], cnt), s
+                assert np.array_equal(b.grad_counts[s].cpu().numpy().reshape(p.n, p.K),
+                                      O.grad_counts(X, lab, p.K)), s
+
+
 def test_batch_grad_matches_oracle(rsr):
     probs, seeds, offsets, Ns = scenarios()
     b = make_batch(rsr, probs, seeds, offsets, Ns)
@@ -121,8 +148,9 @@ def test_batch_replay_and_graph_capture(rsr):
 def test_batch_autotune_leaves_outputs_alone(rsr):
     probs, seeds, offsets, Ns = scenarios()
     b = make_batch(rsr, probs, seeds, offsets, Ns)
-    grid, order, k0, n_tc, staged = rsr.rsr_batch_autotune(b)
+    grid, order, k0, n_tc, staged, tiles = rsr.rsr_batch_autotune(b)
     assert grid >= 1 and order in (0, 1) and k0 in (0, 2, 4, 8, 16, 32) and n_tc == 0 and staged in (0, 1)
+    assert tiles in (1, 2, 4, 8)
     torch.cuda.synchronize()
     assert int(b.counts3.abs().sum()) == 0
     assert all(int(t.abs().sum()) == 0 for t in b.grad_counts)
@@ -223,7 +251,7 @@ def test_mixed_path_batch_matches_oracle_before_and_after_autotune(rsr):
     torch.cuda.synchronize()
     check_batch_round(rsr, b, probs, seeds, offsets, Ns, 0)
     b2 = make_mixed_batch(rsr, probs, seeds, offsets, Ns, paths, dense)
-    grid, order, k0, n_tc, staged = rsr.rsr_batch_autotune(b2)
+    grid, order, k0, n_tc, staged, tiles = rsr.rsr_batch_autotune(b2)
     assert n_tc >= 3                      # the three scenarios that ask for the tensor cores
     torch.cuda.synchronize()
     assert int(b2.counts3.abs().sum()) == 0
