@@ -47,7 +47,7 @@ struct Shared {
 template <int WB>
 __device__ __noinline__ void sample_multi_call(uint64_t h, uint32_t key0, uint32_t key1, int n, int km1,
                                                const uint32_t *s_t32k, uint32_t *col) {
-    sample_multi_words<WB, kThreads>(h, key0, key1, n, km1, s_t32k, col);
+    sample_multi_words_k<WB, kThreads, 0>(h, key0, key1, n, km1, s_t32k, col);   // level loop at run time: fewer spills here
 }
 
 // One item.  First pass (deep == nullptr): samples tile*256 + tid.  A later

@@ -146,9 +146,12 @@ __device__ __forceinline__ void multi_tables_to_smem(const unsigned long long *_
 // block per step, not two as for binary states: the level compares give the
 // step its parallelism, and the kernels that inline this stay within their
 // register budget.)
-template <int WB, int stride>
-__device__ __forceinline__ void sample_multi_words(uint64_t h, uint32_t key0, uint32_t key1, int n, int km1,
-                                                   const uint32_t *s_t32k, uint32_t *col) {
+// KM1 > 0: the level count K-1 is a compile-time constant (level loop
+// unrolled); KM1 = 0: it is km1_rt.
+template <int WB, int stride, int KM1>
+__device__ __forceinline__ void sample_multi_words_k(uint64_t h, uint32_t key0, uint32_t key1, int n, int km1_rt,
+                                                     const uint32_t *s_t32k, uint32_t *col) {
+    const int km1 = KM1 > 0 ? KM1 : km1_rt;
     const int npad = (n + 7) & ~7;
     const uint32_t *s_never = s_t32k + km1 * npad;
     const uint32_t h0 = (uint32_t)h, h1 = (uint32_t)(h >> 32);
@@ -157,6 +160,7 @@ __device__ __forceinline__ void sample_multi_words(uint64_t h, uint32_t key0, ui
     for (int q = 0; 4 * q < n; ++q) {
         const U32x4 r = philox4x32_10(h0, h1, (uint32_t)q, 0u, key0, key1);
         uint32_t x0 = 0u, x1 = 0u, x2 = 0u, x3 = 0u;
+#pragma unroll
         for (int k = 0; k < km1; ++k) {
             const uint4 t = *reinterpret_cast<const uint4 *>(s_t32k + k * npad + 4 * q);
             x0 += r.x >= t.x ? 1u : 0u;
@@ -186,6 +190,16 @@ __device__ __forceinline__ void sample_multi_words(uint64_t h, uint32_t key0, ui
         ++w;
     }
     for (; w < WB; ++w) col[w * stride] = 0u;
+}
+
+// K = 3 and K = 4 (two or three levels per component) with the level loop
+// unrolled; other K with it at run time.
+template <int WB, int stride>
+__device__ __forceinline__ void sample_multi_words(uint64_t h, uint32_t key0, uint32_t key1, int n, int km1,
+                                                   const uint32_t *s_t32k, uint32_t *col) {
+    if (km1 == 3) sample_multi_words_k<WB, stride, 3>(h, key0, key1, n, km1, s_t32k, col);
+    else if (km1 == 2) sample_multi_words_k<WB, stride, 2>(h, key0, key1, n, km1, s_t32k, col);
+    else sample_multi_words_k<WB, stride, 0>(h, key0, key1, n, km1, s_t32k, col);
 }
 
 // ---------------------------------------------------------------------------

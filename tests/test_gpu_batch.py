@@ -244,7 +244,8 @@ def check_batch_round(rsr, b, probs, seeds, offsets, Ns, rnd):
 def test_mixed_path_batch_matches_oracle_before_and_after_autotune(rsr):
     """Tensor-core and bit-packed scenarios in one batch: every scenario equals
     the oracle, before tuning (the reference-count rule) and after (timed paths,
-    k0, order and grid), and on graph replays of the tuned batch."""
+    k0, order, grid and tiles per item), on graph replays of the tuned batch,
+    and on a cycle-profiled launch (zero rows for tensor-core scenarios)."""
     probs, seeds, offsets, Ns, paths, dense = mixed_scenarios()
     b = make_mixed_batch(rsr, probs, seeds, offsets, Ns, paths, dense)
     rsr.rsr_batch(b)
@@ -267,6 +268,18 @@ def test_mixed_path_batch_matches_oracle_before_and_after_autotune(rsr):
         g.replay()
         torch.cuda.synchronize()
         check_batch_round(rsr, b2, probs, seeds, offsets, Ns, rnd)
+    # the cycle-profiled launches continue the rounds; tensor-core scenarios keep zero rows
+    b2.counts3.zero_()
+    for t in b2.grad_counts:
+        t.zero_()
+    prof = rsr.rsr_batch_profile(b2).cpu().numpy()
+    torch.cuda.synchronize()
+    check_batch_round(rsr, b2, probs, seeds, offsets, Ns, 2)
+    for s, pa in enumerate(paths):
+        if pa == 2:
+            assert (prof[s] == 0).all(), s
+        elif pa == 1:
+            assert prof[s, 0] == (Ns[s] + 255) // 256 and (prof[s, 1:4] > 0).all(), s
 
 
 def test_tuning_cache_round_trip(rsr, tmp_path, monkeypatch):
