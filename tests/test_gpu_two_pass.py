@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 def session_with_queue(rsr, prob, n_queue, index=True):
     """A prepared workspace whose deep queue holds n_queue entries (0: none),
-    for a problem that runs two passes whatever N (test flag; without it calls
+    for a problem that runs staged passes whatever N (test flag; without it calls
     of fewer than 2^19 samples run one pass)."""
     from paper_2604_17066_gb300._lib import RSR_FLAG_TEST_TWO_PASS
     P = rsr.Problem(prob.pmf, prob.ref_L, prob.ref_U, path=POPC, index=index)
@@ -58,7 +58,7 @@ def test_two_pass_matches_oracle_and_one_pass(rsr, name):
         assert np.array_equal(got["labels"], lab), n_queue
         assert np.array_equal(got["counts3"], cnt), n_queue
         assert np.array_equal(got["grad_counts"].reshape(prob.n, prob.K), C), n_queue
-    # without the index the two passes hold as well
+    # without the index the staged passes hold as well
     got = run(session_with_queue(rsr, prob, 1 << 20, index=False), 3, 1 << 30, N)
     assert np.array_equal(got["labels"], lab)
 
