@@ -394,8 +394,9 @@ __device__ void item_loop(const BatchDesc *__restrict__ descs, const int64_t *__
                     sh.left = 1;
                 } else {
                     const int64_t ntiles = (sh.d.N + kThreads - 1) / kThreads;
-                    sh.tile = k * sh.d.tiles;
-                    sh.left = (int)min((int64_t)sh.d.tiles, ntiles - (int64_t)sh.tile);
+                    const int tiles = sh.d.tiles > 1 ? sh.d.tiles : 1;   // the host writes >= 1
+                    sh.tile = k * tiles;
+                    sh.left = (int)min((int64_t)tiles, ntiles - (int64_t)sh.tile);
                 }
             } else {
                 sh.changed = 0;

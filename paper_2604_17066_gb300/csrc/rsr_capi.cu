@@ -1104,8 +1104,10 @@ int upload_schedule(void *ws, const BatchLayout &B, const std::vector<BatchDesc>
     total = 0;
     for (int k = 0; k < S; ++k) {
         ordered[k] = descs[order[k]];
+        // first-pass items of d.tiles tiles each (at least one: the kernel's item loop counts them down)
+        ordered[k].tiles = std::max(1, std::min(ordered[k].tiles, kBatchMaxTiles));
         begin[k] = total;
-        // first-pass items of d.tiles tiles each; pair-kernel scenarios: none
+        // pair-kernel scenarios: no bit-packed items
         if (ordered[k].path != RSR_PATH_TC) total += ((ordered[k].N + 255) / 256 + ordered[k].tiles - 1) / ordered[k].tiles;
     }
     begin[S] = total;
