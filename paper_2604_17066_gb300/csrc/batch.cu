@@ -1,17 +1,18 @@
 // batch.cu -- many classification problems (hazard scenarios) in one
-// persistent launch per pass.
+// persistent launch per pass (the kernels are in batch_kernels.cuh; this file
+// launches them without the cycle profile).
 //
 // Each scenario s has its own n, K, pmf thresholds, reference sets, sample
-// count N_s, seed and offset.  Work items are (scenario, 256-sample tile),
-// enumerated scenario by scenario in the order the host chose (longest
-// scenarios first); a persistent grid pulls items from an atomic counter, so
-// short and long scenarios share the machine without per-scenario launch
-// tails.  Per item the block runs the same bit-packed test as classify_popc.cu
+// count N_s, seed and offset.  First-pass work items are (scenario, run of
+// d.tiles consecutive 256-sample tiles), enumerated scenario by scenario in the
+// order the host chose (longest scenarios first); a persistent grid pulls items
+// from an atomic counter, so short and long scenarios share the machine without
+// per-scenario launch tails.  Per tile the block runs the same bit-packed test as classify_popc.cu
 // (Sec. 3.3, Algorithm 1) for the scenario's word count.  Scenarios whose upper
 // set has a component-major index (popc_index.cuh) test their upper chunks
 // through it, after a direct test of their kHot most probable upper references.
 //
-// Two passes.  The 256 samples of a tile walk the reference chunks together
+// Staged passes.  The 256 samples of a tile walk the reference chunks together
 // (one shared copy of each chunk), so a tile costs as many chunk steps as its
 // deepest sample needs, and in scenarios with partial reference sets every
 // tile holds a few samples that match nothing and visit every chunk while the
